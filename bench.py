@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the PonD D2Q16 time step on GB300.
+
+Headline (one JSON line on rank 0): node-updates/s of the plain FP64 step on
+the 2048 x 2048 supersonic workload (uniform u = (1.5, 0.5), rho and T with
+8 seeded sinusoidal perturbations), inputs resident in HBM.  Extra keys
+report the mixed FP32/FP64 form on the same field and on the 4096^2
+temperature-ratio-4 field, the batched ensemble (256 uneven grids, one
+graph-replayed persistent launch per step), the moment error of the mixed
+form against the FP64 run, the roofline of the dominant kernel, the FP64 CPU
+oracle on a bounded sample, and the end-to-end rate through host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the workload
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PonD D2Q16 node-updates/s (FP32 vs FP64 @ moment err); adjoint/forward time"
+UNIT = "node-updates/s"
+WORKLOAD = "supersonic-2048-fp64"
+
+# Algorithmic FP work per predictor-corrector pass of one node (D2Q16,
+# 4 x 4 stencil): 256 (population, source) pairs x 56 fused multiply-adds
+# (3 gauge differences, 8 xi offsets, 24 Lagrange-Taylor terms, 20
+# contraction, 1 weighted accumulate) = 28672 flops, plus 16 departures with
+# their cubic weights (20 flops each) and the moments / gauge update (128).
+FLOP_PER_PASS = 256 * 112 + 16 * 20 + 128
+# Algorithmic HBM bytes per node update: read and write 16 populations and
+# 3 FP64 gauge values (FP64: 2 x 152 B; mixed: 2 x (64 + 24) B).
+BYTES_FP64 = 2 * (16 * 8 + 3 * 8)
+BYTES_MIXED = 2 * (16 * 4 + 3 * 8)
+# Peaks of the arithmetic pipes (nominal, at the 2070 MHz maximum SM clock):
+# FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 flops x 2.07 GHz.
+PEAK_FP64_TFLOPS = 1.25
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pond", choices=["pond", "reference"])
+    ap.add_argument("--no-forms", action="store_true", help="headline only")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(fields, seconds: float, params=None):
+    """Time the FP64 CPU oracle on a bounded sample: one step of the first R
+    rows of the workload, R sized for about `seconds` of CPU time."""
+    import oracle
+    st = oracle.init_equilibrium(fields.rho, fields.ux, fields.uy, fields.T)
+    ny, nx = fields.shape
+    t0 = time.perf_counter()
+    oracle.step(st, params, rows=(0, 1))
+    per_row = max(time.perf_counter() - t0, 1e-4)
+    rows = int(max(1, min(ny, seconds / per_row)))
+    t0 = time.perf_counter()
+    oracle.step(st, params, rows=(0, rows))
+    dt = time.perf_counter() - t0
+    return {"value": rows * nx / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "one FP64 oracle step of rows 0..%d (%d nodes) of the %dx%d field, %.1f s"
+                      % (rows - 1, rows * nx, nx, ny, dt)}
+
+
+def time_steps(sim, stream, steps):
+    """Time `steps` PonD steps on `stream` with CUDA events; returns (seconds,
+    stats)."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats = sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, stats
+
+
+def form_line(name, nodes, steps, secs, stats, precision_peak_tflops, bytes_per_update):
+    passes = stats["passes"] / max(stats["node_updates"], 1)
+    achieved = FLOP_PER_PASS * stats["passes"] / secs / 1e12
+    return {
+        "workload": name,
+        "value": nodes * steps / secs,
+        "unit": UNIT,
+        "steps": steps,
+        "ms_per_step": secs / steps * 1e3,
+        "mean_passes": passes,
+        "max_passes": stats["max_passes"],
+        "nonconverged": stats["nonconverged"],
+        "halo_fallback": stats.get("halo_fallback", 0),
+        "alu_tflops": achieved,
+        "alu_frac": achieved / precision_peak_tflops,
+        "hbm_gbs_algorithmic": nodes * steps * bytes_per_update / secs / 1e9,
+    }
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args, world, rank):
+    from paper_1806_05089_gb300 import workloads
+    if rank != 0:
+        return
+    import oracle
+    fields = workloads.supersonic(2048)
+    st = oracle.init_equilibrium(fields.rho, fields.ux, fields.uy, fields.T)
+    ny, nx = fields.shape
+    t0 = time.perf_counter()
+    oracle.step(st, None, rows=(0, 1))
+    per_row = max(time.perf_counter() - t0, 1e-4)
+    budget = min(15.0, max(0.5, 150.0 / max(args.steps + args.warmup, 1)))
+    rows = int(max(1, min(ny, budget / per_row)))
+    for _ in range(args.warmup):
+        oracle.step(st, None, rows=(0, 1))
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.step(st, None, rows=(0, rows))
+        times.append(time.perf_counter() - t0)
+    secs = float(np.sum(times))
+    value = rows * nx * args.steps / secs
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": nx, "ny": ny,
+                   "sample_rows_per_step": rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": "each step: one FP64 oracle step of rows 0..%d of the %dx%d field"
+                                   % (rows - 1, nx, ny)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_pond(args, world, rank, local):
+    import torch
+    from paper_1806_05089_gb300 import pond, workloads
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    pond.load()
+    peaks = measured_peaks()
+    stream = torch.cuda.Stream()
+    fields = workloads.supersonic(2048)
+    ny, nx = fields.shape
+    nodes = nx * ny
+
+    # ---- headline: FP64 step, state resident in HBM (1.2 GB > L2)
+    sim = pond.Sim(nx, ny, pond.POND_FP64, stream=stream.cuda_stream)
+    sim.set_state(fields.rho, fields.ux, fields.uy, fields.T)
+    torch.cuda.synchronize()
+    sim.step(args.warmup)
+    barrier(world)
+    with ClockSampler(local) as clk:
+        secs, stats = time_steps(sim, stream, args.steps)
+    barrier(world)
+    secs_max = max_over_ranks(world, secs)
+    clocks = clk.summary()
+    rho64, ux64, uy64, T64 = sim.moments()
+    mean_passes = stats["passes"] / stats["node_updates"]
+    kernel_s = secs / args.steps
+    achieved = FLOP_PER_PASS * (stats["passes"] / args.steps) / kernel_s / 1e12
+    line = {
+        "metric": METRIC,
+        "value": world * nodes * args.steps / secs_max,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": secs_max / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "lattice": "D2Q16",
+                   "u": [1.5, 0.5], "perturbation": "8 sinusoids, 0.1/8 each, k 1..8",
+                   "nu": 0.01, "eps": [1e-12, 1e-10], "parallelism": "replica per GPU",
+                   "l2": "no flush: the state read and written per step (1.27 GB) exceeds L2"},
+        "mean_passes": mean_passes,
+        "max_passes": stats["max_passes"],
+        "nonconverged": stats["nonconverged"],
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved,
+                     "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
+                     "peak_source": "nominal FP64 rate at 2070 MHz (profiling recipe)",
+                     "kernel": "k1_step_fp64", "kernel_ms": kernel_s * 1e3,
+                     "hbm_gbs_algorithmic": nodes * BYTES_FP64 / kernel_s / 1e9,
+                     "hbm_peak_gbs": peaks.get("hbm_gbs")},
+        "clocks": clocks,
+    }
+
+    # ---- end to end through the public API with host buffers
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(fields, k))).pin_memory()
+           for k in ("rho", "ux", "uy", "T")}
+    rho_out = torch.empty((ny, nx), dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    for it in range(e2e_steps + 1):
+        if it == 1:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        pond.pond_set_state(sim.ctx, 0, pin["rho"], pin["ux"], pin["uy"], pin["T"])
+        pond.pond_step(sim.ctx, 1, want_stats=False)
+        pond.pond_moments(sim.ctx, 0, rho_out)
+    e2e_s = time.perf_counter() - t0
+    e2e_max = max_over_ranks(world, e2e_s)
+    line["e2e"] = {"value": world * nodes * e2e_steps / e2e_max, "unit": UNIT,
+                   "h2d_bytes_per_step": 4 * 8 * nodes, "d2h_bytes_per_step": 8 * nodes,
+                   "steps": e2e_steps,
+                   "call": "pond_set_state(host rho,u,T) + pond_step(1) + pond_moments(host rho)"}
+    sim.close()
+
+    # ---- other forms (not part of the headline's timed region)
+    if not args.no_forms:
+        forms = {}
+        k2 = max(args.steps, 10)
+        msim = pond.Sim(nx, ny, pond.POND_FP32_MIXED, stream=stream.cuda_stream, use_graph=1)
+        msim.set_state(fields.rho, fields.ux, fields.uy, fields.T)
+        msim.step(args.warmup)
+        msecs, mstats = time_steps(msim, stream, args.steps)
+        rho32, ux32, uy32, T32 = msim.moments()
+        forms["fp32_mixed_2048"] = form_line("supersonic-2048-mixed", nodes, args.steps, msecs,
+                                             mstats, PEAK_FP32_TFLOPS, BYTES_MIXED)
+        forms["fp32_mixed_2048"]["moment_err_vs_fp64"] = {
+            "after_steps": args.warmup + args.steps,
+            "rho": float(np.max(np.abs(rho32 - rho64)) / np.max(np.abs(rho64))),
+            "u": float(max(np.max(np.abs(ux32 - ux64)), np.max(np.abs(uy32 - uy64)))
+                       / np.max(np.hypot(ux64, uy64))),
+            "T": float(np.max(np.abs(T32 - T64)) / np.max(np.abs(T64)))}
+        forms["fp32_mixed_2048"]["speedup_vs_fp64"] = (nodes * args.steps / msecs) / (
+            nodes * args.steps / secs)
+        msim.close()
+
+        pf = workloads.precision(4096)
+        psim = pond.Sim(4096, 4096, pond.POND_FP32_MIXED, stream=stream.cuda_stream, use_graph=1)
+        psim.set_state(pf.rho, pf.ux, pf.uy, pf.T)
+        psim.step(args.warmup)
+        psecs, pstats = time_steps(psim, stream, k2)
+        forms["fp32_mixed_4096"] = form_line("precision-4096-mixed", 4096 * 4096, k2, psecs,
+                                             pstats, PEAK_FP32_TFLOPS, BYTES_MIXED)
+        psim.close()
+        del pf
+
+        nxs, nys = workloads.ensemble_sizes(256)
+        members = workloads.ensemble(256)
+        bsim = pond.Sim(nxs, nys, pond.POND_FP32_MIXED, stream=stream.cuda_stream, use_graph=1)
+        for i, m in enumerate(members):
+            bsim.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
+        bnodes = int(sum(a * b for a, b in zip(nxs, nys)))
+        bsim.step(args.warmup)
+        bsecs, bstats = time_steps(bsim, stream, k2)
+        forms["batched_256"] = form_line("ensemble-256-mixed", bnodes, k2, bsecs, bstats,
+                                         PEAK_FP32_TFLOPS, BYTES_MIXED)
+        bsim.close()
+        line["forms"] = forms
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = oracle_sample(fields, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_pond(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * pond.h -- C ABI of the GB300 Particles-on-Demand (PonD) step library.
+ *
+ * Method: Dorschner, Bosch, Karlin, "Particles-on-Demand for Kinetic
+ * Theory" (arXiv 1806.05089).  One time step on a periodic D2Q16 lattice
+ * (tensor product of the four roots of He4, T_L = 1):
+ *   - departure points x - (sqrt(theta) c_i + u) dt        (Eqs. advection, vi)
+ *   - gauge transform of neighbour populations by moment
+ *     matching, f' = M_target^-1 M_source f                 (Eqs. moments, match,
+ *                                                           transform)
+ *   - bicubic Lagrange reconstruction at the departure point (Eq. interpolation,
+ *                                                           App. C)
+ *   - predictor-corrector fixed point on rho, u, T          (Eqs. conservation_*,
+ *                                                           density..precollision,
+ *                                                           App. E Eq. convergence)
+ *   - BGK relaxation toward rho W in the co-moving gauge     (Eqs. equilibrium,
+ *                                                           postcollision)
+ *
+ * Conventions shared by every entry point:
+ *   - population index q = 4 k + l, k the x-speed index and l the y-speed
+ *     index of the ascending speeds c_0 < c_1 < c_2 < c_3;
+ *   - fields are row-major [ny][nx] (x fastest); populations are
+ *     structure-of-arrays [16][ny][nx];
+ *   - every array crossing this boundary is FP64 (double), whatever the
+ *     internal precision; gauges are (u_x, u_y, T) with theta = T / T_L;
+ *   - lattice units: dx = 1, dt from the config (default 1).
+ *
+ * Ownership: the caller owns every buffer it passes (host memory, or device
+ * memory of the context's device when on_device != 0).  The library copies
+ * into its own device state, allocated by pond_create and freed by
+ * pond_destroy.  All device work is enqueued on the stream given to
+ * pond_create (or pond_set_stream); calls that return data to host memory
+ * synchronise that stream before returning.
+ *
+ * Errors: every call returns a pond_status; nothing throws across the
+ * boundary and no kernel traps.  pond_last_error() gives a message for the
+ * most recent failing call on a context.
+ */
+#ifndef POND_H
+#define POND_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pond_ctx pond_ctx; /* opaque; owned by the library */
+
+typedef enum pond_status {
+    POND_OK = 0,
+    POND_ERR_ARG = 1,           /* invalid argument (NULL, size, grid index) */
+    POND_ERR_OOM = 2,           /* device allocation failed */
+    POND_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed */
+    POND_ERR_NONPHYSICAL = 4,   /* rho <= 0, T <= 0 or NaN met at some node */
+    POND_ERR_NOT_CONVERGED = 5, /* strict mode: a node hit max_iter */
+    POND_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+    POND_ERR_STATE = 7          /* call out of order (e.g. step before set_state) */
+} pond_status;
+
+enum { POND_FP64 = 0, POND_FP32_MIXED = 1 };
+
+/* Run configuration.  Fill with pond_config_default() and override. */
+typedef struct pond_config {
+    int32_t precision;  /* POND_FP64: all arithmetic and storage FP64.
+                           POND_FP32_MIXED: populations and bulk arithmetic
+                           FP32; gauges stored FP64; gauge differences, the
+                           moment-to-gauge update and the convergence test in
+                           FP64 accuracy. */
+    int32_t thermal;    /* 1: energy equation in the predictor-corrector
+                           (compressible); 0: isothermal, T kept fixed
+                           (main text after Eq. postcollision). */
+    double nu;          /* kinematic viscosity; beta = 1/(2 nu/(T_ref dt) + 1)
+                           from nu = T (1/(2 beta) - 1/2) dt (Eq. postcollision) */
+    double T_ref;       /* temperature in that relation (default 1) */
+    double dt;          /* time step (default 1) */
+    double eps_abs;     /* Eq. convergence tolerances (App. E); defaults   */
+    double eps_rel;     /* 1e-12 / 1e-10 (FP64), 1e-6 / 1e-6 (FP32_MIXED)  */
+    int32_t max_iter;   /* predictor-corrector pass limit (default 20) */
+    int32_t fixed_iter; /* > 0: exactly this many passes, no early exit */
+    int32_t ckpt_every; /* adjoint checkpoint interval (used by bindings) */
+    int32_t strict;     /* 1: pond_step returns POND_ERR_NOT_CONVERGED when a
+                           node hit max_iter without converging */
+    int32_t seed_mode;  /* 0: previous gauge at the node (Eq. seed_gauge);
+                           1: {0, T_L}; 2: {-u, T} (seed-independence study) */
+    int32_t use_graph;  /* 1: pond_step replays a CUDA graph of two steps
+                           (captured on first use, re-captured after
+                           set_state / set_stream) */
+} pond_config;
+
+/* Counters accumulated over the steps of one pond_step call. */
+typedef struct pond_stats {
+    int64_t node_updates;  /* nodes x steps */
+    int64_t passes;        /* predictor-corrector passes over all node updates */
+    int32_t max_passes;    /* largest pass count at any node */
+    int32_t reserved;
+    int64_t nonconverged;  /* node updates that hit max_iter unconverged */
+    int64_t nonphysical;   /* node updates that met rho <= 0, T <= 0 or NaN */
+    int64_t halo_fallback; /* stencils read from global memory instead of the
+                              shared-memory halo tile (mixed form only) */
+} pond_stats;
+
+/* Defaults for a precision (POND_FP64 or POND_FP32_MIXED). */
+void pond_config_default(pond_config* cfg, int32_t precision);
+
+/* Create a context for n_grids independent periodic grids of sizes
+ * nx[g] x ny[g] (n_grids == 1: single grid; > 1: batched ensemble advanced
+ * together by one launch per step).  cuda_stream is a cudaStream_t (NULL =
+ * legacy default stream).  Allocates all device state; nothing else
+ * allocates afterwards except pond_adjoint_step's first call.
+ * Errors: POND_ERR_ARG (NULL pointers, n_grids < 1, a side < 1, bad
+ * precision), POND_ERR_OOM, POND_ERR_CUDA. */
+pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* nx,
+                        const int32_t* ny, void* cuda_stream, pond_ctx** out);
+
+/* Replace the stream all later work is enqueued on. */
+pond_status pond_set_stream(pond_ctx* ctx, void* cuda_stream);
+
+/* Set the state of grid `grid` from macroscopic fields, each [ny][nx] FP64:
+ * density rho, velocity (ux, uy), temperature T.  If f is NULL the
+ * populations are the equilibrium f = rho W in each node's own gauge
+ * (Eq. equilibrium; rho is then required).  If f is given ([16][ny][nx]),
+ * it is taken as the populations in the gauge (ux, uy, T) and rho is
+ * ignored (may be NULL).  on_device: pointers are device (1) or host (0).
+ * Errors: POND_ERR_ARG, POND_ERR_NONPHYSICAL (T <= 0 or non-finite gauge on
+ * host input), POND_ERR_CUDA. */
+pond_status pond_set_state(pond_ctx* ctx, int32_t grid, const void* rho, const void* ux,
+                           const void* uy, const void* T, const void* f, int32_t on_device);
+
+/* Advance every grid by nsteps PonD time steps.  stats may be NULL; when
+ * given, the stream is synchronised and the counters filled.
+ * Errors: POND_ERR_STATE (a grid never set), POND_ERR_ARG (nsteps < 0),
+ * POND_ERR_CUDA, and -- only when stats is given -- POND_ERR_NONPHYSICAL /
+ * POND_ERR_NOT_CONVERGED (strict) from the counters. */
+pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats);
+
+/* Macroscopic fields of grid `grid`, each [ny][nx] FP64 (any may be NULL):
+ * rho = sum_q f_q (Eq. conservation_rho) and the stored gauge (u, T), which
+ * is the co-moving frame of the populations (remark after Eq. precollision). */
+pond_status pond_moments(pond_ctx* ctx, int32_t grid, void* rho, void* ux, void* uy,
+                         void* T, int32_t on_device);
+
+/* Raw state of grid `grid`: populations f [16][ny][nx] in the stored gauge
+ * and the gauge (ux, uy, T) [ny][nx]; any pointer may be NULL. */
+pond_status pond_get_state(pond_ctx* ctx, int32_t grid, void* f, void* ux, void* uy,
+                           void* T, int32_t on_device);
+
+/* Predictor-corrector pass counts of the last step at every node of grid
+ * `grid`, int32 [ny][nx] (the map of App. E's iteration figure). */
+pond_status pond_iterations(pond_ctx* ctx, int32_t grid, void* iters, int32_t on_device);
+
+/* Vector-Jacobian product of one step (single-grid contexts).  The context's
+ * current state is the step's INPUT state s; given the cotangents of the
+ * step's output, f_bar_in [16][ny][nx] and gauge_bar_in [3][ny][nx]
+ * (ux, uy, T), writes the cotangents of s to f_bar_out and gauge_bar_out
+ * (same layouts) and adds d(loss)/d(nu) to *nu_bar_accum.  The fixed point
+ * is differentiated implicitly (the limit gauge of Eqs. density..T is a
+ * function of the input state only; the seed gets no gradient).  All array
+ * pointers are device pointers.  The state is left unchanged.
+ * Errors: POND_ERR_ARG, POND_ERR_STATE, POND_ERR_OOM, POND_ERR_CUDA. */
+pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in, const void* gauge_bar_in,
+                              void* f_bar_out, void* gauge_bar_out, double* nu_bar_accum);
+
+void pond_destroy(pond_ctx* ctx);
+
+/* Message of the last failing call on ctx ("" if none; static text if ctx is
+ * NULL). */
+const char* pond_last_error(const pond_ctx* ctx);
+
+/* Library version string. */
+const char* pond_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POND_H */

@@ -243,11 +243,11 @@ int oracle_step(int64_t nx, int64_t ny, const double *f_in, const double *ux_in,
     const double D = 2.0;
 
 #ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 16)
 #endif
-    for (int64_t Y = y_begin; Y < y_end; ++Y) {
-        for (int64_t X = 0; X < nx; ++X) {
-            const int64_t node = Y * nx + X;
+    for (int64_t node = y_begin * nx; node < y_end * nx; ++node) {
+        {
+            const int64_t X = node % nx, Y = node / nx;
             /* seed gauge (Eqs. seed_gauge, seed_gauge_T) */
             double ux = ux_in[node], uy = uy_in[node], T = T_in[node];
             if (p->seed_mode == 1) {

@@ -1,0 +1,533 @@
+// pond_api.cu -- C ABI of the PonD library (see include/pond.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pond_internal.cuh"
+
+using namespace pond;
+
+namespace {
+
+const char* kVersion = "pond-gb300 0.1 (D2Q16, sm_103a)";
+
+// Keep the caller's current device across a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else if (prev == dev) prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+pond_status fail(pond_ctx* c, pond_status s, const char* msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+pond_status cuda_fail(pond_ctx* c, cudaError_t e, const char* where) {
+    if (c) {
+        c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return e == cudaErrorMemoryAllocation ? POND_ERR_OOM : POND_ERR_CUDA;
+}
+
+#define CK(call, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+bool mixed(const pond_ctx* c) { return c->cfg.precision == POND_FP32_MIXED; }
+
+size_t real_size(const pond_ctx* c) { return mixed(c) ? sizeof(float) : sizeof(double); }
+
+template <typename Real>
+StateBuf<Real> buf(pond_ctx* c, int which, int64_t offset) {
+    StateBuf<Real> b;
+    b.f = static_cast<Real*>(c->f[which]) + offset;
+    b.ux = c->ux[which] + offset;
+    b.uy = c->uy[which] + offset;
+    b.st = c->st[which] + offset;
+    return b;
+}
+
+// Staging buffer for host-side input/output (20 FP64 fields of one grid).
+pond_status ensure_staging(pond_ctx* ctx, int64_t nodes) {
+    const size_t need = (size_t)20 * (size_t)nodes * sizeof(double);
+    if (ctx->staging_bytes >= need) return POND_OK;
+    if (ctx->staging) {
+        CK(cudaStreamSynchronize(ctx->stream), "staging sync");
+        CK(cudaFree(ctx->staging), "staging free");
+        ctx->staging = nullptr;
+        ctx->staging_bytes = 0;
+    }
+    CK(cudaMalloc(&ctx->staging, need), "staging alloc");
+    ctx->staging_bytes = need;
+    return POND_OK;
+}
+
+// Window of the mixed kernel from the per-grid velocity spans.
+pond_status update_window(pond_ctx* ctx) {
+    if (!mixed(ctx)) return POND_OK;
+    float sx = 0.f, sy = 0.f;
+    for (int g = 0; g < ctx->n_grids; ++g) {
+        if (!ctx->grid_set[g]) continue;
+        const float* sp = &ctx->spans[4 * g];
+        sx = std::fmax(sx, sp[1] - sp[0]);
+        sy = std::fmax(sy, sp[3] - sp[2]);
+    }
+    const double dt = ctx->cfg.dt, margin = 1.0;
+    TileWindow w;
+    w.tx = MIXED_TX;
+    w.ty = MIXED_TY;
+    w.ww = MIXED_TX + (int)std::ceil(sx * dt + 2 * margin) + 5;
+    w.wh = MIXED_TY + (int)std::ceil(sy * dt + 2 * margin) + 5;
+    // cap the staged window at the shared memory a CTA can have; stencils
+    // beyond it take the global-memory path
+    const size_t cap = 220 * 1024;
+    while (mixed_smem_bytes(w) > cap) {
+        if (w.ww - MIXED_TX >= w.wh - MIXED_TY) --w.ww; else --w.wh;
+    }
+    const size_t smem = mixed_smem_bytes(w);
+    int per_sm = 0;
+    CK(mixed_prepare(smem, &per_sm), "mixed kernel set-up");
+    if (per_sm < 1) return fail(ctx, POND_ERR_CUDA, "mixed kernel does not fit on an SM");
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "SM count");
+    ctx->win = w;
+    ctx->persistent_ctas = per_sm * sms;
+    return POND_OK;
+}
+
+pond_status check_grid(pond_ctx* ctx, int32_t grid) {
+    if (!ctx) return POND_ERR_ARG;
+    if (grid < 0 || grid >= ctx->n_grids) return fail(ctx, POND_ERR_ARG, "grid index out of range");
+    return POND_OK;
+}
+
+}  // namespace
+
+static pond_status launch_one_step(pond_ctx* ctx) {
+    const int in = ctx->cur, out = 1 - ctx->cur;
+    if (mixed(ctx)) {
+        const bool batched = ctx->n_grids > 1;
+        CK(launch_step_mixed(buf<float>(ctx, in, 0), buf<float>(ctx, out, 0), ctx->iters,
+                             ctx->stats, ctx->grids_dev, ctx->tile_prefix_dev, ctx->n_grids,
+                             ctx->n_tiles, ctx->N, batched ? ctx->work_counter : nullptr,
+                             ctx->win, ctx->persistent_ctas, ctx->L, ctx->P, ctx->stream),
+           "mixed step launch");
+    } else {
+        const GridDesc& G = ctx->grids_host[0];
+        CK(launch_step_fp64(buf<double>(ctx, in, 0), buf<double>(ctx, out, 0), ctx->iters,
+                            ctx->stats, G.nx, G.ny, ctx->L, ctx->P, ctx->stream),
+           "fp64 step launch");
+    }
+    ctx->cur = out;
+    return POND_OK;
+}
+
+// Two steps captured as one CUDA graph per buffer parity (the state buffers
+// alternate, so two steps return to the same layout).
+static void drop_graphs(pond_ctx* ctx) {
+    for (int i = 0; i < 2; ++i) {
+        if (ctx->graph_exec[i]) cudaGraphExecDestroy(ctx->graph_exec[i]);
+        ctx->graph_exec[i] = nullptr;
+    }
+}
+
+static pond_status ensure_graph(pond_ctx* ctx) {
+    if (ctx->graph_exec[ctx->cur]) return POND_OK;
+    cudaStream_t cap = nullptr;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "graph stream");
+    cudaStream_t user = ctx->stream;
+    ctx->stream = cap;
+    const int cur0 = ctx->cur;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    pond_status s = POND_OK;
+    if (e == cudaSuccess) {
+        s = launch_one_step(ctx);
+        if (s == POND_OK) s = launch_one_step(ctx);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    ctx->stream = user;
+    ctx->cur = cur0;
+    cudaStreamDestroy(cap);
+    if (s != POND_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    CK(e, "graph capture");
+    e = cudaGraphInstantiate(&ctx->graph_exec[cur0], graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e, "graph instantiate");
+    return POND_OK;
+}
+
+static pond_status read_out(pond_ctx* ctx, int32_t grid, void* rho, void* ux, void* uy, void* T,
+                            void* f, int32_t on_device) {
+    pond_status s = check_grid(ctx, grid);
+    if (s != POND_OK) return s;
+    if (!ctx->grid_set[grid]) return fail(ctx, POND_ERR_STATE, "grid state never set");
+    DeviceGuard dg(ctx->device);
+    const GridDesc& G = ctx->grids_host[grid];
+    const int64_t n = (int64_t)G.nx * G.ny;
+    double *d_rho, *d_ux, *d_uy, *d_T, *d_f;
+    if (on_device) {
+        d_rho = static_cast<double*>(rho);
+        d_ux = static_cast<double*>(ux);
+        d_uy = static_cast<double*>(uy);
+        d_T = static_cast<double*>(T);
+        d_f = static_cast<double*>(f);
+    } else {
+        s = ensure_staging(ctx, n);
+        if (s != POND_OK) return s;
+        double* sb = static_cast<double*>(ctx->staging);
+        d_rho = rho ? sb : nullptr;
+        d_ux = ux ? sb + n : nullptr;
+        d_uy = uy ? sb + 2 * n : nullptr;
+        d_T = T ? sb + 3 * n : nullptr;
+        d_f = f ? sb + 4 * n : nullptr;
+    }
+    if (mixed(ctx)) {
+        CK(launch_read_state<float>(buf<float>(ctx, ctx->cur, G.offset), n, ctx->N, d_rho, d_ux,
+                                    d_uy, d_T, d_f, ctx->L, ctx->stream),
+           "read state");
+    } else {
+        CK(launch_read_state<double>(buf<double>(ctx, ctx->cur, G.offset), n, ctx->N, d_rho, d_ux,
+                                     d_uy, d_T, d_f, ctx->L, ctx->stream),
+           "read state");
+    }
+    if (!on_device) {
+        const size_t fb = sizeof(double) * n;
+        if (rho) CK(cudaMemcpyAsync(rho, d_rho, fb, cudaMemcpyDeviceToHost, ctx->stream), "D2H rho");
+        if (ux) CK(cudaMemcpyAsync(ux, d_ux, fb, cudaMemcpyDeviceToHost, ctx->stream), "D2H ux");
+        if (uy) CK(cudaMemcpyAsync(uy, d_uy, fb, cudaMemcpyDeviceToHost, ctx->stream), "D2H uy");
+        if (T) CK(cudaMemcpyAsync(T, d_T, fb, cudaMemcpyDeviceToHost, ctx->stream), "D2H T");
+        if (f) CK(cudaMemcpyAsync(f, d_f, 16 * fb, cudaMemcpyDeviceToHost, ctx->stream), "D2H f");
+        CK(cudaStreamSynchronize(ctx->stream), "read sync");
+    }
+    return POND_OK;
+}
+
+extern "C" {
+
+const char* pond_version(void) { return kVersion; }
+
+void pond_config_default(pond_config* cfg, int32_t precision) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->precision = precision;
+    cfg->thermal = 1;
+    cfg->nu = 0.01;
+    cfg->T_ref = 1.0;
+    cfg->dt = 1.0;
+    if (precision == POND_FP32_MIXED) {
+        cfg->eps_abs = 1e-6;
+        cfg->eps_rel = 1e-6;
+    } else {
+        cfg->eps_abs = 1e-12;
+        cfg->eps_rel = 1e-10;
+    }
+    cfg->max_iter = 20;
+    cfg->fixed_iter = 0;
+    cfg->ckpt_every = 20;
+    cfg->strict = 0;
+    cfg->seed_mode = 0;
+    cfg->use_graph = 0;
+}
+
+pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* nx,
+                        const int32_t* ny, void* cuda_stream, pond_ctx** out) {
+    if (!out) return POND_ERR_ARG;
+    *out = nullptr;
+    if (!cfg || !nx || !ny || n_grids < 1) return POND_ERR_ARG;
+    if (cfg->precision != POND_FP64 && cfg->precision != POND_FP32_MIXED) return POND_ERR_ARG;
+    if (!(cfg->nu > 0.0) || !(cfg->T_ref > 0.0) || !(cfg->dt > 0.0) || cfg->max_iter < 1 ||
+        cfg->fixed_iter < 0 || cfg->seed_mode < 0 || cfg->seed_mode > 2)
+        return POND_ERR_ARG;
+    if (cfg->precision == POND_FP64 && n_grids != 1) return POND_ERR_ARG;
+    for (int g = 0; g < n_grids; ++g)
+        if (nx[g] < 1 || ny[g] < 1) return POND_ERR_ARG;
+
+    pond_ctx* ctx = new (std::nothrow) pond_ctx();
+    if (!ctx) return POND_ERR_OOM;
+    ctx->cfg = *cfg;
+    ctx->L = make_lattice();
+    ctx->P.beta = 1.0 / (2.0 * cfg->nu / (cfg->T_ref * cfg->dt) + 1.0);
+    ctx->P.dt = cfg->dt;
+    ctx->P.eps_abs = cfg->eps_abs;
+    ctx->P.eps_rel = cfg->eps_rel;
+    ctx->P.T_L = ctx->L.T_L;
+    ctx->P.max_iter = cfg->max_iter;
+    ctx->P.fixed_iter = cfg->fixed_iter;
+    ctx->P.thermal = cfg->thermal;
+    ctx->P.seed_mode = cfg->seed_mode;
+    ctx->n_grids = n_grids;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaGetDevice(&ctx->device);
+    ctx->grid_set.assign(n_grids, 0);
+    ctx->spans.assign(4 * (size_t)n_grids, 0.f);
+    int64_t off = 0, tiles = 0;
+    std::vector<int64_t> prefix(n_grids + 1, 0);
+    for (int g = 0; g < n_grids; ++g) {
+        GridDesc d;
+        d.nx = nx[g];
+        d.ny = ny[g];
+        d.offset = off;
+        ctx->grids_host.push_back(d);
+        off += (int64_t)nx[g] * ny[g];
+        prefix[g] = tiles;
+        tiles += (int64_t)((nx[g] + MIXED_TX - 1) / MIXED_TX) * ((ny[g] + MIXED_TY - 1) / MIXED_TY);
+    }
+    prefix[n_grids] = tiles;
+    ctx->N = off;
+    ctx->n_tiles = tiles;
+
+    pond_status st = POND_OK;
+    auto alloc = [&](void** p, size_t bytes, const char* what) -> bool {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            st = cuda_fail(ctx, e, what);
+            return false;
+        }
+        return true;
+    };
+    const size_t rs = real_size(ctx);
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; ++b) {
+        ok = ok && alloc(&ctx->f[b], rs * 16 * (size_t)ctx->N, "alloc f");
+        ok = ok && alloc((void**)&ctx->ux[b], sizeof(double) * ctx->N, "alloc ux");
+        ok = ok && alloc((void**)&ctx->uy[b], sizeof(double) * ctx->N, "alloc uy");
+        ok = ok && alloc((void**)&ctx->st[b], sizeof(double) * ctx->N, "alloc st");
+    }
+    ok = ok && alloc((void**)&ctx->iters, sizeof(int32_t) * ctx->N, "alloc iters");
+    ok = ok && alloc((void**)&ctx->stats, sizeof(DevStats), "alloc stats");
+    ok = ok && alloc((void**)&ctx->grids_dev, sizeof(GridDesc) * n_grids, "alloc grids");
+    ok = ok && alloc((void**)&ctx->tile_prefix_dev, sizeof(int64_t) * (n_grids + 1), "alloc prefix");
+    ok = ok && alloc((void**)&ctx->work_counter, sizeof(unsigned int), "alloc counter");
+    ok = ok && alloc((void**)&ctx->bounds_dev, 4 * sizeof(float), "alloc bounds");
+    if (ok) {
+        cudaError_t e = cudaMallocHost((void**)&ctx->stats_host, sizeof(DevStats));
+        if (e != cudaSuccess) {
+            st = cuda_fail(ctx, e, "alloc pinned stats");
+            ok = false;
+        }
+    }
+    if (ok) {
+        cudaError_t e = cudaMemcpy(ctx->grids_dev, ctx->grids_host.data(),
+                                   sizeof(GridDesc) * n_grids, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ctx->tile_prefix_dev, prefix.data(), sizeof(int64_t) * (n_grids + 1),
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(ctx->iters, 0, sizeof(int32_t) * ctx->N);
+        if (e == cudaSuccess) e = upload_lattice_fp64(ctx->L);
+        if (e == cudaSuccess) e = upload_lattice_mixed(ctx->L);
+        if (e == cudaSuccess) e = upload_lattice_adjoint(ctx->L);
+        if (e != cudaSuccess) {
+            st = cuda_fail(ctx, e, "context set-up");
+            ok = false;
+        }
+    }
+    if (!ok) {
+        pond_destroy(ctx);
+        return st == POND_OK ? POND_ERR_CUDA : st;
+    }
+    if (mixed(ctx)) {
+        // provisional window until set_state measures the displacements
+        for (int g = 0; g < n_grids; ++g) {
+            ctx->spans[4 * g + 0] = -6.f;
+            ctx->spans[4 * g + 1] = 6.f;
+            ctx->spans[4 * g + 2] = -6.f;
+            ctx->spans[4 * g + 3] = 6.f;
+        }
+        std::vector<char> saved = ctx->grid_set;
+        ctx->grid_set.assign(n_grids, 1);
+        st = update_window(ctx);
+        ctx->grid_set = saved;
+        if (st != POND_OK) {
+            pond_destroy(ctx);
+            return st;
+        }
+    }
+    *out = ctx;
+    return POND_OK;
+}
+
+pond_status pond_set_stream(pond_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return POND_ERR_ARG;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return POND_OK;
+}
+
+pond_status pond_set_state(pond_ctx* ctx, int32_t grid, const void* rho, const void* ux,
+                           const void* uy, const void* T, const void* f, int32_t on_device) {
+    pond_status s = check_grid(ctx, grid);
+    if (s != POND_OK) return s;
+    if (!ux || !uy || !T || (!f && !rho))
+        return fail(ctx, POND_ERR_ARG, "set_state: ux, uy, T and one of rho / f are required");
+    DeviceGuard dg(ctx->device);
+    const GridDesc& G = ctx->grids_host[grid];
+    const int64_t n = (int64_t)G.nx * G.ny;
+    const double *d_rho, *d_ux, *d_uy, *d_T, *d_f;
+    if (on_device) {
+        d_rho = static_cast<const double*>(rho);
+        d_ux = static_cast<const double*>(ux);
+        d_uy = static_cast<const double*>(uy);
+        d_T = static_cast<const double*>(T);
+        d_f = static_cast<const double*>(f);
+    } else {
+        const double* hT = static_cast<const double*>(T);
+        const double* hx = static_cast<const double*>(ux);
+        const double* hy = static_cast<const double*>(uy);
+        for (int64_t i = 0; i < n; ++i)
+            if (!(hT[i] > 0.0) || !std::isfinite(hT[i]) || !std::isfinite(hx[i]) ||
+                !std::isfinite(hy[i]))
+                return fail(ctx, POND_ERR_NONPHYSICAL, "set_state: T <= 0 or non-finite gauge");
+        s = ensure_staging(ctx, n);
+        if (s != POND_OK) return s;
+        double* sb = static_cast<double*>(ctx->staging);
+        double* p_rho = sb;
+        double* p_ux = sb + n;
+        double* p_uy = sb + 2 * n;
+        double* p_T = sb + 3 * n;
+        double* p_f = sb + 4 * n;
+        const size_t fb = sizeof(double) * n;
+        if (rho) CK(cudaMemcpyAsync(p_rho, rho, fb, cudaMemcpyHostToDevice, ctx->stream), "H2D rho");
+        CK(cudaMemcpyAsync(p_ux, ux, fb, cudaMemcpyHostToDevice, ctx->stream), "H2D ux");
+        CK(cudaMemcpyAsync(p_uy, uy, fb, cudaMemcpyHostToDevice, ctx->stream), "H2D uy");
+        CK(cudaMemcpyAsync(p_T, T, fb, cudaMemcpyHostToDevice, ctx->stream), "H2D T");
+        if (f) CK(cudaMemcpyAsync(p_f, f, 16 * fb, cudaMemcpyHostToDevice, ctx->stream), "H2D f");
+        d_rho = rho ? p_rho : nullptr;
+        d_ux = p_ux;
+        d_uy = p_uy;
+        d_T = p_T;
+        d_f = f ? p_f : nullptr;
+    }
+    if (mixed(ctx)) {
+        CK(launch_init_state<float>(d_rho, d_ux, d_uy, d_T, d_f, buf<float>(ctx, ctx->cur, G.offset),
+                                    n, ctx->N, ctx->L, ctx->stream),
+           "init state");
+    } else {
+        CK(launch_init_state<double>(d_rho, d_ux, d_uy, d_T, d_f,
+                                     buf<double>(ctx, ctx->cur, G.offset), n, ctx->N, ctx->L,
+                                     ctx->stream),
+           "init state");
+    }
+    // velocity spans of this grid, for the mixed kernel's halo window
+    CK(launch_disp_bounds(ctx->ux[ctx->cur] + G.offset, ctx->uy[ctx->cur] + G.offset,
+                          ctx->st[ctx->cur] + G.offset, n, ctx->L.c[3], ctx->bounds_dev,
+                          ctx->stream),
+       "bounds");
+    float b4[4];
+    CK(cudaMemcpyAsync(b4, ctx->bounds_dev, sizeof b4, cudaMemcpyDeviceToHost, ctx->stream), "D2H bounds");
+    CK(cudaStreamSynchronize(ctx->stream), "set_state sync");
+    for (int i = 0; i < 4; ++i) ctx->spans[4 * grid + i] = b4[i];
+    if (!(std::isfinite(b4[0]) && std::isfinite(b4[1]) && std::isfinite(b4[2]) && std::isfinite(b4[3])))
+        return fail(ctx, POND_ERR_NONPHYSICAL, "set_state: non-finite gauge");
+    ctx->grid_set[grid] = 1;
+    const TileWindow before = ctx->win;
+    s = update_window(ctx);
+    if (before.ww != ctx->win.ww || before.wh != ctx->win.wh) drop_graphs(ctx);
+    return s;
+}
+
+pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats) {
+    if (!ctx) return POND_ERR_ARG;
+    if (nsteps < 0) return fail(ctx, POND_ERR_ARG, "nsteps < 0");
+    for (int g = 0; g < ctx->n_grids; ++g)
+        if (!ctx->grid_set[g]) return fail(ctx, POND_ERR_STATE, "pond_step before pond_set_state");
+    DeviceGuard dg(ctx->device);
+    if (stats) CK(cudaMemsetAsync(ctx->stats, 0, sizeof(DevStats), ctx->stream), "stats reset");
+    int32_t left = nsteps;
+    if (ctx->cfg.use_graph && left >= 2) {
+        pond_status s = ensure_graph(ctx);
+        if (s != POND_OK) return s;
+        while (left >= 2) {
+            CK(cudaGraphLaunch(ctx->graph_exec[ctx->cur], ctx->stream), "graph launch");
+            left -= 2;
+        }
+    }
+    while (left-- > 0) {
+        pond_status s = launch_one_step(ctx);
+        if (s != POND_OK) return s;
+    }
+    if (stats) {
+        CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, sizeof(DevStats), cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "D2H stats");
+        CK(cudaStreamSynchronize(ctx->stream), "step sync");
+        const DevStats& d = *ctx->stats_host;
+        stats->node_updates = (int64_t)nsteps * ctx->N;
+        stats->passes = (int64_t)d.passes;
+        stats->max_passes = (int32_t)d.max_passes;
+        stats->reserved = 0;
+        stats->nonconverged = (int64_t)d.nonconverged;
+        stats->nonphysical = (int64_t)d.nonphysical;
+        stats->halo_fallback = (int64_t)d.halo_fallback;
+        if (d.nonphysical) return fail(ctx, POND_ERR_NONPHYSICAL, "rho <= 0, T <= 0 or NaN met");
+        if (ctx->cfg.strict && d.nonconverged)
+            return fail(ctx, POND_ERR_NOT_CONVERGED, "a node hit max_iter without converging");
+    }
+    return POND_OK;
+}
+
+pond_status pond_moments(pond_ctx* ctx, int32_t grid, void* rho, void* ux, void* uy, void* T,
+                         int32_t on_device) {
+    return read_out(ctx, grid, rho, ux, uy, T, nullptr, on_device);
+}
+
+pond_status pond_get_state(pond_ctx* ctx, int32_t grid, void* f, void* ux, void* uy, void* T,
+                           int32_t on_device) {
+    return read_out(ctx, grid, nullptr, ux, uy, T, f, on_device);
+}
+
+pond_status pond_iterations(pond_ctx* ctx, int32_t grid, void* iters, int32_t on_device) {
+    pond_status s = check_grid(ctx, grid);
+    if (s != POND_OK) return s;
+    if (!iters) return fail(ctx, POND_ERR_ARG, "iters is NULL");
+    DeviceGuard dg(ctx->device);
+    const GridDesc& G = ctx->grids_host[grid];
+    const size_t bytes = sizeof(int32_t) * (size_t)G.nx * G.ny;
+    CK(cudaMemcpyAsync(iters, ctx->iters + G.offset, bytes,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream),
+       "copy iters");
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream), "iters sync");
+    return POND_OK;
+}
+
+void pond_destroy(pond_ctx* ctx) {
+    if (!ctx) return;
+    DeviceGuard dg(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    destroy_adjoint(ctx);
+    drop_graphs(ctx);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(ctx->f[b]);
+        cudaFree(ctx->ux[b]);
+        cudaFree(ctx->uy[b]);
+        cudaFree(ctx->st[b]);
+    }
+    cudaFree(ctx->iters);
+    cudaFree(ctx->stats);
+    cudaFree(ctx->grids_dev);
+    cudaFree(ctx->tile_prefix_dev);
+    cudaFree(ctx->work_counter);
+    cudaFree(ctx->bounds_dev);
+    cudaFree(ctx->staging);
+    if (ctx->stats_host) cudaFreeHost(ctx->stats_host);
+    delete ctx;
+}
+
+const char* pond_last_error(const pond_ctx* ctx) {
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,200 @@
+// pond_common.cu -- lattice constants, state initialisation / read-out and
+// displacement bounds for the PonD library.
+#include <cmath>
+
+#include "pond_device.cuh"
+
+namespace pond {
+
+// D2Q16 constants from their closed forms (He4 roots and Gauss-Hermite
+// weights) and the Taylor coefficients of the Lagrange basis polynomials
+// L_k(x) = prod_{j != k} (x - c_j)/(c_k - c_j) around each speed c_a.
+Lattice make_lattice() {
+    Lattice L{};
+    const double s6 = std::sqrt(6.0);
+    L.c[0] = -std::sqrt(3.0 + s6);
+    L.c[1] = -std::sqrt(3.0 - s6);
+    L.c[2] = std::sqrt(3.0 - s6);
+    L.c[3] = std::sqrt(3.0 + s6);
+    L.w[0] = L.w[3] = (3.0 - s6) / 12.0;
+    L.w[1] = L.w[2] = (3.0 + s6) / 12.0;
+    L.T_L = 1.0;
+    for (int k = 0; k < 4; ++k) {
+        double p[4] = {1.0, 0.0, 0.0, 0.0};  // coefficients of x^0..x^3
+        double den = 1.0;
+        for (int j = 0; j < 4; ++j) {
+            if (j == k) continue;
+            double np[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int i = 0; i < 4; ++i) {
+                if (i + 1 < 4) np[i + 1] += p[i];
+                np[i] -= L.c[j] * p[i];
+            }
+            for (int i = 0; i < 4; ++i) p[i] = np[i];
+            den *= (L.c[k] - L.c[j]);
+        }
+        for (int i = 0; i < 4; ++i) p[i] /= den;
+        for (int a = 0; a < 4; ++a) {
+            const double x = L.c[a];
+            L.d1[k][a] = p[1] + 2.0 * p[2] * x + 3.0 * p[3] * x * x;
+            L.d2[k][a] = p[2] + 3.0 * p[3] * x;
+        }
+        L.d3[k] = p[3];
+    }
+    return L;
+}
+
+LatticeF to_float(const Lattice& L) {
+    LatticeF F{};
+    for (int i = 0; i < 4; ++i) {
+        F.c[i] = (float)L.c[i];
+        F.w[i] = (float)L.w[i];
+        F.d3[i] = (float)L.d3[i];
+        for (int j = 0; j < 4; ++j) {
+            F.d1[i][j] = (float)L.d1[i][j];
+            F.d2[i][j] = (float)L.d2[i][j];
+        }
+    }
+    return F;
+}
+
+// f_q = rho W_q in the node's own gauge (Eq. equilibrium), or a copy of the
+// given FP64 populations; T -> sqrt(theta).
+template <typename Real>
+__global__ void k_init_state(const double* __restrict__ rho, const double* __restrict__ ux,
+                             const double* __restrict__ uy, const double* __restrict__ T,
+                             const double* __restrict__ f_given, StateBuf<Real> st, int64_t N,
+                             int64_t plane, Lattice L) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    st.ux[i] = ux[i];
+    st.uy[i] = uy[i];
+    st.st[i] = sqrt(T[i] / L.T_L);
+    if (f_given) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) st.f[q * plane + i] = (Real)f_given[q * N + i];
+    } else {
+        const double r = rho[i];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            st.f[q * plane + i] = (Real)(r * L.w[q >> 2] * L.w[q & 3]);
+    }
+}
+
+template <typename Real>
+cudaError_t launch_init_state(const double* rho, const double* ux, const double* uy,
+                              const double* T, const double* f_given, StateBuf<Real> st,
+                              int64_t N, int64_t plane, const Lattice& L, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    const int bs = 256;
+    const unsigned nb = (unsigned)((N + bs - 1) / bs);
+    k_init_state<Real><<<nb, bs, 0, s>>>(rho, ux, uy, T, f_given, st, N, plane, L);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+__global__ void k_read_state(StateBuf<Real> st, int64_t N, int64_t plane, double* rho,
+                             double* ux, double* uy, double* T, double* f, Lattice L) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double r = 0.0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const double v = (double)st.f[q * plane + i];
+        r += v;
+        if (f) f[q * N + i] = v;
+    }
+    if (rho) rho[i] = r;
+    if (ux) ux[i] = st.ux[i];
+    if (uy) uy[i] = st.uy[i];
+    if (T) {
+        const double s = st.st[i];
+        T[i] = s * s * L.T_L;
+    }
+}
+
+template <typename Real>
+cudaError_t launch_read_state(StateBuf<Real> st, int64_t N, int64_t plane, double* rho,
+                              double* ux, double* uy, double* T, double* f, const Lattice& L,
+                              cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    const int bs = 256;
+    const unsigned nb = (unsigned)((N + bs - 1) / bs);
+    k_read_state<Real><<<nb, bs, 0, s>>>(st, N, plane, rho, ux, uy, T, f, L);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_init_state<double>(const double*, const double*, const double*,
+                                               const double*, const double*, StateBuf<double>,
+                                               int64_t, int64_t, const Lattice&, cudaStream_t);
+template cudaError_t launch_init_state<float>(const double*, const double*, const double*,
+                                              const double*, const double*, StateBuf<float>,
+                                              int64_t, int64_t, const Lattice&, cudaStream_t);
+template cudaError_t launch_read_state<double>(StateBuf<double>, int64_t, int64_t, double*,
+                                               double*, double*, double*, double*,
+                                               const Lattice&, cudaStream_t);
+template cudaError_t launch_read_state<float>(StateBuf<float>, int64_t, int64_t, double*,
+                                              double*, double*, double*, double*,
+                                              const Lattice&, cudaStream_t);
+
+// Bounds of the particle velocities over a grid: out4 = {min(u_x - c_max st),
+// max(u_x + c_max st), min(u_y - c_max st), max(u_y + c_max st)} (as floats,
+// combined by integer atomics on an order-preserving encoding).
+__device__ __forceinline__ unsigned int f2ord(float f) {
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void k_disp_bounds(const double* __restrict__ ux, const double* __restrict__ uy,
+                              const double* __restrict__ st, int64_t N, double cmax,
+                              unsigned int* out4) {
+    float lo_x = 3.0e38f, hi_x = -3.0e38f, lo_y = 3.0e38f, hi_y = -3.0e38f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double s = cmax * st[i];
+        lo_x = fminf(lo_x, (float)(ux[i] - s));
+        hi_x = fmaxf(hi_x, (float)(ux[i] + s));
+        lo_y = fminf(lo_y, (float)(uy[i] - s));
+        hi_y = fmaxf(hi_y, (float)(uy[i] + s));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo_x = fminf(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, o));
+        hi_x = fmaxf(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, o));
+        lo_y = fminf(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
+        hi_y = fmaxf(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(out4 + 0, f2ord(lo_x));
+        atomicMax(out4 + 1, f2ord(hi_x));
+        atomicMin(out4 + 2, f2ord(lo_y));
+        atomicMax(out4 + 3, f2ord(hi_y));
+    }
+}
+
+__global__ void k_ord_to_float(unsigned int* v) {
+    const int i = threadIdx.x;
+    if (i < 4) {
+        const unsigned int u = v[i];
+        const unsigned int b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+        v[i] = b;  // now the float bit pattern
+    }
+}
+
+__global__ void k_bounds_reset(unsigned int* v) {
+    const int i = threadIdx.x;
+    if (i < 4) v[i] = (i & 1) ? 0u : 0xffffffffu;
+}
+
+cudaError_t launch_disp_bounds(const double* ux, const double* uy, const double* st, int64_t N,
+                               double c_max, float* out4, cudaStream_t s) {
+    unsigned int* o = reinterpret_cast<unsigned int*>(out4);
+    k_bounds_reset<<<1, 32, 0, s>>>(o);
+    const int bs = 256;
+    int64_t nb = (N + bs - 1) / bs;
+    if (nb > 1024) nb = 1024;
+    if (nb < 1) nb = 1;
+    k_disp_bounds<<<(unsigned)nb, bs, 0, s>>>(ux, uy, st, N, c_max, o);
+    k_ord_to_float<<<1, 32, 0, s>>>(o);
+    return cudaGetLastError();
+}
+
+}  // namespace pond

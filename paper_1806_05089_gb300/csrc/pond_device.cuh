@@ -1,0 +1,41 @@
+// pond_device.cuh -- small device helpers shared by the PonD kernels.
+#pragma once
+
+#include "pond_internal.cuh"
+
+namespace pond {
+
+// Cubic Lagrange weights on the nodes 0, 1, 2, 3 at local coordinate t
+// (App. C: a_n(t) = prod_{k != n} (t - k)/(n - k)).
+__device__ __forceinline__ void lagrange4(double t, double l[4]) {
+    const double a = t, b = t - 1.0, c = t - 2.0, d = t - 3.0;
+    const double cd = c * d, ab = a * b;
+    l[0] = -(b * cd) * (1.0 / 6.0);
+    l[1] = (a * cd) * 0.5;
+    l[2] = -(ab * d) * 0.5;
+    l[3] = (ab * c) * (1.0 / 6.0);
+}
+
+__device__ __forceinline__ void lagrange4f(float t, float l[4]) {
+    const float a = t, b = t - 1.0f, c = t - 2.0f, d = t - 3.0f;
+    const float cd = c * d, ab = a * b;
+    l[0] = -(b * cd) * (1.0f / 6.0f);
+    l[1] = (a * cd) * 0.5f;
+    l[2] = -(ab * d) * 0.5f;
+    l[3] = (ab * c) * (1.0f / 6.0f);
+}
+
+// Periodic wrap of a possibly far out-of-range index.
+__device__ __forceinline__ int wrap_idx(long long v, int n) {
+    long long r = v % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+// Index + small offset (0..3) wrapped, for an already wrapped base.
+__device__ __forceinline__ int wrap_inc(int base, int off, int n) {
+    int v = base + off;
+    while (v >= n) v -= n;
+    return v;
+}
+
+}  // namespace pond

@@ -1,0 +1,175 @@
+// pond_internal.cuh -- shared definitions of the PonD CUDA library (sm_103a).
+//
+// Lattice: D2Q16, the tensor product of the four roots of He4
+// (c^2 = 3 -+ sqrt 6), weights (3 -+ sqrt 6)/12, T_L = 1 (App. A generalised
+// to a fourth-order Hermite set).  Populations q = 4k + l.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pond.h"
+
+namespace pond {
+
+// Lattice constants, computed on the host from their closed forms and passed
+// to kernels by value (they land in the constant bank).
+//
+// The 1D gauge transform is G[k][a] = L_k(xi_a) where L_k is the Lagrange
+// basis polynomial on the speeds c_j (M^-1 M of Eq. transform for a tensor
+// lattice) and xi_a = (sqrt(theta_s) c_a + u_s - u') / sqrt(theta').
+// Written around the identity, xi_a = c_a + delta_a, it is
+//   L_k(c_a + delta) = [k == a] + d1[k][a] delta + d2[k][a] delta^2 + d3[k] delta^3
+// with d1 = L_k'(c_a), d2 = L_k''(c_a)/2, d3 = L_k'''/6 (exact: L_k is cubic).
+struct Lattice {
+    double c[4];
+    double w[4];
+    double d1[4][4];
+    double d2[4][4];
+    double d3[4];
+    double T_L;
+};
+
+struct LatticeF {
+    float c[4];
+    float w[4];
+    float d1[4][4];
+    float d2[4][4];
+    float d3[4];
+};
+
+Lattice make_lattice();
+LatticeF to_float(const Lattice& L);
+
+struct StepParams {
+    double beta;
+    double dt;
+    double eps_abs;
+    double eps_rel;
+    double T_L;
+    int32_t max_iter;
+    int32_t fixed_iter;
+    int32_t thermal;
+    int32_t seed_mode;
+};
+
+// Device-side counters (one per context, zeroed per pond_step call).
+struct DevStats {
+    unsigned long long passes;
+    unsigned long long nonconverged;
+    unsigned long long nonphysical;
+    unsigned long long halo_fallback;
+    unsigned int max_passes;
+    unsigned int pad;
+};
+
+// Per-grid descriptor of a batched context (node offset into packed arrays).
+struct GridDesc {
+    int32_t nx;
+    int32_t ny;
+    int64_t offset;
+};
+
+// Device state of one context: packed over all grids, plane stride = N.
+template <typename Real>
+struct StateBuf {
+    Real* f;        // [16][N]
+    double* ux;     // [N]
+    double* uy;     // [N]
+    double* st;     // [N]  sqrt(theta) = sqrt(T / T_L)
+};
+
+// ---------------------------------------------------------------- kernels
+// Launchers (defined in the .cu files); all return the launch status.
+
+// Per-translation-unit constant-bank copies of the lattice (call once per
+// device before launching).
+cudaError_t upload_lattice_fp64(const Lattice& L);
+cudaError_t upload_lattice_mixed(const Lattice& L);
+cudaError_t upload_lattice_adjoint(const Lattice& L);
+
+// FP64 step of a single grid (one warp per node).
+cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>& out,
+                             int32_t* iters, DevStats* stats, int nx, int ny,
+                             const Lattice& L, const StepParams& P, cudaStream_t s);
+
+// Window (halo tile) size, in nodes, that the mixed tiled kernel stages:
+// chosen by the host from a bound on the displacement spread.
+struct TileWindow {
+    int tx, ty;       // tile of target nodes
+    int ww, wh;       // maximum staged window (tile + halo)
+};
+
+// Mixed-precision step over one or many grids (one CTA per tile; batched
+// contexts use a persistent work list).
+cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& out,
+                              int32_t* iters, DevStats* stats, const GridDesc* grids_dev,
+                              const int64_t* tile_prefix_dev, int n_grids,
+                              int64_t n_tiles, int64_t plane, unsigned int* work_counter,
+                              const TileWindow& win, int persistent_ctas,
+                              const Lattice& L, const StepParams& P, cudaStream_t s);
+
+// Tile shape of the mixed kernel, its shared-memory need for a window, and
+// the per-device attribute set-up (returns resident CTAs per SM).
+constexpr int MIXED_TX = 32, MIXED_TY = 8;
+size_t mixed_smem_bytes(const TileWindow& w);
+cudaError_t mixed_prepare(size_t smem_bytes, int* ctas_per_sm);
+
+// Equilibrium initialisation f = rho W (Eq. equilibrium) and T -> sqrt(theta).
+template <typename Real>
+cudaError_t launch_init_state(const double* rho, const double* ux, const double* uy,
+                              const double* T, const double* f_given, StateBuf<Real> st,
+                              int64_t N, int64_t plane, const Lattice& L, cudaStream_t s);
+
+// rho = sum f, T = st^2 T_L, and f (as FP64) read-out.
+template <typename Real>
+cudaError_t launch_read_state(StateBuf<Real> st, int64_t N, int64_t plane, double* rho,
+                              double* ux, double* uy, double* T, double* f,
+                              const Lattice& L, cudaStream_t s);
+
+// max over nodes of (|u_x| + c_max st, |u_y| + c_max st) and spread bounds.
+cudaError_t launch_disp_bounds(const double* ux, const double* uy, const double* st,
+                               int64_t N, double c_max, float* out4, cudaStream_t s);
+
+// Adjoint (pond_adjoint.cu).
+struct AdjointScratch;
+
+}  // namespace pond
+
+struct pond_ctx {
+    pond_config cfg;
+    pond::Lattice L;
+    pond::StepParams P;
+    int32_t n_grids = 0;
+    std::vector<pond::GridDesc> grids_host;
+    std::vector<float> spans;  // per grid: {min vx, max vx, min vy, max vy}
+    int64_t N = 0;  // total nodes
+    int cur = 0;    // index of the current state buffer
+    void* f[2] = {nullptr, nullptr};
+    double* ux[2] = {nullptr, nullptr};
+    double* uy[2] = {nullptr, nullptr};
+    double* st[2] = {nullptr, nullptr};
+    int32_t* iters = nullptr;
+    pond::DevStats* stats = nullptr;
+    pond::DevStats* stats_host = nullptr;  // pinned
+    pond::GridDesc* grids_dev = nullptr;
+    int64_t* tile_prefix_dev = nullptr;
+    unsigned int* work_counter = nullptr;
+    float* bounds_dev = nullptr;
+    int64_t n_tiles = 0;
+    pond::TileWindow win{};
+    int persistent_ctas = 0;
+    std::vector<char> grid_set;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    void* staging = nullptr;       // device staging for host-side I/O
+    size_t staging_bytes = 0;
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};  // two-step graphs per parity
+    pond::AdjointScratch* adj = nullptr;
+};
+
+void destroy_adjoint(pond_ctx* ctx);

@@ -1,0 +1,217 @@
+// pond_step_fp64.cu -- FP64 PonD time step of one periodic grid.
+//
+// One warp per target node.  Lane = (population q = lane & 15, stencil-row
+// half = lane >> 4): each lane reconstructs population q from two of the four
+// stencil rows, the halves are summed with one shuffle, and the moments of
+// the 16 populations are butterfly-reduced, so every lane holds rho, u, T and
+// takes the same convergence decision: a warp never diverges on the
+// predictor-corrector pass count.  The step is bound by the FP64 pipe; all
+// source reads go through the read-only L1 path.
+//
+// Per predictor-corrector pass (Eqs. advection, vi, interpolation, transform):
+//   departure  y_q = x - (sqrt(theta) c_q + u) dt, origin floor(y_q) - 1
+//   for each of the 16 stencil nodes s:
+//     delta_a = xi_a - c_a = c_a (st_s/st' - 1) + (u_s - u')/st'
+//     G[k][a] = [k==a] + delta (d1[k][a] + delta (d2[k][a] + delta d3[k]))
+//     (G f_s)_q = sum_a Gx[k][a] sum_b Gy[l][b] f_s[4a+b]
+//   f_q = sum_s a_s(y_q - x_s) (G f_s)_q
+// then the moments in central form (algebraically equal to Eqs.
+// conservation_rho/rhou/T):  rho = sum f,  u_{n+1} = u_n + st sum c f / rho,
+// 2 T_{n+1} = st^2 sum |c|^2 f / rho - |u_{n+1} - u_n|^2,
+// the convergence test of App. E on (u_x, u_y, sqrt(theta)), and finally the
+// BGK relaxation f + 2 beta (rho W - f) (Eq. postcollision).
+#include "pond_device.cuh"
+
+namespace pond {
+
+constexpr int K1_WARPS = 4;
+
+// Lattice constants of this translation unit (uploaded once per device).
+__constant__ Lattice c_L;
+
+cudaError_t upload_lattice_fp64(const Lattice& L) {
+    return cudaMemcpyToSymbol(c_L, &L, sizeof(Lattice));
+}
+
+__global__ void __launch_bounds__(K1_WARPS * 32, 3)
+k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ iters,
+             DevStats* __restrict__ stats, int nx, int ny, long long N, StepParams P) {
+    const Lattice& L = c_L;
+    __shared__ unsigned long long s_passes, s_nc, s_np;
+    __shared__ unsigned int s_max;
+    if (threadIdx.x == 0) {
+        s_passes = 0ull;
+        s_nc = 0ull;
+        s_np = 0ull;
+        s_max = 0u;
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const long long node = (long long)blockIdx.x * K1_WARPS + (threadIdx.x >> 5);
+    if (node < N) {  // warp-uniform
+        const int X = (int)(node % nx);
+        const int Y = (int)(node / nx);
+        const int q = lane & 15, k = q >> 2, l = q & 3, half = lane >> 4;
+        const double ck = L.c[k], cl = L.c[l];
+        double d1k[4], d2k[4], d1l[4], d2l[4], ik[4], il[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            d1k[a] = L.d1[k][a];
+            d2k[a] = L.d2[k][a];
+            d1l[a] = L.d1[l][a];
+            d2l[a] = L.d2[l][a];
+            ik[a] = (a == k) ? 1.0 : 0.0;
+            il[a] = (a == l) ? 1.0 : 0.0;
+        }
+        const double d3k = L.d3[k], d3l = L.d3[l];
+
+        // seed gauge (Eqs. seed_gauge, seed_gauge_T)
+        double ux = in.ux[node], uy = in.uy[node], st = in.st[node];
+        if (P.seed_mode == 1) {
+            ux = 0.0;
+            uy = 0.0;
+            st = 1.0;
+        } else if (P.seed_mode == 2) {
+            ux = -ux;
+            uy = -uy;
+        }
+
+        int pass = 0;
+        unsigned int flag = 0u;
+        double total = 0.0, rho = 0.0;
+        for (;;) {
+            ++pass;
+            const double inv = 1.0 / st;
+            const double vx = fma(st, ck, ux), vy = fma(st, cl, uy);
+            const double depx = (double)X - vx * P.dt;
+            const double depy = (double)Y - vy * P.dt;
+            const double flx = floor(depx), fly = floor(depy);
+            double lx[4], ly[4];
+            lagrange4(depx - flx + 1.0, lx);
+            lagrange4(depy - fly + 1.0, ly);
+            const int x0 = wrap_idx((long long)flx - 1, nx);
+            const int y0 = wrap_idx((long long)fly - 1, ny);
+            const double bx = -ux * inv, by = -uy * inv;
+
+            double acc = 0.0;
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                const int jy = 2 * half + jj;
+                const double wy = half ? ly[2 + jj] : ly[jj];
+                const int sy = wrap_inc(y0, jy, ny);
+                double rowacc = 0.0;
+#pragma unroll
+                for (int jx = 0; jx < 4; ++jx) {
+                    const int sx = wrap_inc(x0, jx, nx);
+                    const long long s = (long long)sy * nx + sx;
+                    const double sts = __ldg(in.st + s);
+                    const double uxs = __ldg(in.ux + s);
+                    const double uys = __ldg(in.uy + s);
+                    const double r = fma(sts, inv, -1.0);  // st_s/st' - 1
+                    const double dx = fma(uxs, inv, bx);   // (u_s,x - u'_x)/st'
+                    const double dy = fma(uys, inv, by);
+                    double gx[4], gy[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const double de = fma(L.c[a], r, dx);
+                        gx[a] = fma(fma(fma(d3k, de, d2k[a]), de, d1k[a]), de, ik[a]);
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const double de = fma(L.c[b], r, dy);
+                        gy[b] = fma(fma(fma(d3l, de, d2l[b]), de, d1l[b]), de, il[b]);
+                    }
+                    double g = 0.0;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        double h = 0.0;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            h = fma(gy[b], __ldg(in.f + (long long)(4 * a + b) * N + s), h);
+                        g = fma(gx[a], h, g);
+                    }
+                    rowacc = fma(lx[jx], g, rowacc);
+                }
+                acc = fma(wy, rowacc, acc);
+            }
+            total = acc + __shfl_xor_sync(0xffffffffu, acc, 16);
+
+            // moments of the pass (central form)
+            double m0 = total, m1 = ck * total, m2 = cl * total,
+                   m3 = (ck * ck + cl * cl) * total;
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                m0 += __shfl_xor_sync(0xffffffffu, m0, o);
+                m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+                m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+                m3 += __shfl_xor_sync(0xffffffffu, m3, o);
+            }
+            rho = m0;
+            const double ir = 1.0 / rho;
+            const double dux = st * m1 * ir, duy = st * m2 * ir;
+            const double ux1 = ux + dux, uy1 = uy + duy;
+            double st1 = st;
+            bool ok = (rho > 0.0) && isfinite(ux1) && isfinite(uy1);
+            if (P.thermal) {
+                const double T1 = 0.5 * (st * st * m3 * ir - (dux * dux + duy * duy));
+                ok = ok && (T1 > 0.0) && isfinite(T1);
+                st1 = sqrt(T1 / P.T_L);
+            }
+            if (!ok) {
+                flag |= 2u;
+                break;
+            }
+            const bool conv = fabs(ux1 - ux) < P.eps_abs + P.eps_rel * fabs(ux1) &&
+                              fabs(uy1 - uy) < P.eps_abs + P.eps_rel * fabs(uy1) &&
+                              fabs(st1 - st) < P.eps_abs + P.eps_rel * fabs(st1);
+            bool stop;
+            if (P.fixed_iter > 0) {
+                stop = pass >= P.fixed_iter;
+            } else {
+                stop = conv || pass >= P.max_iter;
+                if (!conv && pass >= P.max_iter) flag |= 1u;
+            }
+            if (stop) break;
+            ux = ux1;
+            uy = uy1;
+            st = st1;
+        }
+
+        // BGK relaxation toward rho W in the kept gauge (Eq. postcollision)
+        if (half == 0) {
+            const double feq = rho * L.w[k] * L.w[l];
+            out.f[(long long)q * N + node] = total + 2.0 * P.beta * (feq - total);
+        }
+        if (lane == 0) {
+            out.ux[node] = ux;
+            out.uy[node] = uy;
+            out.st[node] = st;
+            if (iters) iters[node] = pass;
+            atomicAdd(&s_passes, (unsigned long long)pass);
+            atomicMax(&s_max, (unsigned int)pass);
+            if (flag & 1u) atomicAdd(&s_nc, 1ull);
+            if (flag & 2u) atomicAdd(&s_np, 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && stats) {
+        atomicAdd(&stats->passes, s_passes);
+        atomicMax(&stats->max_passes, s_max);
+        if (s_nc) atomicAdd(&stats->nonconverged, s_nc);
+        if (s_np) atomicAdd(&stats->nonphysical, s_np);
+    }
+}
+
+cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>& out,
+                             int32_t* iters, DevStats* stats, int nx, int ny, const Lattice& L,
+                             const StepParams& P, cudaStream_t s) {
+    const long long N = (long long)nx * ny;
+    if (N == 0) return cudaSuccess;
+    const long long nb = (N + K1_WARPS - 1) / K1_WARPS;
+    (void)L;
+    k1_step_fp64<<<(unsigned)nb, K1_WARPS * 32, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+    return cudaGetLastError();
+}
+
+}  // namespace pond

@@ -1,0 +1,440 @@
+// pond_step_mixed.cu -- mixed-precision PonD time step (FP32 populations and
+// bulk arithmetic, FP64 gauges), for one grid or a batched ensemble.
+//
+// One CTA per tile of TX x TY target nodes, one thread per node.  The CTA
+// first bounds the particle velocities of its tile (u -+ c_max sqrt(theta)),
+// stages the whole window of source nodes that the departure stencils can
+// reach (tile + halo, periodic wrap applied while staging) in shared memory:
+// the 16 FP32 populations and the gauge as FP32 offsets from the tile's
+// reference gauge, formed in FP64.  Gauge differences u_s - u' are then
+// differences of those offsets, so they carry FP32 precision RELATIVE TO THE
+// TILE'S GAUGE SPREAD, which is what FP64 differences rounded to FP32 give
+// (the FP64 part of the "Vandermonde solve" inputs).  The moments are summed
+// in FP32 and turned into the FP64 gauge update; the convergence test of
+// App. E runs in FP64.
+//
+// Threads of a warp are 32 consecutive nodes of a tile row and process the
+// same population at the same time, so their stencil reads hit consecutive
+// shared-memory words (conflict-free up to the one-column jitter of floor()).
+// A stencil that leaves the staged window (displacement beyond the planned
+// halo) is read from global memory instead and counted.
+//
+// Batched ensembles (many grids of uneven sizes) run as a persistent kernel:
+// CTAs take (grid, tile) work items from an atomic counter; the item -> grid
+// map is a prefix sum over the grids' tile counts.
+#include "pond_device.cuh"
+
+namespace pond {
+
+__constant__ LatticeF c_Lf;
+
+cudaError_t upload_lattice_mixed(const Lattice& L) {
+    const LatticeF F = to_float(L);
+    return cudaMemcpyToSymbol(c_Lf, &F, sizeof(LatticeF));
+}
+
+struct MixedArgs {
+    StateBuf<float> in, out;
+    int32_t* iters;
+    DevStats* stats;
+    const GridDesc* grids;
+    const int64_t* tile_prefix;
+    int n_grids;
+    long long n_tiles;
+    long long plane;  // plane stride of the packed state
+    unsigned int* work_counter;
+    int ww, wh;       // allocated window
+    double c_max;
+    float margin;
+    StepParams P;
+};
+
+// One stencil contraction read straight from global memory (window miss).
+__device__ __noinline__ float stencil_global(const MixedArgs& A, const GridDesc& G, long long base,
+                                             int X, int Y, float fx, float fy,
+                                             const float* lxw, const float* lyw, int k, int l,
+                                             double ux, double uy, double st) {
+    const LatticeF& L = c_Lf;
+    const int x0 = wrap_idx((long long)X + (long long)fx - 1, G.nx);
+    const int y0 = wrap_idx((long long)Y + (long long)fy - 1, G.ny);
+    const double inv = 1.0 / st;
+    float acc = 0.0f;
+    for (int jy = 0; jy < 4; ++jy) {
+        const int sy = wrap_inc(y0, jy, G.ny);
+        float rowacc = 0.0f;
+        for (int jx = 0; jx < 4; ++jx) {
+            const int sx = wrap_inc(x0, jx, G.nx);
+            const long long s = base + (long long)sy * G.nx + sx;
+            const float r = (float)((A.in.st[s] - st) * inv);
+            const float dx = (float)((A.in.ux[s] - ux) * inv);
+            const float dy = (float)((A.in.uy[s] - uy) * inv);
+            float gx[4], gy[4];
+            for (int a = 0; a < 4; ++a) {
+                const float de = fmaf(L.c[a], r, dx);
+                gx[a] = fmaf(fmaf(fmaf(L.d3[k], de, L.d2[k][a]), de, L.d1[k][a]), de,
+                             a == k ? 1.0f : 0.0f);
+                const float de2 = fmaf(L.c[a], r, dy);
+                gy[a] = fmaf(fmaf(fmaf(L.d3[l], de2, L.d2[l][a]), de2, L.d1[l][a]), de2,
+                             a == l ? 1.0f : 0.0f);
+            }
+            float g = 0.0f;
+            for (int a = 0; a < 4; ++a) {
+                float h = 0.0f;
+                for (int b = 0; b < 4; ++b) h = fmaf(gy[b], A.in.f[(4 * a + b) * A.plane + s], h);
+                g = fmaf(gx[a], h, g);
+            }
+            rowacc = fmaf(lxw[jx], g, rowacc);
+        }
+        acc = fmaf(lyw[jy], rowacc, acc);
+    }
+    return acc;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_minmax4(float& a, float& b, float& c, float& d,
+                                              float (*red)[NT / 32]) {
+    // a, c: min; b, d: max
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+        c = fminf(c, __shfl_xor_sync(0xffffffffu, c, o));
+        d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+        red[2][w] = c;
+        red[3][w] = d;
+    }
+    __syncthreads();
+    a = red[0][0];
+    b = red[1][0];
+    c = red[2][0];
+    d = red[3][0];
+#pragma unroll
+    for (int i = 1; i < NT / 32; ++i) {
+        a = fminf(a, red[0][i]);
+        b = fmaxf(b, red[1][i]);
+        c = fminf(c, red[2][i]);
+        d = fmaxf(d, red[3][i]);
+    }
+    __syncthreads();
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k2_step_mixed(MixedArgs A) {
+    constexpr int NT = TX * TY;
+    extern __shared__ __align__(16) float smem[];
+    const int WN = A.ww * A.wh;
+    float* s_f = smem;            // [16][WN]
+    float* s_dux = s_f + 16 * WN; // [WN]
+    float* s_duy = s_dux + WN;
+    float* s_dst = s_duy + WN;
+    float* s_acc = s_dst + WN;    // [16][NT]
+    __shared__ float s_red[4][NT / 32];
+    __shared__ long long s_item;
+    __shared__ unsigned long long s_passes, s_nc, s_np, s_fb;
+    __shared__ unsigned int s_max;
+    const LatticeF& L = c_Lf;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_passes = 0ull;
+        s_nc = 0ull;
+        s_np = 0ull;
+        s_fb = 0ull;
+        s_max = 0u;
+    }
+    const int lxi = tid % TX, lyi = tid / TX;
+    const float dt = (float)A.P.dt;
+    const float two_beta = (float)(2.0 * A.P.beta);
+
+    long long item = blockIdx.x;
+    for (;;) {
+        if (A.work_counter) {
+            __syncthreads();
+            if (tid == 0) s_item = (long long)atomicAdd(A.work_counter, 1u);
+            __syncthreads();
+            item = s_item;
+        }
+        if (item >= A.n_tiles) break;
+
+        int g = 0;
+        if (A.n_grids > 1) {
+            int lo = 0, hi = A.n_grids - 1;  // largest g with prefix[g] <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (A.tile_prefix[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            g = lo;
+        }
+        const GridDesc G = A.grids[g];
+        const long long t = item - A.tile_prefix[g];
+        const int tiles_x = (G.nx + TX - 1) / TX;
+        const int tx0 = (int)(t % tiles_x) * TX;
+        const int ty0 = (int)(t / tiles_x) * TY;
+        const int X = tx0 + lxi, Y = ty0 + lyi;
+        const bool valid = X < G.nx && Y < G.ny;
+        const long long base = G.offset;
+        const long long node = base + (long long)Y * G.nx + X;
+
+        // reference gauge of the tile (its origin node always exists)
+        const long long rnode = base + (long long)ty0 * G.nx + tx0;
+        const double rux = A.in.ux[rnode], ruy = A.in.uy[rnode], rst = A.in.st[rnode];
+
+        double ux = 0.0, uy = 0.0, st = 1.0;
+        float vxlo = 3.0e38f, vxhi = -3.0e38f, vylo = 3.0e38f, vyhi = -3.0e38f;
+        if (valid) {
+            ux = A.in.ux[node];
+            uy = A.in.uy[node];
+            st = A.in.st[node];
+            if (A.P.seed_mode == 1) {
+                ux = 0.0;
+                uy = 0.0;
+                st = 1.0;
+            } else if (A.P.seed_mode == 2) {
+                ux = -ux;
+                uy = -uy;
+            }
+            const float sp = (float)(A.c_max * st);
+            vxlo = (float)ux - sp;
+            vxhi = (float)ux + sp;
+            vylo = (float)uy - sp;
+            vyhi = (float)uy + sp;
+        }
+        block_minmax4<NT>(vxlo, vxhi, vylo, vyhi, s_red);
+
+        // staged window in unwrapped grid coordinates (departure = x - v dt)
+        const float m = A.margin;
+        const float bxl = fminf(fmaxf(vxlo, -1.0e6f), 1.0e6f), bxh = fminf(fmaxf(vxhi, -1.0e6f), 1.0e6f);
+        const float byl = fminf(fmaxf(vylo, -1.0e6f), 1.0e6f), byh = fminf(fmaxf(vyhi, -1.0e6f), 1.0e6f);
+        const int wx0 = (int)floorf((float)tx0 - bxh * dt - m) - 1;
+        const int wx1 = (int)floorf((float)(tx0 + TX - 1) - bxl * dt + m) + 2;
+        const int wy0 = (int)floorf((float)ty0 - byh * dt - m) - 1;
+        const int wy1 = (int)floorf((float)(ty0 + TY - 1) - byl * dt + m) + 2;
+        // a tile whose bounds are not finite (NaN gauge) stages a 1 x 1 window
+        // and reads every stencil through the global-memory path
+        const bool fin = isfinite(vxlo) && isfinite(vxhi) && isfinite(vylo) && isfinite(vyhi) &&
+                         vxlo > -1.0e6f && vxhi < 1.0e6f && vylo > -1.0e6f && vyhi < 1.0e6f;
+        const int ww = fin ? max(1, min(wx1 - wx0 + 1, A.ww)) : 1;
+        const int wh = fin ? max(1, min(wy1 - wy0 + 1, A.wh)) : 1;
+
+        for (int i = tid; i < ww * wh; i += NT) {
+            const int cx = i % ww, cy = i / ww;
+            const int gx = wrap_idx((long long)wx0 + cx, G.nx);
+            const int gy = wrap_idx((long long)wy0 + cy, G.ny);
+            const long long gi = base + (long long)gy * G.nx + gx;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) s_f[q * WN + i] = __ldg(A.in.f + q * A.plane + gi);
+            s_dux[i] = (float)(__ldg(A.in.ux + gi) - rux);
+            s_duy[i] = (float)(__ldg(A.in.uy + gi) - ruy);
+            s_dst[i] = (float)(__ldg(A.in.st + gi) - rst);
+        }
+        __syncthreads();
+
+        int pass = 0;
+        unsigned int flag = 0u;
+        unsigned int fallbacks = 0u;
+        double rho = 0.0;
+        if (valid) {
+            for (;;) {
+                ++pass;
+                const float stf = (float)st;
+                const float invf = 1.0f / stf;
+                const float tdux = (float)(ux - rux);
+                const float tduy = (float)(uy - ruy);
+                const float tdst = (float)(st - rst);
+                const float uxf = (float)ux, uyf = (float)uy;
+                float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f;
+#pragma unroll 1
+                for (int q = 0; q < 16; ++q) {
+                    const int k = q >> 2, l = q & 3;
+                    const float ck = L.c[k], cl = L.c[l];
+                    const float dxp = -fmaf(stf, ck, uxf) * dt;
+                    const float dyp = -fmaf(stf, cl, uyf) * dt;
+                    const float fx = floorf(dxp), fy = floorf(dyp);
+                    float lxw[4], lyw[4];
+                    lagrange4f(dxp - fx + 1.0f, lxw);
+                    lagrange4f(dyp - fy + 1.0f, lyw);
+                    const bool near = fabsf(dxp) < 1.0e6f && fabsf(dyp) < 1.0e6f;
+                    const int col = near ? X - wx0 + (int)fx - 1 : -1;
+                    const int row = near ? Y - wy0 + (int)fy - 1 : -1;
+                    float acc;
+                    if (col >= 0 && col + 3 < ww && row >= 0 && row + 3 < wh) {
+                        float d1k[4], d2k[4], d1l[4], d2l[4], ik[4], il[4];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            d1k[a] = L.d1[k][a];
+                            d2k[a] = L.d2[k][a];
+                            d1l[a] = L.d1[l][a];
+                            d2l[a] = L.d2[l][a];
+                            ik[a] = (a == k) ? 1.0f : 0.0f;
+                            il[a] = (a == l) ? 1.0f : 0.0f;
+                        }
+                        const float d3k = L.d3[k], d3l = L.d3[l];
+                        acc = 0.0f;
+#pragma unroll
+                        for (int jy = 0; jy < 4; ++jy) {
+                            float rowacc = 0.0f;
+#pragma unroll
+                            for (int jx = 0; jx < 4; ++jx) {
+                                const int si = (row + jy) * ww + col + jx;
+                                const float r = (s_dst[si] - tdst) * invf;
+                                const float dx = (s_dux[si] - tdux) * invf;
+                                const float dy = (s_duy[si] - tduy) * invf;
+                                float gx[4], gy[4];
+#pragma unroll
+                                for (int a = 0; a < 4; ++a) {
+                                    const float de = fmaf(L.c[a], r, dx);
+                                    gx[a] = fmaf(fmaf(fmaf(d3k, de, d2k[a]), de, d1k[a]), de, ik[a]);
+                                }
+#pragma unroll
+                                for (int b = 0; b < 4; ++b) {
+                                    const float de = fmaf(L.c[b], r, dy);
+                                    gy[b] = fmaf(fmaf(fmaf(d3l, de, d2l[b]), de, d1l[b]), de, il[b]);
+                                }
+                                float gsum = 0.0f;
+#pragma unroll
+                                for (int a = 0; a < 4; ++a) {
+                                    float h = 0.0f;
+#pragma unroll
+                                    for (int b = 0; b < 4; ++b)
+                                        h = fmaf(gy[b], s_f[(4 * a + b) * WN + si], h);
+                                    gsum = fmaf(gx[a], h, gsum);
+                                }
+                                rowacc = fmaf(lxw[jx], gsum, rowacc);
+                            }
+                            acc = fmaf(lyw[jy], rowacc, acc);
+                        }
+                    } else {
+                        acc = stencil_global(A, G, base, X, Y, fx, fy, lxw, lyw, k, l, ux, uy, st);
+                        ++fallbacks;
+                    }
+                    s_acc[q * NT + tid] = acc;
+                    m0 += acc;
+                    m1 = fmaf(ck, acc, m1);
+                    m2 = fmaf(cl, acc, m2);
+                    m3 = fmaf(fmaf(ck, ck, cl * cl), acc, m3);
+                }
+                // FP64 gauge update (central form of Eqs. conservation_*)
+                rho = (double)m0;
+                const double ir = 1.0 / rho;
+                const double dux = st * (double)m1 * ir, duy = st * (double)m2 * ir;
+                const double ux1 = ux + dux, uy1 = uy + duy;
+                double st1 = st;
+                bool ok = (rho > 0.0) && isfinite(ux1) && isfinite(uy1);
+                if (A.P.thermal) {
+                    const double T1 = 0.5 * (st * st * (double)m3 * ir - (dux * dux + duy * duy));
+                    ok = ok && (T1 > 0.0) && isfinite(T1);
+                    st1 = sqrt(T1 / A.P.T_L);
+                }
+                if (!ok) {
+                    flag |= 2u;
+                    break;
+                }
+                const bool conv = fabs(ux1 - ux) < A.P.eps_abs + A.P.eps_rel * fabs(ux1) &&
+                                  fabs(uy1 - uy) < A.P.eps_abs + A.P.eps_rel * fabs(uy1) &&
+                                  fabs(st1 - st) < A.P.eps_abs + A.P.eps_rel * fabs(st1);
+                bool stop;
+                if (A.P.fixed_iter > 0) {
+                    stop = pass >= A.P.fixed_iter;
+                } else {
+                    stop = conv || pass >= A.P.max_iter;
+                    if (!conv && pass >= A.P.max_iter) flag |= 1u;
+                }
+                if (stop) break;
+                ux = ux1;
+                uy = uy1;
+                st = st1;
+            }
+            // BGK relaxation toward rho W in the kept gauge (Eq. postcollision)
+            const float rhof = (float)rho;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float a = s_acc[q * NT + tid];
+                const float feq = rhof * (L.w[q >> 2] * L.w[q & 3]);
+                A.out.f[q * A.plane + node] = fmaf(two_beta, feq - a, a);
+            }
+            A.out.ux[node] = ux;
+            A.out.uy[node] = uy;
+            A.out.st[node] = st;
+            if (A.iters) A.iters[node] = pass;
+            atomicAdd(&s_passes, (unsigned long long)pass);
+            atomicMax(&s_max, (unsigned int)pass);
+            if (flag & 1u) atomicAdd(&s_nc, 1ull);
+            if (flag & 2u) atomicAdd(&s_np, 1ull);
+            if (fallbacks) atomicAdd(&s_fb, (unsigned long long)fallbacks);
+        }
+        if (!A.work_counter) break;
+    }
+    __syncthreads();
+    if (tid == 0 && A.stats) {
+        atomicAdd(&A.stats->passes, s_passes);
+        atomicMax(&A.stats->max_passes, s_max);
+        if (s_nc) atomicAdd(&A.stats->nonconverged, s_nc);
+        if (s_np) atomicAdd(&A.stats->nonphysical, s_np);
+        if (s_fb) atomicAdd(&A.stats->halo_fallback, s_fb);
+    }
+}
+
+constexpr int MX_TX = MIXED_TX, MX_TY = MIXED_TY;
+
+size_t mixed_smem_bytes(const TileWindow& w) {
+    return sizeof(float) * ((size_t)19 * w.ww * w.wh + (size_t)16 * MX_TX * MX_TY);
+}
+
+cudaError_t mixed_prepare(size_t smem_bytes, int* ctas_per_sm) {
+    // the attribute is per function and device: only ever raise it, so that
+    // every live context's window stays launchable
+    static int s_set[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if ((int)smem_bytes > s_set[dev]) {
+        e = cudaFuncSetAttribute(k2_step_mixed<MX_TX, MX_TY>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        if (e != cudaSuccess) return e;
+        s_set[dev] = (int)smem_bytes;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k2_step_mixed<MX_TX, MX_TY>,
+                                                         MX_TX * MX_TY, smem_bytes);
+}
+
+cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& out,
+                              int32_t* iters, DevStats* stats, const GridDesc* grids_dev,
+                              const int64_t* tile_prefix_dev, int n_grids, int64_t n_tiles,
+                              int64_t plane, unsigned int* work_counter, const TileWindow& win,
+                              int persistent_ctas, const Lattice& L, const StepParams& P,
+                              cudaStream_t s) {
+    if (n_tiles == 0) return cudaSuccess;
+    MixedArgs A;
+    A.in = in;
+    A.out = out;
+    A.iters = iters;
+    A.stats = stats;
+    A.grids = grids_dev;
+    A.tile_prefix = tile_prefix_dev;
+    A.n_grids = n_grids;
+    A.n_tiles = n_tiles;
+    A.plane = plane;
+    A.work_counter = work_counter;
+    A.ww = win.ww;
+    A.wh = win.wh;
+    A.c_max = L.c[3];
+    A.margin = 1.0f;
+    A.P = P;
+    const size_t smem = mixed_smem_bytes(win);
+    unsigned int nb;
+    if (work_counter) {
+        cudaError_t e = cudaMemsetAsync(work_counter, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return e;
+        nb = (unsigned int)(persistent_ctas < n_tiles ? persistent_ctas : n_tiles);
+    } else {
+        nb = (unsigned int)n_tiles;
+    }
+    k2_step_mixed<MX_TX, MX_TY><<<nb, MX_TX * MX_TY, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace pond

@@ -1,0 +1,311 @@
+"""Python binding of the PonD C ABI (include/pond.h), argument marshalling only.
+
+Every entry point of libpond.so is exposed under its C name (``pond_create``,
+``pond_set_state``, ``pond_step``, ``pond_moments``, ``pond_get_state``,
+``pond_iterations``, ``pond_adjoint_step``, ``pond_destroy``, ...).  Arrays may
+be NumPy arrays (host) or torch tensors (CUDA tensors are passed as device
+pointers, CPU tensors as host pointers); every array is FP64.  All compute
+runs in the CUDA library: if it cannot be loaded this module raises, there is
+no CPU fallback.
+
+``Sim`` is a small convenience wrapper owning one context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+POND_OK = 0
+POND_ERR_ARG = 1
+POND_ERR_OOM = 2
+POND_ERR_CUDA = 3
+POND_ERR_NONPHYSICAL = 4
+POND_ERR_NOT_CONVERGED = 5
+POND_ERR_TIMEOUT = 6
+POND_ERR_STATE = 7
+POND_FP64 = 0
+POND_FP32_MIXED = 1
+
+_STATUS = {0: "POND_OK", 1: "POND_ERR_ARG", 2: "POND_ERR_OOM", 3: "POND_ERR_CUDA",
+           4: "POND_ERR_NONPHYSICAL", 5: "POND_ERR_NOT_CONVERGED", 6: "POND_ERR_TIMEOUT",
+           7: "POND_ERR_STATE"}
+
+
+class PondError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+class pond_config(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("thermal", ctypes.c_int32),
+        ("nu", ctypes.c_double),
+        ("T_ref", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("eps_abs", ctypes.c_double),
+        ("eps_rel", ctypes.c_double),
+        ("max_iter", ctypes.c_int32),
+        ("fixed_iter", ctypes.c_int32),
+        ("ckpt_every", ctypes.c_int32),
+        ("strict", ctypes.c_int32),
+        ("seed_mode", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+    ]
+
+
+class pond_stats(ctypes.Structure):
+    _fields_ = [
+        ("node_updates", ctypes.c_int64),
+        ("passes", ctypes.c_int64),
+        ("max_passes", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("nonconverged", ctypes.c_int64),
+        ("nonphysical", ctypes.c_int64),
+        ("halo_fallback", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+_LIB = None
+
+# every symbol include/pond.h declares
+EXPORTS = ["pond_config_default", "pond_create", "pond_set_stream", "pond_set_state",
+           "pond_step", "pond_moments", "pond_get_state", "pond_iterations",
+           "pond_adjoint_step", "pond_destroy", "pond_last_error", "pond_version"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpond.so (building it first if needed)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path) or _build._stale():
+        if not build_if_missing:
+            raise RuntimeError("libpond.so is missing; build it with paper_1806_05089_gb300.build")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    i32 = ctypes.c_int32
+    lib.pond_config_default.argtypes = [ctypes.POINTER(pond_config), i32]
+    lib.pond_config_default.restype = None
+    lib.pond_create.argtypes = [ctypes.POINTER(pond_config), i32, ctypes.POINTER(i32),
+                                ctypes.POINTER(i32), vp, ctypes.POINTER(vp)]
+    lib.pond_create.restype = i32
+    lib.pond_set_stream.argtypes = [vp, vp]
+    lib.pond_set_stream.restype = i32
+    lib.pond_set_state.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32]
+    lib.pond_set_state.restype = i32
+    lib.pond_step.argtypes = [vp, i32, ctypes.POINTER(pond_stats)]
+    lib.pond_step.restype = i32
+    lib.pond_moments.argtypes = [vp, i32, vp, vp, vp, vp, i32]
+    lib.pond_moments.restype = i32
+    lib.pond_get_state.argtypes = [vp, i32, vp, vp, vp, vp, i32]
+    lib.pond_get_state.restype = i32
+    lib.pond_iterations.argtypes = [vp, i32, vp, i32]
+    lib.pond_iterations.restype = i32
+    lib.pond_adjoint_step.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.pond_adjoint_step.restype = i32
+    lib.pond_destroy.argtypes = [vp]
+    lib.pond_destroy.restype = None
+    lib.pond_last_error.argtypes = [vp]
+    lib.pond_last_error.restype = ctypes.c_char_p
+    lib.pond_version.argtypes = []
+    lib.pond_version.restype = ctypes.c_char_p
+    _LIB = lib
+    return lib
+
+
+# ------------------------------------------------------------------ marshalling
+
+def _ptr(a, on_device: bool):
+    """(pointer, keepalive) of an FP64 array; torch tensors or NumPy arrays."""
+    if a is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype not in (torch.float64, torch.int32):
+                raise TypeError("PonD arrays are float64 (iteration maps int32)")
+            if not a.is_contiguous():
+                raise ValueError("array must be contiguous")
+            if a.is_cuda != on_device:
+                raise ValueError("all arrays of one call must be on the same side")
+            return ctypes.c_void_p(a.data_ptr()), a
+    except ImportError:
+        pass
+    if on_device:
+        raise ValueError("device call needs torch CUDA tensors")
+    arr = np.ascontiguousarray(a)
+    if arr.dtype not in (np.float64, np.int32):
+        arr = arr.astype(np.float64)
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def _is_device(*arrays) -> bool:
+    for a in arrays:
+        if a is None:
+            continue
+        try:
+            import torch
+            if isinstance(a, torch.Tensor):
+                return a.is_cuda
+        except ImportError:
+            pass
+        return False
+    return False
+
+
+def _check(ctx, status):
+    if status != POND_OK:
+        msg = load().pond_last_error(ctx).decode() if ctx else ""
+        raise PondError(status, msg)
+
+
+def pond_version() -> str:
+    return load().pond_version().decode()
+
+
+def pond_config_default(precision: int = POND_FP64) -> pond_config:
+    cfg = pond_config()
+    load().pond_config_default(ctypes.byref(cfg), precision)
+    return cfg
+
+
+def pond_create(cfg: pond_config, nx, ny, stream=None):
+    nx = [int(v) for v in np.atleast_1d(nx)]
+    ny = [int(v) for v in np.atleast_1d(ny)]
+    n = len(nx)
+    arr_x = (ctypes.c_int32 * n)(*nx)
+    arr_y = (ctypes.c_int32 * n)(*ny)
+    out = ctypes.c_void_p()
+    st = load().pond_create(ctypes.byref(cfg), n, arr_x, arr_y,
+                            ctypes.c_void_p(stream or 0), ctypes.byref(out))
+    if st != POND_OK:
+        raise PondError(st, "pond_create failed")
+    return out
+
+
+def pond_set_stream(ctx, stream):
+    _check(ctx, load().pond_set_stream(ctx, ctypes.c_void_p(stream or 0)))
+
+
+def pond_set_state(ctx, grid, rho, ux, uy, T, f=None):
+    dev = _is_device(ux, uy, T, rho, f)
+    ps = [_ptr(a, dev) for a in (rho, ux, uy, T, f)]
+    _check(ctx, load().pond_set_state(ctx, grid, *[p for p, _ in ps], int(dev)))
+
+
+def pond_step(ctx, nsteps: int, want_stats: bool = True):
+    stats = pond_stats()
+    _check(ctx, load().pond_step(ctx, int(nsteps), ctypes.byref(stats) if want_stats else None))
+    return stats.as_dict() if want_stats else None
+
+
+def pond_moments(ctx, grid, rho=None, ux=None, uy=None, T=None):
+    dev = _is_device(rho, ux, uy, T)
+    ps = [_ptr(a, dev) for a in (rho, ux, uy, T)]
+    _check(ctx, load().pond_moments(ctx, grid, *[p for p, _ in ps], int(dev)))
+
+
+def pond_get_state(ctx, grid, f=None, ux=None, uy=None, T=None):
+    dev = _is_device(f, ux, uy, T)
+    ps = [_ptr(a, dev) for a in (f, ux, uy, T)]
+    _check(ctx, load().pond_get_state(ctx, grid, *[p for p, _ in ps], int(dev)))
+
+
+def pond_iterations(ctx, grid, iters):
+    dev = _is_device(iters)
+    p, _k = _ptr(iters, dev)
+    _check(ctx, load().pond_iterations(ctx, grid, p, int(dev)))
+
+
+def pond_adjoint_step(ctx, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out):
+    """Device tensors only; returns d(loss)/d(nu) of this step."""
+    nu_bar = ctypes.c_double(0.0)
+    ps = [_ptr(a, True) for a in (f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out)]
+    _check(ctx, load().pond_adjoint_step(ctx, *[p for p, _ in ps], ctypes.byref(nu_bar)))
+    return nu_bar.value
+
+
+def pond_destroy(ctx):
+    if ctx:
+        load().pond_destroy(ctx)
+
+
+# ------------------------------------------------------------------ convenience
+
+@dataclass
+class HostState:
+    f: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    T: np.ndarray
+
+
+class Sim:
+    """One PonD context (one grid, or a batched ensemble of grids)."""
+
+    def __init__(self, nx, ny, precision: int = POND_FP64, stream=None, **overrides):
+        self.cfg = pond_config_default(precision)
+        for k, v in overrides.items():
+            if not hasattr(self.cfg, k):
+                raise AttributeError("unknown config field %s" % k)
+            setattr(self.cfg, k, v)
+        self.nx = [int(v) for v in np.atleast_1d(nx)]
+        self.ny = [int(v) for v in np.atleast_1d(ny)]
+        self.ctx = pond_create(self.cfg, self.nx, self.ny, stream)
+
+    def close(self):
+        if self.ctx:
+            pond_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_state(self, rho, ux, uy, T, f=None, grid: int = 0):
+        pond_set_state(self.ctx, grid, rho, ux, uy, T, f)
+
+    def step(self, nsteps: int = 1, stats: bool = True):
+        return pond_step(self.ctx, nsteps, stats)
+
+    def moments(self, grid: int = 0):
+        ny, nx = self.ny[grid], self.nx[grid]
+        out = [np.zeros((ny, nx)) for _ in range(4)]
+        pond_moments(self.ctx, grid, *out)
+        return tuple(out)  # rho, ux, uy, T
+
+    def state(self, grid: int = 0) -> HostState:
+        ny, nx = self.ny[grid], self.nx[grid]
+        f = np.zeros((16, ny, nx))
+        ux, uy, T = (np.zeros((ny, nx)) for _ in range(3))
+        pond_get_state(self.ctx, grid, f, ux, uy, T)
+        return HostState(f, ux, uy, T)
+
+    def iterations(self, grid: int = 0) -> np.ndarray:
+        it = np.zeros((self.ny[grid], self.nx[grid]), dtype=np.int32)
+        pond_iterations(self.ctx, grid, it)
+        return it

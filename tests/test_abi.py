@@ -1,0 +1,67 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every entry
+point include/pond.h declares, and its host-side validation works without a
+GPU (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1806_05089_gb300 import pond
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    hdr = open(os.path.join(ROOT, "include", "pond.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(pond_[a-z_]+)\s*\(", hdr)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = pond.load()
+    names = declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(pond.EXPORTS)
+
+
+def test_version_and_defaults():
+    assert "D2Q16" in pond.pond_version()
+    c64 = pond.pond_config_default(pond.POND_FP64)
+    assert (c64.eps_abs, c64.eps_rel) == (1e-12, 1e-10)  # App. E
+    assert c64.max_iter == 20 and c64.thermal == 1 and c64.dt == 1.0
+    c32 = pond.pond_config_default(pond.POND_FP32_MIXED)
+    assert c32.precision == pond.POND_FP32_MIXED and c32.eps_rel >= 1e-7
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu():
+    cfg = pond.pond_config_default(pond.POND_FP64)
+    lib = pond.load()
+    out = ctypes.c_void_p()
+    nx = (ctypes.c_int32 * 1)(8)
+    ny = (ctypes.c_int32 * 1)(0)
+    assert lib.pond_create(ctypes.byref(cfg), 1, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
+    ny[0] = 8
+    assert lib.pond_create(ctypes.byref(cfg), 0, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
+    bad = pond.pond_config_default(pond.POND_FP64)
+    bad.nu = -1.0
+    assert lib.pond_create(ctypes.byref(bad), 1, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
+    # FP64 contexts are single-grid; batched ensembles use the mixed form
+    nx2 = (ctypes.c_int32 * 2)(8, 8)
+    ny2 = (ctypes.c_int32 * 2)(8, 8)
+    assert lib.pond_create(ctypes.byref(cfg), 2, nx2, ny2, None, ctypes.byref(out)) == pond.POND_ERR_ARG
+    assert lib.pond_step(None, 1, None) == pond.POND_ERR_ARG
+    assert lib.pond_last_error(None) == b"no context"
+
+
+def test_no_cpu_fallback_without_gpu():
+    """Without a GPU the library reports a CUDA error instead of computing."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cfg = pond.pond_config_default(pond.POND_FP64)
+    with pytest.raises(pond.PondError) as e:
+        pond.pond_create(cfg, [8], [8])
+    assert e.value.status in (pond.POND_ERR_CUDA, pond.POND_ERR_OOM)

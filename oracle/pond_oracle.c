@@ -31,9 +31,12 @@
  *    matching them (Eq. match) gives the same f^{lambda'}; the target-side
  *    matrix becomes the constant c_k^m c_l^n and stays well conditioned at
  *    any Mach number.
- *  - the populations kept after the last predictor-corrector pass are
- *    f^{lambda_n} together with their own gauge lambda_n (both within the
- *    convergence tolerance of the limits of Eqs. density..precollision).
+ *  - after the last predictor-corrector pass n, whose populations
+ *    f^{lambda_n} have the moments lambda_{n+1}, the populations are
+ *    re-expressed in lambda_{n+1} (Eq. transform at the node itself) and
+ *    stored with that gauge: the stored gauge is then exactly the co-moving
+ *    frame of the stored populations (remark after Eq. precollision), and
+ *    both tend to the limits of Eqs. density..precollision.
  *  - convergence: |phi_{n+1}-phi_n| < eps_abs + eps_rel |phi_{n+1}| for
  *    phi in {u_x, u_y, sqrt(theta)}; at most max_iter passes; fixed_iter > 0
  *    runs exactly that many passes.
@@ -259,6 +262,7 @@ int oracle_step(int64_t nx, int64_t ny, const double *f_in, const double *ux_in,
                 uy = -uy;
             }
             double fq[16];
+            double ux1 = ux, uy1 = uy, T1 = T; /* gauge defined by the last pass */
             int flag = 0, pass = 0;
             for (;;) {
                 const double st = sqrt(T / L.T_L);
@@ -299,8 +303,9 @@ int oracle_step(int64_t nx, int64_t ny, const double *f_in, const double *ux_in,
                     jy += vy[q] * fq[q];
                     e += (vx[q] * vx[q] + vy[q] * vy[q]) * fq[q];
                 }
-                const double ux1 = jx / rho, uy1 = jy / rho;
-                double T1 = T;
+                ux1 = jx / rho;
+                uy1 = jy / rho;
+                T1 = T;
                 if (p->thermal) T1 = (e / rho - (ux1 * ux1 + uy1 * uy1)) / D;
                 if (!(rho > 0.0) || !(T1 > 0.0) || !isfinite(ux1) ||
                     !isfinite(uy1)) {
@@ -325,7 +330,20 @@ int oracle_step(int64_t nx, int64_t ny, const double *f_in, const double *ux_in,
                 uy = uy1;
                 T = T1;
             }
-            /* BGK relaxation toward rho W in the kept gauge
+            /* The pass's populations f^{lambda_n} have the moments lambda_{n+1};
+             * re-expressed in that gauge (Eq. transform at the node itself)
+             * the gauge is exactly their co-moving frame, as the limit of
+             * Eqs. density..precollision is.  Skipped if the moments were
+             * non-physical. */
+            if (!(flag & ORACLE_FLAG_NONPHYSICAL)) {
+                double fr[16];
+                transfer(&L, ux, uy, T, ux1, uy1, T1, fq, fr);
+                for (int q = 0; q < 16; ++q) fq[q] = fr[q];
+                ux = ux1;
+                uy = uy1;
+                T = T1;
+            }
+            /* BGK relaxation toward rho W in the co-moving gauge
              * (Eqs. equilibrium, postcollision) */
             double rho = 0.0;
             for (int q = 0; q < 16; ++q) rho += fq[q];

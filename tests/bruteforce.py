@@ -74,7 +74,8 @@ def step(f, ux, uy, T, nu=0.01, passes=3, thermal=True, dt=1.0, T_ref=1.0):
                     T1 = (((vx ** 2 + vy ** 2) * fq).sum() / rho - u1x ** 2 - u1y ** 2) / 2.0
                 last = (fq, g)
                 g = (u1x, u1y, T1)
-            fq, g = last
+            fq, g_last = last
+            fq = transfer(g_last, g, fq)  # into the gauge its moments define
             rho = fq.sum()
             W = np.outer(W1, W1).reshape(16)
             fo[:, Y, X] = fq + 2 * beta * (rho * W - fq)

@@ -43,16 +43,21 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str | None = None,
+          build_dir: str | None = None) -> str:
+    """Compile and link; ``extra_flags``/``out``/``build_dir`` build a variant
+    library elsewhere (tuning experiments) without touching the default one."""
+    lib = out or LIB
+    if not force and out is None and not _stale():
         return LIB
     nvcc = _nvcc()
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    bdir = build_dir or BUILD_DIR
+    os.makedirs(bdir, exist_ok=True)
     procs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -66,12 +71,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
             failed.append(src)
     if failed:
         raise RuntimeError("nvcc failed for: " + ", ".join(os.path.basename(f) for f in failed))
-    fd, tmp = tempfile.mkstemp(prefix="libpond.", suffix=".so", dir=HERE)
+    fd, tmp = tempfile.mkstemp(prefix="libpond.", suffix=".so", dir=os.path.dirname(lib))
     os.close(fd)
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lrt", "-lpthread", "-ldl"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

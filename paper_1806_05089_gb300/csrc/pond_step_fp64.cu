@@ -18,8 +18,10 @@
 // then the moments in central form (algebraically equal to Eqs.
 // conservation_rho/rhou/T):  rho = sum f,  u_{n+1} = u_n + st sum c f / rho,
 // 2 T_{n+1} = st^2 sum |c|^2 f / rho - |u_{n+1} - u_n|^2,
-// the convergence test of App. E on (u_x, u_y, sqrt(theta)), and finally the
-// BGK relaxation f + 2 beta (rho W - f) (Eq. postcollision).
+// the convergence test of App. E on (u_x, u_y, sqrt(theta)), then the last
+// pass's populations re-expressed in the gauge their moments define (so the
+// stored gauge is exactly their co-moving frame), and finally the BGK
+// relaxation f + 2 beta (rho W - f) (Eq. postcollision).
 #include "pond_device.cuh"
 
 namespace pond {
@@ -80,6 +82,7 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
         int pass = 0;
         unsigned int flag = 0u;
         double total = 0.0, rho = 0.0;
+        double nux = ux, nuy = uy, nst = st;  // gauge the last pass's moments define
         for (;;) {
             ++pass;
             const double inv = 1.0 / st;
@@ -162,6 +165,9 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
                 flag |= 2u;
                 break;
             }
+            nux = ux1;
+            nuy = uy1;
+            nst = st1;
             const bool conv = fabs(ux1 - ux) < P.eps_abs + P.eps_rel * fabs(ux1) &&
                               fabs(uy1 - uy) < P.eps_abs + P.eps_rel * fabs(uy1) &&
                               fabs(st1 - st) < P.eps_abs + P.eps_rel * fabs(st1);
@@ -178,7 +184,37 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
             st = st1;
         }
 
-        // BGK relaxation toward rho W in the kept gauge (Eq. postcollision)
+        // Re-express f^{lambda_n} in the gauge lambda_{n+1} its moments define
+        // (Eq. transform at the node itself): that gauge is then exactly the
+        // co-moving frame of the stored populations.
+        if (!(flag & 2u)) {
+            const double inv1 = 1.0 / nst;
+            const double r = fma(st, inv1, -1.0);
+            const double dx = (ux - nux) * inv1, dy = (uy - nuy) * inv1;
+            double gx[4], gy[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const double de = fma(L.c[a], r, dx);
+                gx[a] = fma(fma(fma(d3k, de, d2k[a]), de, d1k[a]), de, ik[a]);
+                const double de2 = fma(L.c[a], r, dy);
+                gy[a] = fma(fma(fma(d3l, de2, d2l[a]), de2, d1l[a]), de2, il[a]);
+            }
+            double g = 0.0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                double h = 0.0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    h = fma(gy[b], __shfl_sync(0xffffffffu, total, 4 * a + b), h);
+                g = fma(gx[a], h, g);
+            }
+            total = g;
+            ux = nux;
+            uy = nuy;
+            st = nst;
+        }
+
+        // BGK relaxation toward rho W in the co-moving gauge (Eq. postcollision)
         if (half == 0) {
             const double feq = rho * L.w[k] * L.w[l];
             out.f[(long long)q * N + node] = total + 2.0 * P.beta * (feq - total);

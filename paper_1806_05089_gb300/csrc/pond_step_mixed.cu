@@ -90,6 +90,80 @@ __device__ __noinline__ float stencil_global(const MixedArgs& A, const GridDesc&
     return acc;
 }
 
+// Final part of a node update: re-express the last pass's populations (in
+// this thread's s_acc column) in the gauge lambda_{n+1} their moments define
+// (Eq. transform at the node itself; gauge differences in FP64), then BGK
+// relaxation toward rho W in that co-moving gauge (Eq. postcollision) and the
+// store.  Kept out of line so the pass loop keeps its register budget.
+__device__ __noinline__ void finish_node(const MixedArgs& A, float* s_acc, int NT, int tid,
+                                         long long node, bool regauge, double ux, double uy,
+                                         double st, double nux, double nuy, double nst,
+                                         double rho) {
+    const LatticeF& L = c_Lf;
+    if (regauge) {
+        const double inv1 = 1.0 / nst;
+        const float r = (float)fma(st, inv1, -1.0);
+        const float dx = (float)((ux - nux) * inv1);
+        const float dy = (float)((uy - nuy) * inv1);
+        float ex[4], ey[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            ex[a] = fmaf(L.c[a], r, dx);
+            ey[a] = fmaf(L.c[a], r, dy);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {  // h[a][l] = sum_b Gy[l][b] f[a][b]
+            float f4[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) f4[b] = s_acc[(4 * a + b) * NT + tid];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                float v = 0.0f;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const float e = ey[b];
+                    const float gyl = fmaf(fmaf(fmaf(L.d3[l], e, L.d2[l][b]), e, L.d1[l][b]), e,
+                                           l == b ? 1.0f : 0.0f);
+                    v = fmaf(gyl, f4[b], v);
+                }
+                s_acc[(4 * a + l) * NT + tid] = v;
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {  // f[k][l] = sum_a Gx[k][a] h[a][l]
+            float h4[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) h4[a] = s_acc[(4 * a + l) * NT + tid];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float v = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float e = ex[a];
+                    const float gxk = fmaf(fmaf(fmaf(L.d3[k], e, L.d2[k][a]), e, L.d1[k][a]), e,
+                                           k == a ? 1.0f : 0.0f);
+                    v = fmaf(gxk, h4[a], v);
+                }
+                s_acc[(4 * k + l) * NT + tid] = v;
+            }
+        }
+        ux = nux;
+        uy = nuy;
+        st = nst;
+    }
+    const float two_beta = (float)(2.0 * A.P.beta);
+    const float rhof = (float)rho;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const float a = s_acc[q * NT + tid];
+        const float feq = rhof * (L.w[q >> 2] * L.w[q & 3]);
+        A.out.f[q * A.plane + node] = fmaf(two_beta, feq - a, a);
+    }
+    A.out.ux[node] = ux;
+    A.out.uy[node] = uy;
+    A.out.st[node] = st;
+}
+
 template <int NT>
 __device__ __forceinline__ void block_minmax4(float& a, float& b, float& c, float& d,
                                               float (*red)[NT / 32]) {
@@ -122,8 +196,14 @@ __device__ __forceinline__ void block_minmax4(float& a, float& b, float& c, floa
     __syncthreads();
 }
 
+// Resident CTAs per SM the register allocation targets (1: 256 threads may
+// use up to 255 registers each; 2: at most 128).
+#ifndef POND_MIXED_MIN_BLOCKS
+#define POND_MIXED_MIN_BLOCKS 2
+#endif
+
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k2_step_mixed(MixedArgs A) {
+__global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(MixedArgs A) {
     constexpr int NT = TX * TY;
     extern __shared__ __align__(16) float smem[];
     const int WN = A.ww * A.wh;
@@ -147,7 +227,6 @@ __global__ void __launch_bounds__(TX* TY) k2_step_mixed(MixedArgs A) {
     }
     const int lxi = tid % TX, lyi = tid / TX;
     const float dt = (float)A.P.dt;
-    const float two_beta = (float)(2.0 * A.P.beta);
 
     long long item = blockIdx.x;
     for (;;) {
@@ -237,6 +316,7 @@ __global__ void __launch_bounds__(TX* TY) k2_step_mixed(MixedArgs A) {
         unsigned int fallbacks = 0u;
         double rho = 0.0;
         if (valid) {
+            double nux = ux, nuy = uy, nst = st;  // gauge the last pass's moments define
             for (;;) {
                 ++pass;
                 const float stf = (float)st;
@@ -332,6 +412,9 @@ __global__ void __launch_bounds__(TX* TY) k2_step_mixed(MixedArgs A) {
                     flag |= 2u;
                     break;
                 }
+                nux = ux1;
+                nuy = uy1;
+                nst = st1;
                 const bool conv = fabs(ux1 - ux) < A.P.eps_abs + A.P.eps_rel * fabs(ux1) &&
                                   fabs(uy1 - uy) < A.P.eps_abs + A.P.eps_rel * fabs(uy1) &&
                                   fabs(st1 - st) < A.P.eps_abs + A.P.eps_rel * fabs(st1);
@@ -347,17 +430,7 @@ __global__ void __launch_bounds__(TX* TY) k2_step_mixed(MixedArgs A) {
                 uy = uy1;
                 st = st1;
             }
-            // BGK relaxation toward rho W in the kept gauge (Eq. postcollision)
-            const float rhof = (float)rho;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const float a = s_acc[q * NT + tid];
-                const float feq = rhof * (L.w[q >> 2] * L.w[q & 3]);
-                A.out.f[q * A.plane + node] = fmaf(two_beta, feq - a, a);
-            }
-            A.out.ux[node] = ux;
-            A.out.uy[node] = uy;
-            A.out.st[node] = st;
+            finish_node(A, s_acc, NT, tid, node, !(flag & 2u), ux, uy, st, nux, nuy, nst, rho);
             if (A.iters) A.iters[node] = pass;
             atomicAdd(&s_passes, (unsigned long long)pass);
             atomicMax(&s_max, (unsigned int)pass);

@@ -87,16 +87,18 @@ def lib_path() -> str:
     return _build.LIB
 
 
-def load(build_if_missing: bool = True):
-    """Load libpond.so (building it first if needed)."""
+def load(build_if_missing: bool = True, path: str | None = None):
+    """Load libpond.so (building it first if needed); ``path`` loads another
+    build of the same library instead (tuning experiments)."""
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = _build.LIB
-    if not os.path.exists(path) or _build._stale():
-        if not build_if_missing:
-            raise RuntimeError("libpond.so is missing; build it with paper_1806_05089_gb300.build")
-        _build.build()
+    if path is None:
+        path = _build.LIB
+        if not os.path.exists(path) or _build._stale():
+            if not build_if_missing:
+                raise RuntimeError("libpond.so is missing; build it with paper_1806_05089_gb300.build")
+            _build.build()
     lib = ctypes.CDLL(path)
     vp = ctypes.c_void_p
     i32 = ctypes.c_int32

@@ -367,6 +367,27 @@ def run_pond(args, world, rank, local):
         forms["batched_256"] = form_line("ensemble-256-mixed", bnodes, k2, bsecs, bstats,
                                          PEAK_FP32_TFLOPS, BYTES_MIXED)
         bsim.close()
+        # adjoint / forward time on the 512^2 Taylor-Green + pulse workload
+        from paper_1806_05089_gb300.autograd import pond_rollout
+        af, target = workloads.adjoint(512)
+        dev = torch.device("cuda", local)
+        r = torch.tensor(af.rho, device=dev, requires_grad=True)
+        n = torch.tensor(0.01, dtype=torch.float64, device=dev, requires_grad=True)
+        gauge = [torch.tensor(a, device=dev) for a in (af.ux, af.uy, af.T)]
+        tgt = torch.tensor(target, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rho = pond_rollout(r, n, *gauge, 200, 20)
+        loss = 0.5 * ((rho - tgt) ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        forms["adjoint_512"] = {"workload": "adjoint-512-fp64", "steps": 200, "ckpt_every": 20,
+                                "forward_s": t1 - t0, "backward_s": t2 - t1,
+                                "adjoint_over_forward": (t2 - t1) / (t1 - t0),
+                                "nu_grad": float(n.grad), "loss": float(loss.detach())}
         line["forms"] = forms
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1)

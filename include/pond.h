@@ -161,6 +161,13 @@ pond_status pond_iterations(pond_ctx* ctx, int32_t grid, void* iters, int32_t on
 pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in, const void* gauge_bar_in,
                               void* f_bar_out, void* gauge_bar_out, double* nu_bar_accum);
 
+/* VJP of the equilibrium initialisation of pond_set_state (f = rho W,
+ * Eq. equilibrium): rho_bar[x] = sum_q W_q f_bar[q][x].  Single-grid
+ * contexts; device pointers, f_bar [16][ny][nx], rho_bar [ny][nx].  (The
+ * gauge cotangents pass through unchanged: set_state stores u and T as given.)
+ * Errors: POND_ERR_ARG, POND_ERR_CUDA. */
+pond_status pond_adjoint_init(pond_ctx* ctx, const void* f_bar, void* rho_bar);
+
 void pond_destroy(pond_ctx* ctx);
 
 /* Message of the last failing call on ctx ("" if none; static text if ctx is

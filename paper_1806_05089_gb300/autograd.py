@@ -1,0 +1,101 @@
+"""PonD rollout as a torch.autograd.Function with step checkpointing.
+
+``pond_rollout(rho0, nu, ux0, uy0, T0, steps, ckpt_every)`` runs ``steps``
+FP64 PonD steps from the equilibrium f = rho0 W in the gauge (u0, T0) and
+returns the final density.  Backward recomputes each checkpoint segment
+forward (keeping that segment's states on the device), then walks the steps
+in reverse through ``pond_adjoint_step`` (the hand-written adjoint kernels:
+implicit differentiation of the predictor-corrector fixed point, transposed
+reconstruction and gauge transform, BGK collision) and finally
+``pond_adjoint_init``.  Gradients are returned for rho0 and nu.
+
+All tensors are CUDA float64; every step of the forward and backward runs in
+libpond.so.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import pond
+
+
+def _get_state(sim, ny, nx, dev):
+    f = torch.empty((16, ny, nx), dtype=torch.float64, device=dev)
+    ux = torch.empty((ny, nx), dtype=torch.float64, device=dev)
+    uy = torch.empty_like(ux)
+    T = torch.empty_like(ux)
+    pond.pond_get_state(sim.ctx, 0, f, ux, uy, T)
+    return f, ux, uy, T
+
+
+def _set_state(sim, state):
+    f, ux, uy, T = state
+    pond.pond_set_state(sim.ctx, 0, None, ux, uy, T, f)
+
+
+class PondRollout(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rho0, nu, ux0, uy0, T0, steps: int, ckpt_every: int, overrides=None):
+        if not rho0.is_cuda or rho0.dtype != torch.float64:
+            raise TypeError("rho0 must be a CUDA float64 tensor")
+        ny, nx = rho0.shape
+        dev = rho0.device
+        stream = torch.cuda.current_stream(dev).cuda_stream
+        cfg = dict(overrides or {})
+        sim = pond.Sim(nx, ny, pond.POND_FP64, stream=stream, nu=float(nu), **cfg)
+        pond.pond_set_state(sim.ctx, 0, rho0.contiguous(), ux0.contiguous(), uy0.contiguous(),
+                            T0.contiguous(), None)
+        ckpts = []
+        for t in range(steps):
+            if t % ckpt_every == 0:
+                ckpts.append(_get_state(sim, ny, nx, dev))
+            pond.pond_step(sim.ctx, 1, want_stats=False)
+        rho = torch.empty((ny, nx), dtype=torch.float64, device=dev)
+        pond.pond_moments(sim.ctx, 0, rho)
+        ctx.sim = sim
+        ctx.ckpts = ckpts
+        ctx.steps = steps
+        ctx.ckpt_every = ckpt_every
+        ctx.shape = (ny, nx)
+        return rho
+
+    @staticmethod
+    def backward(ctx, grad_rho):
+        sim = ctx.sim
+        ny, nx = ctx.shape
+        dev = grad_rho.device
+        # rho = sum_q f_q  =>  fbar_q = rho_bar for every q
+        fbar = grad_rho.contiguous().expand(16, ny, nx).contiguous()
+        gbar = torch.zeros((3, ny, nx), dtype=torch.float64, device=dev)
+        fbar_new = torch.empty_like(fbar)
+        gbar_new = torch.empty_like(gbar)
+        nu_bar = 0.0
+        steps, every = ctx.steps, ctx.ckpt_every
+        for seg in reversed(range(len(ctx.ckpts))):
+            start = seg * every
+            end = min(start + every, steps)
+            states = [ctx.ckpts[seg]]
+            _set_state(sim, ctx.ckpts[seg])
+            for _ in range(start, end - 1):
+                pond.pond_step(sim.ctx, 1, want_stats=False)
+                states.append(_get_state(sim, ny, nx, dev))
+            for t in reversed(range(start, end)):
+                _set_state(sim, states[t - start])
+                nu_bar += pond.pond_adjoint_step(sim.ctx, fbar, gbar, fbar_new, gbar_new)
+                fbar, fbar_new = fbar_new, fbar
+                gbar, gbar_new = gbar_new, gbar
+            del states
+        rho_bar = torch.empty((ny, nx), dtype=torch.float64, device=dev)
+        pond.pond_adjoint_init(sim.ctx, fbar, rho_bar)
+        torch.cuda.current_stream(dev).synchronize()
+        sim.close()
+        nu_grad = torch.tensor(nu_bar, dtype=torch.float64, device=dev)
+        return rho_bar, nu_grad, None, None, None, None, None, None
+
+
+def pond_rollout(rho0, nu, ux0, uy0, T0, steps: int, ckpt_every: int = 20, **overrides):
+    """Final density after ``steps`` FP64 PonD steps (differentiable in rho0
+    and nu).  ``nu`` may be a float or a 0-d tensor."""
+    if not torch.is_tensor(nu):
+        nu = torch.tensor(float(nu), dtype=torch.float64, device=rho0.device)
+    return PondRollout.apply(rho0, nu, ux0, uy0, T0, steps, ckpt_every, overrides or None)

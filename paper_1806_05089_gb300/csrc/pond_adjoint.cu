@@ -1,5 +1,34 @@
-// pond_adjoint.cu -- vector-Jacobian product of one PonD step (placeholder
-// until the adjoint kernels land).
+// pond_adjoint.cu -- vector-Jacobian product of one PonD step (FP64).
+//
+// The step maps the input state S = {f_s, lambda_s} to, at every node x,
+//   lambda*(x) = the fixed point of Phi(lambda) = M(A(lambda), lambda)
+//                (Eqs. conservation_*, density..T),
+//   A*(x)      = A(lambda*), A_q(lambda) = sum_j a_j(lambda) (G_{lambda_j}^{lambda} f_j)_q
+//                (Eqs. advection, interpolation, transform),
+//   f_out      = A* + 2 beta (rho W - A*)   (Eq. postcollision),  gauge_out = lambda*.
+// The fixed point is differentiated implicitly.  In the parametrisation
+// lambda = (u_x, u_y, s = sqrt(theta)) the moment map M has, at the fixed point,
+// dM/dlambda = I (its explicit gauge dependence cancels there), so
+// I - dPhi/dlambda = -M_A A_lambda, a 3 x 3 matrix per node, with
+//   M_A[u_x][q] = s c_k / rho,  M_A[u_y][q] = s c_l / rho,
+//   M_A[s][q]   = s (|c_q|^2 - 2 T_L) / (4 rho T_L).
+// Given cotangents (fbar, lambdabar) of the output:
+//   Abar   = (1 - 2 beta) fbar + 2 beta (W . fbar) 1,   betabar = sum 2 (rho W - A) fbar
+//   g      = A_lambda^T Abar + lambdabar
+//   mu     = (I - dPhi/dlambda)^{-T} g = -(M_A A_lambda)^{-T} g
+//   w      = Abar + M_A^T mu
+//   Sbar   = A_S^T w   (transpose of the reconstruction: onto the source
+//                       populations f_j and source gauges lambda_j)
+// The seed gauge gets no gradient: the limit does not depend on it.
+//
+// Phase A (one warp per target node, like the forward step) forms A*, the
+// JVP A_lambda in three directions, the 3 x 3 solve and w.  Phase B (one warp
+// per source node) gathers the transpose: for every population it scans the
+// targets whose departure stencil can contain the source (a window bounded by
+// the particle-velocity range), so the result is deterministic and needs no
+// atomics.
+#include <cmath>
+
 #include "pond_device.cuh"
 
 namespace pond {
@@ -10,13 +39,476 @@ cudaError_t upload_lattice_adjoint(const Lattice& L) {
     return cudaMemcpyToSymbol(c_La, &L, sizeof(Lattice));
 }
 
+struct AdjointScratch {
+    int64_t N = 0;
+    StateBuf<double> fwd{};   // forward step output: gauge = lambda*
+    double* w = nullptr;      // [16][N]
+    int32_t* iters = nullptr;
+    DevStats* stats = nullptr;
+    double* beta_bar = nullptr;  // device accumulator
+    double* minmax = nullptr;    // 6 doubles: min/max of ux*, uy*, s*
+    double host_minmax[6];
+};
+
+// Cubic Lagrange weights on 0..3 and their derivatives at t (App. C).
+__device__ __forceinline__ void lagrange4_d(double t, double l[4], double dl[4]) {
+    const double a = t, b = t - 1.0, c = t - 2.0, d = t - 3.0;
+    l[0] = -(b * c * d) / 6.0;
+    l[1] = (a * c * d) / 2.0;
+    l[2] = -(a * b * d) / 2.0;
+    l[3] = (a * b * c) / 6.0;
+    dl[0] = -(c * d + b * d + b * c) / 6.0;
+    dl[1] = (c * d + a * d + a * c) / 2.0;
+    dl[2] = -(b * d + a * d + a * b) / 2.0;
+    dl[3] = (b * c + a * c + a * b) / 6.0;
+}
+
+// L_k(c_a + de) and its derivative in xi, from the Taylor coefficients.
+__device__ __forceinline__ void lag_taylor(const Lattice& L, int k, int a, double de, double& g,
+                                          double& gd) {
+    const double d1 = L.d1[k][a], d2 = L.d2[k][a], d3 = L.d3[k];
+    g = fma(fma(fma(d3, de, d2), de, d1), de, (k == a) ? 1.0 : 0.0);
+    gd = fma(fma(3.0 * d3, de, 2.0 * d2), de, d1);
+}
+
+struct AdjArgs {
+    StateBuf<double> in;     // input state S
+    const double* ux_s;      // lambda* (forward output gauge)
+    const double* uy_s;
+    const double* st_s;
+    const double* fbar;      // [16][N]
+    const double* gbar;      // [3][N]  (u_x, u_y, T)
+    double* w;               // [16][N]
+    double* fbar_in;         // [16][N]
+    double* gbar_in;         // [3][N]
+    double* beta_bar;
+    int nx, ny;
+    long long N;
+    double beta, dt, T_L;
+    double vlo_x[4], vhi_x[4], vlo_y[4], vhi_y[4];  // particle-velocity bounds per speed
+};
+
+constexpr int ADJ_WARPS = 4;
+
+__global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_targets(AdjArgs A) {
+    const Lattice& L = c_La;
+    const int lane = threadIdx.x & 31;
+    const long long node = (long long)blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
+    if (node >= A.N) return;  // warp-uniform
+    const int X = (int)(node % A.nx), Y = (int)(node / A.nx);
+    const int q = lane & 15, k = q >> 2, l = q & 3, half = lane >> 4;
+    const double ck = L.c[k], cl = L.c[l];
+    const double ux = A.ux_s[node], uy = A.uy_s[node], st = A.st_s[node];
+    const double inv = 1.0 / st;
+
+    // departure of population q at lambda*
+    const double vx = fma(st, ck, ux), vy = fma(st, cl, uy);
+    const double depx = (double)X - vx * A.dt, depy = (double)Y - vy * A.dt;
+    const double flx = floor(depx), fly = floor(depy);
+    double lx[4], dlx[4], ly[4], dly[4];
+    lagrange4_d(depx - flx + 1.0, lx, dlx);
+    lagrange4_d(depy - fly + 1.0, ly, dly);
+    const int x0 = wrap_idx((long long)flx - 1, A.nx);
+    const int y0 = wrap_idx((long long)fly - 1, A.ny);
+
+    double Aq = 0.0, dAux = 0.0, dAuy = 0.0, dAst = 0.0;
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+        const int jy = 2 * half + jj;
+        const double wy = half ? ly[2 + jj] : ly[jj];
+        const double dwy = half ? dly[2 + jj] : dly[jj];
+        const int sy = wrap_inc(y0, jy, A.ny);
+#pragma unroll
+        for (int jx = 0; jx < 4; ++jx) {
+            const int sx = wrap_inc(x0, jx, A.nx);
+            const long long s = (long long)sy * A.nx + sx;
+            const double r = fma(A.in.st[s], inv, -1.0);
+            const double dx = (A.in.ux[s] - ux) * inv;
+            const double dy = (A.in.uy[s] - uy) * inv;
+            double gx[4], gdx[4], gy[4], gdy[4], xix[4], xiy[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const double ex = fma(L.c[a], r, dx), ey = fma(L.c[a], r, dy);
+                xix[a] = L.c[a] + ex;
+                xiy[a] = L.c[a] + ey;
+                lag_taylor(L, k, a, ex, gx[a], gdx[a]);
+                lag_taylor(L, l, a, ey, gy[a], gdy[a]);
+            }
+            double g = 0.0, gux = 0.0, guy = 0.0, gst = 0.0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                double h = 0.0, hp = 0.0, hq = 0.0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const double fv = A.in.f[(long long)(4 * a + b) * A.N + s];
+                    h = fma(gy[b], fv, h);
+                    hp = fma(gdy[b], fv, hp);
+                    hq = fma(gdy[b] * xiy[b], fv, hq);
+                }
+                g = fma(gx[a], h, g);
+                gux = fma(gdx[a], h, gux);
+                guy = fma(gx[a], hp, guy);
+                gst = fma(gdx[a] * xix[a], h, fma(gx[a], hq, gst));
+            }
+            // d xi / d(target u) = -1/s ; d xi / d(target s) = -xi / s
+            gux *= -inv;
+            guy *= -inv;
+            gst *= -inv;
+            const double wx = lx[jx], dwx = dlx[jx];
+            const double a_w = wx * wy;
+            // d t / d u = -dt ; d t / d s = -c dt
+            const double da_ux = -A.dt * dwx * wy;
+            const double da_uy = -A.dt * wx * dwy;
+            const double da_st = -A.dt * (ck * dwx * wy + cl * wx * dwy);
+            Aq = fma(a_w, g, Aq);
+            dAux = fma(a_w, gux, fma(da_ux, g, dAux));
+            dAuy = fma(a_w, guy, fma(da_uy, g, dAuy));
+            dAst = fma(a_w, gst, fma(da_st, g, dAst));
+        }
+    }
+    Aq += __shfl_xor_sync(0xffffffffu, Aq, 16);
+    dAux += __shfl_xor_sync(0xffffffffu, dAux, 16);
+    dAuy += __shfl_xor_sync(0xffffffffu, dAuy, 16);
+    dAst += __shfl_xor_sync(0xffffffffu, dAst, 16);
+
+    auto sum16 = [](double v) {
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
+    const double Wq = L.w[k] * L.w[l];
+    const double fb = A.fbar[(long long)q * A.N + node];
+    const double rho = sum16(Aq);
+    const double wf = sum16(Wq * fb);
+    const double Abar = (1.0 - 2.0 * A.beta) * fb + 2.0 * A.beta * wf;
+    const double bb = sum16(2.0 * (rho * Wq - Aq) * fb);
+
+    // moment-map rows at the fixed point
+    const double c2 = ck * ck + cl * cl;
+    const double mux = st * ck / rho, muy = st * cl / rho;
+    const double mst = st * (c2 - 2.0 * A.T_L) / (4.0 * rho * A.T_L);
+    double J[3][3];
+    J[0][0] = sum16(mux * dAux);
+    J[0][1] = sum16(mux * dAuy);
+    J[0][2] = sum16(mux * dAst);
+    J[1][0] = sum16(muy * dAux);
+    J[1][1] = sum16(muy * dAuy);
+    J[1][2] = sum16(muy * dAst);
+    J[2][0] = sum16(mst * dAux);
+    J[2][1] = sum16(mst * dAuy);
+    J[2][2] = sum16(mst * dAst);
+    // output-gauge cotangent, T -> s: dL/ds = dL/dT * 2 s T_L
+    double g0 = sum16(Abar * dAux) + A.gbar[node];
+    double g1 = sum16(Abar * dAuy) + A.gbar[A.N + node];
+    double g2 = sum16(Abar * dAst) + A.gbar[2 * A.N + node] * 2.0 * st * A.T_L;
+    // solve J^T mu = -g (Cramer's rule on the transpose)
+    const double a00 = J[0][0], a01 = J[1][0], a02 = J[2][0];
+    const double a10 = J[0][1], a11 = J[1][1], a12 = J[2][1];
+    const double a20 = J[0][2], a21 = J[1][2], a22 = J[2][2];
+    const double det = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
+                       a02 * (a10 * a21 - a11 * a20);
+    const double idet = 1.0 / det;
+    const double r0 = -g0, r1 = -g1, r2 = -g2;
+    const double mu0 = (r0 * (a11 * a22 - a12 * a21) - a01 * (r1 * a22 - a12 * r2) +
+                        a02 * (r1 * a21 - a11 * r2)) * idet;
+    const double mu1 = (a00 * (r1 * a22 - a12 * r2) - r0 * (a10 * a22 - a12 * a20) +
+                        a02 * (a10 * r2 - r1 * a20)) * idet;
+    const double mu2 = (a00 * (a11 * r2 - r1 * a21) - a01 * (a10 * r2 - r1 * a20) +
+                        r0 * (a10 * a21 - a11 * a20)) * idet;
+    const double wq = Abar + mux * mu0 + muy * mu1 + mst * mu2;
+    if (half == 0) A.w[(long long)q * A.N + node] = wq;
+    if (lane == 0) atomicAdd(A.beta_bar, bb);
+}
+
+// Transpose of the reconstruction, gathered at each source node.
+__global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A) {
+    const Lattice& L = c_La;
+    const int lane = threadIdx.x & 31;
+    const long long src = (long long)blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
+    if (src >= A.N) return;  // warp-uniform
+    const int JX = (int)(src % A.nx), JY = (int)(src / A.nx);
+    const int q = lane & 15, k = q >> 2, l = q & 3, half = lane >> 4;
+    const double ck = L.c[k], cl = L.c[l];
+    double fj[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) fj[i] = A.in.f[(long long)i * A.N + src];
+    const double uxj = A.in.ux[src], uyj = A.in.uy[src], stj = A.in.st[src];
+
+    double fb[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) fb[i] = 0.0;
+    double bux = 0.0, buy = 0.0, bst = 0.0;
+
+    // candidate targets x with floor(x - v dt) in [J - 2, J + 1]
+    const int xlo = (int)floor((double)JX - 2.0 + A.vlo_x[k] * A.dt) - 1;
+    const int xhi = (int)ceil((double)JX + 2.0 + A.vhi_x[k] * A.dt) + 1;
+    const int ylo = (int)floor((double)JY - 2.0 + A.vlo_y[l] * A.dt) - 1;
+    const int yhi = (int)ceil((double)JY + 2.0 + A.vhi_y[l] * A.dt) + 1;
+    for (int yy = ylo + half; yy <= yhi; yy += 2) {
+        const int ty = wrap_idx(yy, A.ny);
+        for (int xx = xlo; xx <= xhi; ++xx) {
+            const int tx = wrap_idx(xx, A.nx);
+            const long long t = (long long)ty * A.nx + tx;
+            const double ux = A.ux_s[t], uy = A.uy_s[t], st = A.st_s[t];
+            const double depx = (double)xx - fma(st, ck, ux) * A.dt;
+            const double depy = (double)yy - fma(st, cl, uy) * A.dt;
+            const double flx = floor(depx), fly = floor(depy);
+            const long long jx = (long long)JX - ((long long)flx - 1);
+            const long long jy = (long long)JY - ((long long)fly - 1);
+            if (jx < 0 || jx > 3 || jy < 0 || jy > 3) continue;
+            double lx[4], ly[4];
+            lagrange4(depx - flx + 1.0, lx);
+            lagrange4(depy - fly + 1.0, ly);
+            const double wgt = (jx == 0 ? lx[0] : jx == 1 ? lx[1] : jx == 2 ? lx[2] : lx[3]) *
+                               (jy == 0 ? ly[0] : jy == 1 ? ly[1] : jy == 2 ? ly[2] : ly[3]);
+            const double coef = A.w[(long long)q * A.N + t] * wgt;
+            const double inv = 1.0 / st;
+            const double r = fma(stj, inv, -1.0);
+            const double dx = (uxj - ux) * inv, dy = (uyj - uy) * inv;
+            double gx[4], gdx[4], gy[4], gdy[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                lag_taylor(L, k, a, fma(L.c[a], r, dx), gx[a], gdx[a]);
+                lag_taylor(L, l, a, fma(L.c[a], r, dy), gy[a], gdy[a]);
+            }
+            double sux = 0.0, suy = 0.0, sst = 0.0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const double cgx = coef * gx[a];
+                double h = 0.0, hp = 0.0, hq = 0.0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    fb[4 * a + b] = fma(cgx, gy[b], fb[4 * a + b]);
+                    const double fv = fj[4 * a + b];
+                    h = fma(gy[b], fv, h);
+                    hp = fma(gdy[b], fv, hp);
+                    hq = fma(gdy[b] * L.c[b], fv, hq);
+                }
+                sux = fma(gdx[a], h, sux);
+                suy = fma(gx[a], hp, suy);
+                sst = fma(gdx[a] * L.c[a], h, fma(gx[a], hq, sst));
+            }
+            // d xi / d(source u) = 1/s ; d xi / d(source s) = c / s
+            const double ci = coef * inv;
+            bux = fma(ci, sux, bux);
+            buy = fma(ci, suy, buy);
+            bst = fma(ci, sst, bst);
+        }
+    }
+    // reduce over the warp (all populations and both halves)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) fb[i] += __shfl_xor_sync(0xffffffffu, fb[i], o);
+        bux += __shfl_xor_sync(0xffffffffu, bux, o);
+        buy += __shfl_xor_sync(0xffffffffu, buy, o);
+        bst += __shfl_xor_sync(0xffffffffu, bst, o);
+    }
+    if (lane < 16) {
+        double v = fb[0];
+#pragma unroll
+        for (int i = 1; i < 16; ++i)
+            if (lane == i) v = fb[i];
+        A.fbar_in[(long long)lane * A.N + src] = v;
+    } else if (lane == 16) {
+        A.gbar_in[src] = bux;
+    } else if (lane == 17) {
+        A.gbar_in[A.N + src] = buy;
+    } else if (lane == 18) {
+        // s = sqrt(T / T_L): dL/dT = dL/ds / (2 s T_L)
+        A.gbar_in[2 * A.N + src] = bst / (2.0 * stj * A.T_L);
+    }
+}
+
+__global__ void k_minmax3(const double* ux, const double* uy, const double* st, long long N,
+                          double* out6) {
+    // single block; out6 = {min ux, max ux, min uy, max uy, min s, max s}
+    __shared__ double red[6][32];
+    double v[6] = {1e300, -1e300, 1e300, -1e300, 1e300, -1e300};
+    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+        v[0] = fmin(v[0], ux[i]);
+        v[1] = fmax(v[1], ux[i]);
+        v[2] = fmin(v[2], uy[i]);
+        v[3] = fmax(v[3], uy[i]);
+        v[4] = fmin(v[4], st[i]);
+        v[5] = fmax(v[5], st[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int j = 0; j < 6; ++j) {
+            const double u = __shfl_xor_sync(0xffffffffu, v[j], o);
+            v[j] = (j & 1) ? fmax(v[j], u) : fmin(v[j], u);
+        }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int j = 0; j < 6; ++j) red[j][w] = v[j];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int j = 0; j < 6; ++j) {
+            double r = red[j][0];
+            for (int i = 1; i < nw; ++i) r = (j & 1) ? fmax(r, red[j][i]) : fmin(r, red[j][i]);
+            out6[j] = r;
+        }
+    }
+}
+
+__global__ void k_rho_bar(const double* __restrict__ fbar, double* __restrict__ rbar, long long N) {
+    const Lattice& L = c_La;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double r = 0.0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) r = fma(L.w[q >> 2] * L.w[q & 3], fbar[q * N + i], r);
+    rbar[i] = r;
+}
+
 }  // namespace pond
 
-void destroy_adjoint(pond_ctx*) {}
+using namespace pond;
 
-extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void*, const void*, void*, void*,
-                                         double*) {
+void destroy_adjoint(pond_ctx* ctx) {
+    AdjointScratch* a = ctx->adj;
+    if (!a) return;
+    cudaFree(a->fwd.f);
+    cudaFree(a->fwd.ux);
+    cudaFree(a->fwd.uy);
+    cudaFree(a->fwd.st);
+    cudaFree(a->w);
+    cudaFree(a->iters);
+    cudaFree(a->stats);
+    cudaFree(a->beta_bar);
+    cudaFree(a->minmax);
+    delete a;
+    ctx->adj = nullptr;
+}
+
+static pond_status adj_fail(pond_ctx* ctx, cudaError_t e, const char* where) {
+    ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? POND_ERR_OOM : POND_ERR_CUDA;
+}
+
+#define ACK(call, where)                                           \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return adj_fail(ctx, e_, where);    \
+    } while (0)
+
+extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in,
+                                         const void* gauge_bar_in, void* f_bar_out,
+                                         void* gauge_bar_out, double* nu_bar_accum) {
     if (!ctx) return POND_ERR_ARG;
-    ctx->err = "adjoint not available in this build";
-    return POND_ERR_STATE;
+    if (!f_bar_in || !gauge_bar_in || !f_bar_out || !gauge_bar_out || !nu_bar_accum) {
+        ctx->err = "adjoint: NULL argument";
+        return POND_ERR_ARG;
+    }
+    if (ctx->n_grids != 1 || ctx->cfg.precision != POND_FP64 || !ctx->cfg.thermal) {
+        ctx->err = "adjoint: single-grid FP64 thermal contexts only";
+        return POND_ERR_ARG;
+    }
+    if (!ctx->grid_set[0]) {
+        ctx->err = "adjoint before pond_set_state";
+        return POND_ERR_STATE;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    struct Restore {
+        int p, d;
+        ~Restore() {
+            if (p >= 0 && p != d) cudaSetDevice(p);
+        }
+    } restore{prev, ctx->device};
+
+    const int64_t N = ctx->N;
+    if (!ctx->adj) {
+        AdjointScratch* a = new AdjointScratch();
+        ctx->adj = a;
+        a->N = N;
+        ACK(cudaMalloc(&a->fwd.f, sizeof(double) * 16 * N), "adjoint alloc");
+        ACK(cudaMalloc(&a->fwd.ux, sizeof(double) * N), "adjoint alloc");
+        ACK(cudaMalloc(&a->fwd.uy, sizeof(double) * N), "adjoint alloc");
+        ACK(cudaMalloc(&a->fwd.st, sizeof(double) * N), "adjoint alloc");
+        ACK(cudaMalloc(&a->w, sizeof(double) * 16 * N), "adjoint alloc");
+        ACK(cudaMalloc(&a->iters, sizeof(int32_t) * N), "adjoint alloc");
+        ACK(cudaMalloc(&a->stats, sizeof(DevStats)), "adjoint alloc");
+        ACK(cudaMalloc(&a->beta_bar, sizeof(double)), "adjoint alloc");
+        ACK(cudaMalloc(&a->minmax, sizeof(double) * 6), "adjoint alloc");
+    }
+    AdjointScratch* a = ctx->adj;
+    const GridDesc& G = ctx->grids_host[0];
+    StateBuf<double> in;
+    in.f = static_cast<double*>(ctx->f[ctx->cur]);
+    in.ux = ctx->ux[ctx->cur];
+    in.uy = ctx->uy[ctx->cur];
+    in.st = ctx->st[ctx->cur];
+    cudaStream_t s = ctx->stream;
+
+    // 1. forward step into scratch: its gauge is the fixed point lambda*
+    ACK(launch_step_fp64(in, a->fwd, a->iters, a->stats, G.nx, G.ny, ctx->L, ctx->P, s),
+        "adjoint forward");
+    // 2. velocity bounds for the transpose gather
+    k_minmax3<<<1, 1024, 0, s>>>(a->fwd.ux, a->fwd.uy, a->fwd.st, N, a->minmax);
+    ACK(cudaGetLastError(), "adjoint bounds");
+    ACK(cudaMemcpyAsync(a->host_minmax, a->minmax, sizeof(double) * 6, cudaMemcpyDeviceToHost, s),
+        "adjoint bounds copy");
+    ACK(cudaMemsetAsync(a->beta_bar, 0, sizeof(double), s), "adjoint reset");
+    ACK(cudaStreamSynchronize(s), "adjoint sync");
+
+    AdjArgs A;
+    A.in = in;
+    A.ux_s = a->fwd.ux;
+    A.uy_s = a->fwd.uy;
+    A.st_s = a->fwd.st;
+    A.fbar = static_cast<const double*>(f_bar_in);
+    A.gbar = static_cast<const double*>(gauge_bar_in);
+    A.w = a->w;
+    A.fbar_in = static_cast<double*>(f_bar_out);
+    A.gbar_in = static_cast<double*>(gauge_bar_out);
+    A.beta_bar = a->beta_bar;
+    A.nx = G.nx;
+    A.ny = G.ny;
+    A.N = N;
+    A.beta = ctx->P.beta;
+    A.dt = ctx->P.dt;
+    A.T_L = ctx->L.T_L;
+    const double* mm = a->host_minmax;
+    for (int i = 0; i < 4; ++i) {
+        const double c = ctx->L.c[i];
+        const double slo = c >= 0 ? c * mm[4] : c * mm[5];
+        const double shi = c >= 0 ? c * mm[5] : c * mm[4];
+        A.vlo_x[i] = slo + mm[0];
+        A.vhi_x[i] = shi + mm[1];
+        A.vlo_y[i] = slo + mm[2];
+        A.vhi_y[i] = shi + mm[3];
+    }
+    const unsigned nb = (unsigned)((N + ADJ_WARPS - 1) / ADJ_WARPS);
+    k_adjoint_targets<<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    ACK(cudaGetLastError(), "adjoint targets");
+    k_adjoint_sources<<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    ACK(cudaGetLastError(), "adjoint sources");
+    double bb = 0.0;
+    ACK(cudaMemcpyAsync(&bb, a->beta_bar, sizeof(double), cudaMemcpyDeviceToHost, s), "adjoint copy");
+    ACK(cudaStreamSynchronize(s), "adjoint sync");
+    // beta = 1 / (2 nu / (T_ref dt) + 1)  =>  d beta / d nu = -2 beta^2 / (T_ref dt)
+    const double beta = ctx->P.beta;
+    *nu_bar_accum += bb * (-2.0 * beta * beta / (ctx->cfg.T_ref * ctx->cfg.dt));
+    return POND_OK;
+}
+
+extern "C" pond_status pond_adjoint_init(pond_ctx* ctx, const void* f_bar, void* rho_bar) {
+    if (!ctx) return POND_ERR_ARG;
+    if (!f_bar || !rho_bar || ctx->n_grids != 1) {
+        ctx->err = "adjoint_init: NULL argument or batched context";
+        return POND_ERR_ARG;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    const long long N = ctx->N;
+    k_rho_bar<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
+        static_cast<const double*>(f_bar), static_cast<double*>(rho_bar), N);
+    const cudaError_t e = cudaGetLastError();
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return adj_fail(ctx, e, "adjoint_init");
+    return POND_OK;
 }

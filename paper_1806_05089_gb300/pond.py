@@ -80,7 +80,8 @@ _LIB = None
 # every symbol include/pond.h declares
 EXPORTS = ["pond_config_default", "pond_create", "pond_set_stream", "pond_set_state",
            "pond_step", "pond_moments", "pond_get_state", "pond_iterations",
-           "pond_adjoint_step", "pond_destroy", "pond_last_error", "pond_version"]
+           "pond_adjoint_step", "pond_adjoint_init", "pond_destroy", "pond_last_error",
+           "pond_version"]
 
 
 def lib_path() -> str:
@@ -121,6 +122,8 @@ def load(build_if_missing: bool = True, path: str | None = None):
     lib.pond_iterations.restype = i32
     lib.pond_adjoint_step.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
     lib.pond_adjoint_step.restype = i32
+    lib.pond_adjoint_init.argtypes = [vp, vp, vp]
+    lib.pond_adjoint_init.restype = i32
     lib.pond_destroy.argtypes = [vp]
     lib.pond_destroy.restype = None
     lib.pond_last_error.argtypes = [vp]
@@ -241,6 +244,12 @@ def pond_adjoint_step(ctx, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out):
     ps = [_ptr(a, True) for a in (f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out)]
     _check(ctx, load().pond_adjoint_step(ctx, *[p for p, _ in ps], ctypes.byref(nu_bar)))
     return nu_bar.value
+
+
+def pond_adjoint_init(ctx, f_bar, rho_bar):
+    """rho_bar = sum_q W_q f_bar_q (device tensors)."""
+    ps = [_ptr(a, True) for a in (f_bar, rho_bar)]
+    _check(ctx, load().pond_adjoint_init(ctx, *[p for p, _ in ps]))
 
 
 def pond_destroy(ctx):

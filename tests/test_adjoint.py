@@ -1,0 +1,153 @@
+"""Adjoint of the PonD step.
+
+CPU: the plain-PyTorch reference step (oracle/torch_ref.py) matches the C
+oracle, and its autograd gradient matches central finite differences of the
+C oracle -- this pins the reference gradient.
+GPU: the CUDA adjoint (pond_adjoint_step through PondRollout) matches the
+reference gradient, and central finite differences of the GPU forward, up to
+the 512^2 / 200-step / checkpoint-20 workload.
+
+Loss throughout: L = 1/2 sum (rho_T - rho*)^2 with a seeded target rho*.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import torch_ref as tr
+from paper_1806_05089_gb300 import workloads
+
+
+def small_case(nx, ny, seed=0):
+    tg = workloads.taylor_green(nx, ny, 0.3)
+    rng = np.random.default_rng(seed)
+    rho0 = 1.0 + 0.05 * rng.standard_normal((ny, nx))
+    target = 1.0 + 0.01 * rng.standard_normal((ny, nx))
+    T0 = 1.0 + 0.1 * rng.random((ny, nx))
+    return rho0, tg.ux, tg.uy, T0, target
+
+
+def oracle_loss(rho0, ux, uy, T, target, nu, steps, passes):
+    st = oracle.init_equilibrium(rho0, ux, uy, T)
+    p = oracle.Params(nu=nu, fixed_iter=passes)
+    for _ in range(steps):
+        st, _, _ = oracle.step(st, p)
+    return 0.5 * ((st.f.sum(0) - target) ** 2).sum()
+
+
+def reference_grad(rho0, ux, uy, T, target, nu, steps, passes):
+    r = torch.tensor(rho0, requires_grad=True)
+    n = torch.tensor(nu, dtype=torch.float64, requires_grad=True)
+    rho = tr.rollout(r, torch.tensor(ux), torch.tensor(uy), torch.tensor(T), n, steps, passes)
+    loss = 0.5 * ((rho - torch.tensor(target)) ** 2).sum()
+    loss.backward()
+    return float(loss.detach()), r.grad.numpy(), float(n.grad)
+
+
+def test_reference_step_matches_oracle():
+    rho0, ux, uy, T, _ = small_case(7, 5)
+    st = oracle.init_equilibrium(rho0, ux, uy, T)
+    f = torch.tensor(st.f)
+    g = [torch.tensor(a) for a in (st.ux, st.uy, st.T)]
+    o = st
+    for _ in range(2):
+        o, _, _ = oracle.step(o, oracle.Params(nu=0.02, fixed_iter=5))
+        f, *g = tr.step(f, *g, 0.02, 5)
+    assert np.abs(f.numpy() - o.f).max() <= 1e-13
+    assert np.abs(g[0].numpy() - o.ux).max() <= 1e-13
+    assert np.abs(g[2].numpy() - o.T).max() <= 1e-13
+
+
+def test_reference_gradient_matches_oracle_fd():
+    rho0, ux, uy, T, target = small_case(6, 5, seed=1)
+    nu, steps, passes = 0.02, 2, 20
+    L, grho, gnu = reference_grad(rho0, ux, uy, T, target, nu, steps, passes)
+    assert abs(L - oracle_loss(rho0, ux, uy, T, target, nu, steps, passes)) <= 1e-12 * L
+    rng = np.random.default_rng(7)
+    for _ in range(2):
+        d = rng.standard_normal(rho0.shape)
+        h = 1e-5
+        fd = (oracle_loss(rho0 + h * d, ux, uy, T, target, nu, steps, passes)
+              - oracle_loss(rho0 - h * d, ux, uy, T, target, nu, steps, passes)) / (2 * h)
+        assert abs(fd - (grho * d).sum()) <= 1e-6 * abs(fd)
+    h = 1e-6
+    fd = (oracle_loss(rho0, ux, uy, T, target, nu + h, steps, passes)
+          - oracle_loss(rho0, ux, uy, T, target, nu - h, steps, passes)) / (2 * h)
+    assert abs(fd - gnu) <= 1e-6 * abs(fd)
+
+
+# ------------------------------------------------------------------ GPU
+
+
+def gpu_grad(rho0, ux, uy, T, target, nu, steps, ckpt, **cfg):
+    from paper_1806_05089_gb300.autograd import pond_rollout
+    dev = torch.device("cuda")
+    r = torch.tensor(rho0, device=dev, requires_grad=True)
+    n = torch.tensor(nu, dtype=torch.float64, device=dev, requires_grad=True)
+    rho = pond_rollout(r, n, *(torch.tensor(a, device=dev) for a in (ux, uy, T)), steps, ckpt,
+                       **cfg)
+    loss = 0.5 * ((rho - torch.tensor(target, device=dev)) ** 2).sum()
+    loss.backward()
+    return float(loss.detach()), r.grad.cpu().numpy(), float(n.grad)
+
+
+def gpu_loss(rho0, ux, uy, T, target, nu, steps, **cfg):
+    from paper_1806_05089_gb300 import pond
+    ny, nx = rho0.shape
+    with pond.Sim(nx, ny, pond.POND_FP64, nu=nu, **cfg) as s:
+        s.set_state(rho0, ux, uy, T)
+        s.step(steps, stats=False)
+        rho = s.moments()[0]
+    return 0.5 * ((rho - target) ** 2).sum()
+
+
+@pytest.mark.gpu
+def test_adjoint_matches_reference_gradient():
+    rho0, ux, uy, T, target = small_case(10, 8, seed=2)
+    nu, steps, passes = 0.02, 3, 24
+    L, grho, gnu = reference_grad(rho0, ux, uy, T, target, nu, steps, passes)
+    Lg, grho_g, gnu_g = gpu_grad(rho0, ux, uy, T, target, nu, steps, 2, fixed_iter=passes)
+    assert abs(Lg - L) <= 1e-12 * L
+    assert np.abs(grho_g - grho).max() <= 1e-9 * np.abs(grho).max()
+    assert abs(gnu_g - gnu) <= 1e-9 * abs(gnu)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("fixed", [30, 0])
+def test_adjoint_matches_gpu_finite_differences(fixed):
+    rho0, ux, uy, T, target = small_case(32, 24, seed=3)
+    nu, steps, ckpt = 0.01, 6, 4
+    cfg = {"fixed_iter": fixed} if fixed else {}
+    L, grho, gnu = gpu_grad(rho0, ux, uy, T, target, nu, steps, ckpt, **cfg)
+    rng = np.random.default_rng(11)
+    for _ in range(4):
+        d = rng.standard_normal(rho0.shape)
+        h = 1e-5
+        fd = (gpu_loss(rho0 + h * d, ux, uy, T, target, nu, steps, **cfg)
+              - gpu_loss(rho0 - h * d, ux, uy, T, target, nu, steps, **cfg)) / (2 * h)
+        assert abs(fd - (grho * d).sum()) <= 1e-6 * abs(fd), (fd, (grho * d).sum())
+    h = 1e-6
+    fd = (gpu_loss(rho0, ux, uy, T, target, nu + h, steps, **cfg)
+          - gpu_loss(rho0, ux, uy, T, target, nu - h, steps, **cfg)) / (2 * h)
+    assert abs(fd - gnu) <= 1e-6 * abs(fd), (fd, gnu)
+
+
+@pytest.mark.gpu
+def test_adjoint_full_workload_512():
+    """512^2 Taylor-Green (u0 = 0.3) plus a Gaussian pulse, 200 steps,
+    checkpoints every 20; gradient w.r.t. rho0 (8 seeded directions) and nu
+    against central finite differences of the GPU forward."""
+    f, target = workloads.adjoint(512)
+    nu, steps, ckpt = 0.01, 200, 20
+    L, grho, gnu = gpu_grad(f.rho, f.ux, f.uy, f.T, target, nu, steps, ckpt)
+    rng = np.random.default_rng(1806050894)
+    for _ in range(8):
+        d = rng.standard_normal(f.rho.shape)
+        h = 1e-6
+        fd = (gpu_loss(f.rho + h * d, f.ux, f.uy, f.T, target, nu, steps)
+              - gpu_loss(f.rho - h * d, f.ux, f.uy, f.T, target, nu, steps)) / (2 * h)
+        assert abs(fd - (grho * d).sum()) <= 1e-6 * abs(fd), (fd, (grho * d).sum())
+    h = 1e-7
+    fd = (gpu_loss(f.rho, f.ux, f.uy, f.T, target, nu + h, steps)
+          - gpu_loss(f.rho, f.ux, f.uy, f.T, target, nu - h, steps)) / (2 * h)
+    assert abs(fd - gnu) <= 1e-6 * abs(fd), (fd, gnu)

@@ -168,6 +168,42 @@ pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in, const void* g
  * Errors: POND_ERR_ARG, POND_ERR_CUDA. */
 pond_status pond_adjoint_init(pond_ctx* ctx, const void* f_bar, void* rho_bar);
 
+/* Largest grid (nx * ny) pond_step_fp64_noalloc accepts. */
+#define POND_NOALLOC_MAX_NODES 262144
+
+/* One FP64 step of a single periodic grid that allocates nothing and needs
+ * no context.  The paper has no counterpart: this exists for callers that
+ * must not allocate device memory (code running inside a host callback, a
+ * custom allocator or memory pool, a framework that has reserved all device
+ * memory, a real-time loop that may not enter the allocator).
+ *
+ * All array arguments are device pointers of the current device, FP64, in
+ * the layouts above: f_in/f_out [16][ny][nx], ux/uy/T [ny][nx]; iters
+ * (int32 [ny][nx]) and stats may be NULL.  Output arrays must not overlap
+ * the inputs.  cfg must have precision POND_FP64; the other fields mean what
+ * they mean for pond_create.  Work is enqueued on cuda_stream; the call
+ * returns without synchronising unless stats is given.
+ *
+ * The only extra device memory -- sqrt(T/T_L) of the input and output
+ * gauges and the step counters -- is a fixed array inside the library, held
+ * by every GPU that loads the library until the process exits
+ * (2 x 8 x POND_NOALLOC_MAX_NODES + 256 bytes).  Every call on a device
+ * shares that array and the counters are cleared at the start of each call,
+ * so calls whose work can overlap on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller.  The
+ * first call on each device looks up the array's device address and uploads
+ * the lattice constants (synchronous copies), so make it before any stream
+ * capture.  No cudaMalloc, cudaFree or allocating library call is made.
+ *
+ * Errors: POND_ERR_ARG (NULL pointer, bad config, nx * ny above
+ * POND_NOALLOC_MAX_NODES), POND_ERR_CUDA, and with stats given
+ * POND_ERR_NONPHYSICAL / POND_ERR_NOT_CONVERGED (strict) as pond_step. */
+pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx, int32_t ny,
+                                   const double* f_in, const double* ux_in, const double* uy_in,
+                                   const double* T_in, double* f_out, double* ux_out,
+                                   double* uy_out, double* T_out, int32_t* iters,
+                                   pond_stats* stats, void* cuda_stream);
+
 void pond_destroy(pond_ctx* ctx);
 
 /* Message of the last failing call on ctx ("" if none; static text if ctx is

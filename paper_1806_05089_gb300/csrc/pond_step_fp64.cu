@@ -22,6 +22,8 @@
 // pass's populations re-expressed in the gauge their moments define (so the
 // stored gauge is exactly their co-moving frame), and finally the BGK
 // relaxation f + 2 beta (rho W - f) (Eq. postcollision).
+#include <mutex>
+
 #include "pond_device.cuh"
 
 namespace pond {
@@ -251,3 +253,138 @@ cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>&
 }
 
 }  // namespace pond
+
+// ----------------------------------------------------------------------------
+// FP64 step without a context and without any allocation.
+//
+// For callers that cannot allocate device memory: code running where
+// cudaMalloc is not allowed or not wanted (inside a host callback, a custom
+// allocator or memory pool, a process whose device memory is fully reserved
+// by its framework, a real-time loop that must not enter the allocator).
+// They pass their own input and output arrays; the only extra device memory
+// the step needs -- sqrt(T / T_L) of the input and output gauges and the step
+// counters -- lives in the file-scope array below, which every GPU that loads
+// this library holds until the process exits (2 x 8 x 262144 + 256 bytes).
+namespace pond {
+
+constexpr int64_t kNoAllocMaxNodes = POND_NOALLOC_MAX_NODES;
+constexpr size_t kNoAllocStatsOffset = 2 * sizeof(double) * (size_t)kNoAllocMaxNodes;
+constexpr size_t kNoAllocBytes = kNoAllocStatsOffset + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+__global__ void k_noalloc_t_to_st(const double* __restrict__ T, double* __restrict__ st,
+                                  long long N, double T_L) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) st[i] = sqrt(T[i] / T_L);
+}
+
+__global__ void k_noalloc_st_to_t(const double* __restrict__ st, double* __restrict__ T,
+                                  long long N, double T_L) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        const double s = st[i];
+        T[i] = s * s * T_L;
+    }
+}
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {nullptr};  // device address of the scratch, per device
+}  // namespace
+
+// Once per device, with that device current: the device address of the
+// scratch array (its name in host code is only a host-side stand-in) and the
+// lattice constants of this translation unit.
+static cudaError_t noalloc_setup(int dev, unsigned char** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        e = upload_lattice_fp64(make_lattice());
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    return cudaSuccess;
+}
+
+}  // namespace pond
+
+extern "C" pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx, int32_t ny,
+                                              const double* f_in, const double* ux_in,
+                                              const double* uy_in, const double* T_in,
+                                              double* f_out, double* ux_out, double* uy_out,
+                                              double* T_out, int32_t* iters, pond_stats* stats,
+                                              void* cuda_stream) {
+    using namespace pond;
+    if (!cfg || !f_in || !ux_in || !uy_in || !T_in || !f_out || !ux_out || !uy_out || !T_out)
+        return POND_ERR_ARG;
+    if (cfg->precision != POND_FP64 || !(cfg->nu > 0.0) || !(cfg->T_ref > 0.0) ||
+        !(cfg->dt > 0.0) || cfg->max_iter < 1 || cfg->fixed_iter < 0 || cfg->seed_mode < 0 ||
+        cfg->seed_mode > 2)
+        return POND_ERR_ARG;
+    if (nx < 1 || ny < 1 || (int64_t)nx * ny > kNoAllocMaxNodes) return POND_ERR_ARG;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return POND_ERR_CUDA;
+    unsigned char* scratch = nullptr;
+    e = noalloc_setup(dev, &scratch);
+    if (e != cudaSuccess) return POND_ERR_CUDA;
+
+    const Lattice L = make_lattice();
+    StepParams P;
+    P.beta = 1.0 / (2.0 * cfg->nu / (cfg->T_ref * cfg->dt) + 1.0);
+    P.dt = cfg->dt;
+    P.eps_abs = cfg->eps_abs;
+    P.eps_rel = cfg->eps_rel;
+    P.T_L = L.T_L;
+    P.max_iter = cfg->max_iter;
+    P.fixed_iter = cfg->fixed_iter;
+    P.thermal = cfg->thermal;
+    P.seed_mode = cfg->seed_mode;
+
+    const long long N = (long long)nx * ny;
+    double* st_in = reinterpret_cast<double*>(scratch);
+    double* st_out = st_in + kNoAllocMaxNodes;
+    DevStats* dstats = reinterpret_cast<DevStats*>(scratch + kNoAllocStatsOffset);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+    // the counters keep the previous call's values: they must start at zero
+    e = cudaMemsetAsync(dstats, 0, sizeof(DevStats), s);
+    if (e != cudaSuccess) return POND_ERR_CUDA;
+    const unsigned nb = (unsigned)((N + 255) / 256);
+    k_noalloc_t_to_st<<<nb, 256, 0, s>>>(T_in, st_in, N, L.T_L);
+    StateBuf<double> in, out;
+    in.f = const_cast<double*>(f_in);
+    in.ux = const_cast<double*>(ux_in);
+    in.uy = const_cast<double*>(uy_in);
+    in.st = st_in;
+    out.f = f_out;
+    out.ux = ux_out;
+    out.uy = uy_out;
+    out.st = st_out;
+    e = launch_step_fp64(in, out, iters, dstats, nx, ny, L, P, s);
+    if (e != cudaSuccess) return POND_ERR_CUDA;
+    k_noalloc_st_to_t<<<nb, 256, 0, s>>>(st_out, T_out, N, L.T_L);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return POND_ERR_CUDA;
+    if (stats) {
+        DevStats h;
+        e = cudaMemcpyAsync(&h, dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return POND_ERR_CUDA;
+        stats->node_updates = N;
+        stats->passes = (int64_t)h.passes;
+        stats->max_passes = (int32_t)h.max_passes;
+        stats->reserved = 0;
+        stats->nonconverged = (int64_t)h.nonconverged;
+        stats->nonphysical = (int64_t)h.nonphysical;
+        stats->halo_fallback = 0;
+        if (h.nonphysical) return POND_ERR_NONPHYSICAL;
+        if (cfg->strict && h.nonconverged) return POND_ERR_NOT_CONVERGED;
+    }
+    return POND_OK;
+}

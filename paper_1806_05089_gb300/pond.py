@@ -80,8 +80,10 @@ _LIB = None
 # every symbol include/pond.h declares
 EXPORTS = ["pond_config_default", "pond_create", "pond_set_stream", "pond_set_state",
            "pond_step", "pond_moments", "pond_get_state", "pond_iterations",
-           "pond_adjoint_step", "pond_adjoint_init", "pond_destroy", "pond_last_error",
-           "pond_version"]
+           "pond_adjoint_step", "pond_adjoint_init", "pond_step_fp64_noalloc", "pond_destroy",
+           "pond_last_error", "pond_version"]
+
+POND_NOALLOC_MAX_NODES = 262144
 
 
 def lib_path() -> str:
@@ -124,6 +126,10 @@ def load(build_if_missing: bool = True, path: str | None = None):
     lib.pond_adjoint_step.restype = i32
     lib.pond_adjoint_init.argtypes = [vp, vp, vp]
     lib.pond_adjoint_init.restype = i32
+    lib.pond_step_fp64_noalloc.argtypes = [ctypes.POINTER(pond_config), i32, i32,
+                                           vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                           ctypes.POINTER(pond_stats), vp]
+    lib.pond_step_fp64_noalloc.restype = i32
     lib.pond_destroy.argtypes = [vp]
     lib.pond_destroy.restype = None
     lib.pond_last_error.argtypes = [vp]
@@ -250,6 +256,21 @@ def pond_adjoint_init(ctx, f_bar, rho_bar):
     """rho_bar = sum_q W_q f_bar_q (device tensors)."""
     ps = [_ptr(a, True) for a in (f_bar, rho_bar)]
     _check(ctx, load().pond_adjoint_init(ctx, *[p for p, _ in ps]))
+
+
+def pond_step_fp64_noalloc(cfg, f_in, ux_in, uy_in, T_in, f_out, ux_out, uy_out, T_out,
+                           iters=None, want_stats=True, stream=None):
+    """One FP64 step without a context or any allocation (CUDA float64
+    tensors; see include/pond.h).  Returns the step counters."""
+    ny, nx = ux_in.shape
+    ps = [_ptr(a, True) for a in (f_in, ux_in, uy_in, T_in, f_out, ux_out, uy_out, T_out, iters)]
+    stats = pond_stats()
+    st = load().pond_step_fp64_noalloc(ctypes.byref(cfg), nx, ny, *[p for p, _ in ps],
+                                       ctypes.byref(stats) if want_stats else None,
+                                       ctypes.c_void_p(stream or 0))
+    if st != POND_OK:
+        raise PondError(st, "pond_step_fp64_noalloc failed")
+    return stats.as_dict() if want_stats else None
 
 
 def pond_destroy(ctx):

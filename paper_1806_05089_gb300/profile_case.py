@@ -1,0 +1,72 @@
+"""Run one small PonD case for profiling (e.g. under ncu).
+
+  python -m paper_1806_05089_gb300.profile_case --form fp64 --n 1024 --steps 2
+  python -m paper_1806_05089_gb300.profile_case --form mixed --n 2048 --steps 3
+  python -m paper_1806_05089_gb300.profile_case --form batched --grids 64 --steps 2
+  python -m paper_1806_05089_gb300.profile_case --form adjoint --n 256 --steps 2
+
+fp64 / mixed use the supersonic workload (uniform u = (1.5, 0.5), 8 seeded
+sinusoids in rho and T) at n x n; batched uses the first ``--grids`` members
+of the 256-grid ensemble; adjoint runs ``--steps`` forward steps and their
+adjoint on the Taylor-Green + pulse workload at n x n.  One warm-up step
+precedes the measured steps, so ``ncu -s`` can skip it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--form", choices=["fp64", "mixed", "batched", "adjoint"], default="fp64")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--grids", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=2)
+    a = ap.parse_args()
+
+    import torch
+
+    from . import pond, workloads
+    pond.load()
+    out = {"form": a.form}
+    if a.form in ("fp64", "mixed"):
+        prec = pond.POND_FP64 if a.form == "fp64" else pond.POND_FP32_MIXED
+        f = workloads.supersonic(a.n)
+        with pond.Sim(a.n, a.n, prec) as s:
+            s.set_state(f.rho, f.ux, f.uy, f.T)
+            s.step(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = s.step(a.steps)
+            out.update(n=a.n, steps=a.steps, seconds=time.perf_counter() - t0,
+                       passes=st["passes"] / st["node_updates"])
+    elif a.form == "batched":
+        nxs, nys = workloads.ensemble_sizes(256)
+        nxs, nys = nxs[:a.grids], nys[:a.grids]
+        with pond.Sim(nxs, nys, pond.POND_FP32_MIXED) as s:
+            for i in range(a.grids):
+                m = workloads.ensemble_member(i, nxs[i], nys[i])
+                s.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
+            s.step(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = s.step(a.steps)
+            out.update(grids=a.grids, nodes=int(sum(x * y for x, y in zip(nxs, nys))),
+                       steps=a.steps, seconds=time.perf_counter() - t0)
+    else:
+        from .autograd import pond_rollout
+        f, target = workloads.adjoint(a.n)
+        dev = torch.device("cuda")
+        r = torch.tensor(f.rho, device=dev, requires_grad=True)
+        rho = pond_rollout(r, 0.01, *(torch.tensor(v, device=dev) for v in (f.ux, f.uy, f.T)),
+                           a.steps, a.steps)
+        (0.5 * ((rho - torch.tensor(target, device=dev)) ** 2).sum()).backward()
+        torch.cuda.synchronize()
+        out.update(n=a.n, steps=a.steps, grad_norm=float(r.grad.norm()))
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

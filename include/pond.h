@@ -64,9 +64,10 @@ enum { POND_FP64 = 0, POND_FP32_MIXED = 1 };
 typedef struct pond_config {
     int32_t precision;  /* POND_FP64: all arithmetic and storage FP64.
                            POND_FP32_MIXED: populations and bulk arithmetic
-                           FP32; gauges stored FP64; gauge differences, the
-                           moment-to-gauge update and the convergence test in
-                           FP64 accuracy. */
+                           FP32; gauges stored and accumulated in FP64; the
+                           gauge differences of the transform formed from the
+                           FP64 gauges (tile-relative offsets); convergence
+                           test in FP64. */
     int32_t thermal;    /* 1: energy equation in the predictor-corrector
                            (compressible); 0: isothermal, T kept fixed
                            (main text after Eq. postcollision). */

@@ -5,13 +5,14 @@
 // first bounds the particle velocities of its tile (u -+ c_max sqrt(theta)),
 // stages the whole window of source nodes that the departure stencils can
 // reach (tile + halo, periodic wrap applied while staging) in shared memory:
-// the 16 FP32 populations and the gauge as FP32 offsets from the tile's
-// reference gauge, formed in FP64.  Gauge differences u_s - u' are then
+// the 16 FP32 populations as four float4 rows f[a][0..3] (one 16-byte load
+// per row of the 4 x 4 contraction) and the gauge as FP32 offsets from the
+// tile's reference gauge, formed in FP64.  Gauge differences u_s - u' are then
 // differences of those offsets, so they carry FP32 precision RELATIVE TO THE
 // TILE'S GAUGE SPREAD, which is what FP64 differences rounded to FP32 give
-// (the FP64 part of the "Vandermonde solve" inputs).  The moments are summed
-// in FP32 and turned into the FP64 gauge update; the convergence test of
-// App. E runs in FP64.
+// (the FP64 part of the "Vandermonde solve" inputs).  The moments and the
+// gauge increments of a pass are formed in FP32 and accumulated into the FP64
+// gauge; the convergence test of App. E runs in FP64.
 //
 // Threads of a warp are 32 consecutive nodes of a tile row and process the
 // same population at the same time, so their stencil reads hit consecutive
@@ -92,19 +93,15 @@ __device__ __noinline__ float stencil_global(const MixedArgs& A, const GridDesc&
 
 // Final part of a node update: re-express the last pass's populations (in
 // this thread's s_acc column) in the gauge lambda_{n+1} their moments define
-// (Eq. transform at the node itself; gauge differences in FP64), then BGK
-// relaxation toward rho W in that co-moving gauge (Eq. postcollision) and the
-// store.  Kept out of line so the pass loop keeps its register budget.
+// (Eq. transform at the node itself), then BGK relaxation toward rho W in
+// that co-moving gauge (Eq. postcollision) and the store.  (r, dx, dy) are
+// the Taylor offsets of that transform: xi_a = c_a + c_a r + d.  Kept out of
+// line so the pass loop keeps its register budget.
 __device__ __noinline__ void finish_node(const MixedArgs& A, float* s_acc, int NT, int tid,
-                                         long long node, bool regauge, double ux, double uy,
-                                         double st, double nux, double nuy, double nst,
-                                         double rho) {
+                                         long long node, bool regauge, float r, float dx,
+                                         float dy, double ux, double uy, double st, float rho) {
     const LatticeF& L = c_Lf;
     if (regauge) {
-        const double inv1 = 1.0 / nst;
-        const float r = (float)fma(st, inv1, -1.0);
-        const float dx = (float)((ux - nux) * inv1);
-        const float dy = (float)((uy - nuy) * inv1);
         float ex[4], ey[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -147,16 +144,12 @@ __device__ __noinline__ void finish_node(const MixedArgs& A, float* s_acc, int N
                 s_acc[(4 * k + l) * NT + tid] = v;
             }
         }
-        ux = nux;
-        uy = nuy;
-        st = nst;
     }
     const float two_beta = (float)(2.0 * A.P.beta);
-    const float rhof = (float)rho;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const float a = s_acc[q * NT + tid];
-        const float feq = rhof * (L.w[q >> 2] * L.w[q & 3]);
+        const float feq = rho * (L.w[q >> 2] * L.w[q & 3]);
         A.out.f[q * A.plane + node] = fmaf(two_beta, feq - a, a);
     }
     A.out.ux[node] = ux;
@@ -205,13 +198,14 @@ __device__ __forceinline__ void block_minmax4(float& a, float& b, float& c, floa
 template <int TX, int TY>
 __global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(MixedArgs A) {
     constexpr int NT = TX * TY;
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(16) float4 smem4[];
     const int WN = A.ww * A.wh;
-    float* s_f = smem;            // [16][WN]
-    float* s_dux = s_f + 16 * WN; // [WN]
-    float* s_duy = s_dux + WN;
-    float* s_dst = s_duy + WN;
-    float* s_acc = s_dst + WN;    // [16][NT]
+    // staged window, one float4 per (x-speed index a, node): f[a][0..3], so
+    // one 16-byte load feeds one row of the 4 x 4 contraction; and the
+    // tile-relative gauge (s - s_ref, u_x - u_x,ref, u_y - u_y,ref, 0)
+    float4* s_f4 = smem4;          // [4][WN]
+    float4* s_g4 = s_f4 + 4 * WN;  // [WN]
+    float* s_acc = reinterpret_cast<float*>(s_g4 + WN);  // [16][NT]
     __shared__ float s_red[4][NT / 32];
     __shared__ long long s_item;
     __shared__ unsigned long long s_passes, s_nc, s_np, s_fb;
@@ -227,6 +221,7 @@ __global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(M
     }
     const int lxi = tid % TX, lyi = tid / TX;
     const float dt = (float)A.P.dt;
+    const float half_over_TL = (float)(0.5 / A.P.T_L);
 
     long long item = blockIdx.x;
     for (;;) {
@@ -303,28 +298,30 @@ __global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(M
             const int gx = wrap_idx((long long)wx0 + cx, G.nx);
             const int gy = wrap_idx((long long)wy0 + cy, G.ny);
             const long long gi = base + (long long)gy * G.nx + gx;
+            const float* fp = A.in.f + gi;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) s_f[q * WN + i] = __ldg(A.in.f + q * A.plane + gi);
-            s_dux[i] = (float)(__ldg(A.in.ux + gi) - rux);
-            s_duy[i] = (float)(__ldg(A.in.uy + gi) - ruy);
-            s_dst[i] = (float)(__ldg(A.in.st + gi) - rst);
+            for (int a = 0; a < 4; ++a)
+                s_f4[a * WN + i] = make_float4(__ldg(fp + (4 * a + 0) * A.plane), __ldg(fp + (4 * a + 1) * A.plane),
+                                               __ldg(fp + (4 * a + 2) * A.plane), __ldg(fp + (4 * a + 3) * A.plane));
+            s_g4[i] = make_float4((float)(__ldg(A.in.st + gi) - rst), (float)(__ldg(A.in.ux + gi) - rux),
+                                  (float)(__ldg(A.in.uy + gi) - ruy), 0.0f);
         }
         __syncthreads();
 
         int pass = 0;
         unsigned int flag = 0u;
         unsigned int fallbacks = 0u;
-        double rho = 0.0;
         if (valid) {
+            // the pass gauge in FP64 (accumulated) and its FP32 working copies:
+            // absolute (departures) and tile-relative (gauge differences)
+            float stf = (float)st, uxf = (float)ux, uyf = (float)uy;
+            float tdst = (float)(st - rst), tdux = (float)(ux - rux), tduy = (float)(uy - ruy);
             double nux = ux, nuy = uy, nst = st;  // gauge the last pass's moments define
+            float lr = 0.0f, ldx = 0.0f, ldy = 0.0f, rhof = 0.0f;
             for (;;) {
                 ++pass;
-                const float stf = (float)st;
                 const float invf = 1.0f / stf;
-                const float tdux = (float)(ux - rux);
-                const float tduy = (float)(uy - ruy);
-                const float tdst = (float)(st - rst);
-                const float uxf = (float)ux, uyf = (float)uy;
+                const float bst = -tdst * invf, bux = -tdux * invf, buy = -tduy * invf;
                 float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f;
 #pragma unroll 1
                 for (int q = 0; q < 16; ++q) {
@@ -359,9 +356,10 @@ __global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(M
 #pragma unroll
                             for (int jx = 0; jx < 4; ++jx) {
                                 const int si = (row + jy) * ww + col + jx;
-                                const float r = (s_dst[si] - tdst) * invf;
-                                const float dx = (s_dux[si] - tdux) * invf;
-                                const float dy = (s_duy[si] - tduy) * invf;
+                                const float4 g4 = s_g4[si];
+                                const float r = fmaf(g4.x, invf, bst);   // s_s/s' - 1
+                                const float dx = fmaf(g4.y, invf, bux);  // (u_s,x - u'_x)/s'
+                                const float dy = fmaf(g4.z, invf, buy);
                                 float gx[4], gy[4];
 #pragma unroll
                                 for (int a = 0; a < 4; ++a) {
@@ -376,10 +374,11 @@ __global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(M
                                 float gsum = 0.0f;
 #pragma unroll
                                 for (int a = 0; a < 4; ++a) {
-                                    float h = 0.0f;
-#pragma unroll
-                                    for (int b = 0; b < 4; ++b)
-                                        h = fmaf(gy[b], s_f[(4 * a + b) * WN + si], h);
+                                    const float4 f4 = s_f4[a * WN + si];
+                                    float h = gy[0] * f4.x;
+                                    h = fmaf(gy[1], f4.y, h);
+                                    h = fmaf(gy[2], f4.z, h);
+                                    h = fmaf(gy[3], f4.w, h);
                                     gsum = fmaf(gx[a], h, gsum);
                                 }
                                 rowacc = fmaf(lxw[jx], gsum, rowacc);
@@ -396,28 +395,34 @@ __global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(M
                     m2 = fmaf(cl, acc, m2);
                     m3 = fmaf(fmaf(ck, ck, cl * cl), acc, m3);
                 }
-                // FP64 gauge update (central form of Eqs. conservation_*)
-                rho = (double)m0;
-                const double ir = 1.0 / rho;
-                const double dux = st * (double)m1 * ir, duy = st * (double)m2 * ir;
-                const double ux1 = ux + dux, uy1 = uy + duy;
-                double st1 = st;
-                bool ok = (rho > 0.0) && isfinite(ux1) && isfinite(uy1);
+                // gauge update (central form of Eqs. conservation_*) in FP32,
+                // accumulated into the FP64 gauge; convergence test in FP64
+                const float irf = 1.0f / m0;
+                const float dux = stf * m1 * irf, duy = stf * m2 * irf;
+                float dst = 0.0f;
+                bool ok = (m0 > 0.0f) && isfinite(dux) && isfinite(duy);
                 if (A.P.thermal) {
-                    const double T1 = 0.5 * (st * st * (double)m3 * ir - (dux * dux + duy * duy));
-                    ok = ok && (T1 > 0.0) && isfinite(T1);
-                    st1 = sqrt(T1 / A.P.T_L);
+                    // theta_{n+1} / theta_n - 1
+                    const float rm1 = (m3 * irf - (dux * dux + duy * duy) * invf * invf) * half_over_TL - 1.0f;
+                    ok = ok && (rm1 > -1.0f) && isfinite(rm1);
+                    dst = stf * rm1 / (sqrtf(1.0f + rm1) + 1.0f);
                 }
                 if (!ok) {
                     flag |= 2u;
                     break;
                 }
+                rhof = m0;
+                const double ux1 = ux + (double)dux, uy1 = uy + (double)duy, st1 = st + (double)dst;
                 nux = ux1;
                 nuy = uy1;
                 nst = st1;
-                const bool conv = fabs(ux1 - ux) < A.P.eps_abs + A.P.eps_rel * fabs(ux1) &&
-                                  fabs(uy1 - uy) < A.P.eps_abs + A.P.eps_rel * fabs(uy1) &&
-                                  fabs(st1 - st) < A.P.eps_abs + A.P.eps_rel * fabs(st1);
+                const float nstf = (float)st1;
+                lr = -dst / nstf;
+                ldx = -dux / nstf;
+                ldy = -duy / nstf;
+                const bool conv = fabs((double)dux) < A.P.eps_abs + A.P.eps_rel * fabs(ux1) &&
+                                  fabs((double)duy) < A.P.eps_abs + A.P.eps_rel * fabs(uy1) &&
+                                  fabs((double)dst) < A.P.eps_abs + A.P.eps_rel * fabs(st1);
                 bool stop;
                 if (A.P.fixed_iter > 0) {
                     stop = pass >= A.P.fixed_iter;
@@ -429,8 +434,22 @@ __global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(M
                 ux = ux1;
                 uy = uy1;
                 st = st1;
+                stf = nstf;
+                uxf = (float)ux1;
+                uyf = (float)uy1;
+                tdst += dst;
+                tdux += dux;
+                tduy += duy;
             }
-            finish_node(A, s_acc, NT, tid, node, !(flag & 2u), ux, uy, st, nux, nuy, nst, rho);
+            if (flag & 2u) {
+                // non-physical moments: keep the pass's populations and gauge
+                float r0 = 0.0f;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) r0 += s_acc[q * NT + tid];
+                finish_node(A, s_acc, NT, tid, node, false, 0.0f, 0.0f, 0.0f, ux, uy, st, r0);
+            } else {
+                finish_node(A, s_acc, NT, tid, node, true, lr, ldx, ldy, nux, nuy, nst, rhof);
+            }
             if (A.iters) A.iters[node] = pass;
             atomicAdd(&s_passes, (unsigned long long)pass);
             atomicMax(&s_max, (unsigned int)pass);
@@ -453,7 +472,7 @@ __global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(M
 constexpr int MX_TX = MIXED_TX, MX_TY = MIXED_TY;
 
 size_t mixed_smem_bytes(const TileWindow& w) {
-    return sizeof(float) * ((size_t)19 * w.ww * w.wh + (size_t)16 * MX_TX * MX_TY);
+    return sizeof(float) * ((size_t)20 * w.ww * w.wh + (size_t)16 * MX_TX * MX_TY);
 }
 
 cudaError_t mixed_prepare(size_t smem_bytes, int* ctas_per_sm) {

@@ -148,7 +148,8 @@ def max_over_ranks(world, value: float) -> float:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -218,7 +219,7 @@ def run_reference(args, world, rank):
     t0 = time.perf_counter()
     oracle.step(st, None, rows=(0, 1))
     per_row = max(time.perf_counter() - t0, 1e-4)
-    budget = min(15.0, max(0.5, 150.0 / max(args.steps + args.warmup, 1)))
+    budget = min(args.cpu_seconds, max(0.05, 150.0 / max(args.steps + args.warmup, 1)))
     rows = int(max(1, min(ny, budget / per_row)))
     for _ in range(args.warmup):
         oracle.step(st, None, rows=(0, 1))

@@ -59,10 +59,9 @@ __device__ __noinline__ float stencil_global(const MixedArgs& A, const GridDesc&
     const int x0 = wrap_idx((long long)X + (long long)fx - 1, G.nx);
     const int y0 = wrap_idx((long long)Y + (long long)fy - 1, G.ny);
     const double inv = 1.0 / st;
-    float acc = 0.0f;
+    float gv[4][4];
     for (int jy = 0; jy < 4; ++jy) {
         const int sy = wrap_inc(y0, jy, G.ny);
-        float rowacc = 0.0f;
         for (int jx = 0; jx < 4; ++jx) {
             const int sx = wrap_inc(x0, jx, G.nx);
             const long long s = base + (long long)sy * G.nx + sx;
@@ -84,11 +83,18 @@ __device__ __noinline__ float stencil_global(const MixedArgs& A, const GridDesc&
                 for (int b = 0; b < 4; ++b) h = fmaf(gy[b], A.in.f[(4 * a + b) * A.plane + s], h);
                 g = fmaf(gx[a], h, g);
             }
-            rowacc = fmaf(lxw[jx], g, rowacc);
+            gv[jy][jx] = g;
         }
+    }
+    // reconstruction relative to the node nearest the departure point
+    const float gref = gv[1][1];
+    float acc = 0.0f;
+    for (int jy = 0; jy < 4; ++jy) {
+        float rowacc = 0.0f;
+        for (int jx = 0; jx < 4; ++jx) rowacc = fmaf(lxw[jx], gv[jy][jx] - gref, rowacc);
         acc = fmaf(lyw[jy], rowacc, acc);
     }
-    return acc;
+    return acc + gref;
 }
 
 // Final part of a node update: re-express the last pass's populations (in
@@ -145,12 +151,37 @@ __device__ __noinline__ void finish_node(const MixedArgs& A, float* s_acc, int N
             }
         }
     }
+    // BGK in FP32, kept exactly conservative: the relaxed non-equilibrium
+    // part n = f - rho W is first stripped of its mass, momentum and energy
+    // moments (W-weighted projection; the D2Q16 Gram matrix of {1, c_x, c_y,
+    // |c|^2} under W is [[1,0,0,2],[0,1,0,0],[0,0,1,0],[2,0,0,8]] at T_L = 1,
+    // whose dual basis is W(2 - |c|^2/2), W c_x, W c_y, W(|c|^2/4 - 1/2)).  In
+    // exact arithmetic at the fixed point those moments are zero and this is
+    // the plain f + 2 beta (rho W - f) of Eq. postcollision; in FP32 their
+    // rounding would otherwise act on each advected parcel the same way step
+    // after step and drift its mass and temperature.
+    float M0 = 0.0f, M1 = 0.0f, M2 = 0.0f, M3 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int k = q >> 2, l = q & 3;
+        const float n = fmaf(-rho, L.w[k] * L.w[l], s_acc[q * NT + tid]);
+        M0 += n;
+        M1 = fmaf(L.c[k], n, M1);
+        M2 = fmaf(L.c[l], n, M2);
+        M3 = fmaf(fmaf(L.c[k], L.c[k], L.c[l] * L.c[l]), n, M3);
+    }
     const float two_beta = (float)(2.0 * A.P.beta);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
+        const int k = q >> 2, l = q & 3;
+        const float Wq = L.w[k] * L.w[l];
+        const float c2 = fmaf(L.c[k], L.c[k], L.c[l] * L.c[l]);
         const float a = s_acc[q * NT + tid];
-        const float feq = rho * (L.w[q >> 2] * L.w[q & 3]);
-        A.out.f[q * A.plane + node] = fmaf(two_beta, feq - a, a);
+        float n = fmaf(-rho, Wq, a);
+        const float proj = fmaf(M0, fmaf(-0.5f, c2, 2.0f),
+                                fmaf(M1, L.c[k], fmaf(M2, L.c[l], M3 * fmaf(0.25f, c2, -0.5f))));
+        n = fmaf(-Wq, proj, n);
+        A.out.f[q * A.plane + node] = fmaf(-two_beta, n, a);
     }
     A.out.ux[node] = ux;
     A.out.uy[node] = uy;
@@ -349,42 +380,55 @@ __global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(M
                             il[a] = (a == l) ? 1.0f : 0.0f;
                         }
                         const float d3k = L.d3[k], d3l = L.d3[l];
+                        // one (population, source) pair: (G f_s)_q with the
+                        // source's tile-relative gauge offset
+                        auto pair = [&](int jx, int jy) -> float {
+                            const int si = (row + jy) * ww + col + jx;
+                            const float4 g4 = s_g4[si];
+                            const float r = fmaf(g4.x, invf, bst);   // s_s/s' - 1
+                            const float dx = fmaf(g4.y, invf, bux);  // (u_s,x - u'_x)/s'
+                            const float dy = fmaf(g4.z, invf, buy);
+                            float gx[4], gy[4];
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) {
+                                const float de = fmaf(L.c[a], r, dx);
+                                gx[a] = fmaf(fmaf(fmaf(d3k, de, d2k[a]), de, d1k[a]), de, ik[a]);
+                            }
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) {
+                                const float de = fmaf(L.c[b], r, dy);
+                                gy[b] = fmaf(fmaf(fmaf(d3l, de, d2l[b]), de, d1l[b]), de, il[b]);
+                            }
+                            float gsum = 0.0f;
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) {
+                                const float4 f4 = s_f4[a * WN + si];
+                                float h = gy[0] * f4.x;
+                                h = fmaf(gy[1], f4.y, h);
+                                h = fmaf(gy[2], f4.z, h);
+                                h = fmaf(gy[3], f4.w, h);
+                                gsum = fmaf(gx[a], h, gsum);
+                            }
+                            return gsum;
+                        };
+                        // reconstruction relative to the stencil node nearest
+                        // the departure point: the weights sum to one exactly,
+                        // so their FP32 rounding multiplies only differences
+                        // (otherwise it acts coherently on each advected parcel
+                        // step after step)
+                        const float gref = pair(1, 1);
                         acc = 0.0f;
 #pragma unroll
                         for (int jy = 0; jy < 4; ++jy) {
                             float rowacc = 0.0f;
 #pragma unroll
                             for (int jx = 0; jx < 4; ++jx) {
-                                const int si = (row + jy) * ww + col + jx;
-                                const float4 g4 = s_g4[si];
-                                const float r = fmaf(g4.x, invf, bst);   // s_s/s' - 1
-                                const float dx = fmaf(g4.y, invf, bux);  // (u_s,x - u'_x)/s'
-                                const float dy = fmaf(g4.z, invf, buy);
-                                float gx[4], gy[4];
-#pragma unroll
-                                for (int a = 0; a < 4; ++a) {
-                                    const float de = fmaf(L.c[a], r, dx);
-                                    gx[a] = fmaf(fmaf(fmaf(d3k, de, d2k[a]), de, d1k[a]), de, ik[a]);
-                                }
-#pragma unroll
-                                for (int b = 0; b < 4; ++b) {
-                                    const float de = fmaf(L.c[b], r, dy);
-                                    gy[b] = fmaf(fmaf(fmaf(d3l, de, d2l[b]), de, d1l[b]), de, il[b]);
-                                }
-                                float gsum = 0.0f;
-#pragma unroll
-                                for (int a = 0; a < 4; ++a) {
-                                    const float4 f4 = s_f4[a * WN + si];
-                                    float h = gy[0] * f4.x;
-                                    h = fmaf(gy[1], f4.y, h);
-                                    h = fmaf(gy[2], f4.z, h);
-                                    h = fmaf(gy[3], f4.w, h);
-                                    gsum = fmaf(gx[a], h, gsum);
-                                }
-                                rowacc = fmaf(lxw[jx], gsum, rowacc);
+                                if (jx == 1 && jy == 1) continue;
+                                rowacc = fmaf(lxw[jx], pair(jx, jy) - gref, rowacc);
                             }
                             acc = fmaf(lyw[jy], rowacc, acc);
                         }
+                        acc += gref;
                     } else {
                         acc = stencil_global(A, G, base, X, Y, fx, fy, lxw, lyw, k, l, ux, uy, st);
                         ++fallbacks;

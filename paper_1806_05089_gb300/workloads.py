@@ -13,8 +13,9 @@ App. D, and its compressible advected flows):
 2. ``supersonic``    N x N (2048 at scale), uniform u = (1.5, 0.5), rho and T
                      = 1 + a sum of 8 seeded sinusoids (0.1/8 each, integer
                      wavenumbers 1..8)
-3. ``precision``     N x N (4096 at scale), same rho and u, T = 2^s with s a
-                     normalised sum of 8 seeded sinusoids (T in [0.5, 2])
+3. ``precision``     N x N (4096 at scale), same u, T = 2^s with s a
+                     normalised sum of 8 seeded sinusoids (T in [0.5, 2]) at
+                     constant pressure: rho = (1 + the 8-mode perturbation) / T
 4. ``adjoint``       512 x 512 Taylor-Green u0 = 0.3 plus a Gaussian density
                      pulse (amplitude 0.2, sigma 16), and a seeded target
 5. ``ensemble``      256 grids with sides in 32..512, Mach 0..3 in a random
@@ -96,12 +97,15 @@ def supersonic(n: int = 2048, nx: int | None = None, ny: int | None = None) -> F
 
 
 def precision(n: int = 4096) -> Fields:
+    """T = 2^s (ratio 4 across the field) at constant pressure: rho = (1 +
+    the 8-mode perturbation) / T, so the temperature variation is an advected
+    entropy mode rather than a pressure jump that would steepen into shocks."""
     g = rng(3)
-    rho = 1.0 + (0.1 / 8.0) * sinusoids(n, n, g)
+    pert = 1.0 + (0.1 / 8.0) * sinusoids(n, n, g)
     s = sinusoids(n, n, g)
     s /= np.abs(s).max()
     T = np.exp2(s)
-    return Fields(rho, np.full((n, n), 1.5), np.full((n, n), 0.5), T)
+    return Fields(pert / T, np.full((n, n), 1.5), np.full((n, n), 0.5), T)
 
 
 def adjoint(n: int = 512):

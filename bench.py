@@ -200,6 +200,7 @@ def form_line(name, nodes, steps, secs, stats, precision_peak_tflops, bytes_per_
         "max_passes": stats["max_passes"],
         "nonconverged": stats["nonconverged"],
         "halo_fallback": stats.get("halo_fallback", 0),
+        "tile": [32, stats.get("tile_rows", 0)],
         "alu_tflops": achieved,
         "alu_frac": achieved / precision_peak_tflops,
         "hbm_gbs_algorithmic": nodes * steps * bytes_per_update / secs / 1e9,
@@ -330,7 +331,8 @@ def run_pond(args, world, rank, local):
     if not args.no_forms:
         forms = {}
         k2 = max(args.steps, 10)
-        msim = pond.Sim(nx, ny, pond.POND_FP32_MIXED, stream=stream.cuda_stream, use_graph=1)
+        msim = pond.Sim(nx, ny, pond.POND_FP32_MIXED, stream=stream.cuda_stream, use_graph=1,
+                        autotune=1)
         msim.set_state(fields.rho, fields.ux, fields.uy, fields.T)
         msim.step(args.warmup)
         msecs, mstats = time_steps(msim, stream, args.steps)
@@ -348,7 +350,8 @@ def run_pond(args, world, rank, local):
         msim.close()
 
         pf = workloads.precision(4096)
-        psim = pond.Sim(4096, 4096, pond.POND_FP32_MIXED, stream=stream.cuda_stream, use_graph=1)
+        psim = pond.Sim(4096, 4096, pond.POND_FP32_MIXED, stream=stream.cuda_stream, use_graph=1,
+                        autotune=1)
         psim.set_state(pf.rho, pf.ux, pf.uy, pf.T)
         psim.step(args.warmup)
         psecs, pstats = time_steps(psim, stream, k2)
@@ -359,7 +362,8 @@ def run_pond(args, world, rank, local):
 
         nxs, nys = workloads.ensemble_sizes(256)
         members = workloads.ensemble(256)
-        bsim = pond.Sim(nxs, nys, pond.POND_FP32_MIXED, stream=stream.cuda_stream, use_graph=1)
+        bsim = pond.Sim(nxs, nys, pond.POND_FP32_MIXED, stream=stream.cuda_stream, use_graph=1,
+                        autotune=1)
         for i, m in enumerate(members):
             bsim.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
         bnodes = int(sum(a * b for a, b in zip(nxs, nys)))
@@ -389,6 +393,25 @@ def run_pond(args, world, rank, local):
                                 "forward_s": t1 - t0, "backward_s": t2 - t1,
                                 "adjoint_over_forward": (t2 - t1) / (t1 - t0),
                                 "nu_grad": float(n.grad), "loss": float(loss.detach())}
+        g64 = r.grad.detach().clone()
+        r32 = torch.tensor(af.rho, device=dev, requires_grad=True)
+        n32 = torch.tensor(0.01, dtype=torch.float64, device=dev, requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rho32 = pond_rollout(r32, n32, *gauge, 200, 20, precision=pond.POND_FP32_MIXED)
+        loss32 = 0.5 * ((rho32 - tgt) ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss32.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        forms["adjoint_512_mixed"] = {
+            "workload": "adjoint-512-mixed", "steps": 200, "ckpt_every": 20,
+            "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "adjoint_over_forward": (t2 - t1) / (t1 - t0),
+            "grad_rel_err_vs_fp64": float((r32.grad - g64).abs().max() / g64.abs().max()),
+            "nu_grad_rel_err_vs_fp64": abs(float(n32.grad) - float(n.grad)) / abs(float(n.grad)),
+            "backward_speedup_vs_fp64": forms["adjoint_512"]["backward_s"] / (t2 - t1)}
         line["forms"] = forms
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1)

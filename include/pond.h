@@ -87,6 +87,13 @@ typedef struct pond_config {
     int32_t use_graph;  /* 1: pond_step replays a CUDA graph of two steps
                            (captured on first use, re-captured after
                            set_state / set_stream) */
+    int32_t autotune;   /* 1 (mixed form): the first pond_step times the
+                           kernel's tile shapes (32 x 4, 32 x 8, 32 x 16
+                           nodes) on the current state, without advancing it,
+                           and keeps the fastest.  Results are cached per
+                           process by grid-set signature and, when the
+                           environment variable POND_AUTOTUNE_CACHE names a
+                           file, in that JSON file across processes. */
 } pond_config;
 
 /* Counters accumulated over the steps of one pond_step call. */
@@ -94,7 +101,8 @@ typedef struct pond_stats {
     int64_t node_updates;  /* nodes x steps */
     int64_t passes;        /* predictor-corrector passes over all node updates */
     int32_t max_passes;    /* largest pass count at any node */
-    int32_t reserved;
+    int32_t tile_rows;     /* rows of the mixed kernel's tile shape in use
+                              (32 columns); 0 for the FP64 form */
     int64_t nonconverged;  /* node updates that hit max_iter unconverged */
     int64_t nonphysical;   /* node updates that met rho <= 0, T <= 0 or NaN */
     int64_t halo_fallback; /* stencils read from global memory instead of the
@@ -157,7 +165,9 @@ pond_status pond_iterations(pond_ctx* ctx, int32_t grid, void* iters, int32_t on
  * (same layouts) and adds d(loss)/d(nu) to *nu_bar_accum.  The fixed point
  * is differentiated implicitly (the limit gauge of Eqs. density..T is a
  * function of the input state only; the seed gets no gradient).  All array
- * pointers are device pointers.  The state is left unchanged.
+ * pointers are device pointers.  The state is left unchanged.  FP64 and
+ * mixed contexts (the latter with FP32 pair arithmetic and an FP64 3 x 3
+ * solve); single-grid, thermal mode.
  * Errors: POND_ERR_ARG, POND_ERR_STATE, POND_ERR_OOM, POND_ERR_CUDA. */
 pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in, const void* gauge_bar_in,
                               void* f_bar_out, void* gauge_bar_out, double* nu_bar_accum);

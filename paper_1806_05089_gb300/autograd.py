@@ -9,8 +9,9 @@ implicit differentiation of the predictor-corrector fixed point, transposed
 reconstruction and gauge transform, BGK collision) and finally
 ``pond_adjoint_init``.  Gradients are returned for rho0 and nu.
 
-All tensors are CUDA float64; every step of the forward and backward runs in
-libpond.so.
+All tensors are CUDA float64 (the boundary is FP64 for both forms); pass
+``precision=pond.POND_FP32_MIXED`` to run the forward and the adjoint in the
+mixed form.  Every step of the forward and backward runs in libpond.so.
 """
 from __future__ import annotations
 
@@ -42,7 +43,8 @@ class PondRollout(torch.autograd.Function):
         dev = rho0.device
         stream = torch.cuda.current_stream(dev).cuda_stream
         cfg = dict(overrides or {})
-        sim = pond.Sim(nx, ny, pond.POND_FP64, stream=stream, nu=float(nu), **cfg)
+        precision = cfg.pop("precision", pond.POND_FP64)
+        sim = pond.Sim(nx, ny, precision, stream=stream, nu=float(nu), **cfg)
         pond.pond_set_state(sim.ctx, 0, rho0.contiguous(), ux0.contiguous(), uy0.contiguous(),
                             T0.contiguous(), None)
         ckpts = []
@@ -94,8 +96,9 @@ class PondRollout(torch.autograd.Function):
 
 
 def pond_rollout(rho0, nu, ux0, uy0, T0, steps: int, ckpt_every: int = 20, **overrides):
-    """Final density after ``steps`` FP64 PonD steps (differentiable in rho0
-    and nu).  ``nu`` may be a float or a 0-d tensor."""
+    """Final density after ``steps`` PonD steps (differentiable in rho0 and
+    nu).  ``nu`` may be a float or a 0-d tensor; ``overrides`` are config
+    fields (and ``precision``)."""
     if not torch.is_tensor(nu):
         nu = torch.tensor(float(nu), dtype=torch.float64, device=rho0.device)
     return PondRollout.apply(rho0, nu, ux0, uy0, T0, steps, ckpt_every, overrides or None)

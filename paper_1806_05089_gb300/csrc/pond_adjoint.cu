@@ -352,6 +352,12 @@ __global__ void k_minmax3(const double* ux, const double* uy, const double* st, 
     }
 }
 
+cudaError_t launch_minmax3(const double* ux, const double* uy, const double* st, long long N,
+                           double* out6, cudaStream_t s) {
+    k_minmax3<<<1, 1024, 0, s>>>(ux, uy, st, N, out6);
+    return cudaGetLastError();
+}
+
 __global__ void k_rho_bar(const double* __restrict__ fbar, double* __restrict__ rbar, long long N) {
     const Lattice& L = c_La;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -401,8 +407,8 @@ extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in,
         ctx->err = "adjoint: NULL argument";
         return POND_ERR_ARG;
     }
-    if (ctx->n_grids != 1 || ctx->cfg.precision != POND_FP64 || !ctx->cfg.thermal) {
-        ctx->err = "adjoint: single-grid FP64 thermal contexts only";
+    if (ctx->n_grids != 1 || !ctx->cfg.thermal) {
+        ctx->err = "adjoint: single-grid thermal contexts only";
         return POND_ERR_ARG;
     }
     if (!ctx->grid_set[0]) {
@@ -420,21 +426,39 @@ extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in,
     } restore{prev, ctx->device};
 
     const int64_t N = ctx->N;
+    const bool fp64 = ctx->cfg.precision == POND_FP64;
     if (!ctx->adj) {
         AdjointScratch* a = new AdjointScratch();
         ctx->adj = a;
         a->N = N;
-        ACK(cudaMalloc(&a->fwd.f, sizeof(double) * 16 * N), "adjoint alloc");
-        ACK(cudaMalloc(&a->fwd.ux, sizeof(double) * N), "adjoint alloc");
-        ACK(cudaMalloc(&a->fwd.uy, sizeof(double) * N), "adjoint alloc");
-        ACK(cudaMalloc(&a->fwd.st, sizeof(double) * N), "adjoint alloc");
-        ACK(cudaMalloc(&a->w, sizeof(double) * 16 * N), "adjoint alloc");
-        ACK(cudaMalloc(&a->iters, sizeof(int32_t) * N), "adjoint alloc");
-        ACK(cudaMalloc(&a->stats, sizeof(DevStats)), "adjoint alloc");
         ACK(cudaMalloc(&a->beta_bar, sizeof(double)), "adjoint alloc");
         ACK(cudaMalloc(&a->minmax, sizeof(double) * 6), "adjoint alloc");
+        if (fp64) {
+            ACK(cudaMalloc(&a->fwd.f, sizeof(double) * 16 * N), "adjoint alloc");
+            ACK(cudaMalloc(&a->fwd.ux, sizeof(double) * N), "adjoint alloc");
+            ACK(cudaMalloc(&a->fwd.uy, sizeof(double) * N), "adjoint alloc");
+            ACK(cudaMalloc(&a->fwd.st, sizeof(double) * N), "adjoint alloc");
+            ACK(cudaMalloc(&a->w, sizeof(double) * 16 * N), "adjoint alloc");
+            ACK(cudaMalloc(&a->iters, sizeof(int32_t) * N), "adjoint alloc");
+            ACK(cudaMalloc(&a->stats, sizeof(DevStats)), "adjoint alloc");
+        }
     }
     AdjointScratch* a = ctx->adj;
+    if (!fp64) {
+        // FP32 populations: pond_adjoint_mixed.cu
+        ACK(adjoint_step_mixed(ctx, static_cast<const double*>(f_bar_in),
+                               static_cast<const double*>(gauge_bar_in),
+                               static_cast<double*>(f_bar_out), static_cast<double*>(gauge_bar_out),
+                               a->beta_bar, a->minmax, a->host_minmax),
+            "adjoint (mixed)");
+        double bbm = 0.0;
+        ACK(cudaMemcpyAsync(&bbm, a->beta_bar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+            "adjoint copy");
+        ACK(cudaStreamSynchronize(ctx->stream), "adjoint sync");
+        const double beta = ctx->P.beta;
+        *nu_bar_accum += bbm * (-2.0 * beta * beta / (ctx->cfg.T_ref * ctx->cfg.dt));
+        return POND_OK;
+    }
     const GridDesc& G = ctx->grids_host[0];
     StateBuf<double> in;
     in.f = static_cast<double*>(ctx->f[ctx->cur]);

@@ -1,0 +1,419 @@
+// pond_adjoint_mixed.cu -- vector-Jacobian product of one PonD step for
+// mixed-precision contexts (FP32 populations, FP64 gauges).
+//
+// Same mathematics as pond_adjoint.cu (implicit differentiation of the
+// predictor-corrector fixed point, 3 x 3 solve per node, gather-form
+// transpose of the reconstruction and gauge transform, BGK collision); the
+// per-pair arithmetic runs in FP32.  Gauge differences u_s - u' are formed
+// from per-node (hi, lo) FP32 splits of the FP64 gauges,
+// (hi_s - hi') + (lo_s - lo'), which carries FP32 precision relative to the
+// difference itself; the 3 x 3 solve and the collision cotangents use FP64.
+#include <cmath>
+
+#include "pond_device.cuh"
+
+namespace pond {
+
+__constant__ LatticeF c_Lam;
+
+cudaError_t upload_lattice_adjoint_mixed(const Lattice& L) {
+    const LatticeF F = to_float(L);
+    return cudaMemcpyToSymbol(c_Lam, &F, sizeof(LatticeF));
+}
+
+struct AdjMixedScratch {
+    StateBuf<float> fwd{};
+    float* w = nullptr;       // [16][N]
+    float4* gin = nullptr;    // [2][N]: hi / lo splits of the input gauge (s, ux, uy, 0)
+    float4* gstar = nullptr;  // [2][N]: hi / lo splits of lambda*
+    int32_t* iters = nullptr;
+    DevStats* stats = nullptr;
+};
+
+__global__ void k_split_gauge(const double* __restrict__ ux, const double* __restrict__ uy,
+                              const double* __restrict__ st, float4* __restrict__ out,
+                              long long N) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double v[3] = {st[i], ux[i], uy[i]};
+    float hi[3], lo[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        hi[j] = (float)v[j];
+        lo[j] = (float)(v[j] - (double)hi[j]);
+    }
+    out[i] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+    out[N + i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+}
+
+__device__ __forceinline__ void lagrange4_df(float t, float l[4], float dl[4]) {
+    const float a = t, b = t - 1.0f, c = t - 2.0f, d = t - 3.0f;
+    l[0] = -(b * c * d) * (1.0f / 6.0f);
+    l[1] = (a * c * d) * 0.5f;
+    l[2] = -(a * b * d) * 0.5f;
+    l[3] = (a * b * c) * (1.0f / 6.0f);
+    dl[0] = -(c * d + b * d + b * c) * (1.0f / 6.0f);
+    dl[1] = (c * d + a * d + a * c) * 0.5f;
+    dl[2] = -(b * d + a * d + a * b) * 0.5f;
+    dl[3] = (b * c + a * c + a * b) * (1.0f / 6.0f);
+}
+
+__device__ __forceinline__ void lag_taylor_f(const LatticeF& L, int k, int a, float de, float& g,
+                                            float& gd) {
+    const float d1 = L.d1[k][a], d2 = L.d2[k][a], d3 = L.d3[k];
+    g = fmaf(fmaf(fmaf(d3, de, d2), de, d1), de, (k == a) ? 1.0f : 0.0f);
+    gd = fmaf(fmaf(3.0f * d3, de, 2.0f * d2), de, d1);
+}
+
+// difference of two split values: (hi_a - hi_b) + (lo_a - lo_b)
+__device__ __forceinline__ float sdiff(float ha, float la, float hb, float lb) {
+    return (ha - hb) + (la - lb);
+}
+
+struct AdjMixedArgs {
+    const float* f_in;       // input populations [16][N]
+    const float4* gin;       // splits of the input gauge
+    const float4* gstar;     // splits of lambda*
+    const double* st_in;     // input sqrt(theta) (FP64, for the T cotangent)
+    const double* st_star;
+    const double* fbar;      // [16][N]
+    const double* gbar;      // [3][N]
+    float* w;                // [16][N]
+    double* fbar_in;
+    double* gbar_in;
+    double* beta_bar;
+    int nx, ny;
+    long long N;
+    float beta, dt, T_L;
+    float vlo_x[4], vhi_x[4], vlo_y[4], vhi_y[4];
+};
+
+constexpr int ADJM_WARPS = 4;
+
+__global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(AdjMixedArgs A) {
+    const LatticeF& L = c_Lam;
+    const int lane = threadIdx.x & 31;
+    const long long node = (long long)blockIdx.x * ADJM_WARPS + (threadIdx.x >> 5);
+    if (node >= A.N) return;  // warp-uniform
+    const int X = (int)(node % A.nx), Y = (int)(node / A.nx);
+    const int q = lane & 15, k = q >> 2, l = q & 3, half = lane >> 4;
+    const float ck = L.c[k], cl = L.c[l];
+    const float4 th = A.gstar[node], tl = A.gstar[A.N + node];  // (s, ux, uy)
+    const float st = th.x + tl.x, ux = th.y + tl.y, uy = th.z + tl.z;
+    const float inv = 1.0f / st;
+
+    // departure of population q at lambda*, relative to the node
+    const float frx = -fmaf(st, ck, ux) * A.dt, fry = -fmaf(st, cl, uy) * A.dt;
+    const float flx = floorf(frx), fly = floorf(fry);
+    float lx[4], dlx[4], ly[4], dly[4];
+    lagrange4_df(frx - flx + 1.0f, lx, dlx);
+    lagrange4_df(fry - fly + 1.0f, ly, dly);
+    const int x0 = wrap_idx((long long)X + (long long)flx - 1, A.nx);
+    const int y0 = wrap_idx((long long)Y + (long long)fly - 1, A.ny);
+
+    float Aq = 0.0f, dAux = 0.0f, dAuy = 0.0f, dAst = 0.0f;
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+        const int jy = 2 * half + jj;
+        const float wy = half ? ly[2 + jj] : ly[jj];
+        const float dwy = half ? dly[2 + jj] : dly[jj];
+        const int sy = wrap_inc(y0, jy, A.ny);
+#pragma unroll
+        for (int jx = 0; jx < 4; ++jx) {
+            const int sx = wrap_inc(x0, jx, A.nx);
+            const long long s = (long long)sy * A.nx + sx;
+            const float4 sh = A.gin[s], sl = A.gin[A.N + s];
+            const float r = sdiff(sh.x, sl.x, th.x, tl.x) * inv;
+            const float dx = sdiff(sh.y, sl.y, th.y, tl.y) * inv;
+            const float dy = sdiff(sh.z, sl.z, th.z, tl.z) * inv;
+            float gx[4], gdx[4], gy[4], gdy[4], xix[4], xiy[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float ex = fmaf(L.c[a], r, dx), ey = fmaf(L.c[a], r, dy);
+                xix[a] = L.c[a] + ex;
+                xiy[a] = L.c[a] + ey;
+                lag_taylor_f(L, k, a, ex, gx[a], gdx[a]);
+                lag_taylor_f(L, l, a, ey, gy[a], gdy[a]);
+            }
+            float g = 0.0f, gux = 0.0f, guy = 0.0f, gst = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                float h = 0.0f, hp = 0.0f, hq = 0.0f;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const float fv = A.f_in[(long long)(4 * a + b) * A.N + s];
+                    h = fmaf(gy[b], fv, h);
+                    hp = fmaf(gdy[b], fv, hp);
+                    hq = fmaf(gdy[b] * xiy[b], fv, hq);
+                }
+                g = fmaf(gx[a], h, g);
+                gux = fmaf(gdx[a], h, gux);
+                guy = fmaf(gx[a], hp, guy);
+                gst = fmaf(gdx[a] * xix[a], h, fmaf(gx[a], hq, gst));
+            }
+            gux *= -inv;
+            guy *= -inv;
+            gst *= -inv;
+            const float wx = lx[jx], dwx = dlx[jx];
+            const float a_w = wx * wy;
+            const float da_ux = -A.dt * dwx * wy;
+            const float da_uy = -A.dt * wx * dwy;
+            const float da_st = -A.dt * (ck * dwx * wy + cl * wx * dwy);
+            Aq = fmaf(a_w, g, Aq);
+            dAux = fmaf(a_w, gux, fmaf(da_ux, g, dAux));
+            dAuy = fmaf(a_w, guy, fmaf(da_uy, g, dAuy));
+            dAst = fmaf(a_w, gst, fmaf(da_st, g, dAst));
+        }
+    }
+    Aq += __shfl_xor_sync(0xffffffffu, Aq, 16);
+    dAux += __shfl_xor_sync(0xffffffffu, dAux, 16);
+    dAuy += __shfl_xor_sync(0xffffffffu, dAuy, 16);
+    dAst += __shfl_xor_sync(0xffffffffu, dAst, 16);
+
+    auto sum16 = [](double v) {
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
+    const double sd = A.st_star[node];
+    const double Wq = (double)L.w[k] * (double)L.w[l];
+    const double fb = A.fbar[(long long)q * A.N + node];
+    const double Ad = Aq;
+    const double rho = sum16(Ad);
+    const double wf = sum16(Wq * fb);
+    const double beta = A.beta;
+    const double Abar = (1.0 - 2.0 * beta) * fb + 2.0 * beta * wf;
+    const double bb = sum16(2.0 * (rho * Wq - Ad) * fb);
+    const double c2 = (double)ck * ck + (double)cl * cl;
+    const double mux = sd * ck / rho, muy = sd * cl / rho;
+    const double mst = sd * (c2 - 2.0 * A.T_L) / (4.0 * rho * A.T_L);
+    const double d0 = dAux, d1 = dAuy, d2 = dAst;
+    double J[3][3];
+    J[0][0] = sum16(mux * d0);
+    J[0][1] = sum16(mux * d1);
+    J[0][2] = sum16(mux * d2);
+    J[1][0] = sum16(muy * d0);
+    J[1][1] = sum16(muy * d1);
+    J[1][2] = sum16(muy * d2);
+    J[2][0] = sum16(mst * d0);
+    J[2][1] = sum16(mst * d1);
+    J[2][2] = sum16(mst * d2);
+    const double g0 = sum16(Abar * d0) + A.gbar[node];
+    const double g1 = sum16(Abar * d1) + A.gbar[A.N + node];
+    const double g2 = sum16(Abar * d2) + A.gbar[2 * A.N + node] * 2.0 * sd * A.T_L;
+    const double a00 = J[0][0], a01 = J[1][0], a02 = J[2][0];
+    const double a10 = J[0][1], a11 = J[1][1], a12 = J[2][1];
+    const double a20 = J[0][2], a21 = J[1][2], a22 = J[2][2];
+    const double det = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
+                       a02 * (a10 * a21 - a11 * a20);
+    const double idet = 1.0 / det;
+    const double r0 = -g0, r1 = -g1, r2 = -g2;
+    const double mu0 = (r0 * (a11 * a22 - a12 * a21) - a01 * (r1 * a22 - a12 * r2) +
+                        a02 * (r1 * a21 - a11 * r2)) * idet;
+    const double mu1 = (a00 * (r1 * a22 - a12 * r2) - r0 * (a10 * a22 - a12 * a20) +
+                        a02 * (a10 * r2 - r1 * a20)) * idet;
+    const double mu2 = (a00 * (a11 * r2 - r1 * a21) - a01 * (a10 * r2 - r1 * a20) +
+                        r0 * (a10 * a21 - a11 * a20)) * idet;
+    const double wq = Abar + mux * mu0 + muy * mu1 + mst * mu2;
+    if (half == 0) A.w[(long long)q * A.N + node] = (float)wq;
+    if (lane == 0) atomicAdd(A.beta_bar, bb);
+}
+
+__global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_sources_mixed(AdjMixedArgs A) {
+    const LatticeF& L = c_Lam;
+    const int lane = threadIdx.x & 31;
+    const long long src = (long long)blockIdx.x * ADJM_WARPS + (threadIdx.x >> 5);
+    if (src >= A.N) return;  // warp-uniform
+    const int JX = (int)(src % A.nx), JY = (int)(src / A.nx);
+    const int q = lane & 15, k = q >> 2, l = q & 3, half = lane >> 4;
+    const float ck = L.c[k], cl = L.c[l];
+    float fj[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) fj[i] = A.f_in[(long long)i * A.N + src];
+    const float4 jh = A.gin[src], jl = A.gin[A.N + src];
+
+    float fb[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) fb[i] = 0.0f;
+    float bux = 0.0f, buy = 0.0f, bst = 0.0f;
+
+    // candidate targets with floor(x - v dt) in [J - 2, J + 1]
+    const int xlo = (int)floorf((float)JX - 2.0f + A.vlo_x[k] * A.dt) - 1;
+    const int xhi = (int)ceilf((float)JX + 2.0f + A.vhi_x[k] * A.dt) + 1;
+    const int ylo = (int)floorf((float)JY - 2.0f + A.vlo_y[l] * A.dt) - 1;
+    const int yhi = (int)ceilf((float)JY + 2.0f + A.vhi_y[l] * A.dt) + 1;
+    for (int yy = ylo + half; yy <= yhi; yy += 2) {
+        const int ty = wrap_idx(yy, A.ny);
+        for (int xx = xlo; xx <= xhi; ++xx) {
+            const int tx = wrap_idx(xx, A.nx);
+            const long long t = (long long)ty * A.nx + tx;
+            const float4 th = A.gstar[t], tl = A.gstar[A.N + t];
+            const float st = th.x + tl.x, ux = th.y + tl.y, uy = th.z + tl.z;
+            const float frx = -fmaf(st, ck, ux) * A.dt, fry = -fmaf(st, cl, uy) * A.dt;
+            const float flx = floorf(frx), fly = floorf(fry);
+            const int jx = JX - (xx + (int)flx - 1);
+            const int jy = JY - (yy + (int)fly - 1);
+            if (jx < 0 || jx > 3 || jy < 0 || jy > 3) continue;
+            float lx[4], ly[4];
+            lagrange4f(frx - flx + 1.0f, lx);
+            lagrange4f(fry - fly + 1.0f, ly);
+            const float wgt = (jx == 0 ? lx[0] : jx == 1 ? lx[1] : jx == 2 ? lx[2] : lx[3]) *
+                              (jy == 0 ? ly[0] : jy == 1 ? ly[1] : jy == 2 ? ly[2] : ly[3]);
+            const float coef = A.w[(long long)q * A.N + t] * wgt;
+            const float inv = 1.0f / st;
+            const float r = sdiff(jh.x, jl.x, th.x, tl.x) * inv;
+            const float dx = sdiff(jh.y, jl.y, th.y, tl.y) * inv;
+            const float dy = sdiff(jh.z, jl.z, th.z, tl.z) * inv;
+            float gx[4], gdx[4], gy[4], gdy[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                lag_taylor_f(L, k, a, fmaf(L.c[a], r, dx), gx[a], gdx[a]);
+                lag_taylor_f(L, l, a, fmaf(L.c[a], r, dy), gy[a], gdy[a]);
+            }
+            float sux = 0.0f, suy = 0.0f, sst = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float cgx = coef * gx[a];
+                float h = 0.0f, hp = 0.0f, hq = 0.0f;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    fb[4 * a + b] = fmaf(cgx, gy[b], fb[4 * a + b]);
+                    const float fv = fj[4 * a + b];
+                    h = fmaf(gy[b], fv, h);
+                    hp = fmaf(gdy[b], fv, hp);
+                    hq = fmaf(gdy[b] * L.c[b], fv, hq);
+                }
+                sux = fmaf(gdx[a], h, sux);
+                suy = fmaf(gx[a], hp, suy);
+                sst = fmaf(gdx[a] * L.c[a], h, fmaf(gx[a], hq, sst));
+            }
+            const float ci = coef * inv;
+            bux = fmaf(ci, sux, bux);
+            buy = fmaf(ci, suy, buy);
+            bst = fmaf(ci, sst, bst);
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) fb[i] += __shfl_xor_sync(0xffffffffu, fb[i], o);
+        bux += __shfl_xor_sync(0xffffffffu, bux, o);
+        buy += __shfl_xor_sync(0xffffffffu, buy, o);
+        bst += __shfl_xor_sync(0xffffffffu, bst, o);
+    }
+    if (lane < 16) {
+        float v = fb[0];
+#pragma unroll
+        for (int i = 1; i < 16; ++i)
+            if (lane == i) v = fb[i];
+        A.fbar_in[(long long)lane * A.N + src] = (double)v;
+    } else if (lane == 16) {
+        A.gbar_in[src] = (double)bux;
+    } else if (lane == 17) {
+        A.gbar_in[A.N + src] = (double)buy;
+    } else if (lane == 18) {
+        A.gbar_in[2 * A.N + src] = (double)bst / (2.0 * A.st_in[src] * (double)A.T_L);
+    }
+}
+
+}  // namespace pond
+
+using namespace pond;
+
+void destroy_adjoint_mixed(pond_ctx* ctx) {
+    AdjMixedScratch* a = ctx->adjm;
+    if (!a) return;
+    cudaFree(a->fwd.f);
+    cudaFree(a->fwd.ux);
+    cudaFree(a->fwd.uy);
+    cudaFree(a->fwd.st);
+    cudaFree(a->w);
+    cudaFree(a->gin);
+    cudaFree(a->gstar);
+    cudaFree(a->iters);
+    cudaFree(a->stats);
+    delete a;
+    ctx->adjm = nullptr;
+}
+
+// Mixed-precision adjoint step; arguments already validated by
+// pond_adjoint_step.  bounds6 = {min ux*, max ux*, min uy*, max uy*, min s*,
+// max s*} of the forward gauge is filled by the caller's bounds pass.
+cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* fbar, const double* gbar,
+                               double* fbar_out, double* gbar_out, double* beta_bar_dev,
+                               double* minmax_dev, double* minmax_host) {
+    const int64_t N = ctx->N;
+    cudaStream_t s = ctx->stream;
+    cudaError_t e;
+    if (!ctx->adjm) {
+        AdjMixedScratch* a = new AdjMixedScratch();
+        ctx->adjm = a;
+        if ((e = cudaMalloc(&a->fwd.f, sizeof(float) * 16 * N)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->fwd.ux, sizeof(double) * N)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->fwd.uy, sizeof(double) * N)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->fwd.st, sizeof(double) * N)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->w, sizeof(float) * 16 * N)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->gin, sizeof(float4) * 2 * N)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->gstar, sizeof(float4) * 2 * N)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->iters, sizeof(int32_t) * N)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->stats, sizeof(DevStats))) != cudaSuccess) return e;
+    }
+    AdjMixedScratch* a = ctx->adjm;
+    StateBuf<float> in;
+    in.f = static_cast<float*>(ctx->f[ctx->cur]);
+    in.ux = ctx->ux[ctx->cur];
+    in.uy = ctx->uy[ctx->cur];
+    in.st = ctx->st[ctx->cur];
+    // 1. forward step into scratch: its gauge is the fixed point lambda*
+    e = launch_step_mixed(in, a->fwd, a->iters, a->stats, ctx->grids_dev, ctx->tile_prefix_dev,
+                          1, ctx->n_tiles, N, nullptr, ctx->win, ctx->persistent_ctas, ctx->L,
+                          ctx->P, s);
+    if (e != cudaSuccess) return e;
+    const unsigned nb256 = (unsigned)((N + 255) / 256);
+    k_split_gauge<<<nb256, 256, 0, s>>>(in.ux, in.uy, in.st, a->gin, N);
+    k_split_gauge<<<nb256, 256, 0, s>>>(a->fwd.ux, a->fwd.uy, a->fwd.st, a->gstar, N);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_minmax3(a->fwd.ux, a->fwd.uy, a->fwd.st, N, minmax_dev, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(minmax_host, minmax_dev, sizeof(double) * 6, cudaMemcpyDeviceToHost,
+                             s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(beta_bar_dev, 0, sizeof(double), s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+
+    const GridDesc& G = ctx->grids_host[0];
+    AdjMixedArgs A;
+    A.f_in = in.f;
+    A.gin = a->gin;
+    A.gstar = a->gstar;
+    A.st_in = in.st;
+    A.st_star = a->fwd.st;
+    A.fbar = fbar;
+    A.gbar = gbar;
+    A.w = a->w;
+    A.fbar_in = fbar_out;
+    A.gbar_in = gbar_out;
+    A.beta_bar = beta_bar_dev;
+    A.nx = G.nx;
+    A.ny = G.ny;
+    A.N = N;
+    A.beta = (float)ctx->P.beta;
+    A.dt = (float)ctx->P.dt;
+    A.T_L = (float)ctx->L.T_L;
+    const double* mm = minmax_host;
+    for (int i = 0; i < 4; ++i) {
+        const double c = ctx->L.c[i];
+        const double slo = c >= 0 ? c * mm[4] : c * mm[5];
+        const double shi = c >= 0 ? c * mm[5] : c * mm[4];
+        // one cell of slack for the FP32 departures
+        A.vlo_x[i] = (float)(slo + mm[0]) - 1.0f;
+        A.vhi_x[i] = (float)(shi + mm[1]) + 1.0f;
+        A.vlo_y[i] = (float)(slo + mm[2]) - 1.0f;
+        A.vhi_y[i] = (float)(shi + mm[3]) + 1.0f;
+    }
+    const unsigned nb = (unsigned)((N + ADJM_WARPS - 1) / ADJM_WARPS);
+    k_adjoint_targets_mixed<<<nb, ADJM_WARPS * 32, 0, s>>>(A);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_adjoint_sources_mixed<<<nb, ADJM_WARPS * 32, 0, s>>>(A);
+    return cudaGetLastError();
+}

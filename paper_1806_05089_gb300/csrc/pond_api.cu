@@ -2,7 +2,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 
 #include "pond_internal.cuh"
 
@@ -71,6 +76,26 @@ pond_status ensure_staging(pond_ctx* ctx, int64_t nodes) {
     return POND_OK;
 }
 
+// Tile count and per-grid prefix of the mixed kernel for a tile of
+// MIXED_TX x ty nodes (uploaded to the device).
+pond_status set_tile_rows(pond_ctx* ctx, int ty) {
+    std::vector<int64_t> prefix(ctx->n_grids + 1, 0);
+    int64_t tiles = 0;
+    for (int g = 0; g < ctx->n_grids; ++g) {
+        prefix[g] = tiles;
+        const GridDesc& G = ctx->grids_host[g];
+        tiles += (int64_t)((G.nx + MIXED_TX - 1) / MIXED_TX) * ((G.ny + ty - 1) / ty);
+    }
+    prefix[ctx->n_grids] = tiles;
+    CK(cudaMemcpyAsync(ctx->tile_prefix_dev, prefix.data(), sizeof(int64_t) * (ctx->n_grids + 1),
+                       cudaMemcpyHostToDevice, ctx->stream),
+       "tile prefix upload");
+    CK(cudaStreamSynchronize(ctx->stream), "tile prefix sync");
+    ctx->n_tiles = tiles;
+    ctx->tile_ty = ty;
+    return POND_OK;
+}
+
 // Window of the mixed kernel from the per-grid velocity spans.
 pond_status update_window(pond_ctx* ctx) {
     if (!mixed(ctx)) return POND_OK;
@@ -84,18 +109,18 @@ pond_status update_window(pond_ctx* ctx) {
     const double dt = ctx->cfg.dt, margin = 1.0;
     TileWindow w;
     w.tx = MIXED_TX;
-    w.ty = MIXED_TY;
-    w.ww = MIXED_TX + (int)std::ceil(sx * dt + 2 * margin) + 5;
-    w.wh = MIXED_TY + (int)std::ceil(sy * dt + 2 * margin) + 5;
+    w.ty = ctx->tile_ty;
+    w.ww = w.tx + (int)std::ceil(sx * dt + 2 * margin) + 5;
+    w.wh = w.ty + (int)std::ceil(sy * dt + 2 * margin) + 5;
     // cap the staged window at the shared memory a CTA can have; stencils
     // beyond it take the global-memory path
     const size_t cap = 220 * 1024;
     while (mixed_smem_bytes(w) > cap) {
-        if (w.ww - MIXED_TX >= w.wh - MIXED_TY) --w.ww; else --w.wh;
+        if (w.ww - w.tx >= w.wh - w.ty) --w.ww; else --w.wh;
     }
     const size_t smem = mixed_smem_bytes(w);
     int per_sm = 0;
-    CK(mixed_prepare(smem, &per_sm), "mixed kernel set-up");
+    CK(mixed_prepare(w.ty, smem, &per_sm), "mixed kernel set-up");
     if (per_sm < 1) return fail(ctx, POND_ERR_CUDA, "mixed kernel does not fit on an SM");
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "SM count");
@@ -323,13 +348,12 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
     if (ok) {
         cudaError_t e = cudaMemcpy(ctx->grids_dev, ctx->grids_host.data(),
                                    sizeof(GridDesc) * n_grids, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(ctx->tile_prefix_dev, prefix.data(), sizeof(int64_t) * (n_grids + 1),
-                           cudaMemcpyHostToDevice);
+
         if (e == cudaSuccess) e = cudaMemset(ctx->iters, 0, sizeof(int32_t) * ctx->N);
         if (e == cudaSuccess) e = upload_lattice_fp64(ctx->L);
         if (e == cudaSuccess) e = upload_lattice_mixed(ctx->L);
         if (e == cudaSuccess) e = upload_lattice_adjoint(ctx->L);
+        if (e == cudaSuccess) e = upload_lattice_adjoint_mixed(ctx->L);
         if (e != cudaSuccess) {
             st = cuda_fail(ctx, e, "context set-up");
             ok = false;
@@ -340,6 +364,11 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
         return st == POND_OK ? POND_ERR_CUDA : st;
     }
     if (mixed(ctx)) {
+        st = set_tile_rows(ctx, MIXED_TY);
+        if (st != POND_OK) {
+            pond_destroy(ctx);
+            return st;
+        }
         // provisional window until set_state measures the displacements
         for (int g = 0; g < n_grids; ++g) {
             ctx->spans[4 * g + 0] = -6.f;
@@ -438,12 +467,152 @@ pond_status pond_set_state(pond_ctx* ctx, int32_t grid, const void* rho, const v
     return s;
 }
 
+// ---------------------------------------------------------------- autotuner
+// Times each tile shape of the mixed kernel on the current state (the step
+// is recomputed into the spare buffer; the state does not advance) and keeps
+// the fastest.  Choices are cached per process, and in the JSON file named by
+// POND_AUTOTUNE_CACHE when set, under a signature of the grid set.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+std::string tune_key(const pond_ctx* ctx) {
+    int64_t maxside = 0, minside = 1 << 30;
+    for (const GridDesc& G : ctx->grids_host) {
+        maxside = std::max<int64_t>(maxside, std::max(G.nx, G.ny));
+        minside = std::min<int64_t>(minside, std::min(G.nx, G.ny));
+    }
+    float sx = 0.f, sy = 0.f;
+    for (int g = 0; g < ctx->n_grids; ++g) {
+        sx = std::fmax(sx, ctx->spans[4 * g + 1] - ctx->spans[4 * g]);
+        sy = std::fmax(sy, ctx->spans[4 * g + 3] - ctx->spans[4 * g + 2]);
+    }
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "mixed|grids=%d|nodes=%lld|side=%lld-%lld|span=%d-%d",
+                  ctx->n_grids, (long long)ctx->N, (long long)minside, (long long)maxside,
+                  (int)std::ceil(sx), (int)std::ceil(sy));
+    return buf;
+}
+
+void tune_file_load() {
+    const char* path = std::getenv("POND_AUTOTUNE_CACHE");
+    if (!path || g_tune_file_loaded) return;
+    g_tune_file_loaded = true;
+    FILE* fp = std::fopen(path, "r");
+    if (!fp) return;
+    // flat JSON object of "key": rows pairs
+    std::string text;
+    char chunk[4096];
+    size_t n;
+    while ((n = std::fread(chunk, 1, sizeof chunk, fp)) > 0) text.append(chunk, n);
+    std::fclose(fp);
+    size_t pos = 0;
+    while ((pos = text.find('"', pos)) != std::string::npos) {
+        const size_t end = text.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        const std::string key = text.substr(pos + 1, end - pos - 1);
+        const size_t colon = text.find(':', end);
+        if (colon == std::string::npos) break;
+        const int rows = std::atoi(text.c_str() + colon + 1);
+        if (rows == 4 || rows == 8 || rows == 16) g_tune_cache[key] = rows;
+        pos = text.find_first_of(",}", colon);
+        if (pos == std::string::npos) break;
+    }
+}
+
+void tune_file_store() {
+    const char* path = std::getenv("POND_AUTOTUNE_CACHE");
+    if (!path) return;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* fp = std::fopen(tmp.c_str(), "w");
+    if (!fp) return;
+    std::fprintf(fp, "{");
+    bool first = true;
+    for (const auto& kv : g_tune_cache) {
+        std::fprintf(fp, "%s\n  \"%s\": %d", first ? "" : ",", kv.first.c_str(), kv.second);
+        first = false;
+    }
+    std::fprintf(fp, "\n}\n");
+    std::fclose(fp);
+    std::rename(tmp.c_str(), path);
+}
+}  // namespace
+
+static pond_status launch_step_into(pond_ctx* ctx, int in, int out) {
+    const bool batched = ctx->n_grids > 1;
+    CK(launch_step_mixed(buf<float>(ctx, in, 0), buf<float>(ctx, out, 0), ctx->iters, ctx->stats,
+                         ctx->grids_dev, ctx->tile_prefix_dev, ctx->n_grids, ctx->n_tiles, ctx->N,
+                         batched ? ctx->work_counter : nullptr, ctx->win, ctx->persistent_ctas,
+                         ctx->L, ctx->P, ctx->stream),
+       "mixed step launch");
+    return POND_OK;
+}
+
+static pond_status autotune(pond_ctx* ctx) {
+    const std::string key = tune_key(ctx);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_file_load();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            pond_status s = set_tile_rows(ctx, it->second);
+            if (s == POND_OK) s = update_window(ctx);
+            ctx->tuned = true;
+            return s;
+        }
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "autotune event");
+    CK(cudaEventCreate(&e1), "autotune event");
+    float best_ms = 1e30f;
+    int best = ctx->tile_ty;
+    pond_status s = POND_OK;
+    for (int ty : MIXED_TY_CHOICES) {
+        s = set_tile_rows(ctx, ty);
+        if (s == POND_OK) s = update_window(ctx);
+        if (s != POND_OK) break;
+        s = launch_step_into(ctx, ctx->cur, 1 - ctx->cur);  // warm-up
+        if (s != POND_OK) break;
+        cudaEventRecord(e0, ctx->stream);
+        for (int r = 0; r < 3 && s == POND_OK; ++r) s = launch_step_into(ctx, ctx->cur, 1 - ctx->cur);
+        cudaEventRecord(e1, ctx->stream);
+        if (s != POND_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            s = fail(ctx, POND_ERR_CUDA, "autotune timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = ty;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != POND_OK) return s;
+    s = set_tile_rows(ctx, best);
+    if (s == POND_OK) s = update_window(ctx);
+    if (s != POND_OK) return s;
+    ctx->tuned = true;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+    tune_file_store();
+    return POND_OK;
+}
+
 pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats) {
     if (!ctx) return POND_ERR_ARG;
     if (nsteps < 0) return fail(ctx, POND_ERR_ARG, "nsteps < 0");
     for (int g = 0; g < ctx->n_grids; ++g)
         if (!ctx->grid_set[g]) return fail(ctx, POND_ERR_STATE, "pond_step before pond_set_state");
     DeviceGuard dg(ctx->device);
+    if (ctx->cfg.autotune && mixed(ctx) && !ctx->tuned && nsteps > 0) {
+        pond_status s = autotune(ctx);
+        if (s != POND_OK) return s;
+        drop_graphs(ctx);
+    }
     if (stats) CK(cudaMemsetAsync(ctx->stats, 0, sizeof(DevStats), ctx->stream), "stats reset");
     int32_t left = nsteps;
     if (ctx->cfg.use_graph && left >= 2) {
@@ -467,7 +636,7 @@ pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats) {
         stats->node_updates = (int64_t)nsteps * ctx->N;
         stats->passes = (int64_t)d.passes;
         stats->max_passes = (int32_t)d.max_passes;
-        stats->reserved = 0;
+        stats->tile_rows = mixed(ctx) ? ctx->tile_ty : 0;
         stats->nonconverged = (int64_t)d.nonconverged;
         stats->nonphysical = (int64_t)d.nonphysical;
         stats->halo_fallback = (int64_t)d.halo_fallback;
@@ -507,6 +676,7 @@ void pond_destroy(pond_ctx* ctx) {
     DeviceGuard dg(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     destroy_adjoint(ctx);
+    destroy_adjoint_mixed(ctx);
     drop_graphs(ctx);
     for (int b = 0; b < 2; ++b) {
         cudaFree(ctx->f[b]);

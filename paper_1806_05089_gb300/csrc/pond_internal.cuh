@@ -90,6 +90,7 @@ struct StateBuf {
 cudaError_t upload_lattice_fp64(const Lattice& L);
 cudaError_t upload_lattice_mixed(const Lattice& L);
 cudaError_t upload_lattice_adjoint(const Lattice& L);
+cudaError_t upload_lattice_adjoint_mixed(const Lattice& L);
 
 // FP64 step of a single grid (one warp per node).
 cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>& out,
@@ -114,9 +115,10 @@ cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& 
 
 // Tile shape of the mixed kernel, its shared-memory need for a window, and
 // the per-device attribute set-up (returns resident CTAs per SM).
-constexpr int MIXED_TX = 32, MIXED_TY = 8;
+constexpr int MIXED_TX = 32, MIXED_TY = 8;  // default tile: 32 x 8 nodes
+constexpr int MIXED_TY_CHOICES[3] = {4, 8, 16};
 size_t mixed_smem_bytes(const TileWindow& w);
-cudaError_t mixed_prepare(size_t smem_bytes, int* ctas_per_sm);
+cudaError_t mixed_prepare(int ty, size_t smem_bytes, int* ctas_per_sm);
 
 // Equilibrium initialisation f = rho W (Eq. equilibrium) and T -> sqrt(theta).
 template <typename Real>
@@ -134,8 +136,11 @@ cudaError_t launch_read_state(StateBuf<Real> st, int64_t N, int64_t plane, doubl
 cudaError_t launch_disp_bounds(const double* ux, const double* uy, const double* st,
                                int64_t N, double c_max, float* out4, cudaStream_t s);
 
-// Adjoint (pond_adjoint.cu).
+// Adjoint (pond_adjoint.cu, pond_adjoint_mixed.cu).
 struct AdjointScratch;
+struct AdjMixedScratch;
+cudaError_t launch_minmax3(const double* ux, const double* uy, const double* st, long long N,
+                           double* out6, cudaStream_t s);
 
 }  // namespace pond
 
@@ -160,6 +165,8 @@ struct pond_ctx {
     unsigned int* work_counter = nullptr;
     float* bounds_dev = nullptr;
     int64_t n_tiles = 0;
+    int tile_ty = pond::MIXED_TY;  // rows of the mixed kernel's tile
+    bool tuned = false;
     pond::TileWindow win{};
     int persistent_ctas = 0;
     std::vector<char> grid_set;
@@ -170,6 +177,11 @@ struct pond_ctx {
     size_t staging_bytes = 0;
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};  // two-step graphs per parity
     pond::AdjointScratch* adj = nullptr;
+    pond::AdjMixedScratch* adjm = nullptr;
 };
 
 void destroy_adjoint(pond_ctx* ctx);
+void destroy_adjoint_mixed(pond_ctx* ctx);
+cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* fbar, const double* gbar,
+                               double* fbar_out, double* gbar_out, double* beta_bar_dev,
+                               double* minmax_dev, double* minmax_host);

@@ -379,7 +379,7 @@ extern "C" pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx
         stats->node_updates = N;
         stats->passes = (int64_t)h.passes;
         stats->max_passes = (int32_t)h.max_passes;
-        stats->reserved = 0;
+        stats->tile_rows = 0;
         stats->nonconverged = (int64_t)h.nonconverged;
         stats->nonphysical = (int64_t)h.nonphysical;
         stats->halo_fallback = 0;

@@ -108,48 +108,44 @@ __device__ __noinline__ void finish_node(const MixedArgs& A, float* s_acc, int N
                                          float dy, double ux, double uy, double st, float rho) {
     const LatticeF& L = c_Lf;
     if (regauge) {
-        float ex[4], ey[4];
+        // In correction form, f + (G - I) f: at convergence G - I is of the
+        // size of the last gauge increment (~1e-7 to 1e-6), so writing the
+        // diagonal as fl(1 + e) would round e away while the off-diagonal
+        // terms survive -- the columns of G would no longer sum to one and
+        // each parcel would lose or gain mass the same way every step.
+        //   (G f)_kl - f_kl = sum_b ey_lb f_kb + sum_a ex_ka (f_al + sum_b ey_lb f_ab)
+        // with ex, ey the Taylor polynomials without their identity term.
+        float ex[4][4], ey[4][4];  // [k][a]
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            ex[a] = fmaf(L.c[a], r, dx);
-            ey[a] = fmaf(L.c[a], r, dy);
+            const float dex = fmaf(L.c[a], r, dx), dey = fmaf(L.c[a], r, dy);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                ex[k][a] = fmaf(fmaf(L.d3[k], dex, L.d2[k][a]), dex, L.d1[k][a]) * dex;
+                ey[k][a] = fmaf(fmaf(L.d3[k], dey, L.d2[k][a]), dey, L.d1[k][a]) * dey;
+            }
         }
+        float f[16], H[16];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {  // h[a][l] = sum_b Gy[l][b] f[a][b]
-            float f4[4];
+        for (int q = 0; q < 16; ++q) f[q] = s_acc[q * NT + tid];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) f4[b] = s_acc[(4 * a + b) * NT + tid];
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
                 float v = 0.0f;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const float e = ey[b];
-                    const float gyl = fmaf(fmaf(fmaf(L.d3[l], e, L.d2[l][b]), e, L.d1[l][b]), e,
-                                           l == b ? 1.0f : 0.0f);
-                    v = fmaf(gyl, f4[b], v);
-                }
-                s_acc[(4 * a + l) * NT + tid] = v;
+                for (int b = 0; b < 4; ++b) v = fmaf(ey[l][b], f[4 * a + b], v);
+                H[4 * a + l] = v;  // y-correction of row a
             }
-        }
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {  // f[k][l] = sum_a Gx[k][a] h[a][l]
-            float h4[4];
+        for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int a = 0; a < 4; ++a) h4[a] = s_acc[(4 * a + l) * NT + tid];
+            for (int l = 0; l < 4; ++l) {
+                float c = H[4 * k + l];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float v = 0.0f;
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const float e = ex[a];
-                    const float gxk = fmaf(fmaf(fmaf(L.d3[k], e, L.d2[k][a]), e, L.d1[k][a]), e,
-                                           k == a ? 1.0f : 0.0f);
-                    v = fmaf(gxk, h4[a], v);
-                }
-                s_acc[(4 * k + l) * NT + tid] = v;
+                for (int a = 0; a < 4; ++a) c = fmaf(ex[k][a], f[4 * a + l] + H[4 * a + l], c);
+                s_acc[(4 * k + l) * NT + tid] = f[4 * k + l] + c;
             }
-        }
     }
     // BGK in FP32, kept exactly conservative: the relaxed non-equilibrium
     // part n = f - rho W is first stripped of its mass, momentum and energy
@@ -220,14 +216,10 @@ __device__ __forceinline__ void block_minmax4(float& a, float& b, float& c, floa
     __syncthreads();
 }
 
-// Resident CTAs per SM the register allocation targets (1: 256 threads may
-// use up to 255 registers each; 2: at most 128).
-#ifndef POND_MIXED_MIN_BLOCKS
-#define POND_MIXED_MIN_BLOCKS 2
-#endif
-
+// Every tile shape is compiled for 128 registers per thread (512 threads of
+// resident CTAs per SM: 4 x 128, 2 x 256 or 1 x 512).
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(MixedArgs A) {
+__global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedArgs A) {
     constexpr int NT = TX * TY;
     extern __shared__ __align__(16) float4 smem4[];
     const int WN = A.ww * A.wh;
@@ -513,28 +505,36 @@ __global__ void __launch_bounds__(TX* TY, POND_MIXED_MIN_BLOCKS) k2_step_mixed(M
     }
 }
 
-constexpr int MX_TX = MIXED_TX, MX_TY = MIXED_TY;
-
 size_t mixed_smem_bytes(const TileWindow& w) {
-    return sizeof(float) * ((size_t)20 * w.ww * w.wh + (size_t)16 * MX_TX * MX_TY);
+    return sizeof(float) * ((size_t)20 * w.ww * w.wh + (size_t)16 * w.tx * w.ty);
 }
 
-cudaError_t mixed_prepare(size_t smem_bytes, int* ctas_per_sm) {
+template <int TY>
+static cudaError_t prepare_shape(size_t smem_bytes, int* ctas_per_sm, int* s_set) {
+    auto kern = k2_step_mixed<MIXED_TX, TY>;
+    cudaError_t e;
+    if ((int)smem_bytes > *s_set) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        if (e != cudaSuccess) return e;
+        *s_set = (int)smem_bytes;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, MIXED_TX * TY, smem_bytes);
+}
+
+cudaError_t mixed_prepare(int ty, size_t smem_bytes, int* ctas_per_sm) {
     // the attribute is per function and device: only ever raise it, so that
     // every live context's window stays launchable
-    static int s_set[64] = {0};
+    static int s_set[64][3] = {{0}};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if ((int)smem_bytes > s_set[dev]) {
-        e = cudaFuncSetAttribute(k2_step_mixed<MX_TX, MX_TY>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-        if (e != cudaSuccess) return e;
-        s_set[dev] = (int)smem_bytes;
+    switch (ty) {
+        case 4: return prepare_shape<4>(smem_bytes, ctas_per_sm, &s_set[dev][0]);
+        case 8: return prepare_shape<8>(smem_bytes, ctas_per_sm, &s_set[dev][1]);
+        case 16: return prepare_shape<16>(smem_bytes, ctas_per_sm, &s_set[dev][2]);
+        default: return cudaErrorInvalidValue;
     }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k2_step_mixed<MX_TX, MX_TY>,
-                                                         MX_TX * MX_TY, smem_bytes);
 }
 
 cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& out,
@@ -569,7 +569,12 @@ cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& 
     } else {
         nb = (unsigned int)n_tiles;
     }
-    k2_step_mixed<MX_TX, MX_TY><<<nb, MX_TX * MX_TY, smem, s>>>(A);
+    switch (win.ty) {
+        case 4: k2_step_mixed<MIXED_TX, 4><<<nb, MIXED_TX * 4, smem, s>>>(A); break;
+        case 8: k2_step_mixed<MIXED_TX, 8><<<nb, MIXED_TX * 8, smem, s>>>(A); break;
+        case 16: k2_step_mixed<MIXED_TX, 16><<<nb, MIXED_TX * 16, smem, s>>>(A); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -57,6 +57,7 @@ class pond_config(ctypes.Structure):
         ("strict", ctypes.c_int32),
         ("seed_mode", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
     ]
 
 
@@ -65,14 +66,14 @@ class pond_stats(ctypes.Structure):
         ("node_updates", ctypes.c_int64),
         ("passes", ctypes.c_int64),
         ("max_passes", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("tile_rows", ctypes.c_int32),
         ("nonconverged", ctypes.c_int64),
         ("nonphysical", ctypes.c_int64),
         ("halo_fallback", ctypes.c_int64),
     ]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _LIB = None

@@ -18,6 +18,10 @@ App. D, and its compressible advected flows):
                      constant pressure: rho = (1 + the 8-mode perturbation) / T
 4. ``adjoint``       512 x 512 Taylor-Green u0 = 0.3 plus a Gaussian density
                      pulse (amplitude 0.2, sigma 16), and a seeded target
+6. ``vortex``        isentropic vortex u_phi = Ma_v c r exp((1 - r^2)/2), r = r'/R,
+                     c = sqrt(2 T_inf), advected by U = Ma_a c (main text,
+                     vortex benchmark); T and rho from radial equilibrium of
+                     an isentropic gamma = 2 gas
 5. ``ensemble``      256 grids with sides in 32..512, Mach 0..3 in a random
                      direction, T ratio r in [0.5, 4]: T = 1 + (r-1) s(x),
                      s in [0, 1] from 8 modes of wavenumber <= 2 per side (so
@@ -119,6 +123,26 @@ def adjoint(n: int = 512):
     f.rho = f.rho + pulse
     target = 1.0 + 0.01 * sinusoids(n, n, rng(4, 1))
     return f, target
+
+
+def vortex(n: int, radius: float, mach_v: float, mach_a: float, T_inf: float = 1.0,
+           rho_inf: float = 1.0, angle: float = 0.0) -> Fields:
+    """Isentropic vortex centred in an n x n periodic box.  Radial balance
+    dp/dr = rho u_phi^2 / r with p = rho T and p ~ rho^gamma (gamma = 2) gives
+    T = T_inf (1 - Ma_v^2 e^{1-r^2} / 2) and rho = rho_inf T / T_inf."""
+    X, Y = _grid(n, n)
+    c = np.sqrt(2.0 * T_inf)
+    dx = X - n / 2.0
+    dy = Y - n / 2.0
+    r = np.hypot(dx, dy) / radius
+    e = np.exp(0.5 * (1.0 - r * r))
+    uphi = mach_v * c * r * e
+    rr = np.maximum(np.hypot(dx, dy), 1e-300)
+    U = mach_a * c
+    ux = -uphi * dy / rr + U * np.cos(angle)
+    uy = uphi * dx / rr + U * np.sin(angle)
+    T = T_inf * (1.0 - 0.5 * mach_v * mach_v * e * e)
+    return Fields(rho_inf * T / T_inf, ux, uy, T)
 
 
 def ensemble_sizes(count: int = 256, lo: int = 32, hi: int = 512, seed_sub: int = 0):

@@ -151,3 +151,18 @@ def test_adjoint_full_workload_512():
     fd = (gpu_loss(f.rho, f.ux, f.uy, f.T, target, nu + h, steps)
           - gpu_loss(f.rho, f.ux, f.uy, f.T, target, nu - h, steps)) / (2 * h)
     assert abs(fd - gnu) <= 1e-6 * abs(fd), (fd, gnu)
+
+
+@pytest.mark.gpu
+def test_mixed_adjoint_matches_fp64_adjoint():
+    """The FP32 adjoint (mixed context) against the FP64 adjoint on the same
+    rollout: the gradients agree to the accuracy of the FP32 forward."""
+    from paper_1806_05089_gb300 import pond
+    rho0, ux, uy, T, target = small_case(48, 40, seed=5)
+    nu, steps, ckpt = 0.01, 8, 4
+    L64, g64, n64 = gpu_grad(rho0, ux, uy, T, target, nu, steps, ckpt)
+    L32, g32, n32 = gpu_grad(rho0, ux, uy, T, target, nu, steps, ckpt,
+                             precision=pond.POND_FP32_MIXED)
+    assert abs(L32 - L64) <= 1e-4 * L64
+    assert np.abs(g32 - g64).max() <= 1e-4 * np.abs(g64).max()
+    assert abs(n32 - n64) <= 1e-4 * abs(n64)

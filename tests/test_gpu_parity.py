@@ -268,3 +268,25 @@ def test_graph_replay_matches_plain_launches():
             out.append(s.state())
     assert np.array_equal(out[0].f, out[1].f)
     assert np.array_equal(out[0].T, out[1].T)
+
+
+def test_autotune_picks_a_tile_shape_and_matches_oracle(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("POND_AUTOTUNE_CACHE", str(cache))
+    sizes = [(70, 45), (33, 90), (128, 40)]
+    members = [workloads.ensemble_member(10 + i, nx, ny) for i, (nx, ny) in enumerate(sizes)]
+    nxs = [s[0] for s in sizes]
+    nys = [s[1] for s in sizes]
+    with pond.Sim(nxs, nys, pond.POND_FP32_MIXED, autotune=1) as b:
+        for i, m in enumerate(members):
+            b.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
+        stats = b.step(3)
+        out = [b.state(i) for i in range(len(sizes))]
+    assert stats["tile_rows"] in (4, 8, 16)
+    for i, m in enumerate(members):
+        o, _ = oracle_run(m, 3, max_iter=60)
+        assert np.max(np.abs(out[i].T - o.T) / o.T) <= TOL32
+        assert np.max(np.abs(out[i].f.sum(0) - o.f.sum(0)) / o.f.sum(0)) <= TOL32
+    import json
+    saved = json.load(open(cache))
+    assert stats["tile_rows"] in saved.values()

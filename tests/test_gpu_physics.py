@@ -1,0 +1,100 @@
+"""Physics of the GPU step against the paper's claims (through the C ABI).
+
+- Kinematic viscosity from a decaying pi/4-tilted shear wave is nu for
+  advection Mach numbers up to 100 and temperatures T_L/2, T_L, 2 T_L
+  (viscosity experiment, main text: Galilean invariance).
+- The speed of sound is sqrt(2 T) for T from 1e-4 to 1e2, at rest and advected
+  at Ma 10 (speed-of-sound experiment; gamma = 2 for the 2D ideal gas).
+- The isothermal variant (main text after Eq. postcollision) matches the
+  oracle's isothermal step.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_05089_gb300 import pond
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("T", [0.5, 1.0, 2.0])
+@pytest.mark.parametrize("mach", [0.0, 1.0, 10.0, 100.0])
+def test_shear_wave_viscosity_is_galilean_invariant(T, mach):
+    n, A, nu, steps, every = 200, 0.05, 0.02, 2000, 100
+    X, Y = np.meshgrid(np.arange(n, dtype=float), np.arange(n, dtype=float))
+    k = 2 * np.pi / n * np.array([1.0, 1.0])         # wave vector along (1, 1)
+    phase = k[0] * X + k[1] * Y
+    u_long = mach * np.sqrt(T)                      # along k
+    u_tr = A * np.sin(phase)                        # transverse, along (1, -1)
+    ux = (u_long + u_tr) / np.sqrt(2.0)
+    uy = (u_long - u_tr) / np.sqrt(2.0)
+    k2 = float(k @ k)
+    amps = []
+    # nu = T (1/(2 beta) - 1/2) dt at the run's temperature: T_ref = T
+    with pond.Sim(n, n, pond.POND_FP32_MIXED, thermal=0, nu=nu, T_ref=T, use_graph=1) as s:
+        s.set_state(np.ones((n, n)), ux, uy, np.full((n, n), T))
+        for t in range(0, steps, every):
+            stats = s.step(every)
+            assert stats["nonphysical"] == 0 and stats["nonconverged"] == 0
+            _, vx, vy, _ = s.moments()
+            tr = (vx - vy) / np.sqrt(2.0)
+            amps.append(np.abs((tr * np.exp(-1j * phase)).sum()) * 2 / (n * n))
+    t = np.arange(1, len(amps) + 1) * every
+    rate = -np.polyfit(t, np.log(amps), 1)[0]
+    assert abs(rate / (nu * k2) - 1) < 0.03, (rate, nu * k2)
+
+
+@pytest.mark.parametrize("mach", [0.0, 10.0])
+@pytest.mark.parametrize("T,nx", [(1e-4, 16), (1e-2, 64), (1.0, 256), (100.0, 2048)])
+def test_speed_of_sound_over_six_decades(T, nx, mach):
+    eps = 1e-3
+    cs = np.sqrt(2.0 * T)
+    k = 2 * np.pi / nx
+    period = 2 * np.pi / (cs * k)
+    steps = int(1.6 * period) + 2
+    x = np.arange(nx, dtype=float)
+    u = mach * np.sqrt(T)
+    rho = (1.0 + eps * np.cos(k * x))[None, :]
+    with pond.Sim(nx, 1, pond.POND_FP64, nu=0.01) as s:
+        s.set_state(rho, np.full((1, nx), u), np.zeros((1, nx)), np.full((1, nx), T))
+        a = []
+        for t in range(1, steps + 1):
+            s.step(1, stats=False)
+            r, _, _, TT = s.moments()
+            p = (r * TT)[0]
+            # pressure mode in the frame moving with the flow
+            a.append(((p - p.mean()) * np.exp(-1j * k * (x - u * t))).sum().real * 2 / nx)
+    a = np.array(a)
+    zc = [i + a[i] / (a[i] - a[i + 1]) for i in range(len(a) - 1) if a[i] * a[i + 1] < 0]
+    assert len(zc) >= 2
+    half = np.diff(zc).mean()
+    cs_meas = np.pi / half / k
+    assert abs(cs_meas / cs - 1) < 0.01, (cs_meas, cs)
+
+
+@pytest.mark.parametrize("precision,tol", [(pond.POND_FP64, 1e-12), (pond.POND_FP32_MIXED, 1e-5)])
+def test_isothermal_step_matches_oracle(precision, tol):
+    n = 40
+    X, Y = np.meshgrid(np.arange(n, dtype=float), np.arange(n, dtype=float))
+    ux = 0.8 + 0.05 * np.sin(2 * np.pi * Y / n)
+    uy = -0.3 + 0.05 * np.cos(2 * np.pi * X / n)
+    rho = 1.0 + 0.02 * np.cos(2 * np.pi * (X + Y) / n)
+    T = np.full((n, n), 0.7)
+    cfg = {"thermal": 0}
+    if precision == pond.POND_FP64:
+        cfg["fixed_iter"] = 5
+    with pond.Sim(n, n, precision, **cfg) as s:
+        s.set_state(rho, ux, uy, T)
+        s.step(4)
+        st = s.state()
+    o = oracle.init_equilibrium(rho, ux, uy, T)
+    p = oracle.Params(thermal=0, fixed_iter=5 if precision == pond.POND_FP64 else 0)
+    for _ in range(4):
+        o, _, fl = oracle.step(o, p)
+        assert np.all(fl == 0)
+    assert np.abs(st.T - T).max() <= 4e-16 * 0.7
+    orho = o.f.sum(0)
+    assert np.max(np.abs(st.f.sum(0) - orho) / orho) <= tol
+    scale = max(np.abs(o.ux).max(), np.sqrt(0.7))
+    assert np.abs(st.ux - o.ux).max() <= tol * scale
+    assert np.abs(st.uy - o.uy).max() <= tol * scale

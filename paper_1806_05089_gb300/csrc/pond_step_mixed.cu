@@ -156,6 +156,8 @@ __device__ __noinline__ void finish_node(const MixedArgs& A, float* s_acc, int N
     // the plain f + 2 beta (rho W - f) of Eq. postcollision; in FP32 their
     // rounding would otherwise act on each advected parcel the same way step
     // after step and drift its mass and temperature.
+    // (Isothermal runs keep T fixed and do not conserve energy: there only
+    // mass and momentum are projected out, with dual basis W, W c_x, W c_y.)
     float M0 = 0.0f, M1 = 0.0f, M2 = 0.0f, M3 = 0.0f;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -166,6 +168,12 @@ __device__ __noinline__ void finish_node(const MixedArgs& A, float* s_acc, int N
         M2 = fmaf(L.c[l], n, M2);
         M3 = fmaf(fmaf(L.c[k], L.c[k], L.c[l] * L.c[l]), n, M3);
     }
+    float e0 = 2.0f, e2 = -0.5f, t0 = -0.5f, t2 = 0.25f;  // thermal dual basis
+    if (!A.P.thermal) {
+        e0 = 1.0f;
+        e2 = 0.0f;
+        M3 = 0.0f;
+    }
     const float two_beta = (float)(2.0 * A.P.beta);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -174,8 +182,8 @@ __device__ __noinline__ void finish_node(const MixedArgs& A, float* s_acc, int N
         const float c2 = fmaf(L.c[k], L.c[k], L.c[l] * L.c[l]);
         const float a = s_acc[q * NT + tid];
         float n = fmaf(-rho, Wq, a);
-        const float proj = fmaf(M0, fmaf(-0.5f, c2, 2.0f),
-                                fmaf(M1, L.c[k], fmaf(M2, L.c[l], M3 * fmaf(0.25f, c2, -0.5f))));
+        const float proj = fmaf(M0, fmaf(e2, c2, e0),
+                                fmaf(M1, L.c[k], fmaf(M2, L.c[l], M3 * fmaf(t2, c2, t0))));
         n = fmaf(-Wq, proj, n);
         A.out.f[q * A.plane + node] = fmaf(-two_beta, n, a);
     }

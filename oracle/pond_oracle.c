@@ -21,9 +21,11 @@
  *     postcollision)
  *
  * Readings taken where the paper is silent or specific to D2Q9:
- *  - lattice: D2Q16, the tensor product of the four roots of the Hermite
- *    polynomial He4 (c^2 = 3 -+ sqrt 6), weights (3 -+ sqrt 6)/12, T_L = 1;
- *    the paper's general theory (Eq. peculiar, App. A) is lattice-agnostic.
+ *  - lattice: D2Q16 by default, the tensor product of the four roots of the
+ *    Hermite polynomial He4 (c^2 = 3 -+ sqrt 6), weights (3 -+ sqrt 6)/12,
+ *    T_L = 1 (the paper's general theory, Eq. peculiar and App. A, is
+ *    lattice-agnostic); or the paper's own D2Q9 (App. A: c in {0, +-1},
+ *    W = 2/3, 1/6, T_L = 1/3), matching its 9 moments m, n <= 2 (App. B).
  *  - moments for the transform are taken in the monomial basis centred and
  *    scaled on the TARGET gauge, ((v_x-u'_x)/sqrt(theta'))^m ((v_y-u'_y)/
  *    sqrt(theta'))^n, m,n = 0..3.  These 16 polynomials are an invertible
@@ -57,6 +59,8 @@
 typedef struct {
     double nu, T_ref, dt, eps_abs, eps_rel;
     int32_t max_iter, fixed_iter, thermal, seed_mode;
+    int32_t lattice; /* 0: D2Q16 (default), 1: D2Q9 (the paper's App. A lattice) */
+    int32_t pad;
 } oracle_params;
 
 /* per-node flags written by oracle_step */
@@ -64,23 +68,43 @@ typedef struct {
 #define ORACLE_FLAG_NONPHYSICAL 2
 
 typedef struct {
+    int n1;             /* speeds per dimension (4: D2Q16, 3: D2Q9) */
+    int q;              /* populations, n1 * n1 */
     double c[4];        /* 1D peculiar speeds, ascending */
     double w[4];        /* 1D weights */
     double T_L;         /* lattice temperature */
     double minv[16][16];/* inverse of the target-side moment matrix */
 } lattice_t;
 
-/* D2Q16 one-dimensional speeds and weights (App. A, generalised). */
-static void lattice_1d(double c[4], double w[4]) {
-    const double s6 = sqrt(6.0);
-    c[0] = -sqrt(3.0 + s6);
-    c[1] = -sqrt(3.0 - s6);
-    c[2] = sqrt(3.0 - s6);
-    c[3] = sqrt(3.0 + s6);
-    w[0] = (3.0 - s6) / 12.0;
-    w[1] = (3.0 + s6) / 12.0;
-    w[2] = (3.0 + s6) / 12.0;
-    w[3] = (3.0 - s6) / 12.0;
+/* One-dimensional speeds and weights.  D2Q16: the four roots of He4 with
+ * their Gauss-Hermite weights, T_L = 1 (App. A generalised to a fourth-order
+ * set).  D2Q9: c in {-1, 0, 1}, W = {1/6, 2/3, 1/6}, T_L = 1/3 (App. A). */
+static void lattice_1d(int lattice, lattice_t *L) {
+    if (lattice == 1) {
+        L->n1 = 3;
+        L->c[0] = -1.0;
+        L->c[1] = 0.0;
+        L->c[2] = 1.0;
+        L->w[0] = 1.0 / 6.0;
+        L->w[1] = 2.0 / 3.0;
+        L->w[2] = 1.0 / 6.0;
+        L->c[3] = 0.0;
+        L->w[3] = 0.0;
+        L->T_L = 1.0 / 3.0;
+    } else {
+        const double s6 = sqrt(6.0);
+        L->n1 = 4;
+        L->c[0] = -sqrt(3.0 + s6);
+        L->c[1] = -sqrt(3.0 - s6);
+        L->c[2] = sqrt(3.0 - s6);
+        L->c[3] = sqrt(3.0 + s6);
+        L->w[0] = (3.0 - s6) / 12.0;
+        L->w[1] = (3.0 + s6) / 12.0;
+        L->w[2] = (3.0 + s6) / 12.0;
+        L->w[3] = (3.0 - s6) / 12.0;
+        L->T_L = 1.0;
+    }
+    L->q = L->n1 * L->n1;
 }
 
 /* Gauss-Jordan inversion with partial pivoting of an n x n matrix. */
@@ -126,20 +150,23 @@ static double ipow(double x, int p) {
     return r;
 }
 
-static void lattice_init(lattice_t *L) {
-    lattice_1d(L->c, L->w);
-    L->T_L = 1.0;
-    /* Target-side moment matrix: row (m,n) = 4m+n, column (k,l) = 4k+l,
-     * entry c_k^m c_l^n (Eq. moments in the target-centred basis). */
-    double m[16 * 16];
-    for (int mm = 0; mm < 4; ++mm)
-        for (int nn = 0; nn < 4; ++nn)
-            for (int k = 0; k < 4; ++k)
-                for (int l = 0; l < 4; ++l) {
-                    m[(4 * mm + nn) * 16 + (4 * k + l)] =
+static void lattice_init(lattice_t *L, int lattice) {
+    lattice_1d(lattice, L);
+    const int n1 = L->n1, Q = L->q;
+    /* Target-side moment matrix: row (m,n) = n1 m + n, column (k,l) =
+     * n1 k + l, entry c_k^m c_l^n (Eq. moments in the target-centred basis,
+     * m, n < n1: the Q moments of App. B for D2Q9). */
+    double m[16 * 16], inv[16 * 16];
+    for (int mm = 0; mm < n1; ++mm)
+        for (int nn = 0; nn < n1; ++nn)
+            for (int k = 0; k < n1; ++k)
+                for (int l = 0; l < n1; ++l) {
+                    m[(n1 * mm + nn) * Q + (n1 * k + l)] =
                         ipow(L->c[k], mm) * ipow(L->c[l], nn);
                 }
-    invert(16, m, &L->minv[0][0]);
+    invert(Q, m, inv);
+    for (int i = 0; i < Q; ++i)
+        for (int j = 0; j < Q; ++j) L->minv[i][j] = inv[i * Q + j];
 }
 
 /* Gauge transform f^{lambda'} = M_{lambda'}^{-1} M_{lambda} f^{lambda}
@@ -149,25 +176,26 @@ static void transfer(const lattice_t *L, double usx, double usy, double Ts,
                      double utx, double uty, double Tt, const double *fs,
                      double *ft) {
     const double sts = sqrt(Ts / L->T_L), stt = sqrt(Tt / L->T_L);
+    const int n1 = L->n1, Q = L->q;
     double xi_x[4], xi_y[4];
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < n1; ++a) {
         /* source particle velocity (Eq. peculiar) seen from the target frame */
         xi_x[a] = ((sts * L->c[a] + usx) - utx) / stt;
         xi_y[a] = ((sts * L->c[a] + usy) - uty) / stt;
     }
     double mom[16];
-    for (int mm = 0; mm < 4; ++mm)
-        for (int nn = 0; nn < 4; ++nn) {
+    for (int mm = 0; mm < n1; ++mm)
+        for (int nn = 0; nn < n1; ++nn) {
             double acc = 0.0;
-            for (int a = 0; a < 4; ++a)
-                for (int b = 0; b < 4; ++b) {
-                    acc += fs[4 * a + b] * ipow(xi_x[a], mm) * ipow(xi_y[b], nn);
+            for (int a = 0; a < n1; ++a)
+                for (int b = 0; b < n1; ++b) {
+                    acc += fs[n1 * a + b] * ipow(xi_x[a], mm) * ipow(xi_y[b], nn);
                 }
-            mom[4 * mm + nn] = acc;
+            mom[n1 * mm + nn] = acc;
         }
-    for (int q = 0; q < 16; ++q) {
+    for (int q = 0; q < Q; ++q) {
         double acc = 0.0;
-        for (int r = 0; r < 16; ++r) acc += L->minv[q][r] * mom[r];
+        for (int r = 0; r < Q; ++r) acc += L->minv[q][r] * mom[r];
         ft[q] = acc;
     }
 }
@@ -188,18 +216,18 @@ static int64_t wrap(int64_t i, int64_t n) {
 /* ------------------------------------------------------------------ */
 /* exported helpers (for pinning the oracle's parts in tests)          */
 
-void oracle_lattice(double *c, double *w, double *T_L) {
+void oracle_lattice(int lattice, double *c, double *w, double *T_L) {
     lattice_t L;
-    lattice_init(&L);
+    lattice_init(&L, lattice);
     memcpy(c, L.c, sizeof L.c);
     memcpy(w, L.w, sizeof L.w);
     *T_L = L.T_L;
 }
 
-void oracle_transfer(const double *gauge_src, const double *gauge_dst,
+void oracle_transfer(int lattice, const double *gauge_src, const double *gauge_dst,
                      const double *f_src, double *f_dst) {
     lattice_t L;
-    lattice_init(&L);
+    lattice_init(&L, lattice);
     transfer(&L, gauge_src[0], gauge_src[1], gauge_src[2], gauge_dst[0],
              gauge_dst[1], gauge_dst[2], f_src, f_dst);
 }
@@ -210,15 +238,16 @@ void oracle_interp_weights(double t, double *w4) {
 
 /* f_q = rho W_q in each node's own gauge (Eq. equilibrium); the gauge
  * arrays need no change. */
-void oracle_init_equilibrium(int64_t nx, int64_t ny, const double *rho,
+void oracle_init_equilibrium(int lattice, int64_t nx, int64_t ny, const double *rho,
                              double *f) {
     lattice_t L;
-    lattice_init(&L);
+    lattice_init(&L, lattice);
     const int64_t N = nx * ny;
-    for (int k = 0; k < 4; ++k)
-        for (int l = 0; l < 4; ++l)
+    const int n1 = L.n1;
+    for (int k = 0; k < n1; ++k)
+        for (int l = 0; l < n1; ++l)
             for (int64_t i = 0; i < N; ++i)
-                f[(4 * k + l) * N + i] = rho[i] * L.w[k] * L.w[l];
+                f[(n1 * k + l) * N + i] = rho[i] * L.w[k] * L.w[l];
 }
 
 int oracle_num_threads(void) {
@@ -230,7 +259,7 @@ int oracle_num_threads(void) {
 }
 
 /* One PonD time step for rows [y_begin, y_end) of a periodic nx x ny grid.
- * State arrays: f[16][ny][nx] (q = 4k + l; k: x speed index, l: y speed
+ * State arrays: f[Q][ny][nx] (q = n1 k + l; k: x speed index, l: y speed
  * index), ux, uy, T [ny][nx].  Outputs are written for the given rows only.
  * iters[i] = predictor-corrector passes taken at node i; flags[i] holds
  * ORACLE_FLAG_* bits.  Returns 0. */
@@ -240,7 +269,8 @@ int oracle_step(int64_t nx, int64_t ny, const double *f_in, const double *ux_in,
                 int32_t *flags, const oracle_params *p, int64_t y_begin,
                 int64_t y_end) {
     lattice_t L;
-    lattice_init(&L);
+    lattice_init(&L, p->lattice);
+    const int n1 = L.n1, Q = L.q;
     const int64_t N = nx * ny;
     const double beta = 1.0 / (2.0 * p->nu / (p->T_ref * p->dt) + 1.0);
     const double D = 2.0;
@@ -268,9 +298,9 @@ int oracle_step(int64_t nx, int64_t ny, const double *f_in, const double *ux_in,
                 const double st = sqrt(T / L.T_L);
                 double vx[16], vy[16];
                 /* propagation in gauge (ux, uy, T): Eq. advection */
-                for (int k = 0; k < 4; ++k)
-                    for (int l = 0; l < 4; ++l) {
-                        const int q = 4 * k + l;
+                for (int k = 0; k < n1; ++k)
+                    for (int l = 0; l < n1; ++l) {
+                        const int q = n1 * k + l;
                         vx[q] = st * L.c[k] + ux; /* Eq. vi */
                         vy[q] = st * L.c[l] + uy;
                         const double dep_x = (double)X - vx[q] * p->dt;
@@ -285,7 +315,7 @@ int oracle_step(int64_t nx, int64_t ny, const double *f_in, const double *ux_in,
                                 const int64_t sy = wrap((int64_t)y0 + m, ny);
                                 const int64_t s = sy * nx + sx;
                                 double fs[16], ft[16];
-                                for (int r = 0; r < 16; ++r) fs[r] = f_in[r * N + s];
+                                for (int r = 0; r < Q; ++r) fs[r] = f_in[r * N + s];
                                 transfer(&L, ux_in[s], uy_in[s], T_in[s], ux, uy, T,
                                          fs, ft);
                                 acc += lagrange_weight(n, tx) *
@@ -297,7 +327,7 @@ int oracle_step(int64_t nx, int64_t ny, const double *f_in, const double *ux_in,
                 /* moments with the pass's discrete velocities:
                  * Eqs. conservation_rho, conservation_rhou, conservation_T */
                 double rho = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
-                for (int q = 0; q < 16; ++q) {
+                for (int q = 0; q < Q; ++q) {
                     rho += fq[q];
                     jx += vx[q] * fq[q];
                     jy += vy[q] * fq[q];
@@ -338,7 +368,7 @@ int oracle_step(int64_t nx, int64_t ny, const double *f_in, const double *ux_in,
             if (!(flag & ORACLE_FLAG_NONPHYSICAL)) {
                 double fr[16];
                 transfer(&L, ux, uy, T, ux1, uy1, T1, fq, fr);
-                for (int q = 0; q < 16; ++q) fq[q] = fr[q];
+                for (int q = 0; q < Q; ++q) fq[q] = fr[q];
                 ux = ux1;
                 uy = uy1;
                 T = T1;
@@ -346,10 +376,10 @@ int oracle_step(int64_t nx, int64_t ny, const double *f_in, const double *ux_in,
             /* BGK relaxation toward rho W in the co-moving gauge
              * (Eqs. equilibrium, postcollision) */
             double rho = 0.0;
-            for (int q = 0; q < 16; ++q) rho += fq[q];
-            for (int k = 0; k < 4; ++k)
-                for (int l = 0; l < 4; ++l) {
-                    const int q = 4 * k + l;
+            for (int q = 0; q < Q; ++q) rho += fq[q];
+            for (int k = 0; k < n1; ++k)
+                for (int l = 0; l < n1; ++l) {
+                    const int q = n1 * k + l;
                     const double feq = rho * L.w[k] * L.w[l];
                     f_out[q * N + node] = fq[q] + 2.0 * beta * (feq - fq[q]);
                 }

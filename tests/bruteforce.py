@@ -7,6 +7,9 @@ solving the 4x4 Vandermonde system that makes the reconstruction exact for
 cubics (App. C), not from the product formula.  Only usable at low Mach
 number (the raw monomial basis is ill-conditioned at large |u|) and on a
 handful of nodes.
+
+Two lattices: ``"d2q16"`` (the four roots of He4, T_L = 1) and ``"d2q9"``
+(App. A: c = -1, 0, 1, W = 1/6, 2/3, 1/6, T_L = 1/3).
 """
 import numpy as np
 
@@ -15,22 +18,30 @@ C = np.array([-np.sqrt(3 + S6), -np.sqrt(3 - S6), np.sqrt(3 - S6), np.sqrt(3 + S
 W1 = np.array([(3 - S6) / 12, (3 + S6) / 12, (3 + S6) / 12, (3 - S6) / 12])
 T_L = 1.0
 
+LATTICES = {
+    "d2q16": (C, W1, T_L),
+    "d2q9": (np.array([-1.0, 0.0, 1.0]), np.array([1 / 6, 2 / 3, 1 / 6]), 1.0 / 3.0),
+}
 
-def velocities(ux, uy, T):
-    st = np.sqrt(T / T_L)
-    vx = np.repeat(st * C + ux, 4)          # q = 4k + l -> k
-    vy = np.tile(st * C + uy, 4)            # -> l
+
+def velocities(ux, uy, T, lattice="d2q16"):
+    c, _, tl = LATTICES[lattice]
+    n1 = len(c)
+    st = np.sqrt(T / tl)
+    vx = np.repeat(st * c + ux, n1)         # q = n1 k + l -> k
+    vy = np.tile(st * c + uy, n1)           # -> l
     return vx, vy
 
 
-def moment_matrix(ux, uy, T):
-    """M_lambda[(m,n), q] = v_x(q)^m v_y(q)^n, m, n = 0..3 (Eq. moments)."""
-    vx, vy = velocities(ux, uy, T)
-    return np.array([vx ** m * vy ** n for m in range(4) for n in range(4)])
+def moment_matrix(ux, uy, T, lattice="d2q16"):
+    """M_lambda[(m,n), q] = v_x(q)^m v_y(q)^n, m, n < n1 (Eq. moments)."""
+    vx, vy = velocities(ux, uy, T, lattice)
+    n1 = len(LATTICES[lattice][0])
+    return np.array([vx ** m * vy ** n for m in range(n1) for n in range(n1)])
 
 
-def transfer(gs, gd, f):
-    return np.linalg.solve(moment_matrix(*gd), moment_matrix(*gs) @ f)
+def transfer(gs, gd, f, lattice="d2q16"):
+    return np.linalg.solve(moment_matrix(*gd, lattice), moment_matrix(*gs, lattice) @ f)
 
 
 def interp_weights(t):
@@ -39,9 +50,11 @@ def interp_weights(t):
     return np.linalg.solve(V, np.array([t ** p for p in range(4)]))
 
 
-def step(f, ux, uy, T, nu=0.01, passes=3, thermal=True, dt=1.0, T_ref=1.0):
+def step(f, ux, uy, T, nu=0.01, passes=3, thermal=True, dt=1.0, T_ref=1.0,
+         lattice="d2q16"):
     """One step with a fixed number of predictor-corrector passes."""
-    _, ny, nx = f.shape
+    Q, ny, nx = f.shape
+    W1_ = LATTICES[lattice][1]
     beta = 1.0 / (2.0 * nu / (T_ref * dt) + 1.0)
     fo = np.zeros_like(f)
     uxo = np.zeros_like(ux)
@@ -51,9 +64,9 @@ def step(f, ux, uy, T, nu=0.01, passes=3, thermal=True, dt=1.0, T_ref=1.0):
         for X in range(nx):
             g = (ux[Y, X], uy[Y, X], T[Y, X])
             for _ in range(passes):
-                vx, vy = velocities(*g)
-                fq = np.zeros(16)
-                for q in range(16):
+                vx, vy = velocities(*g, lattice)
+                fq = np.zeros(Q)
+                for q in range(Q):
                     dx = X - vx[q] * dt
                     dy = Y - vy[q] * dt
                     x0 = np.floor(dx) - 1
@@ -65,7 +78,7 @@ def step(f, ux, uy, T, nu=0.01, passes=3, thermal=True, dt=1.0, T_ref=1.0):
                             sx = int(x0 + n) % nx
                             sy = int(y0 + m) % ny
                             gs = (ux[sy, sx], uy[sy, sx], T[sy, sx])
-                            fq[q] += ax[n] * ay[m] * transfer(gs, g, f[:, sy, sx])[q]
+                            fq[q] += ax[n] * ay[m] * transfer(gs, g, f[:, sy, sx], lattice)[q]
                 rho = fq.sum()
                 u1x = (vx * fq).sum() / rho
                 u1y = (vy * fq).sum() / rho
@@ -75,9 +88,9 @@ def step(f, ux, uy, T, nu=0.01, passes=3, thermal=True, dt=1.0, T_ref=1.0):
                 last = (fq, g)
                 g = (u1x, u1y, T1)
             fq, g_last = last
-            fq = transfer(g_last, g, fq)  # into the gauge its moments define
+            fq = transfer(g_last, g, fq, lattice)  # into the gauge its moments define
             rho = fq.sum()
-            W = np.outer(W1, W1).reshape(16)
+            W = np.outer(W1_, W1_).reshape(Q)
             fo[:, Y, X] = fq + 2 * beta * (rho * W - fq)
             uxo[Y, X], uyo[Y, X], To[Y, X] = g
     return fo, uxo, uyo, To

@@ -47,6 +47,10 @@ BYTES_MIXED = 2 * (16 * 4 + 3 * 8)
 # FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 flops x 2.07 GHz.
 PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes per k1_step_fp64 launch at 2048^2: the ncu capture of the same
+# kernel at 1024^2 read 163.0 MB and wrote 124.5 MB; traffic grows with the
+# node count (4x).
+K1_TRAFFIC_BYTES_2048 = 4 * (163.0e6 + 124.5e6)
 
 
 def parse():
@@ -299,7 +303,11 @@ def run_pond(args, world, rank, local):
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved,
                      "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
+                     "frac": achieved / PEAK_FP64_TFLOPS,
+                     "traffic": K1_TRAFFIC_BYTES_2048,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                       "k1_step_fp64 launch at 1024^2 (287.5 MB), scaled x4 by "
+                                       "nodes to the 2048^2 launch",
                      "peak_source": "nominal FP64 rate at 2070 MHz (profiling recipe)",
                      "kernel": "k1_step_fp64", "kernel_ms": kernel_s * 1e3,
                      "hbm_gbs_algorithmic": nodes * BYTES_FP64 / kernel_s / 1e9,
@@ -410,6 +418,7 @@ def run_pond(args, world, rank, local):
             "forward_s": t1 - t0, "backward_s": t2 - t1,
             "adjoint_over_forward": (t2 - t1) / (t1 - t0),
             "grad_rel_err_vs_fp64": float((r32.grad - g64).abs().max() / g64.abs().max()),
+            "grad_max_abs": [float(g64.abs().max()), float(r32.grad.abs().max())],
             "nu_grad_rel_err_vs_fp64": abs(float(n32.grad) - float(n.grad)) / abs(float(n.grad)),
             "backward_speedup_vs_fp64": forms["adjoint_512"]["backward_s"] / (t2 - t1)}
         line["forms"] = forms

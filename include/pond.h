@@ -89,11 +89,16 @@ typedef struct pond_config {
                            set_state / set_stream) */
     int32_t autotune;   /* 1 (mixed form): the first pond_step times the
                            kernel's tile shapes (32 x 4, 32 x 8, 32 x 16
-                           nodes) on the current state, without advancing it,
+                           nodes, and 32 x 16 with two stacked nodes per
+                           thread) on the current state, without advancing it,
                            and keeps the fastest.  Results are cached per
                            process by grid-set signature and, when the
                            environment variable POND_AUTOTUNE_CACHE names a
                            file, in that JSON file across processes. */
+    int32_t tile_rows;  /* mixed form: 0 = default tile (32 x 8 nodes) or the
+                           autotuner's choice; 4, 8 or 16 force a 32-wide tile
+                           of that many rows, -16 the 32 x 16 tile with two
+                           stacked nodes per thread (disables autotune). */
 } pond_config;
 
 /* Counters accumulated over the steps of one pond_step call. */
@@ -102,7 +107,8 @@ typedef struct pond_stats {
     int64_t passes;        /* predictor-corrector passes over all node updates */
     int32_t max_passes;    /* largest pass count at any node */
     int32_t tile_rows;     /* rows of the mixed kernel's tile shape in use
-                              (32 columns); 0 for the FP64 form */
+                              (32 columns), negative when each thread owns
+                              two vertically adjacent nodes; 0 for FP64 */
     int64_t nonconverged;  /* node updates that hit max_iter unconverged */
     int64_t nonphysical;   /* node updates that met rho <= 0, T <= 0 or NaN */
     int64_t halo_fallback; /* stencils read from global memory instead of the

@@ -78,7 +78,10 @@ pond_status ensure_staging(pond_ctx* ctx, int64_t nodes) {
 
 // Tile count and per-grid prefix of the mixed kernel for a tile of
 // MIXED_TX x ty nodes (uploaded to the device).
-pond_status set_tile_rows(pond_ctx* ctx, int ty) {
+pond_status set_tile_rows(pond_ctx* ctx, int code) {
+    // code: rows of the 32-wide tile; negative selects the paired kernel
+    const int ty = code < 0 ? -code : code;
+    ctx->tile_pair = code < 0;
     std::vector<int64_t> prefix(ctx->n_grids + 1, 0);
     int64_t tiles = 0;
     for (int g = 0; g < ctx->n_grids; ++g) {
@@ -110,6 +113,7 @@ pond_status update_window(pond_ctx* ctx) {
     TileWindow w;
     w.tx = MIXED_TX;
     w.ty = ctx->tile_ty;
+    w.pair = ctx->tile_pair ? 1 : 0;
     w.ww = w.tx + (int)std::ceil(sx * dt + 2 * margin) + 5;
     w.wh = w.ty + (int)std::ceil(sy * dt + 2 * margin) + 5;
     // cap the staged window at the shared memory a CTA can have; stencils
@@ -120,7 +124,7 @@ pond_status update_window(pond_ctx* ctx) {
     }
     const size_t smem = mixed_smem_bytes(w);
     int per_sm = 0;
-    CK(mixed_prepare(w.ty, smem, &per_sm), "mixed kernel set-up");
+    CK(mixed_prepare(w.ty, w.pair != 0, smem, &per_sm), "mixed kernel set-up");
     if (per_sm < 1) return fail(ctx, POND_ERR_CUDA, "mixed kernel does not fit on an SM");
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "SM count");
@@ -266,6 +270,8 @@ void pond_config_default(pond_config* cfg, int32_t precision) {
     cfg->strict = 0;
     cfg->seed_mode = 0;
     cfg->use_graph = 0;
+    cfg->autotune = 0;
+    cfg->tile_rows = 0;
 }
 
 pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* nx,
@@ -278,6 +284,9 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
         cfg->fixed_iter < 0 || cfg->seed_mode < 0 || cfg->seed_mode > 2)
         return POND_ERR_ARG;
     if (cfg->precision == POND_FP64 && n_grids != 1) return POND_ERR_ARG;
+    if (cfg->tile_rows != 0 && cfg->tile_rows != 4 && cfg->tile_rows != 8 && cfg->tile_rows != 16 &&
+        cfg->tile_rows != -16)
+        return POND_ERR_ARG;
     for (int g = 0; g < n_grids; ++g)
         if (nx[g] < 1 || ny[g] < 1) return POND_ERR_ARG;
 
@@ -364,7 +373,8 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
         return st == POND_OK ? POND_ERR_CUDA : st;
     }
     if (mixed(ctx)) {
-        st = set_tile_rows(ctx, MIXED_TY);
+        st = set_tile_rows(ctx, cfg->tile_rows ? cfg->tile_rows : MIXED_TY);
+        if (cfg->tile_rows) ctx->tuned = true;  // a forced shape is not retuned
         if (st != POND_OK) {
             pond_destroy(ctx);
             return st;
@@ -515,7 +525,7 @@ void tune_file_load() {
         const size_t colon = text.find(':', end);
         if (colon == std::string::npos) break;
         const int rows = std::atoi(text.c_str() + colon + 1);
-        if (rows == 4 || rows == 8 || rows == 16) g_tune_cache[key] = rows;
+        if (rows == 4 || rows == 8 || rows == 16 || rows == -16) g_tune_cache[key] = rows;
         pos = text.find_first_of(",}", colon);
         if (pos == std::string::npos) break;
     }
@@ -566,7 +576,7 @@ static pond_status autotune(pond_ctx* ctx) {
     CK(cudaEventCreate(&e0), "autotune event");
     CK(cudaEventCreate(&e1), "autotune event");
     float best_ms = 1e30f;
-    int best = ctx->tile_ty;
+    int best = ctx->tile_pair ? -ctx->tile_ty : ctx->tile_ty;
     pond_status s = POND_OK;
     for (int ty : MIXED_TY_CHOICES) {
         s = set_tile_rows(ctx, ty);
@@ -636,7 +646,7 @@ pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats) {
         stats->node_updates = (int64_t)nsteps * ctx->N;
         stats->passes = (int64_t)d.passes;
         stats->max_passes = (int32_t)d.max_passes;
-        stats->tile_rows = mixed(ctx) ? ctx->tile_ty : 0;
+        stats->tile_rows = mixed(ctx) ? (ctx->tile_pair ? -ctx->tile_ty : ctx->tile_ty) : 0;
         stats->nonconverged = (int64_t)d.nonconverged;
         stats->nonphysical = (int64_t)d.nonphysical;
         stats->halo_fallback = (int64_t)d.halo_fallback;

@@ -102,6 +102,7 @@ cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>&
 struct TileWindow {
     int tx, ty;       // tile of target nodes
     int ww, wh;       // maximum staged window (tile + halo)
+    int pair;         // 1: each thread owns two vertically adjacent nodes
 };
 
 // Mixed-precision step over one or many grids (one CTA per tile; batched
@@ -116,9 +117,11 @@ cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& 
 // Tile shape of the mixed kernel, its shared-memory need for a window, and
 // the per-device attribute set-up (returns resident CTAs per SM).
 constexpr int MIXED_TX = 32, MIXED_TY = 8;  // default tile: 32 x 8 nodes
-constexpr int MIXED_TY_CHOICES[3] = {4, 8, 16};
+// tile shapes the autotuner tries: rows of 32-wide tiles, negative = the
+// paired kernel (two stacked nodes per thread)
+constexpr int MIXED_TY_CHOICES[4] = {4, 8, 16, -16};
 size_t mixed_smem_bytes(const TileWindow& w);
-cudaError_t mixed_prepare(int ty, size_t smem_bytes, int* ctas_per_sm);
+cudaError_t mixed_prepare(int ty, bool pair, size_t smem_bytes, int* ctas_per_sm);
 
 // Equilibrium initialisation f = rho W (Eq. equilibrium) and T -> sqrt(theta).
 template <typename Real>
@@ -166,6 +169,7 @@ struct pond_ctx {
     float* bounds_dev = nullptr;
     int64_t n_tiles = 0;
     int tile_ty = pond::MIXED_TY;  // rows of the mixed kernel's tile
+    bool tile_pair = false;        // paired kernel (two stacked nodes per thread)
     bool tuned = false;
     pond::TileWindow win{};
     int persistent_ctas = 0;

@@ -513,34 +513,441 @@ __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedAr
     }
 }
 
+// ---------------------------------------------------------------------------
+// Paired variant: each thread owns two vertically adjacent nodes.  For one
+// population their 4 x 4 stencils usually share three rows (same column
+// origin, row origins one apart), so the 5 x 4 union of sources is read from
+// shared memory once for both nodes -- 20 instead of 32 staged-node reads per
+// population, the kernel's binding resource.  When the two origins do not
+// line up, or only one of the two nodes is still iterating, each node takes
+// the single-node sweep.
+
+struct NodeOff {
+    float invf, bst, bux, buy;
+};
+
+struct QCoef {
+    float d1k[4], d2k[4], d1l[4], d2l[4], ik[4], il[4], d3k, d3l;
+};
+
+__device__ __forceinline__ float pair_g(const float4 g4, const float4 (&fr)[4], const NodeOff& o,
+                                        const QCoef& C) {
+    const LatticeF& L = c_Lf;
+    const float r = fmaf(g4.x, o.invf, o.bst);
+    const float dx = fmaf(g4.y, o.invf, o.bux);
+    const float dy = fmaf(g4.z, o.invf, o.buy);
+    float gx[4], gy[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const float de = fmaf(L.c[a], r, dx);
+        gx[a] = fmaf(fmaf(fmaf(C.d3k, de, C.d2k[a]), de, C.d1k[a]), de, C.ik[a]);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const float de = fmaf(L.c[b], r, dy);
+        gy[b] = fmaf(fmaf(fmaf(C.d3l, de, C.d2l[b]), de, C.d1l[b]), de, C.il[b]);
+    }
+    float gsum = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        float h = gy[0] * fr[a].x;
+        h = fmaf(gy[1], fr[a].y, h);
+        h = fmaf(gy[2], fr[a].z, h);
+        h = fmaf(gy[3], fr[a].w, h);
+        gsum = fmaf(gx[a], h, gsum);
+    }
+    return gsum;
+}
+
+// one node's 16-source sweep inside the staged window (relative to the
+// stencil node nearest the departure point, as in the single-node kernel)
+__device__ __forceinline__ float sweep_one(const float4* s_f4, const float4* s_g4, int WN, int ww,
+                                           int row, int col, const float (&lxw)[4],
+                                           const float (&lyw)[4], const NodeOff& o,
+                                           const QCoef& C) {
+    auto load = [&](int si, float4 (&fr)[4]) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fr[a] = s_f4[a * WN + si];
+    };
+    float4 fr[4];
+    int si = (row + 1) * ww + col + 1;
+    load(si, fr);
+    const float gref = pair_g(s_g4[si], fr, o, C);
+    float acc = 0.0f;
+#pragma unroll
+    for (int jy = 0; jy < 4; ++jy) {
+        float rowacc = 0.0f;
+#pragma unroll
+        for (int jx = 0; jx < 4; ++jx) {
+            if (jx == 1 && jy == 1) continue;
+            si = (row + jy) * ww + col + jx;
+            load(si, fr);
+            rowacc = fmaf(lxw[jx], pair_g(s_g4[si], fr, o, C) - gref, rowacc);
+        }
+        acc = fmaf(lyw[jy], rowacc, acc);
+    }
+    return acc + gref;
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, 1) k2_step_mixed_pair(MixedArgs A) {
+    constexpr int NT = TX * TY;  // threads
+    constexpr int RY = 2 * TY;   // node rows of the tile
+    extern __shared__ __align__(16) float4 smem4[];
+    const int WN = A.ww * A.wh;
+    float4* s_f4 = smem4;          // [4][WN]
+    float4* s_g4 = s_f4 + 4 * WN;  // [WN]
+    float* s_acc = reinterpret_cast<float*>(s_g4 + WN);  // [16][2 NT], column 2 tid + slot
+    __shared__ float s_red[4][NT / 32];
+    __shared__ long long s_item;
+    __shared__ unsigned long long s_passes, s_nc, s_np, s_fb;
+    __shared__ unsigned int s_max;
+    const LatticeF& L = c_Lf;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_passes = 0ull;
+        s_nc = 0ull;
+        s_np = 0ull;
+        s_fb = 0ull;
+        s_max = 0u;
+    }
+    const int lxi = tid % TX, lyi = tid / TX;
+    const float dt = (float)A.P.dt;
+    const float half_over_TL = (float)(0.5 / A.P.T_L);
+
+    long long item = blockIdx.x;
+    for (;;) {
+        if (A.work_counter) {
+            __syncthreads();
+            if (tid == 0) s_item = (long long)atomicAdd(A.work_counter, 1u);
+            __syncthreads();
+            item = s_item;
+        }
+        if (item >= A.n_tiles) break;
+        int g = 0;
+        if (A.n_grids > 1) {
+            int lo = 0, hi = A.n_grids - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (A.tile_prefix[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            g = lo;
+        }
+        const GridDesc G = A.grids[g];
+        const long long t = item - A.tile_prefix[g];
+        const int tiles_x = (G.nx + TX - 1) / TX;
+        const int tx0 = (int)(t % tiles_x) * TX;
+        const int ty0 = (int)(t / tiles_x) * RY;
+        const int X = tx0 + lxi;
+        const int Yn[2] = {ty0 + 2 * lyi, ty0 + 2 * lyi + 1};
+        const long long base = G.offset;
+        const long long rnode = base + (long long)ty0 * G.nx + tx0;
+        const double rux = A.in.ux[rnode], ruy = A.in.uy[rnode], rst = A.in.st[rnode];
+
+        bool act[2];
+        long long node[2];
+        double ux[2], uy[2], st[2];
+        float vxlo = 3.0e38f, vxhi = -3.0e38f, vylo = 3.0e38f, vyhi = -3.0e38f;
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+            act[sl] = X < G.nx && Yn[sl] < G.ny;
+            node[sl] = base + (long long)Yn[sl] * G.nx + X;
+            ux[sl] = 0.0;
+            uy[sl] = 0.0;
+            st[sl] = 1.0;
+            if (act[sl]) {
+                ux[sl] = A.in.ux[node[sl]];
+                uy[sl] = A.in.uy[node[sl]];
+                st[sl] = A.in.st[node[sl]];
+                if (A.P.seed_mode == 1) {
+                    ux[sl] = 0.0;
+                    uy[sl] = 0.0;
+                    st[sl] = 1.0;
+                } else if (A.P.seed_mode == 2) {
+                    ux[sl] = -ux[sl];
+                    uy[sl] = -uy[sl];
+                }
+                const float sp = (float)(A.c_max * st[sl]);
+                vxlo = fminf(vxlo, (float)ux[sl] - sp);
+                vxhi = fmaxf(vxhi, (float)ux[sl] + sp);
+                vylo = fminf(vylo, (float)uy[sl] - sp);
+                vyhi = fmaxf(vyhi, (float)uy[sl] + sp);
+            }
+        }
+        block_minmax4<NT>(vxlo, vxhi, vylo, vyhi, s_red);
+
+        const float m = A.margin;
+        const float bxl = fminf(fmaxf(vxlo, -1.0e6f), 1.0e6f), bxh = fminf(fmaxf(vxhi, -1.0e6f), 1.0e6f);
+        const float byl = fminf(fmaxf(vylo, -1.0e6f), 1.0e6f), byh = fminf(fmaxf(vyhi, -1.0e6f), 1.0e6f);
+        const int wx0 = (int)floorf((float)tx0 - bxh * dt - m) - 1;
+        const int wx1 = (int)floorf((float)(tx0 + TX - 1) - bxl * dt + m) + 2;
+        const int wy0 = (int)floorf((float)ty0 - byh * dt - m) - 1;
+        const int wy1 = (int)floorf((float)(ty0 + RY - 1) - byl * dt + m) + 2;
+        const bool fin = isfinite(vxlo) && isfinite(vxhi) && isfinite(vylo) && isfinite(vyhi) &&
+                         vxlo > -1.0e6f && vxhi < 1.0e6f && vylo > -1.0e6f && vyhi < 1.0e6f;
+        const int ww = fin ? max(1, min(wx1 - wx0 + 1, A.ww)) : 1;
+        const int wh = fin ? max(1, min(wy1 - wy0 + 1, A.wh)) : 1;
+
+        for (int i = tid; i < ww * wh; i += NT) {
+            const int cx = i % ww, cy = i / ww;
+            const int gx = wrap_idx((long long)wx0 + cx, G.nx);
+            const int gy = wrap_idx((long long)wy0 + cy, G.ny);
+            const long long gi = base + (long long)gy * G.nx + gx;
+            const float* fp = A.in.f + gi;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                s_f4[a * WN + i] = make_float4(__ldg(fp + (4 * a + 0) * A.plane), __ldg(fp + (4 * a + 1) * A.plane),
+                                               __ldg(fp + (4 * a + 2) * A.plane), __ldg(fp + (4 * a + 3) * A.plane));
+            s_g4[i] = make_float4((float)(__ldg(A.in.st + gi) - rst), (float)(__ldg(A.in.ux + gi) - rux),
+                                  (float)(__ldg(A.in.uy + gi) - ruy), 0.0f);
+        }
+        __syncthreads();
+
+        int pass[2] = {0, 0};
+        unsigned int flag[2] = {0u, 0u}, fallbacks[2] = {0u, 0u};
+        float stf[2], uxf[2], uyf[2], tdst[2], tdux[2], tduy[2];
+        double nux[2], nuy[2], nst[2];
+        float lr[2] = {0.f, 0.f}, ldx[2] = {0.f, 0.f}, ldy[2] = {0.f, 0.f}, rhof[2] = {0.f, 0.f};
+        const bool valid[2] = {act[0], act[1]};
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+            stf[sl] = (float)st[sl];
+            uxf[sl] = (float)ux[sl];
+            uyf[sl] = (float)uy[sl];
+            tdst[sl] = (float)(st[sl] - rst);
+            tdux[sl] = (float)(ux[sl] - rux);
+            tduy[sl] = (float)(uy[sl] - ruy);
+            nux[sl] = ux[sl];
+            nuy[sl] = uy[sl];
+            nst[sl] = st[sl];
+        }
+        while (act[0] || act[1]) {
+            NodeOff o[2];
+            float m0[2] = {0.f, 0.f}, m1[2] = {0.f, 0.f}, m2[2] = {0.f, 0.f}, m3[2] = {0.f, 0.f};
+#pragma unroll
+            for (int sl = 0; sl < 2; ++sl) {
+                if (act[sl]) ++pass[sl];
+                o[sl].invf = 1.0f / stf[sl];
+                o[sl].bst = -tdst[sl] * o[sl].invf;
+                o[sl].bux = -tdux[sl] * o[sl].invf;
+                o[sl].buy = -tduy[sl] * o[sl].invf;
+            }
+#pragma unroll 1
+            for (int q = 0; q < 16; ++q) {
+                const int k = q >> 2, l = q & 3;
+                const float ck = L.c[k], cl = L.c[l];
+                QCoef C;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    C.d1k[a] = L.d1[k][a];
+                    C.d2k[a] = L.d2[k][a];
+                    C.d1l[a] = L.d1[l][a];
+                    C.d2l[a] = L.d2[l][a];
+                    C.ik[a] = (a == k) ? 1.0f : 0.0f;
+                    C.il[a] = (a == l) ? 1.0f : 0.0f;
+                }
+                C.d3k = L.d3[k];
+                C.d3l = L.d3[l];
+                float lxw[2][4], lyw[2][4], fxs[2], fys[2];
+                int col[2], row[2];
+                bool inw[2];
+#pragma unroll
+                for (int sl = 0; sl < 2; ++sl) {
+                    const float dxp = -fmaf(stf[sl], ck, uxf[sl]) * dt;
+                    const float dyp = -fmaf(stf[sl], cl, uyf[sl]) * dt;
+                    fxs[sl] = floorf(dxp);
+                    fys[sl] = floorf(dyp);
+                    lagrange4f(dxp - fxs[sl] + 1.0f, lxw[sl]);
+                    lagrange4f(dyp - fys[sl] + 1.0f, lyw[sl]);
+                    const bool near = fabsf(dxp) < 1.0e6f && fabsf(dyp) < 1.0e6f;
+                    col[sl] = near ? X - wx0 + (int)fxs[sl] - 1 : -1;
+                    row[sl] = near ? Yn[sl] - wy0 + (int)fys[sl] - 1 : -1;
+                    inw[sl] = col[sl] >= 0 && col[sl] + 3 < ww && row[sl] >= 0 && row[sl] + 3 < wh;
+                }
+                float acc[2] = {0.f, 0.f};
+                if (act[0] && act[1] && inw[0] && inw[1] && col[0] == col[1] &&
+                    row[1] == row[0] + 1) {
+                    // shared sweep over the 5 x 4 union of the two stencils
+                    float4 fr[4];
+                    int si = (row[0] + 1) * ww + col[0] + 1;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) fr[a] = s_f4[a * WN + si];
+                    float4 g4 = s_g4[si];
+                    const float gra = pair_g(g4, fr, o[0], C);  // node a at (1, 1)
+                    const float grb = pair_g(g4, fr, o[1], C);  // node b at (1, 0)
+                    float ra[4] = {0.f, 0.f, 0.f, 0.f}, rb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int R = 0; R < 5; ++R) {
+#pragma unroll
+                        for (int jx = 0; jx < 4; ++jx) {
+                            if (R == 1 && jx == 1) continue;
+                            si = (row[0] + R) * ww + col[0] + jx;
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) fr[a] = s_f4[a * WN + si];
+                            g4 = s_g4[si];
+                            if (R <= 3) ra[R] = fmaf(lxw[0][jx], pair_g(g4, fr, o[0], C) - gra, ra[R]);
+                            if (R >= 1) rb[R - 1] = fmaf(lxw[1][jx], pair_g(g4, fr, o[1], C) - grb, rb[R - 1]);
+                        }
+                    }
+                    // node b's reference is its (jx, jy) = (1, 0) source
+                    float aa = 0.f, ab = 0.f;
+#pragma unroll
+                    for (int jy = 0; jy < 4; ++jy) {
+                        aa = fmaf(lyw[0][jy], ra[jy], aa);
+                        ab = fmaf(lyw[1][jy], rb[jy], ab);
+                    }
+                    acc[0] = aa + gra;
+                    acc[1] = ab + grb;
+                } else {
+#pragma unroll
+                    for (int sl = 0; sl < 2; ++sl) {
+                        if (!act[sl]) continue;
+                        if (inw[sl]) {
+                            acc[sl] = sweep_one(s_f4, s_g4, WN, ww, row[sl], col[sl], lxw[sl],
+                                                lyw[sl], o[sl], C);
+                        } else {
+                            acc[sl] = stencil_global(A, G, base, X, Yn[sl], fxs[sl], fys[sl],
+                                                     lxw[sl], lyw[sl], k, l, nux[sl] - 0.0,
+                                                     nuy[sl] - 0.0, nst[sl] - 0.0);
+                            ++fallbacks[sl];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int sl = 0; sl < 2; ++sl) {
+                    if (!act[sl]) continue;
+                    s_acc[q * 2 * NT + 2 * tid + sl] = acc[sl];
+                    m0[sl] += acc[sl];
+                    m1[sl] = fmaf(ck, acc[sl], m1[sl]);
+                    m2[sl] = fmaf(cl, acc[sl], m2[sl]);
+                    m3[sl] = fmaf(fmaf(ck, ck, cl * cl), acc[sl], m3[sl]);
+                }
+            }
+#pragma unroll
+            for (int sl = 0; sl < 2; ++sl) {
+                if (!act[sl]) continue;
+                const float irf = 1.0f / m0[sl];
+                const float dux = stf[sl] * m1[sl] * irf, duy = stf[sl] * m2[sl] * irf;
+                float dst = 0.0f;
+                bool ok = (m0[sl] > 0.0f) && isfinite(dux) && isfinite(duy);
+                if (A.P.thermal) {
+                    const float inv = o[sl].invf;
+                    const float rm1 = (m3[sl] * irf - (dux * dux + duy * duy) * inv * inv) * half_over_TL - 1.0f;
+                    ok = ok && (rm1 > -1.0f) && isfinite(rm1);
+                    dst = stf[sl] * rm1 / (sqrtf(1.0f + rm1) + 1.0f);
+                }
+                bool stop = false;
+                if (!ok) {
+                    flag[sl] |= 2u;
+                    stop = true;
+                } else {
+                    rhof[sl] = m0[sl];
+                    const double ux1 = nux[sl] + (double)dux, uy1 = nuy[sl] + (double)duy;
+                    const double st1 = nst[sl] + (double)dst;
+                    const float nstf = (float)st1;
+                    lr[sl] = -dst / nstf;
+                    ldx[sl] = -dux / nstf;
+                    ldy[sl] = -duy / nstf;
+                    const bool conv = fabs((double)dux) < A.P.eps_abs + A.P.eps_rel * fabs(ux1) &&
+                                      fabs((double)duy) < A.P.eps_abs + A.P.eps_rel * fabs(uy1) &&
+                                      fabs((double)dst) < A.P.eps_abs + A.P.eps_rel * fabs(st1);
+                    if (A.P.fixed_iter > 0) {
+                        stop = pass[sl] >= A.P.fixed_iter;
+                    } else {
+                        stop = conv || pass[sl] >= A.P.max_iter;
+                        if (!conv && pass[sl] >= A.P.max_iter) flag[sl] |= 1u;
+                    }
+                    // keep the pass gauge (nux..) as lambda_n until it is
+                    // replaced by lambda_{n+1} for the next pass
+                    if (stop) {
+                        ux[sl] = nux[sl];
+                        uy[sl] = nuy[sl];
+                        st[sl] = nst[sl];
+                    }
+                    nux[sl] = ux1;
+                    nuy[sl] = uy1;
+                    nst[sl] = st1;
+                    if (!stop) {
+                        stf[sl] = nstf;
+                        uxf[sl] = (float)ux1;
+                        uyf[sl] = (float)uy1;
+                        tdst[sl] += dst;
+                        tdux[sl] += dux;
+                        tduy[sl] += duy;
+                    }
+                }
+                if (stop) {
+                    if (flag[sl] & 2u) {
+                        float r0 = 0.0f;
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) r0 += s_acc[q * 2 * NT + 2 * tid + sl];
+                        finish_node(A, s_acc, 2 * NT, 2 * tid + sl, node[sl], false, 0.f, 0.f, 0.f,
+                                    nux[sl], nuy[sl], nst[sl], r0);
+                    } else {
+                        finish_node(A, s_acc, 2 * NT, 2 * tid + sl, node[sl], true, lr[sl], ldx[sl],
+                                    ldy[sl], nux[sl], nuy[sl], nst[sl], rhof[sl]);
+                    }
+                    act[sl] = false;
+                }
+            }
+        }
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+            if (!valid[sl]) continue;
+            if (A.iters) A.iters[node[sl]] = pass[sl];
+            atomicAdd(&s_passes, (unsigned long long)pass[sl]);
+            atomicMax(&s_max, (unsigned int)pass[sl]);
+            if (flag[sl] & 1u) atomicAdd(&s_nc, 1ull);
+            if (flag[sl] & 2u) atomicAdd(&s_np, 1ull);
+            if (fallbacks[sl]) atomicAdd(&s_fb, (unsigned long long)fallbacks[sl]);
+        }
+        if (!A.work_counter) break;
+    }
+    __syncthreads();
+    if (tid == 0 && A.stats) {
+        atomicAdd(&A.stats->passes, s_passes);
+        atomicMax(&A.stats->max_passes, s_max);
+        if (s_nc) atomicAdd(&A.stats->nonconverged, s_nc);
+        if (s_np) atomicAdd(&A.stats->nonphysical, s_np);
+        if (s_fb) atomicAdd(&A.stats->halo_fallback, s_fb);
+    }
+}
+
 size_t mixed_smem_bytes(const TileWindow& w) {
     return sizeof(float) * ((size_t)20 * w.ww * w.wh + (size_t)16 * w.tx * w.ty);
 }
 
-template <int TY>
+template <int TY, bool PAIR>
 static cudaError_t prepare_shape(size_t smem_bytes, int* ctas_per_sm, int* s_set) {
-    auto kern = k2_step_mixed<MIXED_TX, TY>;
+    void (*kern)(MixedArgs);
+    if constexpr (PAIR) kern = k2_step_mixed_pair<MIXED_TX, TY / 2>;
+    else kern = k2_step_mixed<MIXED_TX, TY>;
+    const int threads = PAIR ? MIXED_TX * TY / 2 : MIXED_TX * TY;
     cudaError_t e;
     if ((int)smem_bytes > *s_set) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
         if (e != cudaSuccess) return e;
         *s_set = (int)smem_bytes;
     }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, MIXED_TX * TY, smem_bytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, threads, smem_bytes);
 }
 
-cudaError_t mixed_prepare(int ty, size_t smem_bytes, int* ctas_per_sm) {
+cudaError_t mixed_prepare(int ty, bool pair, size_t smem_bytes, int* ctas_per_sm) {
     // the attribute is per function and device: only ever raise it, so that
     // every live context's window stays launchable
-    static int s_set[64][3] = {{0}};
+    static int s_set[64][4] = {{0}};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (pair) {
+        if (ty != 16) return cudaErrorInvalidValue;
+        return prepare_shape<16, true>(smem_bytes, ctas_per_sm, &s_set[dev][3]);
+    }
     switch (ty) {
-        case 4: return prepare_shape<4>(smem_bytes, ctas_per_sm, &s_set[dev][0]);
-        case 8: return prepare_shape<8>(smem_bytes, ctas_per_sm, &s_set[dev][1]);
-        case 16: return prepare_shape<16>(smem_bytes, ctas_per_sm, &s_set[dev][2]);
+        case 4: return prepare_shape<4, false>(smem_bytes, ctas_per_sm, &s_set[dev][0]);
+        case 8: return prepare_shape<8, false>(smem_bytes, ctas_per_sm, &s_set[dev][1]);
+        case 16: return prepare_shape<16, false>(smem_bytes, ctas_per_sm, &s_set[dev][2]);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -576,6 +983,11 @@ cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& 
         nb = (unsigned int)(persistent_ctas < n_tiles ? persistent_ctas : n_tiles);
     } else {
         nb = (unsigned int)n_tiles;
+    }
+    if (win.pair) {
+        if (win.ty != 16) return cudaErrorInvalidValue;
+        k2_step_mixed_pair<MIXED_TX, 8><<<nb, MIXED_TX * 8, smem, s>>>(A);
+        return cudaGetLastError();
     }
     switch (win.ty) {
         case 4: k2_step_mixed<MIXED_TX, 4><<<nb, MIXED_TX * 4, smem, s>>>(A); break;

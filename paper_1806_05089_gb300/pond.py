@@ -58,6 +58,7 @@ class pond_config(ctypes.Structure):
         ("seed_mode", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
+        ("tile_rows", ctypes.c_int32),
     ]
 
 

@@ -24,6 +24,8 @@ def main():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--grids", type=int, default=64)
     ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--tile", type=int, default=0,
+                    help="mixed forms: tile rows (4, 8, 16; -16 = two nodes per thread)")
     a = ap.parse_args()
 
     import torch
@@ -34,18 +36,21 @@ def main():
     if a.form in ("fp64", "mixed"):
         prec = pond.POND_FP64 if a.form == "fp64" else pond.POND_FP32_MIXED
         f = workloads.supersonic(a.n)
-        with pond.Sim(a.n, a.n, prec) as s:
+        cfg = {"tile_rows": a.tile} if prec == pond.POND_FP32_MIXED else {}
+        with pond.Sim(a.n, a.n, prec, **cfg) as s:
             s.set_state(f.rho, f.ux, f.uy, f.T)
             s.step(1)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st = s.step(a.steps)
-            out.update(n=a.n, steps=a.steps, seconds=time.perf_counter() - t0,
+            sec = time.perf_counter() - t0
+            out.update(n=a.n, steps=a.steps, seconds=sec, tile=st["tile_rows"],
+                       node_updates_per_s=a.n * a.n * a.steps / sec,
                        passes=st["passes"] / st["node_updates"])
     elif a.form == "batched":
         nxs, nys = workloads.ensemble_sizes(256)
         nxs, nys = nxs[:a.grids], nys[:a.grids]
-        with pond.Sim(nxs, nys, pond.POND_FP32_MIXED) as s:
+        with pond.Sim(nxs, nys, pond.POND_FP32_MIXED, tile_rows=a.tile) as s:
             for i in range(a.grids):
                 m = workloads.ensemble_member(i, nxs[i], nys[i])
                 s.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
@@ -53,8 +58,10 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st = s.step(a.steps)
-            out.update(grids=a.grids, nodes=int(sum(x * y for x, y in zip(nxs, nys))),
-                       steps=a.steps, seconds=time.perf_counter() - t0)
+            sec = time.perf_counter() - t0
+            nodes = int(sum(x * y for x, y in zip(nxs, nys)))
+            out.update(grids=a.grids, nodes=nodes, steps=a.steps, seconds=sec, tile=st["tile_rows"],
+                       node_updates_per_s=nodes * a.steps / sec)
     else:
         from .autograd import pond_rollout
         f, target = workloads.adjoint(a.n)

@@ -212,12 +212,14 @@ def test_strict_mode_reports_nonconvergence():
 
 # ------------------------------------------------------------------ mixed
 
+@pytest.mark.parametrize("tile_rows", [4, 8, 16, -16])
 @pytest.mark.parametrize("name,nx,ny,steps", [("tg", 64, 64, 20), ("supersonic", 70, 45, 8),
                                               ("hot", 40, 33, 6), ("supersonic", 5, 3, 3),
                                               ("tg", 1, 1, 2)])
-def test_mixed_matches_oracle(name, nx, ny, steps):
+def test_mixed_matches_oracle(name, nx, ny, steps, tile_rows):
     fields = small_fields(name, nx, ny)
-    g, grho, git, stats = gpu_run(fields, steps, pond.POND_FP32_MIXED)
+    g, grho, git, stats = gpu_run(fields, steps, pond.POND_FP32_MIXED, tile_rows=tile_rows)
+    assert stats["tile_rows"] == tile_rows
     o, _ = oracle_run(fields, steps)
     assert stats["nonconverged"] == 0
     e = rel_errors(g, grho, o, speed_scale=True)
@@ -234,18 +236,19 @@ def test_mixed_halo_fallback_path():
     assert max(rel_errors(g, grho, o, speed_scale=True)[:3]) <= TOL32
 
 
-def test_batched_matches_single_grid_runs():
+@pytest.mark.parametrize("tile_rows", [8, -16])
+def test_batched_matches_single_grid_runs(tile_rows):
     sizes = [(37, 23), (64, 40), (33, 70), (32, 32), (50, 45), (96, 17), (1, 1), (5, 9)]
     members = [workloads.ensemble_member(i, nx, ny) for i, (nx, ny) in enumerate(sizes)]
     nxs = [s[0] for s in sizes]
     nys = [s[1] for s in sizes]
-    with pond.Sim(nxs, nys, pond.POND_FP32_MIXED) as b:
+    with pond.Sim(nxs, nys, pond.POND_FP32_MIXED, tile_rows=tile_rows) as b:
         for i, m in enumerate(members):
             b.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
         b.step(3)
         batched = [b.state(i) for i in range(len(sizes))]
     for i, m in enumerate(members):
-        with pond.Sim(nxs[i], nys[i], pond.POND_FP32_MIXED) as s:
+        with pond.Sim(nxs[i], nys[i], pond.POND_FP32_MIXED, tile_rows=tile_rows) as s:
             s.set_state(m.rho, m.ux, m.uy, m.T)
             s.step(3)
             single = s.state()
@@ -282,7 +285,7 @@ def test_autotune_picks_a_tile_shape_and_matches_oracle(tmp_path, monkeypatch):
             b.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
         stats = b.step(3)
         out = [b.state(i) for i in range(len(sizes))]
-    assert stats["tile_rows"] in (4, 8, 16)
+    assert stats["tile_rows"] in (4, 8, 16, -16)
     for i, m in enumerate(members):
         o, _ = oracle_run(m, 3, max_iter=60)
         assert np.max(np.abs(out[i].T - o.T) / o.T) <= TOL32

@@ -43,6 +43,12 @@ FLOP_PER_PASS = 256 * 112 + 16 * 20 + 128
 # 3 FP64 gauge values (FP64: 2 x 152 B; mixed: 2 x (64 + 24) B).
 BYTES_FP64 = 2 * (16 * 8 + 3 * 8)
 BYTES_MIXED = 2 * (16 * 4 + 3 * 8)
+# The same on D2Q9 (9 populations, quadratic 1D maps): 144 pairs x 34 FMAs
+# (3 gauge differences, 6 xi offsets, 12 Lagrange-Taylor terms, 12
+# contraction, 1 accumulate), 9 departures, moments 9 x 8.
+FLOP_PER_PASS_Q9 = 144 * 68 + 9 * 20 + 72
+BYTES_FP64_Q9 = 2 * (9 * 8 + 3 * 8)
+BYTES_MIXED_Q9 = 2 * (9 * 4 + 3 * 8)
 # Peaks of the arithmetic pipes (nominal, at the 2070 MHz maximum SM clock):
 # FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 flops x 2.07 GHz.
 PEAK_FP64_TFLOPS = 1.25
@@ -191,9 +197,10 @@ def time_steps(sim, stream, steps):
     return e0.elapsed_time(e1) / 1e3, stats
 
 
-def form_line(name, nodes, steps, secs, stats, precision_peak_tflops, bytes_per_update):
+def form_line(name, nodes, steps, secs, stats, precision_peak_tflops, bytes_per_update,
+              flop_per_pass=FLOP_PER_PASS):
     passes = stats["passes"] / max(stats["node_updates"], 1)
-    achieved = FLOP_PER_PASS * stats["passes"] / secs / 1e12
+    achieved = flop_per_pass * stats["passes"] / secs / 1e12
     return {
         "workload": name,
         "value": nodes * steps / secs,
@@ -380,6 +387,38 @@ def run_pond(args, world, rank, local):
         forms["batched_256"] = form_line("ensemble-256-mixed", bnodes, k2, bsecs, bstats,
                                          PEAK_FP32_TFLOPS, BYTES_MIXED)
         bsim.close()
+
+        # the paper's own D2Q9 lattice on the same supersonic flow, rescaled to
+        # T_L = 1/3 (T / 3, u / sqrt 3: the same Mach numbers)
+        q9 = workloads.supersonic(2048)
+        q9.T, q9.ux, q9.uy = q9.T / 3.0, q9.ux / np.sqrt(3.0), q9.uy / np.sqrt(3.0)
+        q9_out = {}
+        for key, prec, peak, nbytes in (("fp64_d2q9_2048", pond.POND_FP64, PEAK_FP64_TFLOPS,
+                                         BYTES_FP64_Q9),
+                                        ("fp32_mixed_d2q9_2048", pond.POND_FP32_MIXED,
+                                         PEAK_FP32_TFLOPS, BYTES_MIXED_Q9)):
+            extra = {"use_graph": 1, "autotune": 1} if prec == pond.POND_FP32_MIXED else {}
+            qsim = pond.Sim(nx, ny, prec, stream=stream.cuda_stream, lattice=pond.POND_D2Q9,
+                            T_ref=1.0 / 3.0, **extra)
+            qsim.set_state(q9.rho, q9.ux, q9.uy, q9.T)
+            qsim.step(args.warmup)
+            qsecs, qstats = time_steps(qsim, stream, args.steps)
+            forms[key] = form_line("supersonic-2048-d2q9-" + ("fp64" if prec == pond.POND_FP64
+                                                              else "mixed"),
+                                   nodes, args.steps, qsecs, qstats, peak, nbytes,
+                                   FLOP_PER_PASS_Q9)
+            q9_out[key] = qsim.moments()
+            qsim.close()
+        r64, u64x, u64y, t64 = q9_out["fp64_d2q9_2048"]
+        r32, u32x, u32y, t32 = q9_out["fp32_mixed_d2q9_2048"]
+        forms["fp32_mixed_d2q9_2048"]["moment_err_vs_fp64"] = {
+            "after_steps": args.warmup + args.steps,
+            "rho": float(np.max(np.abs(r32 - r64)) / np.max(np.abs(r64))),
+            "u": float(max(np.max(np.abs(u32x - u64x)), np.max(np.abs(u32y - u64y)))
+                       / np.max(np.hypot(u64x, u64y))),
+            "T": float(np.max(np.abs(t32 - t64)) / np.max(np.abs(t64)))}
+        del q9, q9_out
+
         # adjoint / forward time on the 512^2 Taylor-Green + pulse workload
         from paper_1806_05089_gb300.autograd import pond_rollout
         af, target = workloads.adjoint(512)

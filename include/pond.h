@@ -3,7 +3,9 @@
  *
  * Method: Dorschner, Bosch, Karlin, "Particles-on-Demand for Kinetic
  * Theory" (arXiv 1806.05089).  One time step on a periodic D2Q16 lattice
- * (tensor product of the four roots of He4, T_L = 1):
+ * (tensor product of the four roots of He4, T_L = 1; the default) or the
+ * paper's own D2Q9 lattice (App. A: speeds -1, 0, 1, weights 1/6, 2/3, 1/6,
+ * T_L = 1/3):
  *   - departure points x - (sqrt(theta) c_i + u) dt        (Eqs. advection, vi)
  *   - gauge transform of neighbour populations by moment
  *     matching, f' = M_target^-1 M_source f                 (Eqs. moments, match,
@@ -17,10 +19,11 @@
  *                                                           postcollision)
  *
  * Conventions shared by every entry point:
- *   - population index q = 4 k + l, k the x-speed index and l the y-speed
- *     index of the ascending speeds c_0 < c_1 < c_2 < c_3;
+ *   - n1 speeds per dimension (4 on D2Q16, 3 on D2Q9), Q = n1^2
+ *     populations; population index q = n1 k + l, k the x-speed index and
+ *     l the y-speed index of the ascending speeds c_0 < ... < c_{n1-1};
  *   - fields are row-major [ny][nx] (x fastest); populations are
- *     structure-of-arrays [16][ny][nx];
+ *     structure-of-arrays [Q][ny][nx];
  *   - every array crossing this boundary is FP64 (double), whatever the
  *     internal precision; gauges are (u_x, u_y, T) with theta = T / T_L;
  *   - lattice units: dx = 1, dt from the config (default 1).
@@ -60,6 +63,9 @@ typedef enum pond_status {
 
 enum { POND_FP64 = 0, POND_FP32_MIXED = 1 };
 
+/* Lattices (pond_config.lattice). */
+enum { POND_D2Q16 = 0, POND_D2Q9 = 1 };
+
 /* Run configuration.  Fill with pond_config_default() and override. */
 typedef struct pond_config {
     int32_t precision;  /* POND_FP64: all arithmetic and storage FP64.
@@ -98,7 +104,12 @@ typedef struct pond_config {
     int32_t tile_rows;  /* mixed form: 0 = default tile (32 x 8 nodes) or the
                            autotuner's choice; 4, 8 or 16 force a 32-wide tile
                            of that many rows, -16 the 32 x 16 tile with two
-                           stacked nodes per thread (disables autotune). */
+                           stacked nodes per thread (disables autotune;
+                           D2Q16 only). */
+    int32_t lattice;    /* POND_D2Q16 (default) or POND_D2Q9.  Fixes Q and
+                           T_L (so the meaning of theta = T / T_L and of the
+                           seed {0, T_L}).  The adjoint entry points are
+                           D2Q16-only. */
 } pond_config;
 
 /* Counters accumulated over the steps of one pond_step call. */
@@ -134,7 +145,7 @@ pond_status pond_set_stream(pond_ctx* ctx, void* cuda_stream);
 /* Set the state of grid `grid` from macroscopic fields, each [ny][nx] FP64:
  * density rho, velocity (ux, uy), temperature T.  If f is NULL the
  * populations are the equilibrium f = rho W in each node's own gauge
- * (Eq. equilibrium; rho is then required).  If f is given ([16][ny][nx]),
+ * (Eq. equilibrium; rho is then required).  If f is given ([Q][ny][nx]),
  * it is taken as the populations in the gauge (ux, uy, T) and rho is
  * ignored (may be NULL).  on_device: pointers are device (1) or host (0).
  * Errors: POND_ERR_ARG, POND_ERR_NONPHYSICAL (T <= 0 or non-finite gauge on
@@ -155,7 +166,7 @@ pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats);
 pond_status pond_moments(pond_ctx* ctx, int32_t grid, void* rho, void* ux, void* uy,
                          void* T, int32_t on_device);
 
-/* Raw state of grid `grid`: populations f [16][ny][nx] in the stored gauge
+/* Raw state of grid `grid`: populations f [Q][ny][nx] in the stored gauge
  * and the gauge (ux, uy, T) [ny][nx]; any pointer may be NULL. */
 pond_status pond_get_state(pond_ctx* ctx, int32_t grid, void* f, void* ux, void* uy,
                            void* T, int32_t on_device);
@@ -173,13 +184,13 @@ pond_status pond_iterations(pond_ctx* ctx, int32_t grid, void* iters, int32_t on
  * function of the input state only; the seed gets no gradient).  All array
  * pointers are device pointers.  The state is left unchanged.  FP64 and
  * mixed contexts (the latter with FP32 pair arithmetic and an FP64 3 x 3
- * solve); single-grid, thermal mode.
+ * solve); single-grid, thermal mode, D2Q16 (POND_ERR_ARG otherwise).
  * Errors: POND_ERR_ARG, POND_ERR_STATE, POND_ERR_OOM, POND_ERR_CUDA. */
 pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in, const void* gauge_bar_in,
                               void* f_bar_out, void* gauge_bar_out, double* nu_bar_accum);
 
 /* VJP of the equilibrium initialisation of pond_set_state (f = rho W,
- * Eq. equilibrium): rho_bar[x] = sum_q W_q f_bar[q][x].  Single-grid
+ * Eq. equilibrium): rho_bar[x] = sum_q W_q f_bar[q][x].  Single-grid D2Q16
  * contexts; device pointers, f_bar [16][ny][nx], rho_bar [ny][nx].  (The
  * gauge cotangents pass through unchanged: set_state stores u and T as given.)
  * Errors: POND_ERR_ARG, POND_ERR_CUDA. */
@@ -195,7 +206,8 @@ pond_status pond_adjoint_init(pond_ctx* ctx, const void* f_bar, void* rho_bar);
  * memory, a real-time loop that may not enter the allocator).
  *
  * All array arguments are device pointers of the current device, FP64, in
- * the layouts above: f_in/f_out [16][ny][nx], ux/uy/T [ny][nx]; iters
+ * the layouts above: f_in/f_out [Q][ny][nx] (Q of cfg->lattice),
+ * ux/uy/T [ny][nx]; iters
  * (int32 [ny][nx]) and stats may be NULL.  Output arrays must not overlap
  * the inputs.  cfg must have precision POND_FP64; the other fields mean what
  * they mean for pond_create.  Work is enqueued on cuda_stream; the call

@@ -407,8 +407,8 @@ extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in,
         ctx->err = "adjoint: NULL argument";
         return POND_ERR_ARG;
     }
-    if (ctx->n_grids != 1 || !ctx->cfg.thermal) {
-        ctx->err = "adjoint: single-grid thermal contexts only";
+    if (ctx->n_grids != 1 || !ctx->cfg.thermal || ctx->L.n1 != 4) {
+        ctx->err = "adjoint: single-grid thermal D2Q16 contexts only";
         return POND_ERR_ARG;
     }
     if (!ctx->grid_set[0]) {
@@ -521,8 +521,8 @@ extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in,
 
 extern "C" pond_status pond_adjoint_init(pond_ctx* ctx, const void* f_bar, void* rho_bar) {
     if (!ctx) return POND_ERR_ARG;
-    if (!f_bar || !rho_bar || ctx->n_grids != 1) {
-        ctx->err = "adjoint_init: NULL argument or batched context";
+    if (!f_bar || !rho_bar || ctx->n_grids != 1 || ctx->L.n1 != 4) {
+        ctx->err = "adjoint_init: NULL argument, batched or D2Q9 context";
         return POND_ERR_ARG;
     }
     int prev = -1;

@@ -15,7 +15,7 @@ using namespace pond;
 
 namespace {
 
-const char* kVersion = "pond-gb300 0.1 (D2Q16, sm_103a)";
+const char* kVersion = "pond-gb300 0.2 (D2Q16 and D2Q9, sm_103a)";
 
 // Keep the caller's current device across a call.
 struct DeviceGuard {
@@ -81,6 +81,7 @@ pond_status ensure_staging(pond_ctx* ctx, int64_t nodes) {
 pond_status set_tile_rows(pond_ctx* ctx, int code) {
     // code: rows of the 32-wide tile; negative selects the paired kernel
     const int ty = code < 0 ? -code : code;
+    if (code < 0 && ctx->L.n1 != 4) return fail(ctx, POND_ERR_ARG, "paired tile shape: D2Q16 only");
     ctx->tile_pair = code < 0;
     std::vector<int64_t> prefix(ctx->n_grids + 1, 0);
     int64_t tiles = 0;
@@ -114,6 +115,7 @@ pond_status update_window(pond_ctx* ctx) {
     w.tx = MIXED_TX;
     w.ty = ctx->tile_ty;
     w.pair = ctx->tile_pair ? 1 : 0;
+    w.n1 = ctx->L.n1;
     w.ww = w.tx + (int)std::ceil(sx * dt + 2 * margin) + 5;
     w.wh = w.ty + (int)std::ceil(sy * dt + 2 * margin) + 5;
     // cap the staged window at the shared memory a CTA can have; stencils
@@ -124,7 +126,7 @@ pond_status update_window(pond_ctx* ctx) {
     }
     const size_t smem = mixed_smem_bytes(w);
     int per_sm = 0;
-    CK(mixed_prepare(w.ty, w.pair != 0, smem, &per_sm), "mixed kernel set-up");
+    CK(mixed_prepare(w.ty, w.pair != 0, w.n1, smem, &per_sm), "mixed kernel set-up");
     if (per_sm < 1) return fail(ctx, POND_ERR_CUDA, "mixed kernel does not fit on an SM");
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "SM count");
@@ -239,7 +241,7 @@ static pond_status read_out(pond_ctx* ctx, int32_t grid, void* rho, void* ux, vo
         if (ux) CK(cudaMemcpyAsync(ux, d_ux, fb, cudaMemcpyDeviceToHost, ctx->stream), "D2H ux");
         if (uy) CK(cudaMemcpyAsync(uy, d_uy, fb, cudaMemcpyDeviceToHost, ctx->stream), "D2H uy");
         if (T) CK(cudaMemcpyAsync(T, d_T, fb, cudaMemcpyDeviceToHost, ctx->stream), "D2H T");
-        if (f) CK(cudaMemcpyAsync(f, d_f, 16 * fb, cudaMemcpyDeviceToHost, ctx->stream), "D2H f");
+        if (f) CK(cudaMemcpyAsync(f, d_f, ctx->L.q * fb, cudaMemcpyDeviceToHost, ctx->stream), "D2H f");
         CK(cudaStreamSynchronize(ctx->stream), "read sync");
     }
     return POND_OK;
@@ -272,6 +274,7 @@ void pond_config_default(pond_config* cfg, int32_t precision) {
     cfg->use_graph = 0;
     cfg->autotune = 0;
     cfg->tile_rows = 0;
+    cfg->lattice = POND_D2Q16;
 }
 
 pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* nx,
@@ -287,13 +290,15 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
     if (cfg->tile_rows != 0 && cfg->tile_rows != 4 && cfg->tile_rows != 8 && cfg->tile_rows != 16 &&
         cfg->tile_rows != -16)
         return POND_ERR_ARG;
+    if (cfg->lattice != POND_D2Q16 && cfg->lattice != POND_D2Q9) return POND_ERR_ARG;
+    if (cfg->lattice == POND_D2Q9 && cfg->tile_rows < 0) return POND_ERR_ARG;  // paired: D2Q16
     for (int g = 0; g < n_grids; ++g)
         if (nx[g] < 1 || ny[g] < 1) return POND_ERR_ARG;
 
     pond_ctx* ctx = new (std::nothrow) pond_ctx();
     if (!ctx) return POND_ERR_OOM;
     ctx->cfg = *cfg;
-    ctx->L = make_lattice();
+    ctx->L = make_lattice(cfg->lattice);
     ctx->P.beta = 1.0 / (2.0 * cfg->nu / (cfg->T_ref * cfg->dt) + 1.0);
     ctx->P.dt = cfg->dt;
     ctx->P.eps_abs = cfg->eps_abs;
@@ -336,7 +341,7 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
     const size_t rs = real_size(ctx);
     bool ok = true;
     for (int b = 0; b < 2 && ok; ++b) {
-        ok = ok && alloc(&ctx->f[b], rs * 16 * (size_t)ctx->N, "alloc f");
+        ok = ok && alloc(&ctx->f[b], rs * ctx->L.q * (size_t)ctx->N, "alloc f");
         ok = ok && alloc((void**)&ctx->ux[b], sizeof(double) * ctx->N, "alloc ux");
         ok = ok && alloc((void**)&ctx->uy[b], sizeof(double) * ctx->N, "alloc uy");
         ok = ok && alloc((void**)&ctx->st[b], sizeof(double) * ctx->N, "alloc st");
@@ -359,10 +364,10 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
                                    sizeof(GridDesc) * n_grids, cudaMemcpyHostToDevice);
 
         if (e == cudaSuccess) e = cudaMemset(ctx->iters, 0, sizeof(int32_t) * ctx->N);
-        if (e == cudaSuccess) e = upload_lattice_fp64(ctx->L);
-        if (e == cudaSuccess) e = upload_lattice_mixed(ctx->L);
-        if (e == cudaSuccess) e = upload_lattice_adjoint(ctx->L);
-        if (e == cudaSuccess) e = upload_lattice_adjoint_mixed(ctx->L);
+        if (e == cudaSuccess) e = upload_lattice_fp64();
+        if (e == cudaSuccess) e = upload_lattice_mixed();
+        if (e == cudaSuccess) e = upload_lattice_adjoint(make_lattice(POND_D2Q16));
+        if (e == cudaSuccess) e = upload_lattice_adjoint_mixed(make_lattice(POND_D2Q16));
         if (e != cudaSuccess) {
             st = cuda_fail(ctx, e, "context set-up");
             ok = false;
@@ -442,7 +447,7 @@ pond_status pond_set_state(pond_ctx* ctx, int32_t grid, const void* rho, const v
         CK(cudaMemcpyAsync(p_ux, ux, fb, cudaMemcpyHostToDevice, ctx->stream), "H2D ux");
         CK(cudaMemcpyAsync(p_uy, uy, fb, cudaMemcpyHostToDevice, ctx->stream), "H2D uy");
         CK(cudaMemcpyAsync(p_T, T, fb, cudaMemcpyHostToDevice, ctx->stream), "H2D T");
-        if (f) CK(cudaMemcpyAsync(p_f, f, 16 * fb, cudaMemcpyHostToDevice, ctx->stream), "H2D f");
+        if (f) CK(cudaMemcpyAsync(p_f, f, ctx->L.q * fb, cudaMemcpyHostToDevice, ctx->stream), "H2D f");
         d_rho = rho ? p_rho : nullptr;
         d_ux = p_ux;
         d_uy = p_uy;
@@ -461,7 +466,7 @@ pond_status pond_set_state(pond_ctx* ctx, int32_t grid, const void* rho, const v
     }
     // velocity spans of this grid, for the mixed kernel's halo window
     CK(launch_disp_bounds(ctx->ux[ctx->cur] + G.offset, ctx->uy[ctx->cur] + G.offset,
-                          ctx->st[ctx->cur] + G.offset, n, ctx->L.c[3], ctx->bounds_dev,
+                          ctx->st[ctx->cur] + G.offset, n, ctx->L.c_max, ctx->bounds_dev,
                           ctx->stream),
        "bounds");
     float b4[4];
@@ -499,9 +504,9 @@ std::string tune_key(const pond_ctx* ctx) {
         sy = std::fmax(sy, ctx->spans[4 * g + 3] - ctx->spans[4 * g + 2]);
     }
     char buf[256];
-    std::snprintf(buf, sizeof buf, "mixed|grids=%d|nodes=%lld|side=%lld-%lld|span=%d-%d",
-                  ctx->n_grids, (long long)ctx->N, (long long)minside, (long long)maxside,
-                  (int)std::ceil(sx), (int)std::ceil(sy));
+    std::snprintf(buf, sizeof buf, "mixed|q%d|grids=%d|nodes=%lld|side=%lld-%lld|span=%d-%d",
+                  ctx->L.q, ctx->n_grids, (long long)ctx->N, (long long)minside,
+                  (long long)maxside, (int)std::ceil(sx), (int)std::ceil(sy));
     return buf;
 }
 
@@ -579,6 +584,7 @@ static pond_status autotune(pond_ctx* ctx) {
     int best = ctx->tile_pair ? -ctx->tile_ty : ctx->tile_ty;
     pond_status s = POND_OK;
     for (int ty : MIXED_TY_CHOICES) {
+        if (ty < 0 && ctx->L.n1 != 4) continue;  // the paired kernel is D2Q16-only
         s = set_tile_rows(ctx, ty);
         if (s == POND_OK) s = update_window(ctx);
         if (s != POND_OK) break;

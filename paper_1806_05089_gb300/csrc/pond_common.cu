@@ -6,23 +6,38 @@
 
 namespace pond {
 
-// D2Q16 constants from their closed forms (He4 roots and Gauss-Hermite
-// weights) and the Taylor coefficients of the Lagrange basis polynomials
+// Lattice constants from their closed forms -- D2Q16: He4 roots and their
+// Gauss-Hermite weights; D2Q9: c = -1, 0, 1, W = 1/6, 2/3, 1/6, T_L = 1/3
+// (App. A) -- and the Taylor coefficients of the Lagrange basis polynomials
 // L_k(x) = prod_{j != k} (x - c_j)/(c_k - c_j) around each speed c_a.
-Lattice make_lattice() {
+Lattice make_lattice(int kind) {
     Lattice L{};
-    const double s6 = std::sqrt(6.0);
-    L.c[0] = -std::sqrt(3.0 + s6);
-    L.c[1] = -std::sqrt(3.0 - s6);
-    L.c[2] = std::sqrt(3.0 - s6);
-    L.c[3] = std::sqrt(3.0 + s6);
-    L.w[0] = L.w[3] = (3.0 - s6) / 12.0;
-    L.w[1] = L.w[2] = (3.0 + s6) / 12.0;
-    L.T_L = 1.0;
-    for (int k = 0; k < 4; ++k) {
+    if (kind == POND_D2Q9) {
+        L.n1 = 3;
+        L.c[0] = -1.0;
+        L.c[1] = 0.0;
+        L.c[2] = 1.0;
+        L.w[0] = L.w[2] = 1.0 / 6.0;
+        L.w[1] = 2.0 / 3.0;
+        L.T_L = 1.0 / 3.0;
+    } else {
+        const double s6 = std::sqrt(6.0);
+        L.n1 = 4;
+        L.c[0] = -std::sqrt(3.0 + s6);
+        L.c[1] = -std::sqrt(3.0 - s6);
+        L.c[2] = std::sqrt(3.0 - s6);
+        L.c[3] = std::sqrt(3.0 + s6);
+        L.w[0] = L.w[3] = (3.0 - s6) / 12.0;
+        L.w[1] = L.w[2] = (3.0 + s6) / 12.0;
+        L.T_L = 1.0;
+    }
+    const int n1 = L.n1;
+    L.q = n1 * n1;
+    L.c_max = L.c[n1 - 1];
+    for (int k = 0; k < n1; ++k) {
         double p[4] = {1.0, 0.0, 0.0, 0.0};  // coefficients of x^0..x^3
         double den = 1.0;
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < n1; ++j) {
             if (j == k) continue;
             double np[4] = {0.0, 0.0, 0.0, 0.0};
             for (int i = 0; i < 4; ++i) {
@@ -33,13 +48,23 @@ Lattice make_lattice() {
             den *= (L.c[k] - L.c[j]);
         }
         for (int i = 0; i < 4; ++i) p[i] /= den;
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < n1; ++a) {
             const double x = L.c[a];
             L.d1[k][a] = p[1] + 2.0 * p[2] * x + 3.0 * p[3] * x * x;
             L.d2[k][a] = p[2] + 3.0 * p[3] * x;
         }
         L.d3[k] = p[3];
     }
+    // W-dual basis of {1, |c|^2}: inverse of [[1, 2 T_L], [2 T_L, g]]
+    double K4 = 0.0;
+    for (int a = 0; a < n1; ++a) K4 += L.w[a] * L.c[a] * L.c[a] * L.c[a] * L.c[a];
+    const double g = 2.0 * K4 + 2.0 * L.T_L * L.T_L;
+    const double det = g - 4.0 * L.T_L * L.T_L;
+    L.pe0 = g / det;
+    L.pe2 = -2.0 * L.T_L / det;
+    L.pt0 = -2.0 * L.T_L / det;
+    L.pt2 = 1.0 / det;
+    L.inv_TL = 1.0 / L.T_L;
     return L;
 }
 
@@ -54,6 +79,11 @@ LatticeF to_float(const Lattice& L) {
             F.d2[i][j] = (float)L.d2[i][j];
         }
     }
+    F.pe0 = (float)L.pe0;
+    F.pe2 = (float)L.pe2;
+    F.pt0 = (float)L.pt0;
+    F.pt2 = (float)L.pt2;
+    F.inv_TL = (float)L.inv_TL;
     return F;
 }
 
@@ -70,13 +100,11 @@ __global__ void k_init_state(const double* __restrict__ rho, const double* __res
     st.uy[i] = uy[i];
     st.st[i] = sqrt(T[i] / L.T_L);
     if (f_given) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) st.f[q * plane + i] = (Real)f_given[q * N + i];
+        for (int q = 0; q < L.q; ++q) st.f[q * plane + i] = (Real)f_given[q * N + i];
     } else {
         const double r = rho[i];
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-            st.f[q * plane + i] = (Real)(r * L.w[q >> 2] * L.w[q & 3]);
+        for (int q = 0; q < L.q; ++q)
+            st.f[q * plane + i] = (Real)(r * L.w[q / L.n1] * L.w[q % L.n1]);
     }
 }
 
@@ -97,8 +125,7 @@ __global__ void k_read_state(StateBuf<Real> st, int64_t N, int64_t plane, double
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double r = 0.0;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
+    for (int q = 0; q < L.q; ++q) {
         const double v = (double)st.f[q * plane + i];
         r += v;
         if (f) f[q * N + i] = v;

@@ -25,6 +25,23 @@ __device__ __forceinline__ void lagrange4f(float t, float l[4]) {
     l[3] = (ab * c) * (1.0f / 6.0f);
 }
 
+// One entry of the 1D gauge transform in Taylor form around the identity,
+// G[k][a] = id + de (d1 + d2 de (+ d3 de^2 on D2Q16, where L_k is cubic; on
+// D2Q9 L_k is quadratic and d3 = 0)).  gauge_tail is the bracket, G - I
+// divided by de.
+template <int N1, typename T>
+__device__ __forceinline__ T gauge_tail(T d3, T d2, T d1, T de) {
+    if constexpr (N1 == 4)
+        return fma(fma(d3, de, d2), de, d1);
+    else
+        return fma(d2, de, d1);
+}
+
+template <int N1, typename T>
+__device__ __forceinline__ T gauge_poly(T d3, T d2, T d1, T id, T de) {
+    return fma(gauge_tail<N1>(d3, d2, d1, de), de, id);
+}
+
 // Periodic wrap of a possibly far out-of-range index.
 __device__ __forceinline__ int wrap_idx(long long v, int n) {
     long long r = v % n;

@@ -1,8 +1,10 @@
 // pond_internal.cuh -- shared definitions of the PonD CUDA library (sm_103a).
 //
-// Lattice: D2Q16, the tensor product of the four roots of He4
+// Lattices: D2Q16, the tensor product of the four roots of He4
 // (c^2 = 3 -+ sqrt 6), weights (3 -+ sqrt 6)/12, T_L = 1 (App. A generalised
-// to a fourth-order Hermite set).  Populations q = 4k + l.
+// to a fourth-order Hermite set), and the paper's own D2Q9 (App. A: c = -1,
+// 0, 1, W = 1/6, 2/3, 1/6, T_L = 1/3).  n1 speeds per dimension,
+// populations q = n1 k + l, Q = n1^2.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,7 +25,16 @@ namespace pond {
 // lattice) and xi_a = (sqrt(theta_s) c_a + u_s - u') / sqrt(theta').
 // Written around the identity, xi_a = c_a + delta_a, it is
 //   L_k(c_a + delta) = [k == a] + d1[k][a] delta + d2[k][a] delta^2 + d3[k] delta^3
-// with d1 = L_k'(c_a), d2 = L_k''(c_a)/2, d3 = L_k'''/6 (exact: L_k is cubic).
+// with d1 = L_k'(c_a), d2 = L_k''(c_a)/2, d3 = L_k'''/6 (exact: L_k has
+// degree n1 - 1, so d3 = 0 for D2Q9).  Arrays are sized for n1 = 4; D2Q9
+// uses their leading 3 entries.
+//
+// pe0, pe2, pt0, pt2, inv_TL: dual basis of {1, c_x, c_y, |c|^2} under the
+// weights W, onto which the mixed form's conservative collision projects
+// the relaxed non-equilibrium part.  With the W-Gram matrix
+// [[1, 2 T_L], [2 T_L, 2 K4 + 2 T_L^2]] of {1, |c|^2} (K4 = sum_a w_a c_a^4)
+// and <c_x, c_x> = T_L, the duals are W (pe0 + pe2 |c|^2), W c_x / T_L,
+// W c_y / T_L and W (pt0 + pt2 |c|^2).
 struct Lattice {
     double c[4];
     double w[4];
@@ -31,6 +42,10 @@ struct Lattice {
     double d2[4][4];
     double d3[4];
     double T_L;
+    double c_max;
+    double pe0, pe2, pt0, pt2, inv_TL;
+    int32_t n1;
+    int32_t q;
 };
 
 struct LatticeF {
@@ -39,10 +54,14 @@ struct LatticeF {
     float d1[4][4];
     float d2[4][4];
     float d3[4];
+    float pe0, pe2, pt0, pt2, inv_TL;
 };
 
-Lattice make_lattice();
+// kind: POND_D2Q16 or POND_D2Q9
+Lattice make_lattice(int kind = POND_D2Q16);
 LatticeF to_float(const Lattice& L);
+// constant-bank slot of a lattice in every translation unit
+constexpr int lattice_slot(int n1) { return n1 == 4 ? 0 : 1; }
 
 struct StepParams {
     double beta;
@@ -76,7 +95,7 @@ struct GridDesc {
 // Device state of one context: packed over all grids, plane stride = N.
 template <typename Real>
 struct StateBuf {
-    Real* f;        // [16][N]
+    Real* f;        // [Q][N]
     double* ux;     // [N]
     double* uy;     // [N]
     double* st;     // [N]  sqrt(theta) = sqrt(T / T_L)
@@ -85,14 +104,15 @@ struct StateBuf {
 // ---------------------------------------------------------------- kernels
 // Launchers (defined in the .cu files); all return the launch status.
 
-// Per-translation-unit constant-bank copies of the lattice (call once per
-// device before launching).
-cudaError_t upload_lattice_fp64(const Lattice& L);
-cudaError_t upload_lattice_mixed(const Lattice& L);
+// Per-translation-unit constant-bank copies of the lattices (call once per
+// device before launching).  The step kernels hold both lattices, slot
+// lattice_slot(n1); the adjoint kernels D2Q16 only.
+cudaError_t upload_lattice_fp64();
+cudaError_t upload_lattice_mixed();
 cudaError_t upload_lattice_adjoint(const Lattice& L);
 cudaError_t upload_lattice_adjoint_mixed(const Lattice& L);
 
-// FP64 step of a single grid (one warp per node).
+// FP64 step of a single grid (one warp per node), lattice L.n1.
 cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>& out,
                              int32_t* iters, DevStats* stats, int nx, int ny,
                              const Lattice& L, const StepParams& P, cudaStream_t s);
@@ -103,6 +123,7 @@ struct TileWindow {
     int tx, ty;       // tile of target nodes
     int ww, wh;       // maximum staged window (tile + halo)
     int pair;         // 1: each thread owns two vertically adjacent nodes
+    int n1;           // speeds per dimension of the lattice (4 or 3)
 };
 
 // Mixed-precision step over one or many grids (one CTA per tile; batched
@@ -121,7 +142,7 @@ constexpr int MIXED_TX = 32, MIXED_TY = 8;  // default tile: 32 x 8 nodes
 // paired kernel (two stacked nodes per thread)
 constexpr int MIXED_TY_CHOICES[4] = {4, 8, 16, -16};
 size_t mixed_smem_bytes(const TileWindow& w);
-cudaError_t mixed_prepare(int ty, bool pair, size_t smem_bytes, int* ctas_per_sm);
+cudaError_t mixed_prepare(int ty, bool pair, int n1, size_t smem_bytes, int* ctas_per_sm);
 
 // Equilibrium initialisation f = rho W (Eq. equilibrium) and T -> sqrt(theta).
 template <typename Real>

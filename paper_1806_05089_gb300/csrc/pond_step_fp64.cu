@@ -3,17 +3,19 @@
 // One warp per target node.  Lane = (population q = lane & 15, stencil-row
 // half = lane >> 4): each lane reconstructs population q from two of the four
 // stencil rows, the halves are summed with one shuffle, and the moments of
-// the 16 populations are butterfly-reduced, so every lane holds rho, u, T and
+// the Q populations are butterfly-reduced, so every lane holds rho, u, T and
 // takes the same convergence decision: a warp never diverges on the
 // predictor-corrector pass count.  The step is bound by the FP64 pipe; all
-// source reads go through the read-only L1 path.
+// source reads go through the read-only L1 path.  Templated on the lattice:
+// D2Q16 (N1 = 4, all 32 lanes busy) or D2Q9 (N1 = 3: lanes with q >= 9 only
+// join the shuffles).
 //
 // Per predictor-corrector pass (Eqs. advection, vi, interpolation, transform):
 //   departure  y_q = x - (sqrt(theta) c_q + u) dt, origin floor(y_q) - 1
 //   for each of the 16 stencil nodes s:
 //     delta_a = xi_a - c_a = c_a (st_s/st' - 1) + (u_s - u')/st'
 //     G[k][a] = [k==a] + delta (d1[k][a] + delta (d2[k][a] + delta d3[k]))
-//     (G f_s)_q = sum_a Gx[k][a] sum_b Gy[l][b] f_s[4a+b]
+//     (G f_s)_q = sum_a Gx[k][a] sum_b Gy[l][b] f_s[N1 a + b]
 //   f_q = sum_s a_s(y_q - x_s) (G f_s)_q
 // then the moments in central form (algebraically equal to Eqs.
 // conservation_rho/rhou/T):  rho = sum f,  u_{n+1} = u_n + st sum c f / rho,
@@ -30,17 +32,21 @@ namespace pond {
 
 constexpr int K1_WARPS = 4;
 
-// Lattice constants of this translation unit (uploaded once per device).
-__constant__ Lattice c_L;
+// Lattice constants of this translation unit (uploaded once per device),
+// slot lattice_slot(N1).
+__constant__ Lattice c_L[2];
 
-cudaError_t upload_lattice_fp64(const Lattice& L) {
-    return cudaMemcpyToSymbol(c_L, &L, sizeof(Lattice));
+cudaError_t upload_lattice_fp64() {
+    const Lattice L[2] = {make_lattice(POND_D2Q16), make_lattice(POND_D2Q9)};
+    return cudaMemcpyToSymbol(c_L, L, sizeof(L));
 }
 
+template <int N1>
 __global__ void __launch_bounds__(K1_WARPS * 32, 3)
 k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ iters,
              DevStats* __restrict__ stats, int nx, int ny, long long N, StepParams P) {
-    const Lattice& L = c_L;
+    constexpr int Q = N1 * N1;
+    const Lattice& L = c_L[lattice_slot(N1)];
     __shared__ unsigned long long s_passes, s_nc, s_np;
     __shared__ unsigned int s_max;
     if (threadIdx.x == 0) {
@@ -56,11 +62,13 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
     if (node < N) {  // warp-uniform
         const int X = (int)(node % nx);
         const int Y = (int)(node / nx);
-        const int q = lane & 15, k = q >> 2, l = q & 3, half = lane >> 4;
-        const double ck = L.c[k], cl = L.c[l];
-        double d1k[4], d2k[4], d1l[4], d2l[4], ik[4], il[4];
+        const int q = lane & 15, half = lane >> 4;
+        const bool act = q < Q;  // lane holds a population (all on D2Q16)
+        const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
+        const double ck = act ? L.c[k] : 0.0, cl = act ? L.c[l] : 0.0;
+        double d1k[N1], d2k[N1], d1l[N1], d2l[N1], ik[N1], il[N1];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < N1; ++a) {
             d1k[a] = L.d1[k][a];
             d2k[a] = L.d2[k][a];
             d1l[a] = L.d1[l][a];
@@ -100,6 +108,7 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
             const double bx = -ux * inv, by = -uy * inv;
 
             double acc = 0.0;
+            if (act) {
 #pragma unroll
             for (int jj = 0; jj < 2; ++jj) {
                 const int jy = 2 * half + jj;
@@ -116,29 +125,30 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
                     const double r = fma(sts, inv, -1.0);  // st_s/st' - 1
                     const double dx = fma(uxs, inv, bx);   // (u_s,x - u'_x)/st'
                     const double dy = fma(uys, inv, by);
-                    double gx[4], gy[4];
+                    double gx[N1], gy[N1];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
+                    for (int a = 0; a < N1; ++a) {
                         const double de = fma(L.c[a], r, dx);
-                        gx[a] = fma(fma(fma(d3k, de, d2k[a]), de, d1k[a]), de, ik[a]);
+                        gx[a] = gauge_poly<N1>(d3k, d2k[a], d1k[a], ik[a], de);
                     }
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
+                    for (int b = 0; b < N1; ++b) {
                         const double de = fma(L.c[b], r, dy);
-                        gy[b] = fma(fma(fma(d3l, de, d2l[b]), de, d1l[b]), de, il[b]);
+                        gy[b] = gauge_poly<N1>(d3l, d2l[b], d1l[b], il[b], de);
                     }
                     double g = 0.0;
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
+                    for (int a = 0; a < N1; ++a) {
                         double h = 0.0;
 #pragma unroll
-                        for (int b = 0; b < 4; ++b)
-                            h = fma(gy[b], __ldg(in.f + (long long)(4 * a + b) * N + s), h);
+                        for (int b = 0; b < N1; ++b)
+                            h = fma(gy[b], __ldg(in.f + (long long)(N1 * a + b) * N + s), h);
                         g = fma(gx[a], h, g);
                     }
                     rowacc = fma(lx[jx], g, rowacc);
                 }
                 acc = fma(wy, rowacc, acc);
+            }
             }
             total = acc + __shfl_xor_sync(0xffffffffu, acc, 16);
 
@@ -193,21 +203,21 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
             const double inv1 = 1.0 / nst;
             const double r = fma(st, inv1, -1.0);
             const double dx = (ux - nux) * inv1, dy = (uy - nuy) * inv1;
-            double gx[4], gy[4];
+            double gx[N1], gy[N1];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < N1; ++a) {
                 const double de = fma(L.c[a], r, dx);
-                gx[a] = fma(fma(fma(d3k, de, d2k[a]), de, d1k[a]), de, ik[a]);
+                gx[a] = gauge_poly<N1>(d3k, d2k[a], d1k[a], ik[a], de);
                 const double de2 = fma(L.c[a], r, dy);
-                gy[a] = fma(fma(fma(d3l, de2, d2l[a]), de2, d1l[a]), de2, il[a]);
+                gy[a] = gauge_poly<N1>(d3l, d2l[a], d1l[a], il[a], de2);
             }
             double g = 0.0;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < N1; ++a) {
                 double h = 0.0;
 #pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    h = fma(gy[b], __shfl_sync(0xffffffffu, total, 4 * a + b), h);
+                for (int b = 0; b < N1; ++b)
+                    h = fma(gy[b], __shfl_sync(0xffffffffu, total, N1 * a + b), h);
                 g = fma(gx[a], h, g);
             }
             total = g;
@@ -217,7 +227,7 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
         }
 
         // BGK relaxation toward rho W in the co-moving gauge (Eq. postcollision)
-        if (half == 0) {
+        if (half == 0 && act) {
             const double feq = rho * L.w[k] * L.w[l];
             out.f[(long long)q * N + node] = total + 2.0 * P.beta * (feq - total);
         }
@@ -247,8 +257,10 @@ cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>&
     const long long N = (long long)nx * ny;
     if (N == 0) return cudaSuccess;
     const long long nb = (N + K1_WARPS - 1) / K1_WARPS;
-    (void)L;
-    k1_step_fp64<<<(unsigned)nb, K1_WARPS * 32, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+    if (L.n1 == 3)
+        k1_step_fp64<3><<<(unsigned)nb, K1_WARPS * 32, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+    else
+        k1_step_fp64<4><<<(unsigned)nb, K1_WARPS * 32, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
     return cudaGetLastError();
 }
 
@@ -303,7 +315,7 @@ static cudaError_t noalloc_setup(int dev, unsigned char** out) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        e = upload_lattice_fp64(make_lattice());
+        e = upload_lattice_fp64();
         if (e != cudaSuccess) return e;
         g_noalloc_ptr[dev] = p;
     }
@@ -324,7 +336,7 @@ extern "C" pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx
         return POND_ERR_ARG;
     if (cfg->precision != POND_FP64 || !(cfg->nu > 0.0) || !(cfg->T_ref > 0.0) ||
         !(cfg->dt > 0.0) || cfg->max_iter < 1 || cfg->fixed_iter < 0 || cfg->seed_mode < 0 ||
-        cfg->seed_mode > 2)
+        cfg->seed_mode > 2 || (cfg->lattice != POND_D2Q16 && cfg->lattice != POND_D2Q9))
         return POND_ERR_ARG;
     if (nx < 1 || ny < 1 || (int64_t)nx * ny > kNoAllocMaxNodes) return POND_ERR_ARG;
     int dev = 0;
@@ -334,7 +346,7 @@ extern "C" pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx
     e = noalloc_setup(dev, &scratch);
     if (e != cudaSuccess) return POND_ERR_CUDA;
 
-    const Lattice L = make_lattice();
+    const Lattice L = make_lattice(cfg->lattice);
     StepParams P;
     P.beta = 1.0 / (2.0 * cfg->nu / (cfg->T_ref * cfg->dt) + 1.0);
     P.dt = cfg->dt;

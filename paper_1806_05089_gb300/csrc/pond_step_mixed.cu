@@ -5,8 +5,9 @@
 // first bounds the particle velocities of its tile (u -+ c_max sqrt(theta)),
 // stages the whole window of source nodes that the departure stencils can
 // reach (tile + halo, periodic wrap applied while staging) in shared memory:
-// the 16 FP32 populations as four float4 rows f[a][0..3] (one 16-byte load
-// per row of the 4 x 4 contraction) and the gauge as FP32 offsets from the
+// the Q FP32 populations as n1 float4 rows f[a][0..n1-1] (one 16-byte load
+// per row of the n1 x n1 contraction; the fourth word is unused on D2Q9)
+// and the gauge as FP32 offsets from the
 // tile's reference gauge, formed in FP64.  Gauge differences u_s - u' are then
 // differences of those offsets, so they carry FP32 precision RELATIVE TO THE
 // TILE'S GAUGE SPREAD, which is what FP64 differences rounded to FP32 give
@@ -27,11 +28,22 @@
 
 namespace pond {
 
-__constant__ LatticeF c_Lf;
+// FP32 lattice constants, slot lattice_slot(n1) (D2Q16, D2Q9).
+__constant__ LatticeF c_Lf[2];
 
-cudaError_t upload_lattice_mixed(const Lattice& L) {
-    const LatticeF F = to_float(L);
-    return cudaMemcpyToSymbol(c_Lf, &F, sizeof(LatticeF));
+cudaError_t upload_lattice_mixed() {
+    const LatticeF F[2] = {to_float(make_lattice(POND_D2Q16)), to_float(make_lattice(POND_D2Q9))};
+    return cudaMemcpyToSymbol(c_Lf, F, sizeof(F));
+}
+
+// Row a of the n1 x n1 contraction: sum_b gy[b] f[a][b] from one float4.
+template <int N1>
+__device__ __forceinline__ float row_dot(const float (&gy)[N1], const float4 f4) {
+    float h = gy[0] * f4.x;
+    h = fmaf(gy[1], f4.y, h);
+    h = fmaf(gy[2], f4.z, h);
+    if constexpr (N1 == 4) h = fmaf(gy[3], f4.w, h);
+    return h;
 }
 
 struct MixedArgs {
@@ -51,11 +63,12 @@ struct MixedArgs {
 };
 
 // One stencil contraction read straight from global memory (window miss).
+template <int N1>
 __device__ __noinline__ float stencil_global(const MixedArgs& A, const GridDesc& G, long long base,
                                              int X, int Y, float fx, float fy,
                                              const float* lxw, const float* lyw, int k, int l,
                                              double ux, double uy, double st) {
-    const LatticeF& L = c_Lf;
+    const LatticeF& L = c_Lf[lattice_slot(N1)];
     const int x0 = wrap_idx((long long)X + (long long)fx - 1, G.nx);
     const int y0 = wrap_idx((long long)Y + (long long)fy - 1, G.ny);
     const double inv = 1.0 / st;
@@ -68,19 +81,17 @@ __device__ __noinline__ float stencil_global(const MixedArgs& A, const GridDesc&
             const float r = (float)((A.in.st[s] - st) * inv);
             const float dx = (float)((A.in.ux[s] - ux) * inv);
             const float dy = (float)((A.in.uy[s] - uy) * inv);
-            float gx[4], gy[4];
-            for (int a = 0; a < 4; ++a) {
+            float gx[N1], gy[N1];
+            for (int a = 0; a < N1; ++a) {
                 const float de = fmaf(L.c[a], r, dx);
-                gx[a] = fmaf(fmaf(fmaf(L.d3[k], de, L.d2[k][a]), de, L.d1[k][a]), de,
-                             a == k ? 1.0f : 0.0f);
+                gx[a] = gauge_poly<N1>(L.d3[k], L.d2[k][a], L.d1[k][a], a == k ? 1.0f : 0.0f, de);
                 const float de2 = fmaf(L.c[a], r, dy);
-                gy[a] = fmaf(fmaf(fmaf(L.d3[l], de2, L.d2[l][a]), de2, L.d1[l][a]), de2,
-                             a == l ? 1.0f : 0.0f);
+                gy[a] = gauge_poly<N1>(L.d3[l], L.d2[l][a], L.d1[l][a], a == l ? 1.0f : 0.0f, de2);
             }
             float g = 0.0f;
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < N1; ++a) {
                 float h = 0.0f;
-                for (int b = 0; b < 4; ++b) h = fmaf(gy[b], A.in.f[(4 * a + b) * A.plane + s], h);
+                for (int b = 0; b < N1; ++b) h = fmaf(gy[b], A.in.f[(N1 * a + b) * A.plane + s], h);
                 g = fmaf(gx[a], h, g);
             }
             gv[jy][jx] = g;
@@ -103,10 +114,12 @@ __device__ __noinline__ float stencil_global(const MixedArgs& A, const GridDesc&
 // that co-moving gauge (Eq. postcollision) and the store.  (r, dx, dy) are
 // the Taylor offsets of that transform: xi_a = c_a + c_a r + d.  Kept out of
 // line so the pass loop keeps its register budget.
+template <int N1>
 __device__ __noinline__ void finish_node(const MixedArgs& A, float* s_acc, int NT, int tid,
                                          long long node, bool regauge, float r, float dx,
                                          float dy, double ux, double uy, double st, float rho) {
-    const LatticeF& L = c_Lf;
+    constexpr int Q = N1 * N1;
+    const LatticeF& L = c_Lf[lattice_slot(N1)];
     if (regauge) {
         // In correction form, f + (G - I) f: at convergence G - I is of the
         // size of the last gauge increment (~1e-7 to 1e-6), so writing the
@@ -115,69 +128,73 @@ __device__ __noinline__ void finish_node(const MixedArgs& A, float* s_acc, int N
         // each parcel would lose or gain mass the same way every step.
         //   (G f)_kl - f_kl = sum_b ey_lb f_kb + sum_a ex_ka (f_al + sum_b ey_lb f_ab)
         // with ex, ey the Taylor polynomials without their identity term.
-        float ex[4][4], ey[4][4];  // [k][a]
+        float ex[N1][N1], ey[N1][N1];  // [k][a]
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < N1; ++a) {
             const float dex = fmaf(L.c[a], r, dx), dey = fmaf(L.c[a], r, dy);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                ex[k][a] = fmaf(fmaf(L.d3[k], dex, L.d2[k][a]), dex, L.d1[k][a]) * dex;
-                ey[k][a] = fmaf(fmaf(L.d3[k], dey, L.d2[k][a]), dey, L.d1[k][a]) * dey;
+            for (int k = 0; k < N1; ++k) {
+                ex[k][a] = gauge_tail<N1>(L.d3[k], L.d2[k][a], L.d1[k][a], dex) * dex;
+                ey[k][a] = gauge_tail<N1>(L.d3[k], L.d2[k][a], L.d1[k][a], dey) * dey;
             }
         }
-        float f[16], H[16];
+        float f[Q], H[Q];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) f[q] = s_acc[q * NT + tid];
+        for (int q = 0; q < Q; ++q) f[q] = s_acc[q * NT + tid];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < N1; ++a)
 #pragma unroll
-            for (int l = 0; l < 4; ++l) {
+            for (int l = 0; l < N1; ++l) {
                 float v = 0.0f;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) v = fmaf(ey[l][b], f[4 * a + b], v);
-                H[4 * a + l] = v;  // y-correction of row a
+                for (int b = 0; b < N1; ++b) v = fmaf(ey[l][b], f[N1 * a + b], v);
+                H[N1 * a + l] = v;  // y-correction of row a
             }
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < N1; ++k)
 #pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                float c = H[4 * k + l];
+            for (int l = 0; l < N1; ++l) {
+                float c = H[N1 * k + l];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) c = fmaf(ex[k][a], f[4 * a + l] + H[4 * a + l], c);
-                s_acc[(4 * k + l) * NT + tid] = f[4 * k + l] + c;
+                for (int a = 0; a < N1; ++a) c = fmaf(ex[k][a], f[N1 * a + l] + H[N1 * a + l], c);
+                s_acc[(N1 * k + l) * NT + tid] = f[N1 * k + l] + c;
             }
     }
     // BGK in FP32, kept exactly conservative: the relaxed non-equilibrium
     // part n = f - rho W is first stripped of its mass, momentum and energy
-    // moments (W-weighted projection; the D2Q16 Gram matrix of {1, c_x, c_y,
-    // |c|^2} under W is [[1,0,0,2],[0,1,0,0],[0,0,1,0],[2,0,0,8]] at T_L = 1,
-    // whose dual basis is W(2 - |c|^2/2), W c_x, W c_y, W(|c|^2/4 - 1/2)).  In
-    // exact arithmetic at the fixed point those moments are zero and this is
-    // the plain f + 2 beta (rho W - f) of Eq. postcollision; in FP32 their
-    // rounding would otherwise act on each advected parcel the same way step
-    // after step and drift its mass and temperature.
-    // (Isothermal runs keep T fixed and do not conserve energy: there only
-    // mass and momentum are projected out, with dual basis W, W c_x, W c_y.)
+    // moments (W-weighted projection onto the dual basis of {1, c_x, c_y,
+    // |c|^2}: on D2Q16 the W-Gram matrix is [[1,0,0,2],[0,1,0,0],[0,0,1,0],
+    // [2,0,0,8]] and the duals W(2 - |c|^2/2), W c_x, W c_y, W(|c|^2/4 -
+    // 1/2); on D2Q9 (T_L = 1/3) W(2 - 3|c|^2/2), 3 W c_x, 3 W c_y,
+    // W(9|c|^2/4 - 3/2)).  In exact arithmetic at the fixed point those
+    // moments are zero and this is the plain f + 2 beta (rho W - f) of
+    // Eq. postcollision; in FP32 their rounding would otherwise act on each
+    // advected parcel the same way step after step and drift its mass and
+    // temperature.  (Isothermal runs keep T fixed and do not conserve energy:
+    // there only mass and momentum are projected out, with dual basis W,
+    // W c_x / T_L, W c_y / T_L.)
     float M0 = 0.0f, M1 = 0.0f, M2 = 0.0f, M3 = 0.0f;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const int k = q >> 2, l = q & 3;
+    for (int q = 0; q < Q; ++q) {
+        const int k = q / N1, l = q % N1;
         const float n = fmaf(-rho, L.w[k] * L.w[l], s_acc[q * NT + tid]);
         M0 += n;
         M1 = fmaf(L.c[k], n, M1);
         M2 = fmaf(L.c[l], n, M2);
         M3 = fmaf(fmaf(L.c[k], L.c[k], L.c[l] * L.c[l]), n, M3);
     }
-    float e0 = 2.0f, e2 = -0.5f, t0 = -0.5f, t2 = 0.25f;  // thermal dual basis
+    float e0 = L.pe0, e2 = L.pe2, t0 = L.pt0, t2 = L.pt2;  // thermal dual basis
     if (!A.P.thermal) {
         e0 = 1.0f;
         e2 = 0.0f;
         M3 = 0.0f;
     }
+    M1 *= L.inv_TL;
+    M2 *= L.inv_TL;
     const float two_beta = (float)(2.0 * A.P.beta);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const int k = q >> 2, l = q & 3;
+    for (int q = 0; q < Q; ++q) {
+        const int k = q / N1, l = q % N1;
         const float Wq = L.w[k] * L.w[l];
         const float c2 = fmaf(L.c[k], L.c[k], L.c[l] * L.c[l]);
         const float a = s_acc[q * NT + tid];
@@ -226,22 +243,23 @@ __device__ __forceinline__ void block_minmax4(float& a, float& b, float& c, floa
 
 // Every tile shape is compiled for 128 registers per thread (512 threads of
 // resident CTAs per SM: 4 x 128, 2 x 256 or 1 x 512).
-template <int TX, int TY>
+template <int TX, int TY, int N1>
 __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedArgs A) {
     constexpr int NT = TX * TY;
+    constexpr int Q = N1 * N1;
     extern __shared__ __align__(16) float4 smem4[];
     const int WN = A.ww * A.wh;
-    // staged window, one float4 per (x-speed index a, node): f[a][0..3], so
-    // one 16-byte load feeds one row of the 4 x 4 contraction; and the
+    // staged window, one float4 per (x-speed index a, node): f[a][0..n1-1],
+    // so one 16-byte load feeds one row of the n1 x n1 contraction; and the
     // tile-relative gauge (s - s_ref, u_x - u_x,ref, u_y - u_y,ref, 0)
-    float4* s_f4 = smem4;          // [4][WN]
-    float4* s_g4 = s_f4 + 4 * WN;  // [WN]
-    float* s_acc = reinterpret_cast<float*>(s_g4 + WN);  // [16][NT]
+    float4* s_f4 = smem4;           // [N1][WN]
+    float4* s_g4 = s_f4 + N1 * WN;  // [WN]
+    float* s_acc = reinterpret_cast<float*>(s_g4 + WN);  // [Q][NT]
     __shared__ float s_red[4][NT / 32];
     __shared__ long long s_item;
     __shared__ unsigned long long s_passes, s_nc, s_np, s_fb;
     __shared__ unsigned int s_max;
-    const LatticeF& L = c_Lf;
+    const LatticeF& L = c_Lf[lattice_slot(N1)];
     const int tid = threadIdx.x;
     if (tid == 0) {
         s_passes = 0ull;
@@ -331,9 +349,10 @@ __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedAr
             const long long gi = base + (long long)gy * G.nx + gx;
             const float* fp = A.in.f + gi;
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
-                s_f4[a * WN + i] = make_float4(__ldg(fp + (4 * a + 0) * A.plane), __ldg(fp + (4 * a + 1) * A.plane),
-                                               __ldg(fp + (4 * a + 2) * A.plane), __ldg(fp + (4 * a + 3) * A.plane));
+            for (int a = 0; a < N1; ++a)
+                s_f4[a * WN + i] = make_float4(__ldg(fp + (N1 * a + 0) * A.plane), __ldg(fp + (N1 * a + 1) * A.plane),
+                                               __ldg(fp + (N1 * a + 2) * A.plane),
+                                               N1 == 4 ? __ldg(fp + (N1 * a + 3) * A.plane) : 0.0f);
             s_g4[i] = make_float4((float)(__ldg(A.in.st + gi) - rst), (float)(__ldg(A.in.ux + gi) - rux),
                                   (float)(__ldg(A.in.uy + gi) - ruy), 0.0f);
         }
@@ -355,8 +374,8 @@ __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedAr
                 const float bst = -tdst * invf, bux = -tdux * invf, buy = -tduy * invf;
                 float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f;
 #pragma unroll 1
-                for (int q = 0; q < 16; ++q) {
-                    const int k = q >> 2, l = q & 3;
+                for (int q = 0; q < Q; ++q) {
+                    const int k = q / N1, l = q % N1;
                     const float ck = L.c[k], cl = L.c[l];
                     const float dxp = -fmaf(stf, ck, uxf) * dt;
                     const float dyp = -fmaf(stf, cl, uyf) * dt;
@@ -369,9 +388,9 @@ __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedAr
                     const int row = near ? Y - wy0 + (int)fy - 1 : -1;
                     float acc;
                     if (col >= 0 && col + 3 < ww && row >= 0 && row + 3 < wh) {
-                        float d1k[4], d2k[4], d1l[4], d2l[4], ik[4], il[4];
+                        float d1k[N1], d2k[N1], d1l[N1], d2l[N1], ik[N1], il[N1];
 #pragma unroll
-                        for (int a = 0; a < 4; ++a) {
+                        for (int a = 0; a < N1; ++a) {
                             d1k[a] = L.d1[k][a];
                             d2k[a] = L.d2[k][a];
                             d1l[a] = L.d1[l][a];
@@ -388,27 +407,21 @@ __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedAr
                             const float r = fmaf(g4.x, invf, bst);   // s_s/s' - 1
                             const float dx = fmaf(g4.y, invf, bux);  // (u_s,x - u'_x)/s'
                             const float dy = fmaf(g4.z, invf, buy);
-                            float gx[4], gy[4];
+                            float gx[N1], gy[N1];
 #pragma unroll
-                            for (int a = 0; a < 4; ++a) {
+                            for (int a = 0; a < N1; ++a) {
                                 const float de = fmaf(L.c[a], r, dx);
-                                gx[a] = fmaf(fmaf(fmaf(d3k, de, d2k[a]), de, d1k[a]), de, ik[a]);
+                                gx[a] = gauge_poly<N1>(d3k, d2k[a], d1k[a], ik[a], de);
                             }
 #pragma unroll
-                            for (int b = 0; b < 4; ++b) {
+                            for (int b = 0; b < N1; ++b) {
                                 const float de = fmaf(L.c[b], r, dy);
-                                gy[b] = fmaf(fmaf(fmaf(d3l, de, d2l[b]), de, d1l[b]), de, il[b]);
+                                gy[b] = gauge_poly<N1>(d3l, d2l[b], d1l[b], il[b], de);
                             }
                             float gsum = 0.0f;
 #pragma unroll
-                            for (int a = 0; a < 4; ++a) {
-                                const float4 f4 = s_f4[a * WN + si];
-                                float h = gy[0] * f4.x;
-                                h = fmaf(gy[1], f4.y, h);
-                                h = fmaf(gy[2], f4.z, h);
-                                h = fmaf(gy[3], f4.w, h);
-                                gsum = fmaf(gx[a], h, gsum);
-                            }
+                            for (int a = 0; a < N1; ++a)
+                                gsum = fmaf(gx[a], row_dot<N1>(gy, s_f4[a * WN + si]), gsum);
                             return gsum;
                         };
                         // reconstruction relative to the stencil node nearest
@@ -430,7 +443,7 @@ __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedAr
                         }
                         acc += gref;
                     } else {
-                        acc = stencil_global(A, G, base, X, Y, fx, fy, lxw, lyw, k, l, ux, uy, st);
+                        acc = stencil_global<N1>(A, G, base, X, Y, fx, fy, lxw, lyw, k, l, ux, uy, st);
                         ++fallbacks;
                     }
                     s_acc[q * NT + tid] = acc;
@@ -489,10 +502,10 @@ __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedAr
                 // non-physical moments: keep the pass's populations and gauge
                 float r0 = 0.0f;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) r0 += s_acc[q * NT + tid];
-                finish_node(A, s_acc, NT, tid, node, false, 0.0f, 0.0f, 0.0f, ux, uy, st, r0);
+                for (int q = 0; q < Q; ++q) r0 += s_acc[q * NT + tid];
+                finish_node<N1>(A, s_acc, NT, tid, node, false, 0.0f, 0.0f, 0.0f, ux, uy, st, r0);
             } else {
-                finish_node(A, s_acc, NT, tid, node, true, lr, ldx, ldy, nux, nuy, nst, rhof);
+                finish_node<N1>(A, s_acc, NT, tid, node, true, lr, ldx, ldy, nux, nuy, nst, rhof);
             }
             if (A.iters) A.iters[node] = pass;
             atomicAdd(&s_passes, (unsigned long long)pass);
@@ -532,7 +545,7 @@ struct QCoef {
 
 __device__ __forceinline__ float pair_g(const float4 g4, const float4 (&fr)[4], const NodeOff& o,
                                         const QCoef& C) {
-    const LatticeF& L = c_Lf;
+    const LatticeF& L = c_Lf[lattice_slot(4)];
     const float r = fmaf(g4.x, o.invf, o.bst);
     const float dx = fmaf(g4.y, o.invf, o.bux);
     const float dy = fmaf(g4.z, o.invf, o.buy);
@@ -602,7 +615,7 @@ __global__ void __launch_bounds__(TX* TY, 1) k2_step_mixed_pair(MixedArgs A) {
     __shared__ long long s_item;
     __shared__ unsigned long long s_passes, s_nc, s_np, s_fb;
     __shared__ unsigned int s_max;
-    const LatticeF& L = c_Lf;
+    const LatticeF& L = c_Lf[lattice_slot(4)];
     const int tid = threadIdx.x;
     if (tid == 0) {
         s_passes = 0ull;
@@ -806,7 +819,7 @@ __global__ void __launch_bounds__(TX* TY, 1) k2_step_mixed_pair(MixedArgs A) {
                             acc[sl] = sweep_one(s_f4, s_g4, WN, ww, row[sl], col[sl], lxw[sl],
                                                 lyw[sl], o[sl], C);
                         } else {
-                            acc[sl] = stencil_global(A, G, base, X, Yn[sl], fxs[sl], fys[sl],
+                            acc[sl] = stencil_global<4>(A, G, base, X, Yn[sl], fxs[sl], fys[sl],
                                                      lxw[sl], lyw[sl], k, l, nux[sl] - 0.0,
                                                      nuy[sl] - 0.0, nst[sl] - 0.0);
                             ++fallbacks[sl];
@@ -881,10 +894,10 @@ __global__ void __launch_bounds__(TX* TY, 1) k2_step_mixed_pair(MixedArgs A) {
                         float r0 = 0.0f;
 #pragma unroll
                         for (int q = 0; q < 16; ++q) r0 += s_acc[q * 2 * NT + 2 * tid + sl];
-                        finish_node(A, s_acc, 2 * NT, 2 * tid + sl, node[sl], false, 0.f, 0.f, 0.f,
+                        finish_node<4>(A, s_acc, 2 * NT, 2 * tid + sl, node[sl], false, 0.f, 0.f, 0.f,
                                     nux[sl], nuy[sl], nst[sl], r0);
                     } else {
-                        finish_node(A, s_acc, 2 * NT, 2 * tid + sl, node[sl], true, lr[sl], ldx[sl],
+                        finish_node<4>(A, s_acc, 2 * NT, 2 * tid + sl, node[sl], true, lr[sl], ldx[sl],
                                     ldy[sl], nux[sl], nuy[sl], nst[sl], rhof[sl]);
                     }
                     act[sl] = false;
@@ -914,14 +927,17 @@ __global__ void __launch_bounds__(TX* TY, 1) k2_step_mixed_pair(MixedArgs A) {
 }
 
 size_t mixed_smem_bytes(const TileWindow& w) {
-    return sizeof(float) * ((size_t)20 * w.ww * w.wh + (size_t)16 * w.tx * w.ty);
+    // n1 float4 population rows and one float4 gauge per staged node, Q
+    // floats of pass populations per target node
+    const size_t n1 = (size_t)w.n1;
+    return sizeof(float) * (4 * (n1 + 1) * w.ww * w.wh + n1 * n1 * w.tx * w.ty);
 }
 
-template <int TY, bool PAIR>
+template <int TY, bool PAIR, int N1>
 static cudaError_t prepare_shape(size_t smem_bytes, int* ctas_per_sm, int* s_set) {
     void (*kern)(MixedArgs);
     if constexpr (PAIR) kern = k2_step_mixed_pair<MIXED_TX, TY / 2>;
-    else kern = k2_step_mixed<MIXED_TX, TY>;
+    else kern = k2_step_mixed<MIXED_TX, TY, N1>;
     const int threads = PAIR ? MIXED_TX * TY / 2 : MIXED_TX * TY;
     cudaError_t e;
     if ((int)smem_bytes > *s_set) {
@@ -932,22 +948,30 @@ static cudaError_t prepare_shape(size_t smem_bytes, int* ctas_per_sm, int* s_set
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, threads, smem_bytes);
 }
 
-cudaError_t mixed_prepare(int ty, bool pair, size_t smem_bytes, int* ctas_per_sm) {
+cudaError_t mixed_prepare(int ty, bool pair, int n1, size_t smem_bytes, int* ctas_per_sm) {
     // the attribute is per function and device: only ever raise it, so that
     // every live context's window stays launchable
-    static int s_set[64][4] = {{0}};
+    static int s_set[64][7] = {{0}};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (pair) {
-        if (ty != 16) return cudaErrorInvalidValue;
-        return prepare_shape<16, true>(smem_bytes, ctas_per_sm, &s_set[dev][3]);
+        if (ty != 16 || n1 != 4) return cudaErrorInvalidValue;
+        return prepare_shape<16, true, 4>(smem_bytes, ctas_per_sm, &s_set[dev][3]);
+    }
+    if (n1 == 3) {
+        switch (ty) {
+            case 4: return prepare_shape<4, false, 3>(smem_bytes, ctas_per_sm, &s_set[dev][4]);
+            case 8: return prepare_shape<8, false, 3>(smem_bytes, ctas_per_sm, &s_set[dev][5]);
+            case 16: return prepare_shape<16, false, 3>(smem_bytes, ctas_per_sm, &s_set[dev][6]);
+            default: return cudaErrorInvalidValue;
+        }
     }
     switch (ty) {
-        case 4: return prepare_shape<4, false>(smem_bytes, ctas_per_sm, &s_set[dev][0]);
-        case 8: return prepare_shape<8, false>(smem_bytes, ctas_per_sm, &s_set[dev][1]);
-        case 16: return prepare_shape<16, false>(smem_bytes, ctas_per_sm, &s_set[dev][2]);
+        case 4: return prepare_shape<4, false, 4>(smem_bytes, ctas_per_sm, &s_set[dev][0]);
+        case 8: return prepare_shape<8, false, 4>(smem_bytes, ctas_per_sm, &s_set[dev][1]);
+        case 16: return prepare_shape<16, false, 4>(smem_bytes, ctas_per_sm, &s_set[dev][2]);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -959,6 +983,7 @@ cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& 
                               int persistent_ctas, const Lattice& L, const StepParams& P,
                               cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
+    if (win.n1 != L.n1) return cudaErrorInvalidValue;
     MixedArgs A;
     A.in = in;
     A.out = out;
@@ -972,7 +997,7 @@ cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& 
     A.work_counter = work_counter;
     A.ww = win.ww;
     A.wh = win.wh;
-    A.c_max = L.c[3];
+    A.c_max = L.c_max;
     A.margin = 1.0f;
     A.P = P;
     const size_t smem = mixed_smem_bytes(win);
@@ -985,14 +1010,23 @@ cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& 
         nb = (unsigned int)n_tiles;
     }
     if (win.pair) {
-        if (win.ty != 16) return cudaErrorInvalidValue;
+        if (win.ty != 16 || L.n1 != 4) return cudaErrorInvalidValue;
         k2_step_mixed_pair<MIXED_TX, 8><<<nb, MIXED_TX * 8, smem, s>>>(A);
         return cudaGetLastError();
     }
+    if (L.n1 == 3) {
+        switch (win.ty) {
+            case 4: k2_step_mixed<MIXED_TX, 4, 3><<<nb, MIXED_TX * 4, smem, s>>>(A); break;
+            case 8: k2_step_mixed<MIXED_TX, 8, 3><<<nb, MIXED_TX * 8, smem, s>>>(A); break;
+            case 16: k2_step_mixed<MIXED_TX, 16, 3><<<nb, MIXED_TX * 16, smem, s>>>(A); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (win.ty) {
-        case 4: k2_step_mixed<MIXED_TX, 4><<<nb, MIXED_TX * 4, smem, s>>>(A); break;
-        case 8: k2_step_mixed<MIXED_TX, 8><<<nb, MIXED_TX * 8, smem, s>>>(A); break;
-        case 16: k2_step_mixed<MIXED_TX, 16><<<nb, MIXED_TX * 16, smem, s>>>(A); break;
+        case 4: k2_step_mixed<MIXED_TX, 4, 4><<<nb, MIXED_TX * 4, smem, s>>>(A); break;
+        case 8: k2_step_mixed<MIXED_TX, 8, 4><<<nb, MIXED_TX * 8, smem, s>>>(A); break;
+        case 16: k2_step_mixed<MIXED_TX, 16, 4><<<nb, MIXED_TX * 16, smem, s>>>(A); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

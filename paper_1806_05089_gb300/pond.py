@@ -30,6 +30,9 @@ POND_ERR_TIMEOUT = 6
 POND_ERR_STATE = 7
 POND_FP64 = 0
 POND_FP32_MIXED = 1
+POND_D2Q16 = 0
+POND_D2Q9 = 1
+N_SPEEDS = {POND_D2Q16: 4, POND_D2Q9: 3}  # speeds per dimension; Q = n1^2
 
 _STATUS = {0: "POND_OK", 1: "POND_ERR_ARG", 2: "POND_ERR_OOM", 3: "POND_ERR_CUDA",
            4: "POND_ERR_NONPHYSICAL", 5: "POND_ERR_NOT_CONVERGED", 6: "POND_ERR_TIMEOUT",
@@ -59,6 +62,7 @@ class pond_config(ctypes.Structure):
         ("use_graph", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
         ("tile_rows", ctypes.c_int32),
+        ("lattice", ctypes.c_int32),
     ]
 
 
@@ -301,6 +305,7 @@ class Sim:
             setattr(self.cfg, k, v)
         self.nx = [int(v) for v in np.atleast_1d(nx)]
         self.ny = [int(v) for v in np.atleast_1d(ny)]
+        self.Q = N_SPEEDS.get(int(self.cfg.lattice), 4) ** 2
         self.ctx = pond_create(self.cfg, self.nx, self.ny, stream)
 
     def close(self):
@@ -334,7 +339,7 @@ class Sim:
 
     def state(self, grid: int = 0) -> HostState:
         ny, nx = self.ny[grid], self.nx[grid]
-        f = np.zeros((16, ny, nx))
+        f = np.zeros((self.Q, ny, nx))
         ux, uy, T = (np.zeros((ny, nx)) for _ in range(3))
         pond_get_state(self.ctx, grid, f, ux, uy, T)
         return HostState(f, ux, uy, T)

@@ -26,17 +26,31 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--tile", type=int, default=0,
                     help="mixed forms: tile rows (4, 8, 16; -16 = two nodes per thread)")
+    ap.add_argument("--lattice", choices=["d2q16", "d2q9"], default="d2q16",
+                    help="fp64 / mixed / batched: lattice (d2q9 runs the same flow at "
+                         "T_L = 1/3: T/3, u/sqrt 3)")
     a = ap.parse_args()
 
     import torch
 
     from . import pond, workloads
     pond.load()
-    out = {"form": a.form}
+    out = {"form": a.form, "lattice": a.lattice}
+    q9 = a.lattice == "d2q9"
+    lat = {"lattice": pond.POND_D2Q9, "T_ref": 1.0 / 3.0} if q9 else {}
+
+    def scaled(f):
+        if q9:
+            f.T = f.T / 3.0
+            f.ux = f.ux / 3.0 ** 0.5
+            f.uy = f.uy / 3.0 ** 0.5
+        return f
     if a.form in ("fp64", "mixed"):
         prec = pond.POND_FP64 if a.form == "fp64" else pond.POND_FP32_MIXED
-        f = workloads.supersonic(a.n)
-        cfg = {"tile_rows": a.tile} if prec == pond.POND_FP32_MIXED else {}
+        f = scaled(workloads.supersonic(a.n))
+        cfg = dict(lat)
+        if prec == pond.POND_FP32_MIXED:
+            cfg["tile_rows"] = a.tile
         with pond.Sim(a.n, a.n, prec, **cfg) as s:
             s.set_state(f.rho, f.ux, f.uy, f.T)
             s.step(1)
@@ -50,9 +64,9 @@ def main():
     elif a.form == "batched":
         nxs, nys = workloads.ensemble_sizes(256)
         nxs, nys = nxs[:a.grids], nys[:a.grids]
-        with pond.Sim(nxs, nys, pond.POND_FP32_MIXED, tile_rows=a.tile) as s:
+        with pond.Sim(nxs, nys, pond.POND_FP32_MIXED, tile_rows=a.tile, **lat) as s:
             for i in range(a.grids):
-                m = workloads.ensemble_member(i, nxs[i], nys[i])
+                m = scaled(workloads.ensemble_member(i, nxs[i], nys[i]))
                 s.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
             s.step(1)
             torch.cuda.synchronize()

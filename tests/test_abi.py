@@ -28,10 +28,11 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_version_and_defaults():
-    assert "D2Q16" in pond.pond_version()
+    assert "D2Q16" in pond.pond_version() and "D2Q9" in pond.pond_version()
     c64 = pond.pond_config_default(pond.POND_FP64)
     assert (c64.eps_abs, c64.eps_rel) == (1e-12, 1e-10)  # App. E
     assert c64.max_iter == 20 and c64.thermal == 1 and c64.dt == 1.0
+    assert c64.lattice == pond.POND_D2Q16
     c32 = pond.pond_config_default(pond.POND_FP32_MIXED)
     assert c32.precision == pond.POND_FP32_MIXED and c32.eps_rel >= 1e-7
 
@@ -54,6 +55,13 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
     assert lib.pond_create(ctypes.byref(cfg), 2, nx2, ny2, None, ctypes.byref(out)) == pond.POND_ERR_ARG
     assert lib.pond_step(None, 1, None) == pond.POND_ERR_ARG
     assert lib.pond_last_error(None) == b"no context"
+    # lattice: D2Q16 or D2Q9 only; the paired tile shape is D2Q16-only
+    bad = pond.pond_config_default(pond.POND_FP32_MIXED)
+    bad.lattice = 2
+    assert lib.pond_create(ctypes.byref(bad), 1, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
+    bad.lattice = pond.POND_D2Q9
+    bad.tile_rows = -16
+    assert lib.pond_create(ctypes.byref(bad), 1, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
 
 
 def test_no_cpu_fallback_without_gpu():

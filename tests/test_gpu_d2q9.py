@@ -1,0 +1,225 @@
+"""GPU parity on the paper's own D2Q9 lattice (App. A: speeds -1, 0, 1,
+weights 1/6, 2/3, 1/6, T_L = 1/3) against the FP64 oracle on the same
+lattice, and the D2Q9 physics the paper reports on it.
+
+Same tolerances as the D2Q16 parity tests: FP64 fixed passes 1e-12; adaptive
+passes compare pass maps (>= 99.9 % equal) and values at 1e-9; the mixed
+form 1e-5 (velocity against the larger of flow and thermal speed).  Inputs
+are the D2Q16 workloads rescaled to the D2Q9 lattice temperature: T -> T/3,
+u -> u/sqrt(3), the same Mach numbers.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_05089_gb300 import pond, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+Q9 = pond.POND_D2Q9
+T_L = 1.0 / 3.0
+
+
+def d2q9_fields(name, nx, ny):
+    if name == "tg":
+        f = workloads.taylor_green(nx, ny, 0.05)
+    elif name == "supersonic":
+        f = workloads.supersonic(nx=nx, ny=ny)
+    elif name == "hot":
+        f = workloads.supersonic(nx=nx, ny=ny)
+        f.T = 1.0 + 0.5 * (f.T - 1.0) / np.abs(f.T - 1.0).max()
+        f.ux = -0.7 * f.ux
+    else:
+        raise KeyError(name)
+    f.T = f.T * T_L
+    f.ux = f.ux * np.sqrt(T_L)
+    f.uy = f.uy * np.sqrt(T_L)
+    return f
+
+
+def gpu_run(fields, steps, precision=pond.POND_FP64, **cfg):
+    ny, nx = fields.shape
+    cfg.setdefault("T_ref", T_L)
+    with pond.Sim(nx, ny, precision, lattice=Q9, **cfg) as s:
+        s.set_state(fields.rho, fields.ux, fields.uy, fields.T)
+        stats = s.step(steps) if steps else None
+        st = s.state()
+        rho = s.moments()[0]
+        it = s.iterations()
+    assert st.f.shape[0] == 9
+    return st, rho, it, stats
+
+
+def oracle_run(fields, steps, **params):
+    st = oracle.init_equilibrium(fields.rho, fields.ux, fields.uy, fields.T, lattice=oracle.D2Q9)
+    params.setdefault("T_ref", T_L)
+    p = oracle.Params(lattice=oracle.D2Q9, **params)
+    it = None
+    for _ in range(steps):
+        st, it, fl = oracle.step(st, p)
+        assert np.all(fl == 0)
+    return st, it
+
+
+def rel_errors(g, grho, o, speed_scale=False):
+    orho = o.f.sum(axis=0)
+    e_rho = np.max(np.abs(grho - orho) / np.abs(orho))
+    umax = max(np.abs(o.ux).max(), np.abs(o.uy).max(), 1e-300)
+    if speed_scale:
+        umax = max(umax, float(np.sqrt(o.T.mean())))
+    e_u = max(np.abs(g.ux - o.ux).max(), np.abs(g.uy - o.uy).max()) / umax
+    e_T = np.max(np.abs(g.T - o.T) / np.abs(o.T))
+    e_f = np.abs(g.f - o.f).max() / np.abs(o.f).max()
+    return e_rho, e_u, e_T, e_f
+
+
+@pytest.mark.parametrize("name,nx,ny,steps", [("tg", 64, 64, 12), ("supersonic", 37, 29, 6),
+                                              ("hot", 48, 40, 5), ("supersonic", 1, 1, 3),
+                                              ("tg", 3, 5, 4), ("supersonic", 2, 7, 3)])
+def test_d2q9_fp64_fixed_passes_matches_oracle(name, nx, ny, steps):
+    fields = d2q9_fields(name, nx, ny)
+    g, grho, git, _ = gpu_run(fields, steps, fixed_iter=4)
+    o, oit = oracle_run(fields, steps, fixed_iter=4)
+    assert np.all(git == 4) and np.all(oit == 4)
+    e = rel_errors(g, grho, o)
+    assert max(e) <= TOL64, e
+
+
+@pytest.mark.parametrize("thermal", [1, 0])
+def test_d2q9_fp64_adaptive_matches_oracle(thermal):
+    fields = d2q9_fields("tg", 64, 64) if thermal else d2q9_fields("supersonic", 48, 40)
+    steps = 60 if thermal else 8
+    g, grho, git, stats = gpu_run(fields, steps, thermal=thermal)
+    o, oit = oracle_run(fields, steps, thermal=thermal)
+    assert stats["nonconverged"] == 0 and stats["nonphysical"] == 0
+    assert np.mean(git == oit) >= 0.999
+    assert max(rel_errors(g, grho, o)) <= 1e-9
+
+
+@pytest.mark.parametrize("tile_rows", [4, 8, 16])
+@pytest.mark.parametrize("name,nx,ny,steps", [("supersonic", 64, 48, 10), ("hot", 45, 37, 6),
+                                              ("tg", 5, 3, 4)])
+def test_d2q9_mixed_matches_oracle(name, nx, ny, steps, tile_rows):
+    fields = d2q9_fields(name, nx, ny)
+    g, grho, git, stats = gpu_run(fields, steps, pond.POND_FP32_MIXED, tile_rows=tile_rows)
+    assert stats["tile_rows"] == tile_rows and stats["nonphysical"] == 0
+    o, _ = oracle_run(fields, steps)
+    e = rel_errors(g, grho, o, speed_scale=True)
+    assert max(e[:3]) <= TOL32, e
+
+
+def test_d2q9_mixed_isothermal_matches_oracle():
+    fields = d2q9_fields("supersonic", 40, 40)
+    fields.T = np.full_like(fields.T, T_L)
+    g, grho, _, stats = gpu_run(fields, 10, pond.POND_FP32_MIXED, thermal=0)
+    o, _ = oracle_run(fields, 10, thermal=0)
+    e = rel_errors(g, grho, o, speed_scale=True)
+    assert max(e[:3]) <= TOL32, e
+
+
+def test_d2q9_batched_matches_single_grid_runs():
+    sizes = [(40, 33), (17, 64), (64, 9)]
+    members = []
+    for i, (nx, ny) in enumerate(sizes):
+        m = workloads.ensemble_member(i, nx, ny)
+        m.T = m.T * T_L
+        m.ux = m.ux * np.sqrt(T_L)
+        m.uy = m.uy * np.sqrt(T_L)
+        members.append(m)
+    nxs = [s[0] for s in sizes]
+    nys = [s[1] for s in sizes]
+    with pond.Sim(nxs, nys, pond.POND_FP32_MIXED, lattice=Q9, T_ref=T_L) as b:
+        for i, m in enumerate(members):
+            b.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
+        b.step(5)
+        batched = [b.state(i) for i in range(len(sizes))]
+    for i, m in enumerate(members):
+        with pond.Sim(nxs[i], nys[i], pond.POND_FP32_MIXED, lattice=Q9, T_ref=T_L) as s:
+            s.set_state(m.rho, m.ux, m.uy, m.T)
+            s.step(5)
+            single = s.state()
+        assert np.array_equal(batched[i].f, single.f), i
+        assert np.array_equal(batched[i].T, single.T), i
+        if min(nxs[i], nys[i]) < 16:
+            continue  # wavenumber-2 modes are not resolved on so few cells
+        o, _ = oracle_run(m, 5, max_iter=60)
+        assert np.max(np.abs(batched[i].T - o.T) / o.T) <= TOL32
+        assert np.max(np.abs(batched[i].f.sum(0) - o.f.sum(0)) / o.f.sum(0)) <= TOL32
+
+
+@pytest.mark.parametrize("precision", [pond.POND_FP64, pond.POND_FP32_MIXED])
+@pytest.mark.parametrize("mach,T", [(10.0, T_L), (100.0, 0.01)])
+def test_d2q9_uniform_state_is_preserved(precision, mach, T):
+    n = 40
+    ux = np.full((n, n), mach * np.sqrt(T) * np.cos(0.4))
+    uy = np.full((n, n), mach * np.sqrt(T) * np.sin(0.4))
+    with pond.Sim(n, n, precision, lattice=Q9, T_ref=T) as s:
+        s.set_state(np.full((n, n), 1.1), ux, uy, np.full((n, n), T))
+        stats = s.step(20)
+        rho, gux, guy, gT = s.moments()
+    assert stats["max_passes"] == 1 if precision == pond.POND_FP64 else stats["max_passes"] <= 2
+    tol = (1e-12 if precision == pond.POND_FP64 else 1e-6) * (1 + mach)
+    assert np.abs(rho - 1.1).max() <= tol
+    assert np.abs(gux - ux).max() <= tol * np.sqrt(T) * (1 + mach)
+    assert np.abs(gT / T - 1).max() <= tol * (1 + mach)
+
+
+@pytest.mark.parametrize("U", [0.0, 3.0])
+def test_d2q9_thermal_diffusivity_on_gpu(U):
+    """Thermal diffusivity experiment (D2Q9): a density wave at constant
+    pressure decays at alpha k^2 with alpha = (T/4)(1/(2 beta) - 1/2) dt,
+    also when advected at Ma_a = U / sqrt(2T) ~ 3.7 (64 x 4 nodes)."""
+    L, nu, T0, steps = 64, 0.1, T_L, 1500
+    X = np.arange(L, dtype=float)[None, :] + np.zeros((4, 1))
+    rho = 1 + 1e-3 * np.sin(2 * np.pi * X / L)
+    k = 2 * np.pi / L
+    amps = []
+    with pond.Sim(L, 4, pond.POND_FP64, lattice=Q9, nu=nu, T_ref=T0) as s:
+        s.set_state(rho, np.full_like(rho, U), np.zeros_like(rho), T0 / rho)
+        for _ in range(steps // 50):
+            stats = s.step(50)
+            assert stats["nonphysical"] == 0 and stats["nonconverged"] == 0
+            r = s.moments()[0].mean(axis=0)
+            amps.append(abs((r * np.exp(-1j * k * X[0])).sum()) * 2 / L)
+    t = 50 * np.arange(1, len(amps) + 1)
+    sel = t > steps // 5
+    rate = -np.polyfit(t[sel], np.log(np.array(amps)[sel]), 1)[0]
+    beta = 1.0 / (2.0 * nu / T0 + 1.0)
+    theory = (T0 / 4) * (1 / (2 * beta) - 0.5)
+    assert abs(rate / (k * k) / theory - 1) < 0.01, rate / (k * k)
+
+
+def test_d2q9_noalloc_matches_context_step():
+    torch = pytest.importorskip("torch")
+    fields = d2q9_fields("supersonic", 48, 40)
+    ny, nx = fields.shape
+    with pond.Sim(nx, ny, pond.POND_FP64, lattice=Q9, T_ref=T_L) as s:
+        s.set_state(fields.rho, fields.ux, fields.uy, fields.T)
+        start = s.state()
+        s.step(1)
+        ref = s.state()
+    dev = torch.device("cuda")
+    cfg = pond.pond_config_default(pond.POND_FP64)
+    cfg.lattice = Q9
+    cfg.T_ref = T_L
+    cur = [torch.tensor(a, device=dev) for a in (start.f, start.ux, start.uy, start.T)]
+    out = [torch.empty_like(a) for a in cur]
+    pond.pond_step_fp64_noalloc(cfg, *cur, *out, stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    f = out[0].cpu().numpy()
+    assert np.abs(f - ref.f).max() <= TOL64 * np.abs(ref.f).max()
+    assert np.max(np.abs(out[3].cpu().numpy() - ref.T) / ref.T) <= TOL64
+
+
+def test_d2q9_adjoint_is_rejected():
+    torch = pytest.importorskip("torch")
+    with pond.Sim(8, 8, pond.POND_FP64, lattice=Q9) as s:
+        s.set_state(np.ones((8, 8)), np.zeros((8, 8)), np.zeros((8, 8)), np.full((8, 8), T_L))
+        dev = torch.device("cuda")
+        fb = torch.zeros((16, 8, 8), dtype=torch.float64, device=dev)
+        gb = torch.zeros((3, 8, 8), dtype=torch.float64, device=dev)
+        with pytest.raises(pond.PondError) as e:
+            pond.pond_adjoint_step(s.ctx, fb, gb, fb.clone(), gb.clone())
+        assert e.value.status == pond.POND_ERR_ARG

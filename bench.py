@@ -54,9 +54,9 @@ BYTES_MIXED_Q9 = 2 * (9 * 4 + 3 * 8)
 PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per k1_step_fp64 launch at 2048^2: the ncu capture of the same
-# kernel at 1024^2 read 163.0 MB and wrote 124.5 MB; traffic grows with the
-# node count (4x).
-K1_TRAFFIC_BYTES_2048 = 4 * (163.0e6 + 124.5e6)
+# kernel (two nodes per warp) at 1024^2 read 164.3 MB and wrote 124.8 MB;
+# traffic grows with the node count (4x).
+K1_TRAFFIC_BYTES_2048 = 4 * (164.3e6 + 124.8e6)
 
 
 def parse():
@@ -177,10 +177,22 @@ def oracle_sample(fields, seconds: float, params=None):
     t0 = time.perf_counter()
     oracle.step(st, params, rows=(0, rows))
     dt = time.perf_counter() - t0
-    return {"value": rows * nx / dt, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": "one FP64 oracle step of rows 0..%d (%d nodes) of the %dx%d field, %.1f s"
-                      % (rows - 1, rows * nx, nx, ny, dt)}
+    cores = oracle.num_threads()
+    out = {"value": rows * nx / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "one FP64 oracle step of rows 0..%d (%d nodes) of the %dx%d field, %.1f s"
+                     % (rows - 1, rows * nx, nx, ny, dt)}
+    # the same oracle on one core, on a sample a few times smaller
+    rows1 = max(1, rows // max(2, 2 * cores))
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.step(st, params, rows=(0, rows1))
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    out["single_thread"] = {"value": rows1 * nx / dt1, "cores": 1,
+                            "sample": "rows 0..%d (%d nodes), %.1f s" % (rows1 - 1, rows1 * nx, dt1)}
+    return out
 
 
 def time_steps(sim, stream, steps):
@@ -313,8 +325,8 @@ def run_pond(args, world, rank, local):
                      "frac": achieved / PEAK_FP64_TFLOPS,
                      "traffic": K1_TRAFFIC_BYTES_2048,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                       "k1_step_fp64 launch at 1024^2 (287.5 MB), scaled x4 by "
-                                       "nodes to the 2048^2 launch",
+                                       "k1_step_fp64<4, 2> launch at 1024^2 (289.1 MB), scaled "
+                                       "x4 by nodes to the 2048^2 launch",
                      "peak_source": "nominal FP64 rate at 2070 MHz (profiling recipe)",
                      "kernel": "k1_step_fp64", "kernel_ms": kernel_s * 1e3,
                      "hbm_gbs_algorithmic": nodes * BYTES_FP64 / kernel_s / 1e9,

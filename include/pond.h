@@ -110,6 +110,11 @@ typedef struct pond_config {
                            T_L (so the meaning of theta = T / T_L and of the
                            seed {0, T_L}).  The adjoint entry points are
                            D2Q16-only. */
+    int32_t nodes_per_warp; /* FP64 form: target nodes per warp of the step
+                           kernel, 1 (16 lanes per node, each lane half the
+                           stencil rows) or 2 (each lane all rows); 0 = the
+                           library default.  The two agree to rounding
+                           (the stencil rows are summed in another order). */
 } pond_config;
 
 /* Counters accumulated over the steps of one pond_step call. */

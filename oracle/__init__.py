@@ -87,6 +87,8 @@ def _lib():
         lib.oracle_interp_weights.argtypes = [ctypes.c_double, dp]
         lib.oracle_init_equilibrium.argtypes = [ci, ctypes.c_int64, ctypes.c_int64, dp, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_num_threads.restype = ctypes.c_int
         lib.oracle_step.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp,
                                     dp, dp, dp, dp, ip, ip,
                                     ctypes.POINTER(_Params), ctypes.c_int64,
@@ -108,6 +110,11 @@ def _i(a: np.ndarray):
 
 def num_threads() -> int:
     return int(_lib().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> int:
+    """Threads (OpenMP) of later steps; returns the count in effect."""
+    return int(_lib().oracle_set_num_threads(int(n)))
 
 
 def lattice(kind: int = D2Q16):

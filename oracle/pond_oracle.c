@@ -258,6 +258,18 @@ int oracle_num_threads(void) {
 #endif
 }
 
+/* Threads of the following oracle_step calls (n >= 1); returns the count in
+ * effect afterwards. */
+int oracle_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* One PonD time step for rows [y_begin, y_end) of a periodic nx x ny grid.
  * State arrays: f[Q][ny][nx] (q = n1 k + l; k: x speed index, l: y speed
  * index), ux, uy, T [ny][nx].  Outputs are written for the given rows only.

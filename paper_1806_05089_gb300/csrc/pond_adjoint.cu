@@ -468,7 +468,8 @@ extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in,
     cudaStream_t s = ctx->stream;
 
     // 1. forward step into scratch: its gauge is the fixed point lambda*
-    ACK(launch_step_fp64(in, a->fwd, a->iters, a->stats, G.nx, G.ny, ctx->L, ctx->P, s),
+    ACK(launch_step_fp64(in, a->fwd, a->iters, a->stats, G.nx, G.ny, ctx->L, ctx->P,
+                         fp64_npw(ctx), s),
         "adjoint forward");
     // 2. velocity bounds for the transpose gather
     k_minmax3<<<1, 1024, 0, s>>>(a->fwd.ux, a->fwd.uy, a->fwd.st, N, a->minmax);

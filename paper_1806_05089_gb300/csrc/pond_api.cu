@@ -155,7 +155,7 @@ static pond_status launch_one_step(pond_ctx* ctx) {
     } else {
         const GridDesc& G = ctx->grids_host[0];
         CK(launch_step_fp64(buf<double>(ctx, in, 0), buf<double>(ctx, out, 0), ctx->iters,
-                            ctx->stats, G.nx, G.ny, ctx->L, ctx->P, ctx->stream),
+                            ctx->stats, G.nx, G.ny, ctx->L, ctx->P, fp64_npw(ctx), ctx->stream),
            "fp64 step launch");
     }
     ctx->cur = out;
@@ -291,6 +291,7 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
         cfg->tile_rows != -16)
         return POND_ERR_ARG;
     if (cfg->lattice != POND_D2Q16 && cfg->lattice != POND_D2Q9) return POND_ERR_ARG;
+    if (cfg->nodes_per_warp < 0 || cfg->nodes_per_warp > 2) return POND_ERR_ARG;
     if (cfg->lattice == POND_D2Q9 && cfg->tile_rows < 0) return POND_ERR_ARG;  // paired: D2Q16
     for (int g = 0; g < n_grids; ++g)
         if (nx[g] < 1 || ny[g] < 1) return POND_ERR_ARG;

@@ -112,10 +112,12 @@ cudaError_t upload_lattice_mixed();
 cudaError_t upload_lattice_adjoint(const Lattice& L);
 cudaError_t upload_lattice_adjoint_mixed(const Lattice& L);
 
-// FP64 step of a single grid (one warp per node), lattice L.n1.
+// FP64 step of a single grid, lattice L.n1, nodes_per_warp 1 or 2.
+constexpr int FP64_NODES_PER_WARP = 2;  // default mapping (measured faster)
 cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>& out,
                              int32_t* iters, DevStats* stats, int nx, int ny,
-                             const Lattice& L, const StepParams& P, cudaStream_t s);
+                             const Lattice& L, const StepParams& P, int nodes_per_warp,
+                             cudaStream_t s);
 
 // Window (halo tile) size, in nodes, that the mixed tiled kernel stages:
 // chosen by the host from a bound on the displacement spread.
@@ -204,6 +206,11 @@ struct pond_ctx {
     pond::AdjointScratch* adj = nullptr;
     pond::AdjMixedScratch* adjm = nullptr;
 };
+
+// nodes per warp of the context's FP64 step kernel
+inline int fp64_npw(const pond_ctx* ctx) {
+    return ctx->cfg.nodes_per_warp ? ctx->cfg.nodes_per_warp : pond::FP64_NODES_PER_WARP;
+}
 
 void destroy_adjoint(pond_ctx* ctx);
 void destroy_adjoint_mixed(pond_ctx* ctx);

@@ -1,14 +1,14 @@
 // pond_step_fp64.cu -- FP64 PonD time step of one periodic grid.
 //
-// One warp per target node.  Lane = (population q = lane & 15, stencil-row
-// half = lane >> 4): each lane reconstructs population q from two of the four
-// stencil rows, the halves are summed with one shuffle, and the moments of
-// the Q populations are butterfly-reduced, so every lane holds rho, u, T and
-// takes the same convergence decision: a warp never diverges on the
-// predictor-corrector pass count.  The step is bound by the FP64 pipe; all
-// source reads go through the read-only L1 path.  Templated on the lattice:
-// D2Q16 (N1 = 4, all 32 lanes busy) or D2Q9 (N1 = 3: lanes with q >= 9 only
-// join the shuffles).
+// One or two target nodes per warp, 16 lanes per node (lane & 15 = the
+// population q).  With one node, the lane's other index (lane >> 4) halves
+// the four stencil rows and one shuffle sums the halves; with two, it picks
+// the node and each lane sweeps all four rows.  The moments of the Q
+// populations are butterfly-reduced within the 16 lanes, so every lane of a
+// node holds rho, u, T and takes the same convergence decision.  The step is
+// bound by the FP64 pipe; all source reads go through the read-only L1 path.
+// Templated on the lattice: D2Q16 (N1 = 4, all 16 lanes of a node busy) or
+// D2Q9 (N1 = 3: lanes with q >= 9 only join the shuffles).
 //
 // Per predictor-corrector pass (Eqs. advection, vi, interpolation, transform):
 //   departure  y_q = x - (sqrt(theta) c_q + u) dt, origin floor(y_q) - 1
@@ -41,11 +41,19 @@ cudaError_t upload_lattice_fp64() {
     return cudaMemcpyToSymbol(c_L, L, sizeof(L));
 }
 
-template <int N1>
+// NPW nodes per warp.  NPW = 1: lane = (q, half of the stencil rows), the
+// halves summed by one shuffle; the warp never diverges on the pass count.
+// NPW = 2: lane = (q, node of the pair), each lane sweeps all four stencil
+// rows; the per-node scalar work of a pass (reciprocals, square root, cubic
+// weights, moment butterflies, convergence test) is then issued once per
+// two nodes, at the price of the two nodes' pass counts diverging (the pair
+// runs the larger count, the finished node's lanes idle).
+template <int N1, int NPW>
 __global__ void __launch_bounds__(K1_WARPS * 32, 3)
 k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ iters,
              DevStats* __restrict__ stats, int nx, int ny, long long N, StepParams P) {
     constexpr int Q = N1 * N1;
+    constexpr unsigned FULL = 0xffffffffu;
     const Lattice& L = c_L[lattice_slot(N1)];
     __shared__ unsigned long long s_passes, s_nc, s_np;
     __shared__ unsigned int s_max;
@@ -58,11 +66,16 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    const long long node = (long long)blockIdx.x * K1_WARPS + (threadIdx.x >> 5);
-    if (node < N) {  // warp-uniform
-        const int X = (int)(node % nx);
-        const int Y = (int)(node / nx);
-        const int q = lane & 15, half = lane >> 4;
+    const int q = lane & 15, sub = lane >> 4;
+    const long long warp = (long long)blockIdx.x * K1_WARPS + (threadIdx.x >> 5);
+    const long long node = NPW == 1 ? warp : warp * 2 + sub;
+    const bool valid = node < N;  // warp-uniform when NPW == 1
+    const int half = NPW == 1 ? sub : 0;
+    const int qbase = NPW == 1 ? 0 : (lane & 16);  // first lane of this node
+    if (__any_sync(FULL, valid)) {
+        const long long nd = valid ? node : 0;
+        const int X = (int)(nd % nx);
+        const int Y = (int)(nd / nx);
         const bool act = q < Q;  // lane holds a population (all on D2Q16)
         const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
         const double ck = act ? L.c[k] : 0.0, cl = act ? L.c[l] : 0.0;
@@ -79,7 +92,7 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
         const double d3k = L.d3[k], d3l = L.d3[l];
 
         // seed gauge (Eqs. seed_gauge, seed_gauge_T)
-        double ux = in.ux[node], uy = in.uy[node], st = in.st[node];
+        double ux = in.ux[nd], uy = in.uy[nd], st = in.st[nd];
         if (P.seed_mode == 1) {
             ux = 0.0;
             uy = 0.0;
@@ -93,113 +106,125 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
         unsigned int flag = 0u;
         double total = 0.0, rho = 0.0;
         double nux = ux, nuy = uy, nst = st;  // gauge the last pass's moments define
-        for (;;) {
-            ++pass;
-            const double inv = 1.0 / st;
-            const double vx = fma(st, ck, ux), vy = fma(st, cl, uy);
-            const double depx = (double)X - vx * P.dt;
-            const double depy = (double)Y - vy * P.dt;
-            const double flx = floor(depx), fly = floor(depy);
-            double lx[4], ly[4];
-            lagrange4(depx - flx + 1.0, lx);
-            lagrange4(depy - fly + 1.0, ly);
-            const int x0 = wrap_idx((long long)flx - 1, nx);
-            const int y0 = wrap_idx((long long)fly - 1, ny);
-            const double bx = -ux * inv, by = -uy * inv;
-
+        bool done = !valid;
+        while (__any_sync(FULL, !done)) {
+            const bool work = !done;
             double acc = 0.0;
-            if (act) {
+            if (work) {
+                ++pass;
+                const double inv = 1.0 / st;
+                const double vx = fma(st, ck, ux), vy = fma(st, cl, uy);
+                const double depx = (double)X - vx * P.dt;
+                const double depy = (double)Y - vy * P.dt;
+                const double flx = floor(depx), fly = floor(depy);
+                double lx[4], ly[4];
+                lagrange4(depx - flx + 1.0, lx);
+                lagrange4(depy - fly + 1.0, ly);
+                const int x0 = wrap_idx((long long)flx - 1, nx);
+                const int y0 = wrap_idx((long long)fly - 1, ny);
+                const double bx = -ux * inv, by = -uy * inv;
+                if (act) {
+                    constexpr int ROWS = NPW == 1 ? 2 : 4;
 #pragma unroll
-            for (int jj = 0; jj < 2; ++jj) {
-                const int jy = 2 * half + jj;
-                const double wy = half ? ly[2 + jj] : ly[jj];
-                const int sy = wrap_inc(y0, jy, ny);
-                double rowacc = 0.0;
+                    for (int jj = 0; jj < ROWS; ++jj) {
+                        const int jy = NPW == 1 ? 2 * half + jj : jj;
+                        const double wy = NPW == 1 ? (half ? ly[2 + jj] : ly[jj]) : ly[jj];
+                        const int sy = wrap_inc(y0, jy, ny);
+                        double rowacc = 0.0;
 #pragma unroll
-                for (int jx = 0; jx < 4; ++jx) {
-                    const int sx = wrap_inc(x0, jx, nx);
-                    const long long s = (long long)sy * nx + sx;
-                    const double sts = __ldg(in.st + s);
-                    const double uxs = __ldg(in.ux + s);
-                    const double uys = __ldg(in.uy + s);
-                    const double r = fma(sts, inv, -1.0);  // st_s/st' - 1
-                    const double dx = fma(uxs, inv, bx);   // (u_s,x - u'_x)/st'
-                    const double dy = fma(uys, inv, by);
-                    double gx[N1], gy[N1];
+                        for (int jx = 0; jx < 4; ++jx) {
+                            const int sx = wrap_inc(x0, jx, nx);
+                            const long long s = (long long)sy * nx + sx;
+                            const double sts = __ldg(in.st + s);
+                            const double uxs = __ldg(in.ux + s);
+                            const double uys = __ldg(in.uy + s);
+                            const double r = fma(sts, inv, -1.0);  // st_s/st' - 1
+                            const double dx = fma(uxs, inv, bx);   // (u_s,x - u'_x)/st'
+                            const double dy = fma(uys, inv, by);
+                            double gx[N1], gy[N1];
 #pragma unroll
-                    for (int a = 0; a < N1; ++a) {
-                        const double de = fma(L.c[a], r, dx);
-                        gx[a] = gauge_poly<N1>(d3k, d2k[a], d1k[a], ik[a], de);
+                            for (int a = 0; a < N1; ++a) {
+                                const double de = fma(L.c[a], r, dx);
+                                gx[a] = gauge_poly<N1>(d3k, d2k[a], d1k[a], ik[a], de);
+                            }
+#pragma unroll
+                            for (int b = 0; b < N1; ++b) {
+                                const double de = fma(L.c[b], r, dy);
+                                gy[b] = gauge_poly<N1>(d3l, d2l[b], d1l[b], il[b], de);
+                            }
+                            double g = 0.0;
+#pragma unroll
+                            for (int a = 0; a < N1; ++a) {
+                                double h = 0.0;
+#pragma unroll
+                                for (int b = 0; b < N1; ++b)
+                                    h = fma(gy[b], __ldg(in.f + (long long)(N1 * a + b) * N + s), h);
+                                g = fma(gx[a], h, g);
+                            }
+                            rowacc = fma(lx[jx], g, rowacc);
+                        }
+                        acc = fma(wy, rowacc, acc);
                     }
-#pragma unroll
-                    for (int b = 0; b < N1; ++b) {
-                        const double de = fma(L.c[b], r, dy);
-                        gy[b] = gauge_poly<N1>(d3l, d2l[b], d1l[b], il[b], de);
-                    }
-                    double g = 0.0;
-#pragma unroll
-                    for (int a = 0; a < N1; ++a) {
-                        double h = 0.0;
-#pragma unroll
-                        for (int b = 0; b < N1; ++b)
-                            h = fma(gy[b], __ldg(in.f + (long long)(N1 * a + b) * N + s), h);
-                        g = fma(gx[a], h, g);
-                    }
-                    rowacc = fma(lx[jx], g, rowacc);
                 }
-                acc = fma(wy, rowacc, acc);
             }
-            }
-            total = acc + __shfl_xor_sync(0xffffffffu, acc, 16);
+            double tp = acc;
+            if (NPW == 1) tp = acc + __shfl_xor_sync(FULL, acc, 16);
 
-            // moments of the pass (central form)
-            double m0 = total, m1 = ck * total, m2 = cl * total,
-                   m3 = (ck * ck + cl * cl) * total;
+            // moments of the pass (central form), butterflies within 16 lanes
+            double m0 = tp, m1 = ck * tp, m2 = cl * tp, m3 = (ck * ck + cl * cl) * tp;
 #pragma unroll
             for (int o = 1; o < 16; o <<= 1) {
-                m0 += __shfl_xor_sync(0xffffffffu, m0, o);
-                m1 += __shfl_xor_sync(0xffffffffu, m1, o);
-                m2 += __shfl_xor_sync(0xffffffffu, m2, o);
-                m3 += __shfl_xor_sync(0xffffffffu, m3, o);
+                m0 += __shfl_xor_sync(FULL, m0, o);
+                m1 += __shfl_xor_sync(FULL, m1, o);
+                m2 += __shfl_xor_sync(FULL, m2, o);
+                m3 += __shfl_xor_sync(FULL, m3, o);
             }
-            rho = m0;
-            const double ir = 1.0 / rho;
-            const double dux = st * m1 * ir, duy = st * m2 * ir;
-            const double ux1 = ux + dux, uy1 = uy + duy;
-            double st1 = st;
-            bool ok = (rho > 0.0) && isfinite(ux1) && isfinite(uy1);
-            if (P.thermal) {
-                const double T1 = 0.5 * (st * st * m3 * ir - (dux * dux + duy * duy));
-                ok = ok && (T1 > 0.0) && isfinite(T1);
-                st1 = sqrt(T1 / P.T_L);
+            if (work) {
+                total = tp;
+                rho = m0;
+                const double ir = 1.0 / rho;
+                const double dux = st * m1 * ir, duy = st * m2 * ir;
+                const double ux1 = ux + dux, uy1 = uy + duy;
+                double st1 = st;
+                bool ok = (rho > 0.0) && isfinite(ux1) && isfinite(uy1);
+                if (P.thermal) {
+                    const double T1 = 0.5 * (st * st * m3 * ir - (dux * dux + duy * duy));
+                    ok = ok && (T1 > 0.0) && isfinite(T1);
+                    st1 = sqrt(T1 / P.T_L);
+                }
+                if (!ok) {
+                    flag |= 2u;
+                    done = true;
+                } else {
+                    nux = ux1;
+                    nuy = uy1;
+                    nst = st1;
+                    const bool conv = fabs(ux1 - ux) < P.eps_abs + P.eps_rel * fabs(ux1) &&
+                                      fabs(uy1 - uy) < P.eps_abs + P.eps_rel * fabs(uy1) &&
+                                      fabs(st1 - st) < P.eps_abs + P.eps_rel * fabs(st1);
+                    bool stop;
+                    if (P.fixed_iter > 0) {
+                        stop = pass >= P.fixed_iter;
+                    } else {
+                        stop = conv || pass >= P.max_iter;
+                        if (!conv && pass >= P.max_iter) flag |= 1u;
+                    }
+                    if (stop) {
+                        done = true;
+                    } else {
+                        ux = ux1;
+                        uy = uy1;
+                        st = st1;
+                    }
+                }
             }
-            if (!ok) {
-                flag |= 2u;
-                break;
-            }
-            nux = ux1;
-            nuy = uy1;
-            nst = st1;
-            const bool conv = fabs(ux1 - ux) < P.eps_abs + P.eps_rel * fabs(ux1) &&
-                              fabs(uy1 - uy) < P.eps_abs + P.eps_rel * fabs(uy1) &&
-                              fabs(st1 - st) < P.eps_abs + P.eps_rel * fabs(st1);
-            bool stop;
-            if (P.fixed_iter > 0) {
-                stop = pass >= P.fixed_iter;
-            } else {
-                stop = conv || pass >= P.max_iter;
-                if (!conv && pass >= P.max_iter) flag |= 1u;
-            }
-            if (stop) break;
-            ux = ux1;
-            uy = uy1;
-            st = st1;
         }
 
         // Re-express f^{lambda_n} in the gauge lambda_{n+1} its moments define
         // (Eq. transform at the node itself): that gauge is then exactly the
-        // co-moving frame of the stored populations.
-        if (!(flag & 2u)) {
+        // co-moving frame of the stored populations.  The shuffles run on
+        // every lane; a node with non-physical moments keeps its populations.
+        {
             const double inv1 = 1.0 / nst;
             const double r = fma(st, inv1, -1.0);
             const double dx = (ux - nux) * inv1, dy = (uy - nuy) * inv1;
@@ -217,21 +242,23 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
                 double h = 0.0;
 #pragma unroll
                 for (int b = 0; b < N1; ++b)
-                    h = fma(gy[b], __shfl_sync(0xffffffffu, total, N1 * a + b), h);
+                    h = fma(gy[b], __shfl_sync(FULL, total, qbase + N1 * a + b), h);
                 g = fma(gx[a], h, g);
             }
-            total = g;
-            ux = nux;
-            uy = nuy;
-            st = nst;
+            if (!(flag & 2u)) {
+                total = g;
+                ux = nux;
+                uy = nuy;
+                st = nst;
+            }
         }
 
         // BGK relaxation toward rho W in the co-moving gauge (Eq. postcollision)
-        if (half == 0 && act) {
+        if (valid && half == 0 && act) {
             const double feq = rho * L.w[k] * L.w[l];
             out.f[(long long)q * N + node] = total + 2.0 * P.beta * (feq - total);
         }
-        if (lane == 0) {
+        if (valid && q == 0 && half == 0) {
             out.ux[node] = ux;
             out.uy[node] = uy;
             out.st[node] = st;
@@ -253,14 +280,20 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
 
 cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>& out,
                              int32_t* iters, DevStats* stats, int nx, int ny, const Lattice& L,
-                             const StepParams& P, cudaStream_t s) {
+                             const StepParams& P, int nodes_per_warp, cudaStream_t s) {
     const long long N = (long long)nx * ny;
     if (N == 0) return cudaSuccess;
-    const long long nb = (N + K1_WARPS - 1) / K1_WARPS;
-    if (L.n1 == 3)
-        k1_step_fp64<3><<<(unsigned)nb, K1_WARPS * 32, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
-    else
-        k1_step_fp64<4><<<(unsigned)nb, K1_WARPS * 32, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+    const int npw = nodes_per_warp == 2 ? 2 : 1;
+    const long long per_cta = (long long)K1_WARPS * npw;
+    const unsigned nb = (unsigned)((N + per_cta - 1) / per_cta);
+    const int T = K1_WARPS * 32;
+    if (L.n1 == 3) {
+        if (npw == 2) k1_step_fp64<3, 2><<<nb, T, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+        else k1_step_fp64<3, 1><<<nb, T, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+    } else {
+        if (npw == 2) k1_step_fp64<4, 2><<<nb, T, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+        else k1_step_fp64<4, 1><<<nb, T, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+    }
     return cudaGetLastError();
 }
 
@@ -336,7 +369,8 @@ extern "C" pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx
         return POND_ERR_ARG;
     if (cfg->precision != POND_FP64 || !(cfg->nu > 0.0) || !(cfg->T_ref > 0.0) ||
         !(cfg->dt > 0.0) || cfg->max_iter < 1 || cfg->fixed_iter < 0 || cfg->seed_mode < 0 ||
-        cfg->seed_mode > 2 || (cfg->lattice != POND_D2Q16 && cfg->lattice != POND_D2Q9))
+        cfg->seed_mode > 2 || (cfg->lattice != POND_D2Q16 && cfg->lattice != POND_D2Q9) ||
+        cfg->nodes_per_warp < 0 || cfg->nodes_per_warp > 2)
         return POND_ERR_ARG;
     if (nx < 1 || ny < 1 || (int64_t)nx * ny > kNoAllocMaxNodes) return POND_ERR_ARG;
     int dev = 0;
@@ -378,7 +412,8 @@ extern "C" pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx
     out.ux = ux_out;
     out.uy = uy_out;
     out.st = st_out;
-    e = launch_step_fp64(in, out, iters, dstats, nx, ny, L, P, s);
+    e = launch_step_fp64(in, out, iters, dstats, nx, ny, L, P,
+                         cfg->nodes_per_warp ? cfg->nodes_per_warp : FP64_NODES_PER_WARP, s);
     if (e != cudaSuccess) return POND_ERR_CUDA;
     k_noalloc_st_to_t<<<nb, 256, 0, s>>>(st_out, T_out, N, L.T_L);
     e = cudaGetLastError();

@@ -63,6 +63,7 @@ class pond_config(ctypes.Structure):
         ("autotune", ctypes.c_int32),
         ("tile_rows", ctypes.c_int32),
         ("lattice", ctypes.c_int32),
+        ("nodes_per_warp", ctypes.c_int32),
     ]
 
 

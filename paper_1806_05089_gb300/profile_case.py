@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--tile", type=int, default=0,
                     help="mixed forms: tile rows (4, 8, 16; -16 = two nodes per thread)")
+    ap.add_argument("--npw", type=int, default=0,
+                    help="fp64: nodes per warp of the step kernel (1 or 2; 0 = default)")
     ap.add_argument("--lattice", choices=["d2q16", "d2q9"], default="d2q16",
                     help="fp64 / mixed / batched: lattice (d2q9 runs the same flow at "
                          "T_L = 1/3: T/3, u/sqrt 3)")
@@ -51,6 +53,8 @@ def main():
         cfg = dict(lat)
         if prec == pond.POND_FP32_MIXED:
             cfg["tile_rows"] = a.tile
+        else:
+            cfg["nodes_per_warp"] = a.npw
         with pond.Sim(a.n, a.n, prec, **cfg) as s:
             s.set_state(f.rho, f.ux, f.uy, f.T)
             s.step(1)

@@ -75,12 +75,13 @@ def rel_errors(g, grho, o, speed_scale=False):
     return e_rho, e_u, e_T, e_f
 
 
+@pytest.mark.parametrize("npw", [1, 2])
 @pytest.mark.parametrize("name,nx,ny,steps", [("tg", 64, 64, 12), ("supersonic", 37, 29, 6),
                                               ("hot", 48, 40, 5), ("supersonic", 1, 1, 3),
                                               ("tg", 3, 5, 4), ("supersonic", 2, 7, 3)])
-def test_d2q9_fp64_fixed_passes_matches_oracle(name, nx, ny, steps):
+def test_d2q9_fp64_fixed_passes_matches_oracle(name, nx, ny, steps, npw):
     fields = d2q9_fields(name, nx, ny)
-    g, grho, git, _ = gpu_run(fields, steps, fixed_iter=4)
+    g, grho, git, _ = gpu_run(fields, steps, fixed_iter=4, nodes_per_warp=npw)
     o, oit = oracle_run(fields, steps, fixed_iter=4)
     assert np.all(git == 4) and np.all(oit == 4)
     e = rel_errors(g, grho, o)

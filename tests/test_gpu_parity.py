@@ -77,22 +77,25 @@ def small_fields(name, nx, ny):
 
 # ------------------------------------------------------------------ FP64
 
+@pytest.mark.parametrize("npw", [1, 2])
 @pytest.mark.parametrize("name,nx,ny,steps", [("tg", 64, 64, 12), ("supersonic", 37, 29, 6),
                                               ("hot", 48, 40, 5), ("supersonic", 1, 1, 3),
                                               ("tg", 3, 5, 4), ("supersonic", 2, 7, 3)])
-def test_fp64_fixed_passes_matches_oracle(name, nx, ny, steps):
+def test_fp64_fixed_passes_matches_oracle(name, nx, ny, steps, npw):
     fields = small_fields(name, nx, ny)
-    g, grho, git, _ = gpu_run(fields, steps, fixed_iter=4)
+    g, grho, git, _ = gpu_run(fields, steps, fixed_iter=4, nodes_per_warp=npw)
     o, oit = oracle_run(fields, steps, fixed_iter=4)
     assert np.all(git == 4) and np.all(oit == 4)
     e = rel_errors(g, grho, o)
     assert max(e) <= TOL64, e
 
 
-def test_fp64_taylor_green_full_config_adaptive():
-    """64^2 Taylor-Green, u0 = 0.05, nu = 0.01, 100 steps, adaptive passes."""
+@pytest.mark.parametrize("npw", [1, 2])
+def test_fp64_taylor_green_full_config_adaptive(npw):
+    """64^2 Taylor-Green, u0 = 0.05, nu = 0.01, 100 steps, adaptive passes
+    (one and two nodes per warp)."""
     fields = workloads.tg64()
-    g, grho, git, stats = gpu_run(fields, 100)
+    g, grho, git, stats = gpu_run(fields, 100, nodes_per_warp=npw)
     o, oit = oracle_run(fields, 100)
     assert stats["nonconverged"] == 0 and stats["nonphysical"] == 0
     assert np.mean(git == oit) >= 0.999
@@ -100,9 +103,12 @@ def test_fp64_taylor_green_full_config_adaptive():
     assert max(e) <= 1e-9, e
 
 
-def test_fp64_supersonic_adaptive_pass_map():
-    fields = small_fields("supersonic", 64, 48)
-    g, grho, git, stats = gpu_run(fields, 4)
+@pytest.mark.parametrize("npw", [1, 2])
+def test_fp64_supersonic_adaptive_pass_map(npw):
+    # 63 x 47: an odd node count leaves the last warp of the two-node mapping
+    # with one node
+    fields = small_fields("supersonic", 63, 47)
+    g, grho, git, stats = gpu_run(fields, 4, nodes_per_warp=npw)
     o, oit = oracle_run(fields, 4)
     assert np.mean(git == oit) >= 0.999
     assert max(rel_errors(g, grho, o)) <= 1e-9

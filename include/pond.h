@@ -194,6 +194,19 @@ pond_status pond_iterations(pond_ctx* ctx, int32_t grid, void* iters, int32_t on
 pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in, const void* gauge_bar_in,
                               void* f_bar_out, void* gauge_bar_out, double* nu_bar_accum);
 
+/* pond_adjoint_step with the step's output gauge given: ux_out, uy_out,
+ * T_out (device, [ny][nx]) are the gauge that pond_step stores when it
+ * advances the context's current state by one step (for instance read back
+ * with pond_get_state after the forward step, as a checkpointed rollout has
+ * it).  The adjoint then does not recompute the forward step.  The result
+ * equals pond_adjoint_step's when the gauge is that step's output; another
+ * gauge gives the VJP at another linearisation point, which is not detected.
+ * Errors: as pond_adjoint_step, and POND_ERR_ARG for a NULL output gauge. */
+pond_status pond_adjoint_step_given(pond_ctx* ctx, const void* ux_out, const void* uy_out,
+                                    const void* T_out, const void* f_bar_in,
+                                    const void* gauge_bar_in, void* f_bar_out,
+                                    void* gauge_bar_out, double* nu_bar_accum);
+
 /* VJP of the equilibrium initialisation of pond_set_state (f = rho W,
  * Eq. equilibrium): rho_bar[x] = sum_q W_q f_bar[q][x].  Single-grid D2Q16
  * contexts; device pointers, f_bar [16][ny][nx], rho_bar [ny][nx].  (The

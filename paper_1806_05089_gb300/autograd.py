@@ -4,10 +4,12 @@
 FP64 PonD steps from the equilibrium f = rho0 W in the gauge (u0, T0) and
 returns the final density.  Backward recomputes each checkpoint segment
 forward (keeping that segment's states on the device), then walks the steps
-in reverse through ``pond_adjoint_step`` (the hand-written adjoint kernels:
-implicit differentiation of the predictor-corrector fixed point, transposed
-reconstruction and gauge transform, BGK collision) and finally
-``pond_adjoint_init``.  Gradients are returned for rho0 and nu.
+in reverse through ``pond_adjoint_step_given`` (the hand-written adjoint
+kernels: implicit differentiation of the predictor-corrector fixed point,
+transposed reconstruction and gauge transform, BGK collision), handing it
+each step's output gauge -- the next recomputed state, the next checkpoint or
+the final state -- so that it need not recompute the forward step, and
+finally ``pond_adjoint_init``.  Gradients are returned for rho0 and nu.
 
 All tensors are CUDA float64 (the boundary is FP64 for both forms); pass
 ``precision=pond.POND_FP32_MIXED`` to run the forward and the adjoint in the
@@ -54,6 +56,7 @@ class PondRollout(torch.autograd.Function):
             pond.pond_step(sim.ctx, 1, want_stats=False)
         rho = torch.empty((ny, nx), dtype=torch.float64, device=dev)
         pond.pond_moments(sim.ctx, 0, rho)
+        ctx.final = _get_state(sim, ny, nx, dev)
         ctx.sim = sim
         ctx.ckpts = ckpts
         ctx.steps = steps
@@ -82,8 +85,16 @@ class PondRollout(torch.autograd.Function):
                 pond.pond_step(sim.ctx, 1, want_stats=False)
                 states.append(_get_state(sim, ny, nx, dev))
             for t in reversed(range(start, end)):
+                # the step's output state: recomputed, the next checkpoint, or final
+                if t + 1 < end:
+                    nxt = states[t + 1 - start]
+                elif seg + 1 < len(ctx.ckpts):
+                    nxt = ctx.ckpts[seg + 1]
+                else:
+                    nxt = ctx.final
                 _set_state(sim, states[t - start])
-                nu_bar += pond.pond_adjoint_step(sim.ctx, fbar, gbar, fbar_new, gbar_new)
+                nu_bar += pond.pond_adjoint_step_given(sim.ctx, nxt[1], nxt[2], nxt[3], fbar, gbar,
+                                                       fbar_new, gbar_new)
                 fbar, fbar_new = fbar_new, fbar
                 gbar, gbar_new = gbar_new, gbar
             del states

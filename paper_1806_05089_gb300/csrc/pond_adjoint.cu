@@ -399,9 +399,40 @@ static pond_status adj_fail(pond_ctx* ctx, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return adj_fail(ctx, e_, where);    \
     } while (0)
 
-extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in,
-                                         const void* gauge_bar_in, void* f_bar_out,
-                                         void* gauge_bar_out, double* nu_bar_accum) {
+namespace pond {
+
+// The step's output gauge (u_x, u_y, T) given by the caller, stored as the
+// scratch forward gauge (u_x, u_y, sqrt(T / T_L)), the form the forward step
+// itself stores.
+__global__ void k_gauge_from_T(const double* __restrict__ ux, const double* __restrict__ uy,
+                               const double* __restrict__ T, double* __restrict__ ux_o,
+                               double* __restrict__ uy_o, double* __restrict__ st_o, long long N,
+                               double T_L) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        ux_o[i] = ux[i];
+        uy_o[i] = uy[i];
+        st_o[i] = sqrt(T[i] / T_L);
+    }
+}
+
+cudaError_t launch_gauge_from_T(const double* ux, const double* uy, const double* T,
+                                double* ux_o, double* uy_o, double* st_o, long long N,
+                                double T_L, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    k_gauge_from_T<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ux, uy, T, ux_o, uy_o, st_o, N, T_L);
+    return cudaGetLastError();
+}
+
+}  // namespace pond
+
+// Both entry points: out_gauge = {u_x, u_y, T} of the step's output when
+// the caller has it (pond_adjoint_step_given), else NULLs and the forward
+// step is recomputed here.
+static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gauge[3],
+                                     const void* f_bar_in, const void* gauge_bar_in,
+                                     void* f_bar_out, void* gauge_bar_out,
+                                     double* nu_bar_accum) {
     if (!ctx) return POND_ERR_ARG;
     if (!f_bar_in || !gauge_bar_in || !f_bar_out || !gauge_bar_out || !nu_bar_accum) {
         ctx->err = "adjoint: NULL argument";
@@ -446,7 +477,7 @@ extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in,
     AdjointScratch* a = ctx->adj;
     if (!fp64) {
         // FP32 populations: pond_adjoint_mixed.cu
-        ACK(adjoint_step_mixed(ctx, static_cast<const double*>(f_bar_in),
+        ACK(adjoint_step_mixed(ctx, out_gauge, static_cast<const double*>(f_bar_in),
                                static_cast<const double*>(gauge_bar_in),
                                static_cast<double*>(f_bar_out), static_cast<double*>(gauge_bar_out),
                                a->beta_bar, a->minmax, a->host_minmax),
@@ -467,10 +498,17 @@ extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in,
     in.st = ctx->st[ctx->cur];
     cudaStream_t s = ctx->stream;
 
-    // 1. forward step into scratch: its gauge is the fixed point lambda*
-    ACK(launch_step_fp64(in, a->fwd, a->iters, a->stats, G.nx, G.ny, ctx->L, ctx->P,
-                         fp64_npw(ctx), s),
-        "adjoint forward");
+    // 1. the fixed point lambda*: the gauge the forward step stores, given by
+    //    the caller or recomputed into scratch
+    if (out_gauge[0]) {
+        ACK(launch_gauge_from_T(out_gauge[0], out_gauge[1], out_gauge[2], a->fwd.ux, a->fwd.uy,
+                                a->fwd.st, N, ctx->L.T_L, s),
+            "adjoint given gauge");
+    } else {
+        ACK(launch_step_fp64(in, a->fwd, a->iters, a->stats, G.nx, G.ny, ctx->L, ctx->P,
+                             fp64_npw(ctx), s),
+            "adjoint forward");
+    }
     // 2. velocity bounds for the transpose gather
     k_minmax3<<<1, 1024, 0, s>>>(a->fwd.ux, a->fwd.uy, a->fwd.st, N, a->minmax);
     ACK(cudaGetLastError(), "adjoint bounds");
@@ -518,6 +556,30 @@ extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in,
     const double beta = ctx->P.beta;
     *nu_bar_accum += bb * (-2.0 * beta * beta / (ctx->cfg.T_ref * ctx->cfg.dt));
     return POND_OK;
+}
+
+extern "C" pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in,
+                                         const void* gauge_bar_in, void* f_bar_out,
+                                         void* gauge_bar_out, double* nu_bar_accum) {
+    const double* none[3] = {nullptr, nullptr, nullptr};
+    return adjoint_step_impl(ctx, none, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out,
+                             nu_bar_accum);
+}
+
+extern "C" pond_status pond_adjoint_step_given(pond_ctx* ctx, const void* ux_out,
+                                               const void* uy_out, const void* T_out,
+                                               const void* f_bar_in, const void* gauge_bar_in,
+                                               void* f_bar_out, void* gauge_bar_out,
+                                               double* nu_bar_accum) {
+    if (!ctx) return POND_ERR_ARG;
+    if (!ux_out || !uy_out || !T_out) {
+        ctx->err = "adjoint: NULL output gauge";
+        return POND_ERR_ARG;
+    }
+    const double* given[3] = {static_cast<const double*>(ux_out), static_cast<const double*>(uy_out),
+                              static_cast<const double*>(T_out)};
+    return adjoint_step_impl(ctx, given, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out,
+                             nu_bar_accum);
 }
 
 extern "C" pond_status pond_adjoint_init(pond_ctx* ctx, const void* f_bar, void* rho_bar) {

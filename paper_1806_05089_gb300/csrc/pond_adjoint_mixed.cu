@@ -339,9 +339,10 @@ void destroy_adjoint_mixed(pond_ctx* ctx) {
 // Mixed-precision adjoint step; arguments already validated by
 // pond_adjoint_step.  bounds6 = {min ux*, max ux*, min uy*, max uy*, min s*,
 // max s*} of the forward gauge is filled by the caller's bounds pass.
-cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* fbar, const double* gbar,
-                               double* fbar_out, double* gbar_out, double* beta_bar_dev,
-                               double* minmax_dev, double* minmax_host) {
+cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
+                               const double* fbar, const double* gbar, double* fbar_out,
+                               double* gbar_out, double* beta_bar_dev, double* minmax_dev,
+                               double* minmax_host) {
     const int64_t N = ctx->N;
     cudaStream_t s = ctx->stream;
     cudaError_t e;
@@ -364,10 +365,15 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* fbar, const double* 
     in.ux = ctx->ux[ctx->cur];
     in.uy = ctx->uy[ctx->cur];
     in.st = ctx->st[ctx->cur];
-    // 1. forward step into scratch: its gauge is the fixed point lambda*
-    e = launch_step_mixed(in, a->fwd, a->iters, a->stats, ctx->grids_dev, ctx->tile_prefix_dev,
-                          1, ctx->n_tiles, N, nullptr, ctx->win, ctx->persistent_ctas, ctx->L,
-                          ctx->P, s);
+    // 1. the fixed point lambda*: the gauge the forward step stores, given by
+    //    the caller or recomputed into scratch
+    if (out_gauge[0])
+        e = launch_gauge_from_T(out_gauge[0], out_gauge[1], out_gauge[2], a->fwd.ux, a->fwd.uy,
+                                a->fwd.st, N, ctx->L.T_L, s);
+    else
+        e = launch_step_mixed(in, a->fwd, a->iters, a->stats, ctx->grids_dev,
+                              ctx->tile_prefix_dev, 1, ctx->n_tiles, N, nullptr, ctx->win,
+                              ctx->persistent_ctas, ctx->L, ctx->P, s);
     if (e != cudaSuccess) return e;
     const unsigned nb256 = (unsigned)((N + 255) / 256);
     k_split_gauge<<<nb256, 256, 0, s>>>(in.ux, in.uy, in.st, a->gin, N);

@@ -167,6 +167,10 @@ struct AdjointScratch;
 struct AdjMixedScratch;
 cudaError_t launch_minmax3(const double* ux, const double* uy, const double* st, long long N,
                            double* out6, cudaStream_t s);
+// (u_x, u_y, T) -> (u_x, u_y, sqrt(T / T_L)) into the adjoint's forward gauge
+cudaError_t launch_gauge_from_T(const double* ux, const double* uy, const double* T,
+                                double* ux_o, double* uy_o, double* st_o, long long N,
+                                double T_L, cudaStream_t s);
 
 }  // namespace pond
 
@@ -214,6 +218,8 @@ inline int fp64_npw(const pond_ctx* ctx) {
 
 void destroy_adjoint(pond_ctx* ctx);
 void destroy_adjoint_mixed(pond_ctx* ctx);
-cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* fbar, const double* gbar,
-                               double* fbar_out, double* gbar_out, double* beta_bar_dev,
-                               double* minmax_dev, double* minmax_host);
+// out_gauge: {u_x, u_y, T} of the step's output, or NULLs to recompute it
+cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
+                               const double* fbar, const double* gbar, double* fbar_out,
+                               double* gbar_out, double* beta_bar_dev, double* minmax_dev,
+                               double* minmax_host);

@@ -251,10 +251,13 @@ __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedAr
     const int WN = A.ww * A.wh;
     // staged window, one float4 per (x-speed index a, node): f[a][0..n1-1],
     // so one 16-byte load feeds one row of the n1 x n1 contraction; and the
-    // tile-relative gauge (s - s_ref, u_x - u_x,ref, u_y - u_y,ref, 0)
+    // tile-relative gauge (s - s_ref, u_x - u_x,ref, u_y - u_y,ref): on D2Q16
+    // a float4 of its own per node, on D2Q9 the spare fourth words of the
+    // three rows (one 16-byte load fewer per pair)
+    constexpr int GROWS = N1 == 4 ? 1 : 0;
     float4* s_f4 = smem4;           // [N1][WN]
-    float4* s_g4 = s_f4 + N1 * WN;  // [WN]
-    float* s_acc = reinterpret_cast<float*>(s_g4 + WN);  // [Q][NT]
+    float4* s_g4 = s_f4 + N1 * WN;  // [GROWS][WN]
+    float* s_acc = reinterpret_cast<float*>(s_g4 + GROWS * WN);  // [Q][NT]
     __shared__ float s_red[4][NT / 32];
     __shared__ long long s_item;
     __shared__ unsigned long long s_passes, s_nc, s_np, s_fb;
@@ -348,13 +351,14 @@ __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedAr
             const int gy = wrap_idx((long long)wy0 + cy, G.ny);
             const long long gi = base + (long long)gy * G.nx + gx;
             const float* fp = A.in.f + gi;
+            const float go[3] = {(float)(__ldg(A.in.st + gi) - rst), (float)(__ldg(A.in.ux + gi) - rux),
+                                 (float)(__ldg(A.in.uy + gi) - ruy)};
 #pragma unroll
             for (int a = 0; a < N1; ++a)
                 s_f4[a * WN + i] = make_float4(__ldg(fp + (N1 * a + 0) * A.plane), __ldg(fp + (N1 * a + 1) * A.plane),
                                                __ldg(fp + (N1 * a + 2) * A.plane),
-                                               N1 == 4 ? __ldg(fp + (N1 * a + 3) * A.plane) : 0.0f);
-            s_g4[i] = make_float4((float)(__ldg(A.in.st + gi) - rst), (float)(__ldg(A.in.ux + gi) - rux),
-                                  (float)(__ldg(A.in.uy + gi) - ruy), 0.0f);
+                                               N1 == 4 ? __ldg(fp + (N1 * a + 3) * A.plane) : go[a]);
+            if constexpr (GROWS == 1) s_g4[i] = make_float4(go[0], go[1], go[2], 0.0f);
         }
         __syncthreads();
 
@@ -403,7 +407,15 @@ __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedAr
                         // source's tile-relative gauge offset
                         auto pair = [&](int jx, int jy) -> float {
                             const int si = (row + jy) * ww + col + jx;
-                            const float4 g4 = s_g4[si];
+                            float4 g4;       // gauge offsets of the source
+                            float4 fr[N1];   // D2Q9: rows read up front (they hold the gauge)
+                            if constexpr (GROWS == 1) {
+                                g4 = s_g4[si];
+                            } else {
+#pragma unroll
+                                for (int a = 0; a < N1; ++a) fr[a] = s_f4[a * WN + si];
+                                g4 = make_float4(fr[0].w, fr[1].w, fr[2].w, 0.0f);
+                            }
                             const float r = fmaf(g4.x, invf, bst);   // s_s/s' - 1
                             const float dx = fmaf(g4.y, invf, bux);  // (u_s,x - u'_x)/s'
                             const float dy = fmaf(g4.z, invf, buy);
@@ -420,8 +432,11 @@ __global__ void __launch_bounds__(TX* TY, 512 / (TX * TY)) k2_step_mixed(MixedAr
                             }
                             float gsum = 0.0f;
 #pragma unroll
-                            for (int a = 0; a < N1; ++a)
-                                gsum = fmaf(gx[a], row_dot<N1>(gy, s_f4[a * WN + si]), gsum);
+                            for (int a = 0; a < N1; ++a) {
+                                // D2Q16: each row read where it is used
+                                const float4 f4 = GROWS == 1 ? s_f4[a * WN + si] : fr[a];
+                                gsum = fmaf(gx[a], row_dot<N1>(gy, f4), gsum);
+                            }
                             return gsum;
                         };
                         // reconstruction relative to the stencil node nearest
@@ -927,10 +942,12 @@ __global__ void __launch_bounds__(TX* TY, 1) k2_step_mixed_pair(MixedArgs A) {
 }
 
 size_t mixed_smem_bytes(const TileWindow& w) {
-    // n1 float4 population rows and one float4 gauge per staged node, Q
-    // floats of pass populations per target node
+    // n1 float4 population rows per staged node, plus a float4 gauge on
+    // D2Q16 (D2Q9 keeps it in the rows' spare words); Q floats of pass
+    // populations per target node
     const size_t n1 = (size_t)w.n1;
-    return sizeof(float) * (4 * (n1 + 1) * w.ww * w.wh + n1 * n1 * w.tx * w.ty);
+    const size_t rows = n1 + (n1 == 4 ? 1 : 0);
+    return sizeof(float) * (4 * rows * w.ww * w.wh + n1 * n1 * w.tx * w.ty);
 }
 
 template <int TY, bool PAIR, int N1>

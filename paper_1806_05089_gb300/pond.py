@@ -87,7 +87,8 @@ _LIB = None
 # every symbol include/pond.h declares
 EXPORTS = ["pond_config_default", "pond_create", "pond_set_stream", "pond_set_state",
            "pond_step", "pond_moments", "pond_get_state", "pond_iterations",
-           "pond_adjoint_step", "pond_adjoint_init", "pond_step_fp64_noalloc", "pond_destroy",
+           "pond_adjoint_step", "pond_adjoint_step_given", "pond_adjoint_init",
+           "pond_step_fp64_noalloc", "pond_destroy",
            "pond_last_error", "pond_version"]
 
 POND_NOALLOC_MAX_NODES = 262144
@@ -131,6 +132,9 @@ def load(build_if_missing: bool = True, path: str | None = None):
     lib.pond_iterations.restype = i32
     lib.pond_adjoint_step.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
     lib.pond_adjoint_step.restype = i32
+    lib.pond_adjoint_step_given.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp,
+                                            ctypes.POINTER(ctypes.c_double)]
+    lib.pond_adjoint_step_given.restype = i32
     lib.pond_adjoint_init.argtypes = [vp, vp, vp]
     lib.pond_adjoint_init.restype = i32
     lib.pond_step_fp64_noalloc.argtypes = [ctypes.POINTER(pond_config), i32, i32,
@@ -256,6 +260,17 @@ def pond_adjoint_step(ctx, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out):
     nu_bar = ctypes.c_double(0.0)
     ps = [_ptr(a, True) for a in (f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out)]
     _check(ctx, load().pond_adjoint_step(ctx, *[p for p, _ in ps], ctypes.byref(nu_bar)))
+    return nu_bar.value
+
+
+def pond_adjoint_step_given(ctx, ux_out, uy_out, T_out, f_bar_in, gauge_bar_in, f_bar_out,
+                            gauge_bar_out):
+    """pond_adjoint_step with the step's output gauge (device tensors) given,
+    so the forward step is not recomputed; returns d(loss)/d(nu) of this step."""
+    nu_bar = ctypes.c_double(0.0)
+    ps = [_ptr(a, True) for a in (ux_out, uy_out, T_out, f_bar_in, gauge_bar_in, f_bar_out,
+                                  gauge_bar_out)]
+    _check(ctx, load().pond_adjoint_step_given(ctx, *[p for p, _ in ps], ctypes.byref(nu_bar)))
     return nu_bar.value
 
 

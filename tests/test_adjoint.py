@@ -166,3 +166,41 @@ def test_mixed_adjoint_matches_fp64_adjoint():
     assert abs(L32 - L64) <= 1e-4 * L64
     assert np.abs(g32 - g64).max() <= 1e-4 * np.abs(g64).max()
     assert abs(n32 - n64) <= 1e-4 * abs(n64)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [0, 1])
+def test_adjoint_given_output_gauge_matches_recomputed(precision):
+    """pond_adjoint_step_given (the step's output gauge handed in) gives the
+    same VJP as pond_adjoint_step (forward step recomputed inside), FP64 and
+    mixed; a NULL output gauge is refused."""
+    from paper_1806_05089_gb300 import pond
+    rho0, ux, uy, T, _ = small_case(40, 36, seed=7)
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(8)
+    fbar = torch.tensor(rng.standard_normal((16, 36, 40)), device=dev)
+    gbar = torch.tensor(rng.standard_normal((3, 36, 40)), device=dev)
+    with pond.Sim(40, 36, precision, nu=0.01) as s:
+        s.set_state(rho0, ux, uy, T)
+        s.step(2)                         # a state with a non-equilibrium part
+        st0 = s.state()
+        s.step(1)
+        st1 = s.state()                   # the step's output
+        s.set_state(None, st0.ux, st0.uy, st0.T, st0.f)
+        outs = []
+        for given in (False, True):
+            fo = torch.empty_like(fbar)
+            go = torch.empty_like(gbar)
+            if given:
+                g1 = [torch.tensor(a, device=dev) for a in (st1.ux, st1.uy, st1.T)]
+                nb = pond.pond_adjoint_step_given(s.ctx, *g1, fbar, gbar, fo, go)
+            else:
+                nb = pond.pond_adjoint_step(s.ctx, fbar, gbar, fo, go)
+            outs.append((fo.cpu().numpy(), go.cpu().numpy(), nb))
+        with pytest.raises(pond.PondError) as e:
+            pond.pond_adjoint_step_given(s.ctx, None, g1[1], g1[2], fbar, gbar, fo, go)
+        assert e.value.status == pond.POND_ERR_ARG
+    (f_a, g_a, n_a), (f_b, g_b, n_b) = outs
+    assert np.abs(f_a - f_b).max() <= 1e-14 * np.abs(f_a).max()
+    assert np.abs(g_a - g_b).max() <= 1e-14 * np.abs(g_a).max()
+    assert abs(n_a - n_b) <= 1e-14 * abs(n_a)

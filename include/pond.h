@@ -112,9 +112,10 @@ typedef struct pond_config {
                            D2Q16-only. */
     int32_t nodes_per_warp; /* FP64 form: target nodes per warp of the step
                            kernel, 1 (16 lanes per node, each lane half the
-                           stencil rows) or 2 (each lane all rows); 0 = the
-                           library default.  The two agree to rounding
-                           (the stencil rows are summed in another order). */
+                           stencil rows), 2 (each lane all rows) or, on D2Q9
+                           only, 3 (10 lanes per node); 0 = the library
+                           default.  They agree to rounding (the stencil
+                           rows and the moments are summed in other orders). */
 } pond_config;
 
 /* Counters accumulated over the steps of one pond_step call. */

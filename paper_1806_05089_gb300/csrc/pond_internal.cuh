@@ -112,8 +112,12 @@ cudaError_t upload_lattice_mixed();
 cudaError_t upload_lattice_adjoint(const Lattice& L);
 cudaError_t upload_lattice_adjoint_mixed(const Lattice& L);
 
-// FP64 step of a single grid, lattice L.n1, nodes_per_warp 1 or 2.
-constexpr int FP64_NODES_PER_WARP = 2;  // default mapping (measured faster)
+// FP64 step of a single grid, lattice L.n1, nodes_per_warp 1, 2 or (D2Q9) 3.
+constexpr int FP64_NODES_PER_WARP = 2;  // default mapping on D2Q16 (measured faster)
+constexpr int FP64_NODES_PER_WARP_Q9 = 3;  // default mapping on D2Q9 (measured faster)
+constexpr int fp64_default_npw(int n1) {
+    return n1 == 3 ? FP64_NODES_PER_WARP_Q9 : FP64_NODES_PER_WARP;
+}
 cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>& out,
                              int32_t* iters, DevStats* stats, int nx, int ny,
                              const Lattice& L, const StepParams& P, int nodes_per_warp,
@@ -213,7 +217,7 @@ struct pond_ctx {
 
 // nodes per warp of the context's FP64 step kernel
 inline int fp64_npw(const pond_ctx* ctx) {
-    return ctx->cfg.nodes_per_warp ? ctx->cfg.nodes_per_warp : pond::FP64_NODES_PER_WARP;
+    return ctx->cfg.nodes_per_warp ? ctx->cfg.nodes_per_warp : pond::fp64_default_npw(ctx->L.n1);
 }
 
 void destroy_adjoint(pond_ctx* ctx);

@@ -47,13 +47,17 @@ cudaError_t upload_lattice_fp64() {
 // rows; the per-node scalar work of a pass (reciprocals, square root, cubic
 // weights, moment butterflies, convergence test) is then issued once per
 // two nodes, at the price of the two nodes' pass counts diverging (the pair
-// runs the larger count, the finished node's lanes idle).
+// runs the larger count, the finished node's lanes idle).  NPW = 3 (D2Q9
+// only): three nodes in 10-lane groups (lanes 0-8, 10-18, 20-28 hold the
+// nine populations), 27 busy lanes instead of 18; the moments are summed by
+// nine indexed shuffles instead of the xor butterflies.
 template <int N1, int NPW>
 __global__ void __launch_bounds__(K1_WARPS * 32, 3)
 k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ iters,
              DevStats* __restrict__ stats, int nx, int ny, long long N, StepParams P) {
     constexpr int Q = N1 * N1;
     constexpr unsigned FULL = 0xffffffffu;
+    static_assert(NPW != 3 || N1 == 3, "three nodes per warp: D2Q9 only");
     const Lattice& L = c_L[lattice_slot(N1)];
     __shared__ unsigned long long s_passes, s_nc, s_np;
     __shared__ unsigned int s_max;
@@ -66,12 +70,16 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    const int q = lane & 15, sub = lane >> 4;
+    // sub: node of the warp (NPW 2, 3) or half of the stencil rows (NPW 1)
+    const int sub = NPW == 3 ? lane / 10 : lane >> 4;
+    const int q = NPW == 3 ? lane - 10 * sub : lane & 15;
     const long long warp = (long long)blockIdx.x * K1_WARPS + (threadIdx.x >> 5);
-    const long long node = NPW == 1 ? warp : warp * 2 + sub;
-    const bool valid = node < N;  // warp-uniform when NPW == 1
+    const long long node = NPW == 1 ? warp : warp * NPW + sub;
+    // warp-uniform when NPW == 1 (both halves hold the same node)
+    const bool valid = node < N && (NPW == 1 || sub < NPW);
     const int half = NPW == 1 ? sub : 0;
-    const int qbase = NPW == 1 ? 0 : (lane & 16);  // first lane of this node
+    // first lane of this node (lanes 30, 31 of NPW 3 hold no node)
+    const int qbase = NPW == 1 ? 0 : (NPW == 2 ? (lane & 16) : 10 * min(sub, 2));
     if (__any_sync(FULL, valid)) {
         const long long nd = valid ? node : 0;
         const int X = (int)(nd % nx);
@@ -170,14 +178,26 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
             double tp = acc;
             if (NPW == 1) tp = acc + __shfl_xor_sync(FULL, acc, 16);
 
-            // moments of the pass (central form), butterflies within 16 lanes
+            // moments of the pass (central form), summed over the node's lanes
             double m0 = tp, m1 = ck * tp, m2 = cl * tp, m3 = (ck * ck + cl * cl) * tp;
+            if constexpr (NPW == 3) {
+                const double v0 = m0, v1 = m1, v2 = m2, v3 = m3;
+                m0 = m1 = m2 = m3 = 0.0;
 #pragma unroll
-            for (int o = 1; o < 16; o <<= 1) {
-                m0 += __shfl_xor_sync(FULL, m0, o);
-                m1 += __shfl_xor_sync(FULL, m1, o);
-                m2 += __shfl_xor_sync(FULL, m2, o);
-                m3 += __shfl_xor_sync(FULL, m3, o);
+                for (int j = 0; j < Q; ++j) {
+                    m0 += __shfl_sync(FULL, v0, qbase + j);
+                    m1 += __shfl_sync(FULL, v1, qbase + j);
+                    m2 += __shfl_sync(FULL, v2, qbase + j);
+                    m3 += __shfl_sync(FULL, v3, qbase + j);
+                }
+            } else {
+#pragma unroll
+                for (int o = 1; o < 16; o <<= 1) {
+                    m0 += __shfl_xor_sync(FULL, m0, o);
+                    m1 += __shfl_xor_sync(FULL, m1, o);
+                    m2 += __shfl_xor_sync(FULL, m2, o);
+                    m3 += __shfl_xor_sync(FULL, m3, o);
+                }
             }
             if (work) {
                 total = tp;
@@ -283,12 +303,13 @@ cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>&
                              const StepParams& P, int nodes_per_warp, cudaStream_t s) {
     const long long N = (long long)nx * ny;
     if (N == 0) return cudaSuccess;
-    const int npw = nodes_per_warp == 2 ? 2 : 1;
+    const int npw = (nodes_per_warp == 3 && L.n1 == 3) ? 3 : (nodes_per_warp == 1 ? 1 : 2);
     const long long per_cta = (long long)K1_WARPS * npw;
     const unsigned nb = (unsigned)((N + per_cta - 1) / per_cta);
     const int T = K1_WARPS * 32;
     if (L.n1 == 3) {
-        if (npw == 2) k1_step_fp64<3, 2><<<nb, T, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+        if (npw == 3) k1_step_fp64<3, 3><<<nb, T, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+        else if (npw == 2) k1_step_fp64<3, 2><<<nb, T, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
         else k1_step_fp64<3, 1><<<nb, T, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
     } else {
         if (npw == 2) k1_step_fp64<4, 2><<<nb, T, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
@@ -370,7 +391,8 @@ extern "C" pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx
     if (cfg->precision != POND_FP64 || !(cfg->nu > 0.0) || !(cfg->T_ref > 0.0) ||
         !(cfg->dt > 0.0) || cfg->max_iter < 1 || cfg->fixed_iter < 0 || cfg->seed_mode < 0 ||
         cfg->seed_mode > 2 || (cfg->lattice != POND_D2Q16 && cfg->lattice != POND_D2Q9) ||
-        cfg->nodes_per_warp < 0 || cfg->nodes_per_warp > 2)
+        cfg->nodes_per_warp < 0 || cfg->nodes_per_warp > 3 ||
+        (cfg->nodes_per_warp == 3 && cfg->lattice != POND_D2Q9))
         return POND_ERR_ARG;
     if (nx < 1 || ny < 1 || (int64_t)nx * ny > kNoAllocMaxNodes) return POND_ERR_ARG;
     int dev = 0;
@@ -413,7 +435,7 @@ extern "C" pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx
     out.uy = uy_out;
     out.st = st_out;
     e = launch_step_fp64(in, out, iters, dstats, nx, ny, L, P,
-                         cfg->nodes_per_warp ? cfg->nodes_per_warp : FP64_NODES_PER_WARP, s);
+                         cfg->nodes_per_warp ? cfg->nodes_per_warp : fp64_default_npw(L.n1), s);
     if (e != cudaSuccess) return POND_ERR_CUDA;
     k_noalloc_st_to_t<<<nb, 256, 0, s>>>(st_out, T_out, N, L.T_L);
     e = cudaGetLastError();

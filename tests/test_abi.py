@@ -62,6 +62,13 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
     bad.lattice = pond.POND_D2Q9
     bad.tile_rows = -16
     assert lib.pond_create(ctypes.byref(bad), 1, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
+    # three nodes per warp is a D2Q9 mapping
+    bad = pond.pond_config_default(pond.POND_FP64)
+    bad.nodes_per_warp = 3
+    assert lib.pond_create(ctypes.byref(bad), 1, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
+    bad.nodes_per_warp = 4
+    bad.lattice = pond.POND_D2Q9
+    assert lib.pond_create(ctypes.byref(bad), 1, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
 
 
 def test_no_cpu_fallback_without_gpu():

@@ -170,25 +170,31 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(Ad
     dAuy += __shfl_xor_sync(0xffffffffu, dAuy, 16);
     dAst += __shfl_xor_sync(0xffffffffu, dAst, 16);
 
-    auto sum16 = [](double v) {
+    // Per-node epilogue in FP32: the inputs (A, its gauge derivatives) are
+    // FP32 already, and the 3 x 3 system is J = M_A A_lambda = -(I - Phi_lambda)
+    // with Phi_lambda the contraction of the fixed-point iteration, close to
+    // -I and well conditioned, so FP64 here (1/64 of the FP32 rate) would buy
+    // nothing; only the beta cotangent is accumulated in FP64.
+    auto sum16 = [](float v) {
 #pragma unroll
         for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         return v;
     };
-    const double sd = A.st_star[node];
-    const double Wq = (double)L.w[k] * (double)L.w[l];
-    const double fb = A.fbar[(long long)q * A.N + node];
-    const double Ad = Aq;
-    const double rho = sum16(Ad);
-    const double wf = sum16(Wq * fb);
-    const double beta = A.beta;
-    const double Abar = (1.0 - 2.0 * beta) * fb + 2.0 * beta * wf;
-    const double bb = sum16(2.0 * (rho * Wq - Ad) * fb);
-    const double c2 = (double)ck * ck + (double)cl * cl;
-    const double mux = sd * ck / rho, muy = sd * cl / rho;
-    const double mst = sd * (c2 - 2.0 * A.T_L) / (4.0 * rho * A.T_L);
-    const double d0 = dAux, d1 = dAuy, d2 = dAst;
-    double J[3][3];
+    const float sd = (float)A.st_star[node];
+    const float T_L = A.T_L;
+    const float Wq = L.w[k] * L.w[l];
+    const float fb = (float)A.fbar[(long long)q * A.N + node];
+    const float rho = sum16(Aq);
+    const float wf = sum16(Wq * fb);
+    const float beta = A.beta;
+    const float Abar = fmaf(1.0f - 2.0f * beta, fb, 2.0f * beta * wf);
+    const float bb = sum16(2.0f * fmaf(rho, Wq, -Aq) * fb);
+    const float c2 = fmaf(ck, ck, cl * cl);
+    const float irho = 1.0f / rho;
+    const float mux = sd * ck * irho, muy = sd * cl * irho;
+    const float mst = sd * (c2 - 2.0f * T_L) * irho / (4.0f * T_L);
+    const float d0 = dAux, d1 = dAuy, d2 = dAst;
+    float J[3][3];
     J[0][0] = sum16(mux * d0);
     J[0][1] = sum16(mux * d1);
     J[0][2] = sum16(mux * d2);
@@ -198,25 +204,25 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(Ad
     J[2][0] = sum16(mst * d0);
     J[2][1] = sum16(mst * d1);
     J[2][2] = sum16(mst * d2);
-    const double g0 = sum16(Abar * d0) + A.gbar[node];
-    const double g1 = sum16(Abar * d1) + A.gbar[A.N + node];
-    const double g2 = sum16(Abar * d2) + A.gbar[2 * A.N + node] * 2.0 * sd * A.T_L;
-    const double a00 = J[0][0], a01 = J[1][0], a02 = J[2][0];
-    const double a10 = J[0][1], a11 = J[1][1], a12 = J[2][1];
-    const double a20 = J[0][2], a21 = J[1][2], a22 = J[2][2];
-    const double det = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
-                       a02 * (a10 * a21 - a11 * a20);
-    const double idet = 1.0 / det;
-    const double r0 = -g0, r1 = -g1, r2 = -g2;
-    const double mu0 = (r0 * (a11 * a22 - a12 * a21) - a01 * (r1 * a22 - a12 * r2) +
-                        a02 * (r1 * a21 - a11 * r2)) * idet;
-    const double mu1 = (a00 * (r1 * a22 - a12 * r2) - r0 * (a10 * a22 - a12 * a20) +
-                        a02 * (a10 * r2 - r1 * a20)) * idet;
-    const double mu2 = (a00 * (a11 * r2 - r1 * a21) - a01 * (a10 * r2 - r1 * a20) +
-                        r0 * (a10 * a21 - a11 * a20)) * idet;
-    const double wq = Abar + mux * mu0 + muy * mu1 + mst * mu2;
-    if (half == 0) A.w[(long long)q * A.N + node] = (float)wq;
-    if (lane == 0) atomicAdd(A.beta_bar, bb);
+    const float g0 = sum16(Abar * d0) + (float)A.gbar[node];
+    const float g1 = sum16(Abar * d1) + (float)A.gbar[A.N + node];
+    const float g2 = sum16(Abar * d2) + (float)A.gbar[2 * A.N + node] * 2.0f * sd * T_L;
+    const float a00 = J[0][0], a01 = J[1][0], a02 = J[2][0];
+    const float a10 = J[0][1], a11 = J[1][1], a12 = J[2][1];
+    const float a20 = J[0][2], a21 = J[1][2], a22 = J[2][2];
+    const float det = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
+                      a02 * (a10 * a21 - a11 * a20);
+    const float idet = 1.0f / det;
+    const float r0 = -g0, r1 = -g1, r2 = -g2;
+    const float mu0 = (r0 * (a11 * a22 - a12 * a21) - a01 * (r1 * a22 - a12 * r2) +
+                       a02 * (r1 * a21 - a11 * r2)) * idet;
+    const float mu1 = (a00 * (r1 * a22 - a12 * r2) - r0 * (a10 * a22 - a12 * a20) +
+                       a02 * (a10 * r2 - r1 * a20)) * idet;
+    const float mu2 = (a00 * (a11 * r2 - r1 * a21) - a01 * (a10 * r2 - r1 * a20) +
+                       r0 * (a10 * a21 - a11 * a20)) * idet;
+    const float wq = Abar + mux * mu0 + muy * mu1 + mst * mu2;
+    if (half == 0) A.w[(long long)q * A.N + node] = wq;
+    if (lane == 0) atomicAdd(A.beta_bar, (double)bb);
 }
 
 __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_sources_mixed(AdjMixedArgs A) {

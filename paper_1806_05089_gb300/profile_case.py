@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--tile", type=int, default=0,
                     help="mixed forms: tile rows (4, 8, 16; -16 = two nodes per thread)")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="adjoint: precision of the rollout and its adjoint")
     ap.add_argument("--npw", type=int, default=0,
                     help="fp64: nodes per warp of the step kernel (1 or 2; 0 = default)")
     ap.add_argument("--lattice", choices=["d2q16", "d2q9"], default="d2q16",
@@ -85,11 +87,12 @@ def main():
         f, target = workloads.adjoint(a.n)
         dev = torch.device("cuda")
         r = torch.tensor(f.rho, device=dev, requires_grad=True)
+        prec = pond.POND_FP64 if a.precision == "fp64" else pond.POND_FP32_MIXED
         rho = pond_rollout(r, 0.01, *(torch.tensor(v, device=dev) for v in (f.ux, f.uy, f.T)),
-                           a.steps, a.steps)
+                           a.steps, a.steps, precision=prec)
         (0.5 * ((rho - torch.tensor(target, device=dev)) ** 2).sum()).backward()
         torch.cuda.synchronize()
-        out.update(n=a.n, steps=a.steps, grad_norm=float(r.grad.norm()))
+        out.update(n=a.n, steps=a.steps, precision=a.precision, grad_norm=float(r.grad.norm()))
     print(json.dumps(out))
 
 

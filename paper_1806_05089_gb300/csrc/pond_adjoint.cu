@@ -239,11 +239,18 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A
     for (int i = 0; i < 16; ++i) fb[i] = 0.0;
     double bux = 0.0, buy = 0.0, bst = 0.0;
 
-    // candidate targets x with floor(x - v dt) in [J - 2, J + 1]
-    const int xlo = (int)floor((double)JX - 2.0 + A.vlo_x[k] * A.dt) - 1;
-    const int xhi = (int)ceil((double)JX + 2.0 + A.vhi_x[k] * A.dt) + 1;
-    const int ylo = (int)floor((double)JY - 2.0 + A.vlo_y[l] * A.dt) - 1;
-    const int yhi = (int)ceil((double)JY + 2.0 + A.vhi_y[l] * A.dt) + 1;
+    // candidate targets: J is in the stencil of the target at x when
+    // floor(x - v dt) is in [J - 2, J + 1], i.e. x in [J - 2 + v dt, J + 2 + v dt);
+    // over v in [vlo, vhi] the integers x from ceil(J - 2 + vlo dt) to
+    // ceil(J + 2 + vhi dt) - 1, widened by a rounding margin (the exact test
+    // below decides).  ceil(J + a) = J + ceil(a) for integer J, so the bounds
+    // are formed relative to J.
+    const double ex = 1e-9 * (1.0 + fabs(A.vlo_x[k]) + fabs(A.vhi_x[k])) * A.dt;
+    const double ey = 1e-9 * (1.0 + fabs(A.vlo_y[l]) + fabs(A.vhi_y[l])) * A.dt;
+    const int xlo = JX + (int)ceil(-2.0 + A.vlo_x[k] * A.dt - ex);
+    const int xhi = JX + (int)ceil(2.0 + A.vhi_x[k] * A.dt + ex) - 1;
+    const int ylo = JY + (int)ceil(-2.0 + A.vlo_y[l] * A.dt - ey);
+    const int yhi = JY + (int)ceil(2.0 + A.vhi_y[l] * A.dt + ey) - 1;
     for (int yy = ylo + half; yy <= yhi; yy += 2) {
         const int ty = wrap_idx(yy, A.ny);
         for (int xx = xlo; xx <= xhi; ++xx) {

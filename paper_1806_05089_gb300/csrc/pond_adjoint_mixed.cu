@@ -243,11 +243,17 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_sources_mixed(Ad
     for (int i = 0; i < 16; ++i) fb[i] = 0.0f;
     float bux = 0.0f, buy = 0.0f, bst = 0.0f;
 
-    // candidate targets with floor(x - v dt) in [J - 2, J + 1]
-    const int xlo = (int)floorf((float)JX - 2.0f + A.vlo_x[k] * A.dt) - 1;
-    const int xhi = (int)ceilf((float)JX + 2.0f + A.vhi_x[k] * A.dt) + 1;
-    const int ylo = (int)floorf((float)JY - 2.0f + A.vlo_y[l] * A.dt) - 1;
-    const int yhi = (int)ceilf((float)JY + 2.0f + A.vhi_y[l] * A.dt) + 1;
+    // candidate targets: J is in the stencil of the target at x when
+    // floor(x - v dt) is in [J - 2, J + 1], i.e. x in [J - 2 + v dt, J + 2 + v dt);
+    // over v in [vlo, vhi] (the bounds carry a 1e-3-cell margin for the FP32
+    // departures) the integers x from ceil(J - 2 + vlo dt) to
+    // ceil(J + 2 + vhi dt) - 1; the exact test below decides.  ceil(J + a) =
+    // J + ceil(a) for integer J, so the bounds are free of the rounding of
+    // large coordinates.
+    const int xlo = JX + (int)ceilf(-2.0f + A.vlo_x[k] * A.dt);
+    const int xhi = JX + (int)ceilf(2.0f + A.vhi_x[k] * A.dt) - 1;
+    const int ylo = JY + (int)ceilf(-2.0f + A.vlo_y[l] * A.dt);
+    const int yhi = JY + (int)ceilf(2.0f + A.vhi_y[l] * A.dt) - 1;
     for (int yy = ylo + half; yy <= yhi; yy += 2) {
         const int ty = wrap_idx(yy, A.ny);
         for (int xx = xlo; xx <= xhi; ++xx) {
@@ -417,11 +423,12 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
         const double c = ctx->L.c[i];
         const double slo = c >= 0 ? c * mm[4] : c * mm[5];
         const double shi = c >= 0 ? c * mm[5] : c * mm[4];
-        // one cell of slack for the FP32 departures
-        A.vlo_x[i] = (float)(slo + mm[0]) - 1.0f;
-        A.vhi_x[i] = (float)(shi + mm[1]) + 1.0f;
-        A.vlo_y[i] = (float)(slo + mm[2]) - 1.0f;
-        A.vhi_y[i] = (float)(shi + mm[3]) + 1.0f;
+        // slack for the FP32 departures (their rounding is ~1e-6 cells)
+        const double sl = 1e-3 / ctx->P.dt;
+        A.vlo_x[i] = (float)(slo + mm[0] - sl);
+        A.vhi_x[i] = (float)(shi + mm[1] + sl);
+        A.vlo_y[i] = (float)(slo + mm[2] - sl);
+        A.vhi_y[i] = (float)(shi + mm[3] + sl);
     }
     const unsigned nb = (unsigned)((N + ADJM_WARPS - 1) / ADJM_WARPS);
     k_adjoint_targets_mixed<<<nb, ADJM_WARPS * 32, 0, s>>>(A);

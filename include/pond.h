@@ -108,8 +108,7 @@ typedef struct pond_config {
                            D2Q16 only). */
     int32_t lattice;    /* POND_D2Q16 (default) or POND_D2Q9.  Fixes Q and
                            T_L (so the meaning of theta = T / T_L and of the
-                           seed {0, T_L}).  The adjoint entry points are
-                           D2Q16-only. */
+                           seed {0, T_L}). */
     int32_t nodes_per_warp; /* FP64 form: target nodes per warp of the step
                            kernel, 1 (16 lanes per node, each lane half the
                            stencil rows), 2 (each lane all rows) or, on D2Q9
@@ -183,14 +182,14 @@ pond_status pond_iterations(pond_ctx* ctx, int32_t grid, void* iters, int32_t on
 
 /* Vector-Jacobian product of one step (single-grid contexts).  The context's
  * current state is the step's INPUT state s; given the cotangents of the
- * step's output, f_bar_in [16][ny][nx] and gauge_bar_in [3][ny][nx]
+ * step's output, f_bar_in [Q][ny][nx] and gauge_bar_in [3][ny][nx]
  * (ux, uy, T), writes the cotangents of s to f_bar_out and gauge_bar_out
  * (same layouts) and adds d(loss)/d(nu) to *nu_bar_accum.  The fixed point
  * is differentiated implicitly (the limit gauge of Eqs. density..T is a
  * function of the input state only; the seed gets no gradient).  All array
  * pointers are device pointers.  The state is left unchanged.  FP64 and
  * mixed contexts (the latter with FP32 pair arithmetic and an FP64 3 x 3
- * solve); single-grid, thermal mode, D2Q16 (POND_ERR_ARG otherwise).
+ * solve); single-grid, thermal mode, either lattice (POND_ERR_ARG otherwise).
  * Errors: POND_ERR_ARG, POND_ERR_STATE, POND_ERR_OOM, POND_ERR_CUDA. */
 pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in, const void* gauge_bar_in,
                               void* f_bar_out, void* gauge_bar_out, double* nu_bar_accum);
@@ -209,8 +208,8 @@ pond_status pond_adjoint_step_given(pond_ctx* ctx, const void* ux_out, const voi
                                     void* gauge_bar_out, double* nu_bar_accum);
 
 /* VJP of the equilibrium initialisation of pond_set_state (f = rho W,
- * Eq. equilibrium): rho_bar[x] = sum_q W_q f_bar[q][x].  Single-grid D2Q16
- * contexts; device pointers, f_bar [16][ny][nx], rho_bar [ny][nx].  (The
+ * Eq. equilibrium): rho_bar[x] = sum_q W_q f_bar[q][x].  Single-grid
+ * contexts; device pointers, f_bar [Q][ny][nx], rho_bar [ny][nx].  (The
  * gauge cotangents pass through unchanged: set_state stores u and T as given.)
  * Errors: POND_ERR_ARG, POND_ERR_CUDA. */
 pond_status pond_adjoint_init(pond_ctx* ctx, const void* f_bar, void* rho_bar);

@@ -13,7 +13,8 @@ finally ``pond_adjoint_init``.  Gradients are returned for rho0 and nu.
 
 All tensors are CUDA float64 (the boundary is FP64 for both forms); pass
 ``precision=pond.POND_FP32_MIXED`` to run the forward and the adjoint in the
-mixed form.  Every step of the forward and backward runs in libpond.so.
+mixed form, and ``lattice=pond.POND_D2Q9`` (with its ``T_ref``) for the D2Q9
+lattice.  Every step of the forward and backward runs in libpond.so.
 """
 from __future__ import annotations
 
@@ -23,7 +24,7 @@ from . import pond
 
 
 def _get_state(sim, ny, nx, dev):
-    f = torch.empty((16, ny, nx), dtype=torch.float64, device=dev)
+    f = torch.empty((sim.Q, ny, nx), dtype=torch.float64, device=dev)
     ux = torch.empty((ny, nx), dtype=torch.float64, device=dev)
     uy = torch.empty_like(ux)
     T = torch.empty_like(ux)
@@ -70,7 +71,7 @@ class PondRollout(torch.autograd.Function):
         ny, nx = ctx.shape
         dev = grad_rho.device
         # rho = sum_q f_q  =>  fbar_q = rho_bar for every q
-        fbar = grad_rho.contiguous().expand(16, ny, nx).contiguous()
+        fbar = grad_rho.contiguous().expand(sim.Q, ny, nx).contiguous()
         gbar = torch.zeros((3, ny, nx), dtype=torch.float64, device=dev)
         fbar_new = torch.empty_like(fbar)
         gbar_new = torch.empty_like(gbar)

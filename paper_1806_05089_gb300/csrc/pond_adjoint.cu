@@ -33,16 +33,18 @@
 
 namespace pond {
 
-__constant__ Lattice c_La;
+// Lattice constants of the adjoint kernels, slot lattice_slot(n1).
+__constant__ Lattice c_La[2];
 
-cudaError_t upload_lattice_adjoint(const Lattice& L) {
-    return cudaMemcpyToSymbol(c_La, &L, sizeof(Lattice));
+cudaError_t upload_lattice_adjoint() {
+    const Lattice L[2] = {make_lattice(POND_D2Q16), make_lattice(POND_D2Q9)};
+    return cudaMemcpyToSymbol(c_La, L, sizeof(L));
 }
 
 struct AdjointScratch {
     int64_t N = 0;
     StateBuf<double> fwd{};   // forward step output: gauge = lambda*
-    double* w = nullptr;      // [16][N]
+    double* w = nullptr;      // [Q][N] (allocated for 16)
     int32_t* iters = nullptr;
     DevStats* stats = nullptr;
     double* beta_bar = nullptr;  // device accumulator
@@ -76,10 +78,10 @@ struct AdjArgs {
     const double* ux_s;      // lambda* (forward output gauge)
     const double* uy_s;
     const double* st_s;
-    const double* fbar;      // [16][N]
+    const double* fbar;      // [Q][N]
     const double* gbar;      // [3][N]  (u_x, u_y, T)
-    double* w;               // [16][N]
-    double* fbar_in;         // [16][N]
+    double* w;               // [Q][N]
+    double* fbar_in;         // [Q][N]
     double* gbar_in;         // [3][N]
     double* beta_bar;
     int nx, ny;
@@ -90,14 +92,20 @@ struct AdjArgs {
 
 constexpr int ADJ_WARPS = 4;
 
+template <int N1>
 __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_targets(AdjArgs A) {
-    const Lattice& L = c_La;
+    constexpr int Q = N1 * N1;
+    const Lattice& L = c_La[lattice_slot(N1)];
     const int lane = threadIdx.x & 31;
     const long long node = (long long)blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
     if (node >= A.N) return;  // warp-uniform
     const int X = (int)(node % A.nx), Y = (int)(node / A.nx);
-    const int q = lane & 15, k = q >> 2, l = q & 3, half = lane >> 4;
-    const double ck = L.c[k], cl = L.c[l];
+    // lane = (population q, half); on D2Q9 lanes with q >= 9 hold no
+    // population: they contribute zeros to the 16-lane sums and read nothing
+    const int q = lane & 15, half = lane >> 4;
+    const bool act = q < Q;
+    const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
+    const double ck = act ? L.c[k] : 0.0, cl = act ? L.c[l] : 0.0;
     const double ux = A.ux_s[node], uy = A.uy_s[node], st = A.st_s[node];
     const double inv = 1.0 / st;
 
@@ -112,6 +120,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_targets(AdjArgs A
     const int y0 = wrap_idx((long long)fly - 1, A.ny);
 
     double Aq = 0.0, dAux = 0.0, dAuy = 0.0, dAst = 0.0;
+    if (act) {
 #pragma unroll
     for (int jj = 0; jj < 2; ++jj) {
         const int jy = 2 * half + jj;
@@ -125,9 +134,9 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_targets(AdjArgs A
             const double r = fma(A.in.st[s], inv, -1.0);
             const double dx = (A.in.ux[s] - ux) * inv;
             const double dy = (A.in.uy[s] - uy) * inv;
-            double gx[4], gdx[4], gy[4], gdy[4], xix[4], xiy[4];
+            double gx[N1], gdx[N1], gy[N1], gdy[N1], xix[N1], xiy[N1];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < N1; ++a) {
                 const double ex = fma(L.c[a], r, dx), ey = fma(L.c[a], r, dy);
                 xix[a] = L.c[a] + ex;
                 xiy[a] = L.c[a] + ey;
@@ -136,11 +145,11 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_targets(AdjArgs A
             }
             double g = 0.0, gux = 0.0, guy = 0.0, gst = 0.0;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < N1; ++a) {
                 double h = 0.0, hp = 0.0, hq = 0.0;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const double fv = A.in.f[(long long)(4 * a + b) * A.N + s];
+                for (int b = 0; b < N1; ++b) {
+                    const double fv = A.in.f[(long long)(N1 * a + b) * A.N + s];
                     h = fma(gy[b], fv, h);
                     hp = fma(gdy[b], fv, hp);
                     hq = fma(gdy[b] * xiy[b], fv, hq);
@@ -166,6 +175,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_targets(AdjArgs A
             dAst = fma(a_w, gst, fma(da_st, g, dAst));
         }
     }
+    }
     Aq += __shfl_xor_sync(0xffffffffu, Aq, 16);
     dAux += __shfl_xor_sync(0xffffffffu, dAux, 16);
     dAuy += __shfl_xor_sync(0xffffffffu, dAuy, 16);
@@ -176,8 +186,8 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_targets(AdjArgs A
         for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         return v;
     };
-    const double Wq = L.w[k] * L.w[l];
-    const double fb = A.fbar[(long long)q * A.N + node];
+    const double Wq = act ? L.w[k] * L.w[l] : 0.0;
+    const double fb = act ? A.fbar[(long long)q * A.N + node] : 0.0;
     const double rho = sum16(Aq);
     const double wf = sum16(Wq * fb);
     const double Abar = (1.0 - 2.0 * A.beta) * fb + 2.0 * A.beta * wf;
@@ -216,27 +226,33 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_targets(AdjArgs A
     const double mu2 = (a00 * (a11 * r2 - r1 * a21) - a01 * (a10 * r2 - r1 * a20) +
                         r0 * (a10 * a21 - a11 * a20)) * idet;
     const double wq = Abar + mux * mu0 + muy * mu1 + mst * mu2;
-    if (half == 0) A.w[(long long)q * A.N + node] = wq;
+    if (half == 0 && act) A.w[(long long)q * A.N + node] = wq;
     if (lane == 0) atomicAdd(A.beta_bar, bb);
 }
 
 // Transpose of the reconstruction, gathered at each source node.
+template <int N1>
 __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A) {
-    const Lattice& L = c_La;
+    constexpr int Q = N1 * N1;
+    const Lattice& L = c_La[lattice_slot(N1)];
     const int lane = threadIdx.x & 31;
     const long long src = (long long)blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
     if (src >= A.N) return;  // warp-uniform
     const int JX = (int)(src % A.nx), JY = (int)(src / A.nx);
-    const int q = lane & 15, k = q >> 2, l = q & 3, half = lane >> 4;
-    const double ck = L.c[k], cl = L.c[l];
-    double fj[16];
+    // lane = (population q, half); on D2Q9 lanes with q >= 9 hold no
+    // population: they contribute zeros to the 16-lane sums and read nothing
+    const int q = lane & 15, half = lane >> 4;
+    const bool act = q < Q;
+    const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
+    const double ck = act ? L.c[k] : 0.0, cl = act ? L.c[l] : 0.0;
+    double fj[Q];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) fj[i] = A.in.f[(long long)i * A.N + src];
+    for (int i = 0; i < Q; ++i) fj[i] = A.in.f[(long long)i * A.N + src];
     const double uxj = A.in.ux[src], uyj = A.in.uy[src], stj = A.in.st[src];
 
-    double fb[16];
+    double fb[Q];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) fb[i] = 0.0;
+    for (int i = 0; i < Q; ++i) fb[i] = 0.0;
     double bux = 0.0, buy = 0.0, bst = 0.0;
 
     // candidate targets: J is in the stencil of the target at x when
@@ -251,7 +267,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A
     const int xhi = JX + (int)ceil(2.0 + A.vhi_x[k] * A.dt + ex) - 1;
     const int ylo = JY + (int)ceil(-2.0 + A.vlo_y[l] * A.dt - ey);
     const int yhi = JY + (int)ceil(2.0 + A.vhi_y[l] * A.dt + ey) - 1;
-    for (int yy = ylo + half; yy <= yhi; yy += 2) {
+    for (int yy = ylo + half; act && yy <= yhi; yy += 2) {
         const int ty = wrap_idx(yy, A.ny);
         for (int xx = xlo; xx <= xhi; ++xx) {
             const int tx = wrap_idx(xx, A.nx);
@@ -272,21 +288,21 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A
             const double inv = 1.0 / st;
             const double r = fma(stj, inv, -1.0);
             const double dx = (uxj - ux) * inv, dy = (uyj - uy) * inv;
-            double gx[4], gdx[4], gy[4], gdy[4];
+            double gx[N1], gdx[N1], gy[N1], gdy[N1];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < N1; ++a) {
                 lag_taylor(L, k, a, fma(L.c[a], r, dx), gx[a], gdx[a]);
                 lag_taylor(L, l, a, fma(L.c[a], r, dy), gy[a], gdy[a]);
             }
             double sux = 0.0, suy = 0.0, sst = 0.0;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < N1; ++a) {
                 const double cgx = coef * gx[a];
                 double h = 0.0, hp = 0.0, hq = 0.0;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    fb[4 * a + b] = fma(cgx, gy[b], fb[4 * a + b]);
-                    const double fv = fj[4 * a + b];
+                for (int b = 0; b < N1; ++b) {
+                    fb[N1 * a + b] = fma(cgx, gy[b], fb[N1 * a + b]);
+                    const double fv = fj[N1 * a + b];
                     h = fma(gy[b], fv, h);
                     hp = fma(gdy[b], fv, hp);
                     hq = fma(gdy[b] * L.c[b], fv, hq);
@@ -306,15 +322,15 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) fb[i] += __shfl_xor_sync(0xffffffffu, fb[i], o);
+        for (int i = 0; i < Q; ++i) fb[i] += __shfl_xor_sync(0xffffffffu, fb[i], o);
         bux += __shfl_xor_sync(0xffffffffu, bux, o);
         buy += __shfl_xor_sync(0xffffffffu, buy, o);
         bst += __shfl_xor_sync(0xffffffffu, bst, o);
     }
-    if (lane < 16) {
+    if (lane < Q) {
         double v = fb[0];
 #pragma unroll
-        for (int i = 1; i < 16; ++i)
+        for (int i = 1; i < Q; ++i)
             if (lane == i) v = fb[i];
         A.fbar_in[(long long)lane * A.N + src] = v;
     } else if (lane == 16) {
@@ -365,13 +381,14 @@ cudaError_t launch_minmax3(const double* ux, const double* uy, const double* st,
     return cudaGetLastError();
 }
 
+template <int N1>
 __global__ void k_rho_bar(const double* __restrict__ fbar, double* __restrict__ rbar, long long N) {
-    const Lattice& L = c_La;
+    const Lattice& L = c_La[lattice_slot(N1)];
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double r = 0.0;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) r = fma(L.w[q >> 2] * L.w[q & 3], fbar[q * N + i], r);
+    for (int q = 0; q < N1 * N1; ++q) r = fma(L.w[q / N1] * L.w[q % N1], fbar[q * N + i], r);
     rbar[i] = r;
 }
 
@@ -445,8 +462,8 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
         ctx->err = "adjoint: NULL argument";
         return POND_ERR_ARG;
     }
-    if (ctx->n_grids != 1 || !ctx->cfg.thermal || ctx->L.n1 != 4) {
-        ctx->err = "adjoint: single-grid thermal D2Q16 contexts only";
+    if (ctx->n_grids != 1 || !ctx->cfg.thermal) {
+        ctx->err = "adjoint: single-grid thermal contexts only";
         return POND_ERR_ARG;
     }
     if (!ctx->grid_set[0]) {
@@ -552,9 +569,11 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
         A.vhi_y[i] = shi + mm[3];
     }
     const unsigned nb = (unsigned)((N + ADJ_WARPS - 1) / ADJ_WARPS);
-    k_adjoint_targets<<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    if (ctx->L.n1 == 3) k_adjoint_targets<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    else k_adjoint_targets<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
     ACK(cudaGetLastError(), "adjoint targets");
-    k_adjoint_sources<<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    if (ctx->L.n1 == 3) k_adjoint_sources<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    else k_adjoint_sources<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
     ACK(cudaGetLastError(), "adjoint sources");
     double bb = 0.0;
     ACK(cudaMemcpyAsync(&bb, a->beta_bar, sizeof(double), cudaMemcpyDeviceToHost, s), "adjoint copy");
@@ -591,16 +610,21 @@ extern "C" pond_status pond_adjoint_step_given(pond_ctx* ctx, const void* ux_out
 
 extern "C" pond_status pond_adjoint_init(pond_ctx* ctx, const void* f_bar, void* rho_bar) {
     if (!ctx) return POND_ERR_ARG;
-    if (!f_bar || !rho_bar || ctx->n_grids != 1 || ctx->L.n1 != 4) {
-        ctx->err = "adjoint_init: NULL argument, batched or D2Q9 context";
+    if (!f_bar || !rho_bar || ctx->n_grids != 1) {
+        ctx->err = "adjoint_init: NULL argument or batched context";
         return POND_ERR_ARG;
     }
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != ctx->device) cudaSetDevice(ctx->device);
     const long long N = ctx->N;
-    k_rho_bar<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
-        static_cast<const double*>(f_bar), static_cast<double*>(rho_bar), N);
+    const unsigned nb = (unsigned)((N + 255) / 256);
+    if (ctx->L.n1 == 3)
+        k_rho_bar<3><<<nb, 256, 0, ctx->stream>>>(static_cast<const double*>(f_bar),
+                                                   static_cast<double*>(rho_bar), N);
+    else
+        k_rho_bar<4><<<nb, 256, 0, ctx->stream>>>(static_cast<const double*>(f_bar),
+                                                   static_cast<double*>(rho_bar), N);
     const cudaError_t e = cudaGetLastError();
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return adj_fail(ctx, e, "adjoint_init");

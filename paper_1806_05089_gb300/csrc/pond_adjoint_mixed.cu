@@ -7,23 +7,26 @@
 // per-pair arithmetic runs in FP32.  Gauge differences u_s - u' are formed
 // from per-node (hi, lo) FP32 splits of the FP64 gauges,
 // (hi_s - hi') + (lo_s - lo'), which carries FP32 precision relative to the
-// difference itself; the 3 x 3 solve and the collision cotangents use FP64.
+// difference itself.  The per-node epilogue (sums, cotangents, 3 x 3 solve)
+// runs in FP32 as well; only the beta cotangent is accumulated in FP64.
+// Templated on the lattice like the FP64 adjoint.
 #include <cmath>
 
 #include "pond_device.cuh"
 
 namespace pond {
 
-__constant__ LatticeF c_Lam;
+// FP32 lattice constants of these kernels, slot lattice_slot(n1).
+__constant__ LatticeF c_Lam[2];
 
-cudaError_t upload_lattice_adjoint_mixed(const Lattice& L) {
-    const LatticeF F = to_float(L);
-    return cudaMemcpyToSymbol(c_Lam, &F, sizeof(LatticeF));
+cudaError_t upload_lattice_adjoint_mixed() {
+    const LatticeF F[2] = {to_float(make_lattice(POND_D2Q16)), to_float(make_lattice(POND_D2Q9))};
+    return cudaMemcpyToSymbol(c_Lam, F, sizeof(F));
 }
 
 struct AdjMixedScratch {
     StateBuf<float> fwd{};
-    float* w = nullptr;       // [16][N]
+    float* w = nullptr;       // [Q][N] (allocated for 16)
     float4* gin = nullptr;    // [2][N]: hi / lo splits of the input gauge (s, ux, uy, 0)
     float4* gstar = nullptr;  // [2][N]: hi / lo splits of lambda*
     int32_t* iters = nullptr;
@@ -71,14 +74,14 @@ __device__ __forceinline__ float sdiff(float ha, float la, float hb, float lb) {
 }
 
 struct AdjMixedArgs {
-    const float* f_in;       // input populations [16][N]
+    const float* f_in;       // input populations [Q][N]
     const float4* gin;       // splits of the input gauge
     const float4* gstar;     // splits of lambda*
     const double* st_in;     // input sqrt(theta) (FP64, for the T cotangent)
     const double* st_star;
-    const double* fbar;      // [16][N]
+    const double* fbar;      // [Q][N]
     const double* gbar;      // [3][N]
-    float* w;                // [16][N]
+    float* w;                // [Q][N]
     double* fbar_in;
     double* gbar_in;
     double* beta_bar;
@@ -90,14 +93,20 @@ struct AdjMixedArgs {
 
 constexpr int ADJM_WARPS = 4;
 
+template <int N1>
 __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(AdjMixedArgs A) {
-    const LatticeF& L = c_Lam;
+    constexpr int Q = N1 * N1;
+    const LatticeF& L = c_Lam[lattice_slot(N1)];
     const int lane = threadIdx.x & 31;
     const long long node = (long long)blockIdx.x * ADJM_WARPS + (threadIdx.x >> 5);
     if (node >= A.N) return;  // warp-uniform
     const int X = (int)(node % A.nx), Y = (int)(node / A.nx);
-    const int q = lane & 15, k = q >> 2, l = q & 3, half = lane >> 4;
-    const float ck = L.c[k], cl = L.c[l];
+    // lane = (population q, half); on D2Q9 lanes with q >= 9 hold no
+    // population: they contribute zeros to the 16-lane sums and read nothing
+    const int q = lane & 15, half = lane >> 4;
+    const bool act = q < Q;
+    const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
+    const float ck = act ? L.c[k] : 0.0f, cl = act ? L.c[l] : 0.0f;
     const float4 th = A.gstar[node], tl = A.gstar[A.N + node];  // (s, ux, uy)
     const float st = th.x + tl.x, ux = th.y + tl.y, uy = th.z + tl.z;
     const float inv = 1.0f / st;
@@ -112,6 +121,7 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(Ad
     const int y0 = wrap_idx((long long)Y + (long long)fly - 1, A.ny);
 
     float Aq = 0.0f, dAux = 0.0f, dAuy = 0.0f, dAst = 0.0f;
+    if (act) {
 #pragma unroll
     for (int jj = 0; jj < 2; ++jj) {
         const int jy = 2 * half + jj;
@@ -126,9 +136,9 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(Ad
             const float r = sdiff(sh.x, sl.x, th.x, tl.x) * inv;
             const float dx = sdiff(sh.y, sl.y, th.y, tl.y) * inv;
             const float dy = sdiff(sh.z, sl.z, th.z, tl.z) * inv;
-            float gx[4], gdx[4], gy[4], gdy[4], xix[4], xiy[4];
+            float gx[N1], gdx[N1], gy[N1], gdy[N1], xix[N1], xiy[N1];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < N1; ++a) {
                 const float ex = fmaf(L.c[a], r, dx), ey = fmaf(L.c[a], r, dy);
                 xix[a] = L.c[a] + ex;
                 xiy[a] = L.c[a] + ey;
@@ -137,11 +147,11 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(Ad
             }
             float g = 0.0f, gux = 0.0f, guy = 0.0f, gst = 0.0f;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < N1; ++a) {
                 float h = 0.0f, hp = 0.0f, hq = 0.0f;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const float fv = A.f_in[(long long)(4 * a + b) * A.N + s];
+                for (int b = 0; b < N1; ++b) {
+                    const float fv = A.f_in[(long long)(N1 * a + b) * A.N + s];
                     h = fmaf(gy[b], fv, h);
                     hp = fmaf(gdy[b], fv, hp);
                     hq = fmaf(gdy[b] * xiy[b], fv, hq);
@@ -165,6 +175,7 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(Ad
             dAst = fmaf(a_w, gst, fmaf(da_st, g, dAst));
         }
     }
+    }
     Aq += __shfl_xor_sync(0xffffffffu, Aq, 16);
     dAux += __shfl_xor_sync(0xffffffffu, dAux, 16);
     dAuy += __shfl_xor_sync(0xffffffffu, dAuy, 16);
@@ -182,8 +193,8 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(Ad
     };
     const float sd = (float)A.st_star[node];
     const float T_L = A.T_L;
-    const float Wq = L.w[k] * L.w[l];
-    const float fb = (float)A.fbar[(long long)q * A.N + node];
+    const float Wq = act ? L.w[k] * L.w[l] : 0.0f;
+    const float fb = act ? (float)A.fbar[(long long)q * A.N + node] : 0.0f;
     const float rho = sum16(Aq);
     const float wf = sum16(Wq * fb);
     const float beta = A.beta;
@@ -221,26 +232,32 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(Ad
     const float mu2 = (a00 * (a11 * r2 - r1 * a21) - a01 * (a10 * r2 - r1 * a20) +
                        r0 * (a10 * a21 - a11 * a20)) * idet;
     const float wq = Abar + mux * mu0 + muy * mu1 + mst * mu2;
-    if (half == 0) A.w[(long long)q * A.N + node] = wq;
+    if (half == 0 && act) A.w[(long long)q * A.N + node] = wq;
     if (lane == 0) atomicAdd(A.beta_bar, (double)bb);
 }
 
+template <int N1>
 __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_sources_mixed(AdjMixedArgs A) {
-    const LatticeF& L = c_Lam;
+    constexpr int Q = N1 * N1;
+    const LatticeF& L = c_Lam[lattice_slot(N1)];
     const int lane = threadIdx.x & 31;
     const long long src = (long long)blockIdx.x * ADJM_WARPS + (threadIdx.x >> 5);
     if (src >= A.N) return;  // warp-uniform
     const int JX = (int)(src % A.nx), JY = (int)(src / A.nx);
-    const int q = lane & 15, k = q >> 2, l = q & 3, half = lane >> 4;
-    const float ck = L.c[k], cl = L.c[l];
-    float fj[16];
+    // lane = (population q, half); on D2Q9 lanes with q >= 9 hold no
+    // population: they contribute zeros to the 16-lane sums and read nothing
+    const int q = lane & 15, half = lane >> 4;
+    const bool act = q < Q;
+    const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
+    const float ck = act ? L.c[k] : 0.0f, cl = act ? L.c[l] : 0.0f;
+    float fj[Q];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) fj[i] = A.f_in[(long long)i * A.N + src];
+    for (int i = 0; i < Q; ++i) fj[i] = A.f_in[(long long)i * A.N + src];
     const float4 jh = A.gin[src], jl = A.gin[A.N + src];
 
-    float fb[16];
+    float fb[Q];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) fb[i] = 0.0f;
+    for (int i = 0; i < Q; ++i) fb[i] = 0.0f;
     float bux = 0.0f, buy = 0.0f, bst = 0.0f;
 
     // candidate targets: J is in the stencil of the target at x when
@@ -254,7 +271,7 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_sources_mixed(Ad
     const int xhi = JX + (int)ceilf(2.0f + A.vhi_x[k] * A.dt) - 1;
     const int ylo = JY + (int)ceilf(-2.0f + A.vlo_y[l] * A.dt);
     const int yhi = JY + (int)ceilf(2.0f + A.vhi_y[l] * A.dt) - 1;
-    for (int yy = ylo + half; yy <= yhi; yy += 2) {
+    for (int yy = ylo + half; act && yy <= yhi; yy += 2) {
         const int ty = wrap_idx(yy, A.ny);
         for (int xx = xlo; xx <= xhi; ++xx) {
             const int tx = wrap_idx(xx, A.nx);
@@ -276,21 +293,21 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_sources_mixed(Ad
             const float r = sdiff(jh.x, jl.x, th.x, tl.x) * inv;
             const float dx = sdiff(jh.y, jl.y, th.y, tl.y) * inv;
             const float dy = sdiff(jh.z, jl.z, th.z, tl.z) * inv;
-            float gx[4], gdx[4], gy[4], gdy[4];
+            float gx[N1], gdx[N1], gy[N1], gdy[N1];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < N1; ++a) {
                 lag_taylor_f(L, k, a, fmaf(L.c[a], r, dx), gx[a], gdx[a]);
                 lag_taylor_f(L, l, a, fmaf(L.c[a], r, dy), gy[a], gdy[a]);
             }
             float sux = 0.0f, suy = 0.0f, sst = 0.0f;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < N1; ++a) {
                 const float cgx = coef * gx[a];
                 float h = 0.0f, hp = 0.0f, hq = 0.0f;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    fb[4 * a + b] = fmaf(cgx, gy[b], fb[4 * a + b]);
-                    const float fv = fj[4 * a + b];
+                for (int b = 0; b < N1; ++b) {
+                    fb[N1 * a + b] = fmaf(cgx, gy[b], fb[N1 * a + b]);
+                    const float fv = fj[N1 * a + b];
                     h = fmaf(gy[b], fv, h);
                     hp = fmaf(gdy[b], fv, hp);
                     hq = fmaf(gdy[b] * L.c[b], fv, hq);
@@ -308,15 +325,15 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_sources_mixed(Ad
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) fb[i] += __shfl_xor_sync(0xffffffffu, fb[i], o);
+        for (int i = 0; i < Q; ++i) fb[i] += __shfl_xor_sync(0xffffffffu, fb[i], o);
         bux += __shfl_xor_sync(0xffffffffu, bux, o);
         buy += __shfl_xor_sync(0xffffffffu, buy, o);
         bst += __shfl_xor_sync(0xffffffffu, bst, o);
     }
-    if (lane < 16) {
+    if (lane < Q) {
         float v = fb[0];
 #pragma unroll
-        for (int i = 1; i < 16; ++i)
+        for (int i = 1; i < Q; ++i)
             if (lane == i) v = fb[i];
         A.fbar_in[(long long)lane * A.N + src] = (double)v;
     } else if (lane == 16) {
@@ -431,8 +448,10 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
         A.vhi_y[i] = (float)(shi + mm[3] + sl);
     }
     const unsigned nb = (unsigned)((N + ADJM_WARPS - 1) / ADJM_WARPS);
-    k_adjoint_targets_mixed<<<nb, ADJM_WARPS * 32, 0, s>>>(A);
+    if (ctx->L.n1 == 3) k_adjoint_targets_mixed<3><<<nb, ADJM_WARPS * 32, 0, s>>>(A);
+    else k_adjoint_targets_mixed<4><<<nb, ADJM_WARPS * 32, 0, s>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_adjoint_sources_mixed<<<nb, ADJM_WARPS * 32, 0, s>>>(A);
+    if (ctx->L.n1 == 3) k_adjoint_sources_mixed<3><<<nb, ADJM_WARPS * 32, 0, s>>>(A);
+    else k_adjoint_sources_mixed<4><<<nb, ADJM_WARPS * 32, 0, s>>>(A);
     return cudaGetLastError();
 }

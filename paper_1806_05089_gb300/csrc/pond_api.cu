@@ -368,8 +368,8 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
         if (e == cudaSuccess) e = cudaMemset(ctx->iters, 0, sizeof(int32_t) * ctx->N);
         if (e == cudaSuccess) e = upload_lattice_fp64();
         if (e == cudaSuccess) e = upload_lattice_mixed();
-        if (e == cudaSuccess) e = upload_lattice_adjoint(make_lattice(POND_D2Q16));
-        if (e == cudaSuccess) e = upload_lattice_adjoint_mixed(make_lattice(POND_D2Q16));
+        if (e == cudaSuccess) e = upload_lattice_adjoint();
+        if (e == cudaSuccess) e = upload_lattice_adjoint_mixed();
         if (e != cudaSuccess) {
             st = cuda_fail(ctx, e, "context set-up");
             ok = false;

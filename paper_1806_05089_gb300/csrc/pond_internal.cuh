@@ -105,12 +105,11 @@ struct StateBuf {
 // Launchers (defined in the .cu files); all return the launch status.
 
 // Per-translation-unit constant-bank copies of the lattices (call once per
-// device before launching).  The step kernels hold both lattices, slot
-// lattice_slot(n1); the adjoint kernels D2Q16 only.
+// device before launching): both D2Q16 and D2Q9, slot lattice_slot(n1).
 cudaError_t upload_lattice_fp64();
 cudaError_t upload_lattice_mixed();
-cudaError_t upload_lattice_adjoint(const Lattice& L);
-cudaError_t upload_lattice_adjoint_mixed(const Lattice& L);
+cudaError_t upload_lattice_adjoint();
+cudaError_t upload_lattice_adjoint_mixed();
 
 // FP64 step of a single grid, lattice L.n1, nodes_per_warp 1, 2 or (D2Q9) 3.
 constexpr int FP64_NODES_PER_WARP = 2;  // default mapping on D2Q16 (measured faster)

@@ -5,7 +5,7 @@ oracle, and its autograd gradient matches central finite differences of the
 C oracle -- this pins the reference gradient.
 GPU: the CUDA adjoint (pond_adjoint_step through PondRollout) matches the
 reference gradient, and central finite differences of the GPU forward, up to
-the 512^2 / 200-step / checkpoint-20 workload.
+the 512^2 / 200-step / checkpoint-20 workload; on D2Q16 and on D2Q9.
 
 Loss throughout: L = 1/2 sum (rho_T - rho*)^2 with a seeded target rho*.
 """
@@ -18,61 +18,70 @@ from oracle import torch_ref as tr
 from paper_1806_05089_gb300 import workloads
 
 
-def small_case(nx, ny, seed=0):
+def small_case(nx, ny, seed=0, T_L=1.0):
+    """Taylor-Green (u0 = 0.3) with seeded density and temperature; on D2Q9
+    (T_L = 1/3) T and u are rescaled to the same Mach numbers."""
     tg = workloads.taylor_green(nx, ny, 0.3)
     rng = np.random.default_rng(seed)
     rho0 = 1.0 + 0.05 * rng.standard_normal((ny, nx))
     target = 1.0 + 0.01 * rng.standard_normal((ny, nx))
-    T0 = 1.0 + 0.1 * rng.random((ny, nx))
-    return rho0, tg.ux, tg.uy, T0, target
+    T0 = (1.0 + 0.1 * rng.random((ny, nx))) * T_L
+    return rho0, tg.ux * np.sqrt(T_L), tg.uy * np.sqrt(T_L), T0, target
 
 
-def oracle_loss(rho0, ux, uy, T, target, nu, steps, passes):
-    st = oracle.init_equilibrium(rho0, ux, uy, T)
-    p = oracle.Params(nu=nu, fixed_iter=passes)
+def oracle_loss(rho0, ux, uy, T, target, nu, steps, passes, lattice=0, T_ref=1.0):
+    st = oracle.init_equilibrium(rho0, ux, uy, T, lattice=lattice)
+    p = oracle.Params(nu=nu, fixed_iter=passes, lattice=lattice, T_ref=T_ref)
     for _ in range(steps):
         st, _, _ = oracle.step(st, p)
     return 0.5 * ((st.f.sum(0) - target) ** 2).sum()
 
 
-def reference_grad(rho0, ux, uy, T, target, nu, steps, passes):
+def reference_grad(rho0, ux, uy, T, target, nu, steps, passes, lattice=0, T_ref=1.0):
     r = torch.tensor(rho0, requires_grad=True)
     n = torch.tensor(nu, dtype=torch.float64, requires_grad=True)
-    rho = tr.rollout(r, torch.tensor(ux), torch.tensor(uy), torch.tensor(T), n, steps, passes)
+    rho = tr.rollout(r, torch.tensor(ux), torch.tensor(uy), torch.tensor(T), n, steps, passes,
+                     T_ref=T_ref, lattice_kind=lattice)
     loss = 0.5 * ((rho - torch.tensor(target)) ** 2).sum()
     loss.backward()
     return float(loss.detach()), r.grad.numpy(), float(n.grad)
 
 
-def test_reference_step_matches_oracle():
-    rho0, ux, uy, T, _ = small_case(7, 5)
-    st = oracle.init_equilibrium(rho0, ux, uy, T)
+LATTICES = [(0, 1.0), (1, 1.0 / 3.0)]  # (lattice, T_L): D2Q16, D2Q9
+
+
+@pytest.mark.parametrize("lattice,T_L", LATTICES)
+def test_reference_step_matches_oracle(lattice, T_L):
+    rho0, ux, uy, T, _ = small_case(7, 5, T_L=T_L)
+    st = oracle.init_equilibrium(rho0, ux, uy, T, lattice=lattice)
     f = torch.tensor(st.f)
     g = [torch.tensor(a) for a in (st.ux, st.uy, st.T)]
     o = st
     for _ in range(2):
-        o, _, _ = oracle.step(o, oracle.Params(nu=0.02, fixed_iter=5))
-        f, *g = tr.step(f, *g, 0.02, 5)
+        o, _, _ = oracle.step(o, oracle.Params(nu=0.02, fixed_iter=5, lattice=lattice, T_ref=T_L))
+        f, *g = tr.step(f, *g, 0.02, 5, T_ref=T_L, lattice_kind=lattice)
     assert np.abs(f.numpy() - o.f).max() <= 1e-13
     assert np.abs(g[0].numpy() - o.ux).max() <= 1e-13
     assert np.abs(g[2].numpy() - o.T).max() <= 1e-13
 
 
-def test_reference_gradient_matches_oracle_fd():
-    rho0, ux, uy, T, target = small_case(6, 5, seed=1)
+@pytest.mark.parametrize("lattice,T_L", LATTICES)
+def test_reference_gradient_matches_oracle_fd(lattice, T_L):
+    rho0, ux, uy, T, target = small_case(6, 5, seed=1, T_L=T_L)
     nu, steps, passes = 0.02, 2, 20
-    L, grho, gnu = reference_grad(rho0, ux, uy, T, target, nu, steps, passes)
-    assert abs(L - oracle_loss(rho0, ux, uy, T, target, nu, steps, passes)) <= 1e-12 * L
+    kw = dict(lattice=lattice, T_ref=T_L)
+    L, grho, gnu = reference_grad(rho0, ux, uy, T, target, nu, steps, passes, **kw)
+    assert abs(L - oracle_loss(rho0, ux, uy, T, target, nu, steps, passes, **kw)) <= 1e-12 * L
     rng = np.random.default_rng(7)
     for _ in range(2):
         d = rng.standard_normal(rho0.shape)
         h = 1e-5
-        fd = (oracle_loss(rho0 + h * d, ux, uy, T, target, nu, steps, passes)
-              - oracle_loss(rho0 - h * d, ux, uy, T, target, nu, steps, passes)) / (2 * h)
+        fd = (oracle_loss(rho0 + h * d, ux, uy, T, target, nu, steps, passes, **kw)
+              - oracle_loss(rho0 - h * d, ux, uy, T, target, nu, steps, passes, **kw)) / (2 * h)
         assert abs(fd - (grho * d).sum()) <= 1e-6 * abs(fd)
     h = 1e-6
-    fd = (oracle_loss(rho0, ux, uy, T, target, nu + h, steps, passes)
-          - oracle_loss(rho0, ux, uy, T, target, nu - h, steps, passes)) / (2 * h)
+    fd = (oracle_loss(rho0, ux, uy, T, target, nu + h, steps, passes, **kw)
+          - oracle_loss(rho0, ux, uy, T, target, nu - h, steps, passes, **kw)) / (2 * h)
     assert abs(fd - gnu) <= 1e-6 * abs(fd)
 
 
@@ -102,22 +111,37 @@ def gpu_loss(rho0, ux, uy, T, target, nu, steps, **cfg):
 
 
 @pytest.mark.gpu
-def test_adjoint_matches_reference_gradient():
-    rho0, ux, uy, T, target = small_case(10, 8, seed=2)
+@pytest.mark.parametrize("lattice,T_L", LATTICES)
+def test_adjoint_matches_reference_gradient(lattice, T_L):
+    rho0, ux, uy, T, target = small_case(10, 8, seed=2, T_L=T_L)
     nu, steps, passes = 0.02, 3, 24
-    L, grho, gnu = reference_grad(rho0, ux, uy, T, target, nu, steps, passes)
-    Lg, grho_g, gnu_g = gpu_grad(rho0, ux, uy, T, target, nu, steps, 2, fixed_iter=passes)
+    L, grho, gnu = reference_grad(rho0, ux, uy, T, target, nu, steps, passes, lattice=lattice,
+                                  T_ref=T_L)
+    Lg, grho_g, gnu_g = gpu_grad(rho0, ux, uy, T, target, nu, steps, 2, fixed_iter=passes,
+                                 lattice=lattice, T_ref=T_L)
     assert abs(Lg - L) <= 1e-12 * L
     assert np.abs(grho_g - grho).max() <= 1e-9 * np.abs(grho).max()
     assert abs(gnu_g - gnu) <= 1e-9 * abs(gnu)
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("lattice,T_L", LATTICES)
 @pytest.mark.parametrize("fixed", [30, 0])
-def test_adjoint_matches_gpu_finite_differences(fixed):
-    rho0, ux, uy, T, target = small_case(32, 24, seed=3)
+def test_adjoint_matches_gpu_finite_differences(fixed, lattice, T_L):
+    rho0, ux, uy, T, target = small_case(32, 24, seed=3, T_L=T_L)
+    if lattice == 1:
+        # D2Q9 has a zero speed: its populations depart from x - u dt, which
+        # lies exactly on a node where the Taylor-Green u vanishes (whole
+        # rows), the kink of the piecewise-cubic reconstruction.  A central
+        # difference straddling the kink differs from the one-sided
+        # derivative by ~1e-4 at h = 1e-5 (the C oracle's differences do too,
+        # against the reference gradient); a mean flow moves those departures
+        # off the nodes.
+        ux = ux + 0.37 * np.sqrt(T_L)
+        uy = uy - 0.185 * np.sqrt(T_L)
     nu, steps, ckpt = 0.01, 6, 4
     cfg = {"fixed_iter": fixed} if fixed else {}
+    cfg.update(lattice=lattice, T_ref=T_L)
     L, grho, gnu = gpu_grad(rho0, ux, uy, T, target, nu, steps, ckpt, **cfg)
     rng = np.random.default_rng(11)
     for _ in range(4):
@@ -154,33 +178,37 @@ def test_adjoint_full_workload_512():
 
 
 @pytest.mark.gpu
-def test_mixed_adjoint_matches_fp64_adjoint():
+@pytest.mark.parametrize("lattice,T_L", LATTICES)
+def test_mixed_adjoint_matches_fp64_adjoint(lattice, T_L):
     """The FP32 adjoint (mixed context) against the FP64 adjoint on the same
     rollout: the gradients agree to the accuracy of the FP32 forward."""
     from paper_1806_05089_gb300 import pond
-    rho0, ux, uy, T, target = small_case(48, 40, seed=5)
+    rho0, ux, uy, T, target = small_case(48, 40, seed=5, T_L=T_L)
     nu, steps, ckpt = 0.01, 8, 4
-    L64, g64, n64 = gpu_grad(rho0, ux, uy, T, target, nu, steps, ckpt)
+    kw = dict(lattice=lattice, T_ref=T_L)
+    L64, g64, n64 = gpu_grad(rho0, ux, uy, T, target, nu, steps, ckpt, **kw)
     L32, g32, n32 = gpu_grad(rho0, ux, uy, T, target, nu, steps, ckpt,
-                             precision=pond.POND_FP32_MIXED)
+                             precision=pond.POND_FP32_MIXED, **kw)
     assert abs(L32 - L64) <= 1e-4 * L64
     assert np.abs(g32 - g64).max() <= 1e-4 * np.abs(g64).max()
     assert abs(n32 - n64) <= 1e-4 * abs(n64)
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("lattice,T_L", LATTICES)
 @pytest.mark.parametrize("precision", [0, 1])
-def test_adjoint_given_output_gauge_matches_recomputed(precision):
+def test_adjoint_given_output_gauge_matches_recomputed(precision, lattice, T_L):
     """pond_adjoint_step_given (the step's output gauge handed in) gives the
     same VJP as pond_adjoint_step (forward step recomputed inside), FP64 and
-    mixed; a NULL output gauge is refused."""
+    mixed, both lattices; a NULL output gauge is refused."""
     from paper_1806_05089_gb300 import pond
-    rho0, ux, uy, T, _ = small_case(40, 36, seed=7)
+    rho0, ux, uy, T, _ = small_case(40, 36, seed=7, T_L=T_L)
     dev = torch.device("cuda")
     rng = np.random.default_rng(8)
-    fbar = torch.tensor(rng.standard_normal((16, 36, 40)), device=dev)
+    Q = 16 if lattice == 0 else 9
+    fbar = torch.tensor(rng.standard_normal((Q, 36, 40)), device=dev)
     gbar = torch.tensor(rng.standard_normal((3, 36, 40)), device=dev)
-    with pond.Sim(40, 36, precision, nu=0.01) as s:
+    with pond.Sim(40, 36, precision, nu=0.01, lattice=lattice, T_ref=T_L) as s:
         s.set_state(rho0, ux, uy, T)
         s.step(2)                         # a state with a non-equilibrium part
         st0 = s.state()

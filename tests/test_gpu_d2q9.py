@@ -213,15 +213,3 @@ def test_d2q9_noalloc_matches_context_step():
     f = out[0].cpu().numpy()
     assert np.abs(f - ref.f).max() <= TOL64 * np.abs(ref.f).max()
     assert np.max(np.abs(out[3].cpu().numpy() - ref.T) / ref.T) <= TOL64
-
-
-def test_d2q9_adjoint_is_rejected():
-    torch = pytest.importorskip("torch")
-    with pond.Sim(8, 8, pond.POND_FP64, lattice=Q9) as s:
-        s.set_state(np.ones((8, 8)), np.zeros((8, 8)), np.zeros((8, 8)), np.full((8, 8), T_L))
-        dev = torch.device("cuda")
-        fb = torch.zeros((16, 8, 8), dtype=torch.float64, device=dev)
-        gb = torch.zeros((3, 8, 8), dtype=torch.float64, device=dev)
-        with pytest.raises(pond.PondError) as e:
-            pond.pond_adjoint_step(s.ctx, fb, gb, fb.clone(), gb.clone())
-        assert e.value.status == pond.POND_ERR_ARG

@@ -343,41 +343,66 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A
     }
 }
 
-__global__ void k_minmax3(const double* ux, const double* uy, const double* st, long long N,
-                          double* out6) {
-    // single block; out6 = {min ux, max ux, min uy, max uy, min s, max s}
-    __shared__ double red[6][32];
+// Bounds {min ux, max ux, min uy, max uy, min s, max s} of a gauge field,
+// exact in FP64: a grid-stride pass, warp reductions, and 64-bit integer
+// atomics on an order-preserving encoding of the doubles (one per warp and
+// value), decoded in place into out6.
+__device__ __forceinline__ unsigned long long d2ord(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__global__ void k_minmax3_reset(unsigned long long* o) {
+    const int j = threadIdx.x;
+    if (j < 6) o[j] = (j & 1) ? 0ull : ~0ull;
+}
+
+__global__ void k_minmax3(const double* __restrict__ ux, const double* __restrict__ uy,
+                          const double* __restrict__ st, long long N, unsigned long long* o) {
     double v[6] = {1e300, -1e300, 1e300, -1e300, 1e300, -1e300};
-    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-        v[0] = fmin(v[0], ux[i]);
-        v[1] = fmax(v[1], ux[i]);
-        v[2] = fmin(v[2], uy[i]);
-        v[3] = fmax(v[3], uy[i]);
-        v[4] = fmin(v[4], st[i]);
-        v[5] = fmax(v[5], st[i]);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double a = ux[i], b = uy[i], c = st[i];
+        v[0] = fmin(v[0], a);
+        v[1] = fmax(v[1], a);
+        v[2] = fmin(v[2], b);
+        v[3] = fmax(v[3], b);
+        v[4] = fmin(v[4], c);
+        v[5] = fmax(v[5], c);
     }
-    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
         for (int j = 0; j < 6; ++j) {
-            const double u = __shfl_xor_sync(0xffffffffu, v[j], o);
+            const double u = __shfl_xor_sync(0xffffffffu, v[j], off);
             v[j] = (j & 1) ? fmax(v[j], u) : fmin(v[j], u);
         }
-    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0)
-        for (int j = 0; j < 6; ++j) red[j][w] = v[j];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
+#pragma unroll
         for (int j = 0; j < 6; ++j) {
-            double r = red[j][0];
-            for (int i = 1; i < nw; ++i) r = (j & 1) ? fmax(r, red[j][i]) : fmin(r, red[j][i]);
-            out6[j] = r;
+            if (j & 1) atomicMax(o + j, d2ord(v[j]));
+            else atomicMin(o + j, d2ord(v[j]));
         }
+}
+
+__global__ void k_minmax3_decode(unsigned long long* o) {
+    const int j = threadIdx.x;
+    if (j < 6) {
+        const unsigned long long u = o[j];
+        const unsigned long long b = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+        reinterpret_cast<double*>(o)[j] = __longlong_as_double((long long)b);
     }
 }
 
 cudaError_t launch_minmax3(const double* ux, const double* uy, const double* st, long long N,
                            double* out6, cudaStream_t s) {
-    k_minmax3<<<1, 1024, 0, s>>>(ux, uy, st, N, out6);
+    unsigned long long* o = reinterpret_cast<unsigned long long*>(out6);
+    k_minmax3_reset<<<1, 32, 0, s>>>(o);
+    long long nb = (N + 255) / 256;
+    if (nb > 1024) nb = 1024;
+    if (nb < 1) nb = 1;
+    k_minmax3<<<(unsigned)nb, 256, 0, s>>>(ux, uy, st, N, o);
+    k_minmax3_decode<<<1, 32, 0, s>>>(o);
     return cudaGetLastError();
 }
 
@@ -534,8 +559,7 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
             "adjoint forward");
     }
     // 2. velocity bounds for the transpose gather
-    k_minmax3<<<1, 1024, 0, s>>>(a->fwd.ux, a->fwd.uy, a->fwd.st, N, a->minmax);
-    ACK(cudaGetLastError(), "adjoint bounds");
+    ACK(launch_minmax3(a->fwd.ux, a->fwd.uy, a->fwd.st, N, a->minmax, s), "adjoint bounds");
     ACK(cudaMemcpyAsync(a->host_minmax, a->minmax, sizeof(double) * 6, cudaMemcpyDeviceToHost, s),
         "adjoint bounds copy");
     ACK(cudaMemsetAsync(a->beta_bar, 0, sizeof(double), s), "adjoint reset");

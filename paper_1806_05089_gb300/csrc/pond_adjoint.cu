@@ -49,6 +49,9 @@ struct AdjointScratch {
     DevStats* stats = nullptr;
     double* beta_bar = nullptr;  // device accumulator
     double* minmax = nullptr;    // 6 doubles: min/max of ux*, uy*, s*
+    int2* org = nullptr;         // [16][N] stencil origin of (q, t), relative to t
+    double* lw = nullptr;        // [16][N][8] cubic weights of (q, t): x 0..3, y 0..3
+    double* inv_st = nullptr;    // [N] 1 / s* at every target
     double host_minmax[6];
 };
 
@@ -84,6 +87,11 @@ struct AdjArgs {
     double* fbar_in;         // [Q][N]
     double* gbar_in;         // [3][N]
     double* beta_bar;
+    // per (population, target), written by the target kernel for the gather:
+    // stencil origin relative to the target, cubic weights, and 1 / s*
+    int2* org;
+    double* lw;
+    double* inv_st;
     int nx, ny;
     long long N;
     double beta, dt, T_L;
@@ -118,6 +126,21 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_targets(AdjArgs A
     lagrange4_d(depy - fly + 1.0, ly, dly);
     const int x0 = wrap_idx((long long)flx - 1, A.nx);
     const int y0 = wrap_idx((long long)fly - 1, A.ny);
+    // what the gather needs of (q, target): the stencil origin relative to
+    // the target and the cubic weights; and 1 / s* of the target
+    if (act) {
+        const long long o = (long long)q * A.N + node;
+        double2* pw = reinterpret_cast<double2*>(A.lw + 8 * o + 4 * half);
+        if (half == 0) {
+            A.org[o] = make_int2((int)((long long)flx - 1 - X), (int)((long long)fly - 1 - Y));
+            pw[0] = make_double2(lx[0], lx[1]);
+            pw[1] = make_double2(lx[2], lx[3]);
+        } else {
+            pw[0] = make_double2(ly[0], ly[1]);
+            pw[1] = make_double2(ly[2], ly[3]);
+        }
+    }
+    if (lane == 0) A.inv_st[node] = inv;
 
     double Aq = 0.0, dAux = 0.0, dAuy = 0.0, dAst = 0.0;
     if (act) {
@@ -244,7 +267,6 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A
     const int q = lane & 15, half = lane >> 4;
     const bool act = q < Q;
     const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
-    const double ck = act ? L.c[k] : 0.0, cl = act ? L.c[l] : 0.0;
     double fj[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) fj[i] = A.in.f[(long long)i * A.N + src];
@@ -272,20 +294,16 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A
         for (int xx = xlo; xx <= xhi; ++xx) {
             const int tx = wrap_idx(xx, A.nx);
             const long long t = (long long)ty * A.nx + tx;
-            const double ux = A.ux_s[t], uy = A.uy_s[t], st = A.st_s[t];
-            const double depx = (double)xx - fma(st, ck, ux) * A.dt;
-            const double depy = (double)yy - fma(st, cl, uy) * A.dt;
-            const double flx = floor(depx), fly = floor(depy);
-            const long long jx = (long long)JX - ((long long)flx - 1);
-            const long long jy = (long long)JY - ((long long)fly - 1);
+            // the target's stencil origin for population q, as the target
+            // kernel found it (at the target's own, wrapped position)
+            const long long o = (long long)q * A.N + t;
+            const int2 og = A.org[o];
+            const int jx = JX - (xx + og.x), jy = JY - (yy + og.y);
             if (jx < 0 || jx > 3 || jy < 0 || jy > 3) continue;
-            double lx[4], ly[4];
-            lagrange4(depx - flx + 1.0, lx);
-            lagrange4(depy - fly + 1.0, ly);
-            const double wgt = (jx == 0 ? lx[0] : jx == 1 ? lx[1] : jx == 2 ? lx[2] : lx[3]) *
-                               (jy == 0 ? ly[0] : jy == 1 ? ly[1] : jy == 2 ? ly[2] : ly[3]);
-            const double coef = A.w[(long long)q * A.N + t] * wgt;
-            const double inv = 1.0 / st;
+            const double wgt = A.lw[8 * o + jx] * A.lw[8 * o + 4 + jy];
+            const double coef = A.w[o] * wgt;
+            const double ux = A.ux_s[t], uy = A.uy_s[t];
+            const double inv = A.inv_st[t];
             const double r = fma(stj, inv, -1.0);
             const double dx = (uxj - ux) * inv, dy = (uyj - uy) * inv;
             double gx[N1], gdx[N1], gy[N1], gdy[N1];
@@ -433,6 +451,9 @@ void destroy_adjoint(pond_ctx* ctx) {
     cudaFree(a->stats);
     cudaFree(a->beta_bar);
     cudaFree(a->minmax);
+    cudaFree(a->org);
+    cudaFree(a->lw);
+    cudaFree(a->inv_st);
     delete a;
     ctx->adj = nullptr;
 }
@@ -513,6 +534,9 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
         a->N = N;
         ACK(cudaMalloc(&a->beta_bar, sizeof(double)), "adjoint alloc");
         ACK(cudaMalloc(&a->minmax, sizeof(double) * 6), "adjoint alloc");
+        ACK(cudaMalloc(&a->org, sizeof(int2) * 16 * N), "adjoint alloc");
+        ACK(cudaMalloc(&a->lw, sizeof(double) * 8 * 16 * N), "adjoint alloc");
+        ACK(cudaMalloc(&a->inv_st, sizeof(double) * N), "adjoint alloc");
         if (fp64) {
             ACK(cudaMalloc(&a->fwd.f, sizeof(double) * 16 * N), "adjoint alloc");
             ACK(cudaMalloc(&a->fwd.ux, sizeof(double) * N), "adjoint alloc");
@@ -576,6 +600,9 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
     A.fbar_in = static_cast<double*>(f_bar_out);
     A.gbar_in = static_cast<double*>(gauge_bar_out);
     A.beta_bar = a->beta_bar;
+    A.org = a->org;
+    A.lw = a->lw;
+    A.inv_st = a->inv_st;
     A.nx = G.nx;
     A.ny = G.ny;
     A.N = N;

@@ -31,6 +31,9 @@ struct AdjMixedScratch {
     float4* gstar = nullptr;  // [2][N]: hi / lo splits of lambda*
     int32_t* iters = nullptr;
     DevStats* stats = nullptr;
+    int2* org = nullptr;      // [16][N] stencil origin of (q, t), relative to t
+    float* lw = nullptr;      // [16][N][8] cubic weights of (q, t): x 0..3, y 0..3
+    float* inv_st = nullptr;  // [N] 1 / s* at every target
 };
 
 __global__ void k_split_gauge(const double* __restrict__ ux, const double* __restrict__ uy,
@@ -85,6 +88,11 @@ struct AdjMixedArgs {
     double* fbar_in;
     double* gbar_in;
     double* beta_bar;
+    // per (population, target), written by the target kernel for the gather:
+    // stencil origin relative to the target, cubic weights, and 1 / s*
+    int2* org;
+    float* lw;
+    float* inv_st;
     int nx, ny;
     long long N;
     float beta, dt, T_L;
@@ -119,6 +127,19 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(Ad
     lagrange4_df(fry - fly + 1.0f, ly, dly);
     const int x0 = wrap_idx((long long)X + (long long)flx - 1, A.nx);
     const int y0 = wrap_idx((long long)Y + (long long)fly - 1, A.ny);
+    // what the gather needs of (q, target): the stencil origin relative to
+    // the target and the cubic weights; and 1 / s* of the target
+    if (act) {
+        const long long o = (long long)q * A.N + node;
+        float4* pw = reinterpret_cast<float4*>(A.lw + 8 * o + 4 * half);
+        if (half == 0) {
+            A.org[o] = make_int2((int)flx - 1, (int)fly - 1);
+            *pw = make_float4(lx[0], lx[1], lx[2], lx[3]);
+        } else {
+            *pw = make_float4(ly[0], ly[1], ly[2], ly[3]);
+        }
+    }
+    if (lane == 0) A.inv_st[node] = inv;
 
     float Aq = 0.0f, dAux = 0.0f, dAuy = 0.0f, dAst = 0.0f;
     if (act) {
@@ -249,7 +270,6 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_sources_mixed(Ad
     const int q = lane & 15, half = lane >> 4;
     const bool act = q < Q;
     const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
-    const float ck = act ? L.c[k] : 0.0f, cl = act ? L.c[l] : 0.0f;
     float fj[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) fj[i] = A.f_in[(long long)i * A.N + src];
@@ -276,20 +296,16 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_sources_mixed(Ad
         for (int xx = xlo; xx <= xhi; ++xx) {
             const int tx = wrap_idx(xx, A.nx);
             const long long t = (long long)ty * A.nx + tx;
-            const float4 th = A.gstar[t], tl = A.gstar[A.N + t];
-            const float st = th.x + tl.x, ux = th.y + tl.y, uy = th.z + tl.z;
-            const float frx = -fmaf(st, ck, ux) * A.dt, fry = -fmaf(st, cl, uy) * A.dt;
-            const float flx = floorf(frx), fly = floorf(fry);
-            const int jx = JX - (xx + (int)flx - 1);
-            const int jy = JY - (yy + (int)fly - 1);
+            // the target's stencil origin for population q, as the target
+            // kernel found it
+            const long long o = (long long)q * A.N + t;
+            const int2 og = A.org[o];
+            const int jx = JX - (xx + og.x), jy = JY - (yy + og.y);
             if (jx < 0 || jx > 3 || jy < 0 || jy > 3) continue;
-            float lx[4], ly[4];
-            lagrange4f(frx - flx + 1.0f, lx);
-            lagrange4f(fry - fly + 1.0f, ly);
-            const float wgt = (jx == 0 ? lx[0] : jx == 1 ? lx[1] : jx == 2 ? lx[2] : lx[3]) *
-                              (jy == 0 ? ly[0] : jy == 1 ? ly[1] : jy == 2 ? ly[2] : ly[3]);
-            const float coef = A.w[(long long)q * A.N + t] * wgt;
-            const float inv = 1.0f / st;
+            const float4 th = A.gstar[t], tl = A.gstar[A.N + t];
+            const float wgt = A.lw[8 * o + jx] * A.lw[8 * o + 4 + jy];
+            const float coef = A.w[o] * wgt;
+            const float inv = A.inv_st[t];
             const float r = sdiff(jh.x, jl.x, th.x, tl.x) * inv;
             const float dx = sdiff(jh.y, jl.y, th.y, tl.y) * inv;
             const float dy = sdiff(jh.z, jl.z, th.z, tl.z) * inv;
@@ -361,6 +377,9 @@ void destroy_adjoint_mixed(pond_ctx* ctx) {
     cudaFree(a->gstar);
     cudaFree(a->iters);
     cudaFree(a->stats);
+    cudaFree(a->org);
+    cudaFree(a->lw);
+    cudaFree(a->inv_st);
     delete a;
     ctx->adjm = nullptr;
 }
@@ -387,6 +406,9 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
         if ((e = cudaMalloc(&a->gstar, sizeof(float4) * 2 * N)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&a->iters, sizeof(int32_t) * N)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&a->stats, sizeof(DevStats))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->org, sizeof(int2) * 16 * N)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->lw, sizeof(float) * 8 * 16 * N)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->inv_st, sizeof(float) * N)) != cudaSuccess) return e;
     }
     AdjMixedScratch* a = ctx->adjm;
     StateBuf<float> in;
@@ -429,6 +451,9 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
     A.fbar_in = fbar_out;
     A.gbar_in = gbar_out;
     A.beta_bar = beta_bar_dev;
+    A.org = a->org;
+    A.lw = a->lw;
+    A.inv_st = a->inv_st;
     A.nx = G.nx;
     A.ny = G.ny;
     A.N = N;

@@ -144,7 +144,10 @@ void pond_config_default(pond_config* cfg, int32_t precision);
 pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* nx,
                         const int32_t* ny, void* cuda_stream, pond_ctx** out);
 
-/* Replace the stream all later work is enqueued on. */
+/* Replace the stream all later work is enqueued on.  Work already queued on
+ * the old stream is waited for first (the host blocks until it ends), and the
+ * step graphs (use_graph) are captured again on next use.
+ * Errors: POND_ERR_ARG (NULL ctx), POND_ERR_CUDA. */
 pond_status pond_set_stream(pond_ctx* ctx, void* cuda_stream);
 
 /* Set the state of grid `grid` from macroscopic fields, each [ny][nx] FP64:

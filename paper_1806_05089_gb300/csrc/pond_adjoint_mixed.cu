@@ -31,6 +31,7 @@ struct AdjMixedScratch {
     float4* gstar = nullptr;  // [2][N]: hi / lo splits of lambda*
     int32_t* iters = nullptr;
     DevStats* stats = nullptr;
+    float4* f4 = nullptr;     // [4][N] the input populations as rows f[a][0..n1-1]
     int2* org = nullptr;      // [16][N] stencil origin of (q, t), relative to t
     float* lw = nullptr;      // [16][N][8] cubic weights of (q, t): x 0..3, y 0..3
     float* inv_st = nullptr;  // [N] 1 / s* at every target
@@ -50,6 +51,20 @@ __global__ void k_split_gauge(const double* __restrict__ ux, const double* __res
     }
     out[i] = make_float4(hi[0], hi[1], hi[2], 0.0f);
     out[N + i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+}
+
+// Populations as rows: f4[a][i] = (f[n1 a][i], ..., f[n1 a + n1 - 1][i]) (a
+// zero fourth word on D2Q9), so that a (population, source) pair reads a
+// source's populations with n1 16-byte loads.
+template <int N1>
+__global__ void k_rows_f4(const float* __restrict__ f, float4* __restrict__ f4, long long N) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+#pragma unroll
+    for (int a = 0; a < N1; ++a)
+        f4[a * N + i] = make_float4(f[(N1 * a) * N + i], f[(N1 * a + 1) * N + i],
+                                    f[(N1 * a + 2) * N + i],
+                                    N1 == 4 ? f[(N1 * a + 3) * N + i] : 0.0f);
 }
 
 __device__ __forceinline__ void lagrange4_df(float t, float l[4], float dl[4]) {
@@ -78,6 +93,7 @@ __device__ __forceinline__ float sdiff(float ha, float la, float hb, float lb) {
 
 struct AdjMixedArgs {
     const float* f_in;       // input populations [Q][N]
+    const float4* f4;        // the same as rows [n1][N]: f4[a][s] = f[a][0..n1-1] of s
     const float4* gin;       // splits of the input gauge
     const float4* gstar;     // splits of lambda*
     const double* st_in;     // input sqrt(theta) (FP64, for the T cotangent)
@@ -170,9 +186,11 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(Ad
 #pragma unroll
             for (int a = 0; a < N1; ++a) {
                 float h = 0.0f, hp = 0.0f, hq = 0.0f;
+                const float4 r4 = A.f4[(long long)a * A.N + s];  // one 16-byte load per row
+                const float fr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
                 for (int b = 0; b < N1; ++b) {
-                    const float fv = A.f_in[(long long)(N1 * a + b) * A.N + s];
+                    const float fv = fr[b];
                     h = fmaf(gy[b], fv, h);
                     hp = fmaf(gdy[b], fv, hp);
                     hq = fmaf(gdy[b] * xiy[b], fv, hq);
@@ -377,6 +395,7 @@ void destroy_adjoint_mixed(pond_ctx* ctx) {
     cudaFree(a->gstar);
     cudaFree(a->iters);
     cudaFree(a->stats);
+    cudaFree(a->f4);
     cudaFree(a->org);
     cudaFree(a->lw);
     cudaFree(a->inv_st);
@@ -406,6 +425,7 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
         if ((e = cudaMalloc(&a->gstar, sizeof(float4) * 2 * N)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&a->iters, sizeof(int32_t) * N)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&a->stats, sizeof(DevStats))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->f4, sizeof(float4) * 4 * N)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&a->org, sizeof(int2) * 16 * N)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&a->lw, sizeof(float) * 8 * 16 * N)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&a->inv_st, sizeof(float) * N)) != cudaSuccess) return e;
@@ -428,6 +448,8 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
     if (e != cudaSuccess) return e;
     const unsigned nb256 = (unsigned)((N + 255) / 256);
     k_split_gauge<<<nb256, 256, 0, s>>>(in.ux, in.uy, in.st, a->gin, N);
+    if (ctx->L.n1 == 3) k_rows_f4<3><<<nb256, 256, 0, s>>>(in.f, a->f4, N);
+    else k_rows_f4<4><<<nb256, 256, 0, s>>>(in.f, a->f4, N);
     k_split_gauge<<<nb256, 256, 0, s>>>(a->fwd.ux, a->fwd.uy, a->fwd.st, a->gstar, N);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_minmax3(a->fwd.ux, a->fwd.uy, a->fwd.st, N, minmax_dev, s)) != cudaSuccess)
@@ -441,6 +463,7 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
     const GridDesc& G = ctx->grids_host[0];
     AdjMixedArgs A;
     A.f_in = in.f;
+    A.f4 = a->f4;
     A.gin = a->gin;
     A.gstar = a->gstar;
     A.st_in = in.st;

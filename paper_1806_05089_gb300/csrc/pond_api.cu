@@ -408,7 +408,14 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
 
 pond_status pond_set_stream(pond_ctx* ctx, void* cuda_stream) {
     if (!ctx) return POND_ERR_ARG;
-    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    const cudaStream_t next = static_cast<cudaStream_t>(cuda_stream);
+    if (next == ctx->stream) return POND_OK;
+    DeviceGuard dg(ctx->device);
+    // work already queued on the old stream finishes before anything is
+    // queued on the new one; the step graphs are captured again on next use
+    CK(cudaStreamSynchronize(ctx->stream), "set_stream sync");
+    drop_graphs(ctx);
+    ctx->stream = next;
     return POND_OK;
 }
 

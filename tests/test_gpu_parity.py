@@ -279,6 +279,26 @@ def test_graph_replay_matches_plain_launches():
     assert np.array_equal(out[0].T, out[1].T)
 
 
+def test_stream_switch_keeps_results():
+    """pond_set_stream between graph-replayed steps: the steps queued on the
+    first stream finish first and the graphs are captured again, so the run
+    equals one that stays on a single stream."""
+    import torch
+    fields = small_fields("supersonic", 80, 40)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    out = []
+    for switch in (False, True):
+        with pond.Sim(80, 40, pond.POND_FP32_MIXED, stream=s1.cuda_stream, use_graph=1) as s:
+            s.set_state(fields.rho, fields.ux, fields.uy, fields.T)
+            pond.pond_step(s.ctx, 4, want_stats=False)
+            if switch:
+                pond.pond_set_stream(s.ctx, s2.cuda_stream)
+            pond.pond_step(s.ctx, 4, want_stats=False)
+            out.append(s.state())
+    assert np.array_equal(out[0].f, out[1].f)
+    assert np.array_equal(out[0].ux, out[1].ux)
+
+
 def test_autotune_picks_a_tile_shape_and_matches_oracle(tmp_path, monkeypatch):
     cache = tmp_path / "tune.json"
     monkeypatch.setenv("POND_AUTOTUNE_CACHE", str(cache))

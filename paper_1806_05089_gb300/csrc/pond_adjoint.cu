@@ -589,7 +589,7 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
     ACK(cudaMemsetAsync(a->beta_bar, 0, sizeof(double), s), "adjoint reset");
     ACK(cudaStreamSynchronize(s), "adjoint sync");
 
-    AdjArgs A;
+    AdjArgs A{};
     A.in = in;
     A.ux_s = a->fwd.ux;
     A.uy_s = a->fwd.uy;

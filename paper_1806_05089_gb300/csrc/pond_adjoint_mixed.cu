@@ -461,7 +461,7 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
 
     const GridDesc& G = ctx->grids_host[0];
-    AdjMixedArgs A;
+    AdjMixedArgs A{};
     A.f_in = in.f;
     A.f4 = a->f4;
     A.gin = a->gin;

@@ -231,4 +231,6 @@ def test_adjoint_given_output_gauge_matches_recomputed(precision, lattice, T_L):
     (f_a, g_a, n_a), (f_b, g_b, n_b) = outs
     assert np.abs(f_a - f_b).max() <= 1e-14 * np.abs(f_a).max()
     assert np.abs(g_a - g_b).max() <= 1e-14 * np.abs(g_a).max()
-    assert abs(n_a - n_b) <= 1e-14 * abs(n_a)
+    # nu_bar is a sum of per-node double atomics whose order varies from run
+    # to run: equal to rounding of that sum
+    assert abs(n_a - n_b) <= 1e-12 * abs(n_a)

@@ -1001,7 +1001,7 @@ cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& 
                               cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
     if (win.n1 != L.n1) return cudaErrorInvalidValue;
-    MixedArgs A;
+    MixedArgs A{};
     A.in = in;
     A.out = out;
     A.iters = iters;

@@ -145,3 +145,28 @@ def test_taylor_green_converges_at_second_order(lattice, T_L):
     assert all(a > b for a, b in zip(errs, errs[1:])), errs
     order = -np.polyfit(np.log(Ls), np.log(errs), 1)[0]
     assert order >= g["order"] - 0.1, (order, errs)
+
+
+@pytest.mark.parametrize("lattice,T_L", [(pond.POND_D2Q16, 1.0), (pond.POND_D2Q9, 1 / 3)])
+def test_taylor_green_decay_rate_long_run(lattice, T_L):
+    """App. D / configuration 1 run long: 64^2 Taylor-Green (u0 = 0.05 sqrt(T),
+    nu = 0.01), 2000 steps.  The fitted decay rate of u lies within 3 % of
+    2 nu k^2 (the oracle's 100-step pin allows 5 %).  Measured: D2Q16 2.3 %
+    faster, D2Q9 under 2 %; the excess is the cubic reconstruction's
+    numerical damping, the same effect the convergence test measures."""
+    from paper_1806_05089_gb300 import workloads
+    n, nu, steps, every = 64, 0.01, 2000, 100
+    tg = workloads.taylor_green(n, n, 0.05)
+    ux, uy = tg.ux * np.sqrt(T_L), tg.uy * np.sqrt(T_L)
+    basis = ux / np.abs(ux).max()
+    amps = []
+    with pond.Sim(n, n, pond.POND_FP64, lattice=lattice, T_ref=T_L, nu=nu) as s:
+        s.set_state(tg.rho, ux, uy, tg.T * T_L)
+        for _ in range(steps // every):
+            stats = s.step(every)
+            assert stats["nonphysical"] == 0 and stats["nonconverged"] == 0
+            amps.append((s.moments()[1] * basis).sum() / (basis * basis).sum())
+    t = every * np.arange(1, len(amps) + 1)
+    rate = -np.polyfit(t[1:], np.log(np.array(amps)[1:]), 1)[0]
+    k = 2 * np.pi / n
+    assert abs(rate / (2 * nu * k * k) - 1) < 0.03, rate / (2 * nu * k * k)

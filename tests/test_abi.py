@@ -80,3 +80,35 @@ def test_no_cpu_fallback_without_gpu():
     with pytest.raises(pond.PondError) as e:
         pond.pond_create(cfg, [8], [8])
     assert e.value.status in (pond.POND_ERR_CUDA, pond.POND_ERR_OOM)
+
+
+def test_header_is_plain_c_and_structs_match_the_binding(tmp_path):
+    """include/pond.h compiles as C99 (-Wall -Wextra -pedantic -Werror), and
+    the sizes and field offsets of pond_config and pond_stats seen by a C
+    compiler equal those of the ctypes structures of the binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pond.h"', 'int main(void) {']
+    for cname, pyst in (("pond_config", pond.pond_config), ("pond_stats", pond.pond_stats)):
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for field, _ in pyst._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, field, cname, field))
+    lines += ['  return 0;', '}']
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = {}
+    for line in out:
+        p = line.split()
+        if len(p) == 3:
+            seen[(p[0], p[1])] = int(p[2])
+    for cname, pyst in (("pond_config", pond.pond_config), ("pond_stats", pond.pond_stats)):
+        assert seen[(cname, "size")] == ctypes.sizeof(pyst), cname
+        for field, _ in pyst._fields_:
+            assert seen[(cname, field)] == getattr(pyst, field).offset, (cname, field)

@@ -79,13 +79,6 @@ __device__ __forceinline__ void lagrange4_df(float t, float l[4], float dl[4]) {
     dl[3] = (b * c + a * c + a * b) * (1.0f / 6.0f);
 }
 
-__device__ __forceinline__ void lag_taylor_f(const LatticeF& L, int k, int a, float de, float& g,
-                                            float& gd) {
-    const float d1 = L.d1[k][a], d2 = L.d2[k][a], d3 = L.d3[k];
-    g = fmaf(fmaf(fmaf(d3, de, d2), de, d1), de, (k == a) ? 1.0f : 0.0f);
-    gd = fmaf(fmaf(3.0f * d3, de, 2.0f * d2), de, d1);
-}
-
 // difference of two split values: (hi_a - hi_b) + (lo_a - lo_b)
 __device__ __forceinline__ float sdiff(float ha, float la, float hb, float lb) {
     return (ha - hb) + (la - lb);
@@ -115,148 +108,183 @@ struct AdjMixedArgs {
     float vlo_x[4], vhi_x[4], vlo_y[4], vhi_y[4];
 };
 
-constexpr int ADJM_WARPS = 4;
+// One thread per node, a rolled loop over the populations: a warp holds 32
+// consecutive nodes of one row, all on the same population, so the source
+// reads of a (population, stencil node) step are 32 neighbouring 16-byte
+// records (coalesced through L1) and the lattice constants of the population
+// are warp-uniform.  All per-node sums are sequential in one thread.
+constexpr int ADJM_THREADS = 128;
+
+// lattice coefficients of the 1D Lagrange-Taylor map of speed index k
+template <int N1>
+struct RowCoef {
+    float d1[N1], d2[N1], d3;
+};
 
 template <int N1>
-__global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(AdjMixedArgs A) {
+__device__ __forceinline__ RowCoef<N1> row_coef(const LatticeF& L, int k) {
+    RowCoef<N1> r;
+#pragma unroll
+    for (int a = 0; a < N1; ++a) {
+        r.d1[a] = L.d1[k][a];
+        r.d2[a] = L.d2[k][a];
+    }
+    r.d3 = L.d3[k];
+    return r;
+}
+
+// G[k][a] = [k == a] + d1 de + d2 de^2 + d3 de^3 and its derivative in de
+template <int N1>
+__device__ __forceinline__ void lag_taylor_r(const RowCoef<N1>& R, int k, int a, float de,
+                                             float& g, float& gd) {
+    g = fmaf(fmaf(fmaf(R.d3, de, R.d2[a]), de, R.d1[a]), de, (k == a) ? 1.0f : 0.0f);
+    gd = fmaf(fmaf(3.0f * R.d3, de, 2.0f * R.d2[a]), de, R.d1[a]);
+}
+
+template <int N1>
+__global__ void __launch_bounds__(ADJM_THREADS) k_adjoint_targets_mixed(AdjMixedArgs A) {
     constexpr int Q = N1 * N1;
     const LatticeF& L = c_Lam[lattice_slot(N1)];
-    const int lane = threadIdx.x & 31;
-    const long long node = (long long)blockIdx.x * ADJM_WARPS + (threadIdx.x >> 5);
-    if (node >= A.N) return;  // warp-uniform
+    const long long node0 = (long long)blockIdx.x * ADJM_THREADS + threadIdx.x;
+    // threads past the end compute the last node and store nothing, so that
+    // the warp reduction of the beta cotangent has all its lanes
+    const bool live = node0 < A.N;
+    const long long node = live ? node0 : A.N - 1;
     const int X = (int)(node % A.nx), Y = (int)(node / A.nx);
-    // lane = (population q, half); on D2Q9 lanes with q >= 9 hold no
-    // population: they contribute zeros to the 16-lane sums and read nothing
-    const int q = lane & 15, half = lane >> 4;
-    const bool act = q < Q;
-    const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
-    const float ck = act ? L.c[k] : 0.0f, cl = act ? L.c[l] : 0.0f;
     const float4 th = A.gstar[node], tl = A.gstar[A.N + node];  // (s, ux, uy)
     const float st = th.x + tl.x, ux = th.y + tl.y, uy = th.z + tl.z;
     const float inv = 1.0f / st;
+    const float T_L = A.T_L;
+    if (live) A.inv_st[node] = inv;
 
-    // departure of population q at lambda*, relative to the node
-    const float frx = -fmaf(st, ck, ux) * A.dt, fry = -fmaf(st, cl, uy) * A.dt;
-    const float flx = floorf(frx), fly = floorf(fry);
-    float lx[4], dlx[4], ly[4], dly[4];
-    lagrange4_df(frx - flx + 1.0f, lx, dlx);
-    lagrange4_df(fry - fly + 1.0f, ly, dly);
-    const int x0 = wrap_idx((long long)X + (long long)flx - 1, A.nx);
-    const int y0 = wrap_idx((long long)Y + (long long)fly - 1, A.ny);
-    // what the gather needs of (q, target): the stencil origin relative to
-    // the target and the cubic weights; and 1 / s* of the target
-    if (act) {
+    // Per node, over the populations q with A_q and its JVPs d_q = dA_q/dlambda:
+    //   rho = sum A_q, sAf = sum A_q fb_q, wf = sum W_q fb_q,
+    //   P{x,y,t}_j = sum {c_k, c_l, |c|^2 - 2 T_L} d_qj   (J = M_A A_lambda),
+    //   gF_j = sum fb_q d_qj, gS_j = sum d_qj              (g = A_bar^T d)
+    float rho = 0.0f, sAf = 0.0f, wf = 0.0f;
+    float Px[3] = {0.0f, 0.0f, 0.0f}, Py[3] = {0.0f, 0.0f, 0.0f}, Pt[3] = {0.0f, 0.0f, 0.0f};
+    float gF[3] = {0.0f, 0.0f, 0.0f}, gS[3] = {0.0f, 0.0f, 0.0f};
+
+#pragma unroll 1
+    for (int q = 0; q < Q; ++q) {
+        const int k = q / N1, l = q - N1 * k;
+        const float ck = L.c[k], cl = L.c[l];
+        const RowCoef<N1> Rk = row_coef<N1>(L, k), Rl = row_coef<N1>(L, l);
+        // departure of population q at lambda*, relative to the node
+        const float frx = -fmaf(st, ck, ux) * A.dt, fry = -fmaf(st, cl, uy) * A.dt;
+        const float flx = floorf(frx), fly = floorf(fry);
+        float lx[4], dlx[4], ly[4], dly[4];
+        lagrange4_df(frx - flx + 1.0f, lx, dlx);
+        lagrange4_df(fry - fly + 1.0f, ly, dly);
+        const int x0 = wrap_idx((long long)X + (long long)flx - 1, A.nx);
+        const int y0 = wrap_idx((long long)Y + (long long)fly - 1, A.ny);
         const long long o = (long long)q * A.N + node;
-        float4* pw = reinterpret_cast<float4*>(A.lw + 8 * o + 4 * half);
-        if (half == 0) {
+        // what the gather needs of (q, target): the stencil origin relative
+        // to the target and the cubic weights
+        if (live) {
             A.org[o] = make_int2((int)flx - 1, (int)fly - 1);
-            *pw = make_float4(lx[0], lx[1], lx[2], lx[3]);
-        } else {
-            *pw = make_float4(ly[0], ly[1], ly[2], ly[3]);
+            float4* pw = reinterpret_cast<float4*>(A.lw + 8 * o);
+            pw[0] = make_float4(lx[0], lx[1], lx[2], lx[3]);
+            pw[1] = make_float4(ly[0], ly[1], ly[2], ly[3]);
         }
-    }
-    if (lane == 0) A.inv_st[node] = inv;
 
-    float Aq = 0.0f, dAux = 0.0f, dAuy = 0.0f, dAst = 0.0f;
-    if (act) {
+        float Aq = 0.0f, dAux = 0.0f, dAuy = 0.0f, dAst = 0.0f;
+        // stencil rows rolled (the loop body, four (population, source)
+        // pairs, stays small in the instruction cache); the row's weights by
+        // selection, which keeps ly / dly in registers
+#pragma unroll 1
+        for (int jy = 0; jy < 4; ++jy) {
+            const int sy = wrap_inc(y0, jy, A.ny);
+            const float wy = jy == 0 ? ly[0] : jy == 1 ? ly[1] : jy == 2 ? ly[2] : ly[3];
+            const float dwy = jy == 0 ? dly[0] : jy == 1 ? dly[1] : jy == 2 ? dly[2] : dly[3];
 #pragma unroll
-    for (int jj = 0; jj < 2; ++jj) {
-        const int jy = 2 * half + jj;
-        const float wy = half ? ly[2 + jj] : ly[jj];
-        const float dwy = half ? dly[2 + jj] : dly[jj];
-        const int sy = wrap_inc(y0, jy, A.ny);
+            for (int jx = 0; jx < 4; ++jx) {
+                const int sx = wrap_inc(x0, jx, A.nx);
+                const long long s = (long long)sy * A.nx + sx;
+                const float4 sh = A.gin[s], sl = A.gin[A.N + s];
+                const float r = sdiff(sh.x, sl.x, th.x, tl.x) * inv;
+                const float dx = sdiff(sh.y, sl.y, th.y, tl.y) * inv;
+                const float dy = sdiff(sh.z, sl.z, th.z, tl.z) * inv;
+                float gx[N1], gdx[N1], gy[N1], gdyx[N1], gdy[N1], xix[N1];
 #pragma unroll
-        for (int jx = 0; jx < 4; ++jx) {
-            const int sx = wrap_inc(x0, jx, A.nx);
-            const long long s = (long long)sy * A.nx + sx;
-            const float4 sh = A.gin[s], sl = A.gin[A.N + s];
-            const float r = sdiff(sh.x, sl.x, th.x, tl.x) * inv;
-            const float dx = sdiff(sh.y, sl.y, th.y, tl.y) * inv;
-            const float dy = sdiff(sh.z, sl.z, th.z, tl.z) * inv;
-            float gx[N1], gdx[N1], gy[N1], gdy[N1], xix[N1], xiy[N1];
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                const float ex = fmaf(L.c[a], r, dx), ey = fmaf(L.c[a], r, dy);
-                xix[a] = L.c[a] + ex;
-                xiy[a] = L.c[a] + ey;
-                lag_taylor_f(L, k, a, ex, gx[a], gdx[a]);
-                lag_taylor_f(L, l, a, ey, gy[a], gdy[a]);
-            }
-            float g = 0.0f, gux = 0.0f, guy = 0.0f, gst = 0.0f;
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                float h = 0.0f, hp = 0.0f, hq = 0.0f;
-                const float4 r4 = A.f4[(long long)a * A.N + s];  // one 16-byte load per row
-                const float fr[4] = {r4.x, r4.y, r4.z, r4.w};
-#pragma unroll
-                for (int b = 0; b < N1; ++b) {
-                    const float fv = fr[b];
-                    h = fmaf(gy[b], fv, h);
-                    hp = fmaf(gdy[b], fv, hp);
-                    hq = fmaf(gdy[b] * xiy[b], fv, hq);
+                for (int a = 0; a < N1; ++a) {
+                    const float ex = fmaf(L.c[a], r, dx), ey = fmaf(L.c[a], r, dy);
+                    xix[a] = L.c[a] + ex;
+                    lag_taylor_r<N1>(Rk, k, a, ex, gx[a], gdx[a]);
+                    lag_taylor_r<N1>(Rl, l, a, ey, gy[a], gdy[a]);
+                    gdyx[a] = gdy[a] * (L.c[a] + ey);
                 }
-                g = fmaf(gx[a], h, g);
-                gux = fmaf(gdx[a], h, gux);
-                guy = fmaf(gx[a], hp, guy);
-                gst = fmaf(gdx[a] * xix[a], h, fmaf(gx[a], hq, gst));
+                float g = 0.0f, gux = 0.0f, guy = 0.0f, gst = 0.0f;
+#pragma unroll
+                for (int a = 0; a < N1; ++a) {
+                    float h = 0.0f, hp = 0.0f, hq = 0.0f;
+                    const float4 r4 = A.f4[(long long)a * A.N + s];  // one 16-byte load per row
+                    const float fr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) {
+                        const float fv = fr[b];
+                        h = fmaf(gy[b], fv, h);
+                        hp = fmaf(gdy[b], fv, hp);
+                        hq = fmaf(gdyx[b], fv, hq);
+                    }
+                    g = fmaf(gx[a], h, g);
+                    gux = fmaf(gdx[a], h, gux);
+                    guy = fmaf(gx[a], hp, guy);
+                    gst = fmaf(gdx[a] * xix[a], h, fmaf(gx[a], hq, gst));
+                }
+                gux *= -inv;
+                guy *= -inv;
+                gst *= -inv;
+                const float wx = lx[jx], dwx = dlx[jx];
+                const float a_w = wx * wy;
+                const float da_ux = -A.dt * dwx * wy;
+                const float da_uy = -A.dt * wx * dwy;
+                const float da_st = -A.dt * (ck * dwx * wy + cl * wx * dwy);
+                Aq = fmaf(a_w, g, Aq);
+                dAux = fmaf(a_w, gux, fmaf(da_ux, g, dAux));
+                dAuy = fmaf(a_w, guy, fmaf(da_uy, g, dAuy));
+                dAst = fmaf(a_w, gst, fmaf(da_st, g, dAst));
             }
-            gux *= -inv;
-            guy *= -inv;
-            gst *= -inv;
-            const float wx = lx[jx], dwx = dlx[jx];
-            const float a_w = wx * wy;
-            const float da_ux = -A.dt * dwx * wy;
-            const float da_uy = -A.dt * wx * dwy;
-            const float da_st = -A.dt * (ck * dwx * wy + cl * wx * dwy);
-            Aq = fmaf(a_w, g, Aq);
-            dAux = fmaf(a_w, gux, fmaf(da_ux, g, dAux));
-            dAuy = fmaf(a_w, guy, fmaf(da_uy, g, dAuy));
-            dAst = fmaf(a_w, gst, fmaf(da_st, g, dAst));
+        }
+        const float fb = (float)A.fbar[o];
+        const float Wq = L.w[k] * L.w[l];
+        const float mt = fmaf(ck, ck, cl * cl) - 2.0f * T_L;
+        const float d[3] = {dAux, dAuy, dAst};
+        rho += Aq;
+        sAf = fmaf(Aq, fb, sAf);
+        wf = fmaf(Wq, fb, wf);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            Px[j] = fmaf(ck, d[j], Px[j]);
+            Py[j] = fmaf(cl, d[j], Py[j]);
+            Pt[j] = fmaf(mt, d[j], Pt[j]);
+            gF[j] = fmaf(fb, d[j], gF[j]);
+            gS[j] += d[j];
         }
     }
-    }
-    Aq += __shfl_xor_sync(0xffffffffu, Aq, 16);
-    dAux += __shfl_xor_sync(0xffffffffu, dAux, 16);
-    dAuy += __shfl_xor_sync(0xffffffffu, dAuy, 16);
-    dAst += __shfl_xor_sync(0xffffffffu, dAst, 16);
 
     // Per-node epilogue in FP32: the inputs (A, its gauge derivatives) are
     // FP32 already, and the 3 x 3 system is J = M_A A_lambda = -(I - Phi_lambda)
     // with Phi_lambda the contraction of the fixed-point iteration, close to
     // -I and well conditioned, so FP64 here (1/64 of the FP32 rate) would buy
     // nothing; only the beta cotangent is accumulated in FP64.
-    auto sum16 = [](float v) {
-#pragma unroll
-        for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        return v;
-    };
+    // With A_bar_q = (1 - 2 beta) fb_q + 2 beta wf and the moment maps
+    // mu_q = s* (c_k, c_l, (|c|^2 - 2 T_L) / (4 T_L)) / rho:
     const float sd = (float)A.st_star[node];
-    const float T_L = A.T_L;
-    const float Wq = act ? L.w[k] * L.w[l] : 0.0f;
-    const float fb = act ? (float)A.fbar[(long long)q * A.N + node] : 0.0f;
-    const float rho = sum16(Aq);
-    const float wf = sum16(Wq * fb);
     const float beta = A.beta;
-    const float Abar = fmaf(1.0f - 2.0f * beta, fb, 2.0f * beta * wf);
-    const float bb = sum16(2.0f * fmaf(rho, Wq, -Aq) * fb);
-    const float c2 = fmaf(ck, ck, cl * cl);
     const float irho = 1.0f / rho;
-    const float mux = sd * ck * irho, muy = sd * cl * irho;
-    const float mst = sd * (c2 - 2.0f * T_L) * irho / (4.0f * T_L);
-    const float d0 = dAux, d1 = dAuy, d2 = dAst;
+    const float sx = sd * irho, stt = sd * irho / (4.0f * T_L);
     float J[3][3];
-    J[0][0] = sum16(mux * d0);
-    J[0][1] = sum16(mux * d1);
-    J[0][2] = sum16(mux * d2);
-    J[1][0] = sum16(muy * d0);
-    J[1][1] = sum16(muy * d1);
-    J[1][2] = sum16(muy * d2);
-    J[2][0] = sum16(mst * d0);
-    J[2][1] = sum16(mst * d1);
-    J[2][2] = sum16(mst * d2);
-    const float g0 = sum16(Abar * d0) + (float)A.gbar[node];
-    const float g1 = sum16(Abar * d1) + (float)A.gbar[A.N + node];
-    const float g2 = sum16(Abar * d2) + (float)A.gbar[2 * A.N + node] * 2.0f * sd * T_L;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        J[0][j] = sx * Px[j];
+        J[1][j] = sx * Py[j];
+        J[2][j] = stt * Pt[j];
+    }
+    const float c1 = 1.0f - 2.0f * beta, c2b = 2.0f * beta * wf;
+    const float g0 = fmaf(c1, gF[0], c2b * gS[0]) + (float)A.gbar[node];
+    const float g1 = fmaf(c1, gF[1], c2b * gS[1]) + (float)A.gbar[A.N + node];
+    const float g2 = fmaf(c1, gF[2], c2b * gS[2]) + (float)A.gbar[2 * A.N + node] * 2.0f * sd * T_L;
     const float a00 = J[0][0], a01 = J[1][0], a02 = J[2][0];
     const float a10 = J[0][1], a11 = J[1][1], a12 = J[2][1];
     const float a20 = J[0][2], a21 = J[1][2], a22 = J[2][2];
@@ -270,24 +298,33 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_targets_mixed(Ad
                        a02 * (a10 * r2 - r1 * a20)) * idet;
     const float mu2 = (a00 * (a11 * r2 - r1 * a21) - a01 * (a10 * r2 - r1 * a20) +
                        r0 * (a10 * a21 - a11 * a20)) * idet;
-    const float wq = Abar + mux * mu0 + muy * mu1 + mst * mu2;
-    if (half == 0 && act) A.w[(long long)q * A.N + node] = wq;
-    if (lane == 0) atomicAdd(A.beta_bar, (double)bb);
+    if (live) {
+        const float m0 = sx * mu0, m1 = sx * mu1, m2 = stt * mu2;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int k = q / N1, l = q % N1;
+            const float ck = L.c[k], cl = L.c[l];
+            const float mt = fmaf(ck, ck, cl * cl) - 2.0f * T_L;
+            const long long o = (long long)q * A.N + node;
+            const float Abar = fmaf(c1, (float)A.fbar[o], c2b);
+            A.w[o] = fmaf(ck, m0, fmaf(cl, m1, fmaf(mt, m2, Abar)));
+        }
+    }
+    // beta cotangent sum 2 (rho W_q - A_q) fb_q, reduced over the warp in FP64
+    double bb = live ? 2.0 * ((double)rho * (double)wf - (double)sAf) : 0.0;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) bb += __shfl_xor_sync(0xffffffffu, bb, m);
+    if ((threadIdx.x & 31) == 0) atomicAdd(A.beta_bar, bb);
 }
 
 template <int N1>
-__global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_sources_mixed(AdjMixedArgs A) {
+__global__ void __launch_bounds__(ADJM_THREADS) k_adjoint_sources_mixed(AdjMixedArgs A) {
     constexpr int Q = N1 * N1;
     const LatticeF& L = c_Lam[lattice_slot(N1)];
-    const int lane = threadIdx.x & 31;
-    const long long src = (long long)blockIdx.x * ADJM_WARPS + (threadIdx.x >> 5);
-    if (src >= A.N) return;  // warp-uniform
+    const long long src0 = (long long)blockIdx.x * ADJM_THREADS + threadIdx.x;
+    if (src0 >= A.N) return;  // no warp-wide operation follows
+    const long long src = src0;
     const int JX = (int)(src % A.nx), JY = (int)(src / A.nx);
-    // lane = (population q, half); on D2Q9 lanes with q >= 9 hold no
-    // population: they contribute zeros to the 16-lane sums and read nothing
-    const int q = lane & 15, half = lane >> 4;
-    const bool act = q < Q;
-    const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
     float fj[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) fj[i] = A.f_in[(long long)i * A.N + src];
@@ -297,86 +334,79 @@ __global__ void __launch_bounds__(ADJM_WARPS * 32, 4) k_adjoint_sources_mixed(Ad
 #pragma unroll
     for (int i = 0; i < Q; ++i) fb[i] = 0.0f;
     float bux = 0.0f, buy = 0.0f, bst = 0.0f;
-
-    // candidate targets: J is in the stencil of the target at x when
-    // floor(x - v dt) is in [J - 2, J + 1], i.e. x in [J - 2 + v dt, J + 2 + v dt);
-    // over v in [vlo, vhi] (the bounds carry a 1e-3-cell margin for the FP32
-    // departures) the integers x from ceil(J - 2 + vlo dt) to
-    // ceil(J + 2 + vhi dt) - 1; the exact test below decides.  ceil(J + a) =
-    // J + ceil(a) for integer J, so the bounds are free of the rounding of
-    // large coordinates.
-    const int xlo = JX + (int)ceilf(-2.0f + A.vlo_x[k] * A.dt);
-    const int xhi = JX + (int)ceilf(2.0f + A.vhi_x[k] * A.dt) - 1;
-    const int ylo = JY + (int)ceilf(-2.0f + A.vlo_y[l] * A.dt);
-    const int yhi = JY + (int)ceilf(2.0f + A.vhi_y[l] * A.dt) - 1;
-    for (int yy = ylo + half; act && yy <= yhi; yy += 2) {
-        const int ty = wrap_idx(yy, A.ny);
-        for (int xx = xlo; xx <= xhi; ++xx) {
-            const int tx = wrap_idx(xx, A.nx);
-            const long long t = (long long)ty * A.nx + tx;
-            // the target's stencil origin for population q, as the target
-            // kernel found it
-            const long long o = (long long)q * A.N + t;
-            const int2 og = A.org[o];
-            const int jx = JX - (xx + og.x), jy = JY - (yy + og.y);
-            if (jx < 0 || jx > 3 || jy < 0 || jy > 3) continue;
-            const float4 th = A.gstar[t], tl = A.gstar[A.N + t];
-            const float wgt = A.lw[8 * o + jx] * A.lw[8 * o + 4 + jy];
-            const float coef = A.w[o] * wgt;
-            const float inv = A.inv_st[t];
-            const float r = sdiff(jh.x, jl.x, th.x, tl.x) * inv;
-            const float dx = sdiff(jh.y, jl.y, th.y, tl.y) * inv;
-            const float dy = sdiff(jh.z, jl.z, th.z, tl.z) * inv;
-            float gx[N1], gdx[N1], gy[N1], gdy[N1];
+#pragma unroll 1
+    for (int q = 0; q < Q; ++q) {
+        const int k = q / N1, l = q - N1 * k;
+        const RowCoef<N1> Rk = row_coef<N1>(L, k), Rl = row_coef<N1>(L, l);
+        // candidate targets: J is in the stencil of the target at x when
+        // floor(x - v dt) is in [J - 2, J + 1], i.e. x in [J - 2 + v dt, J + 2 + v dt);
+        // over v in [vlo, vhi] (the bounds carry a 1e-3-cell margin for the
+        // FP32 departures) the integers x from ceil(J - 2 + vlo dt) to
+        // ceil(J + 2 + vhi dt) - 1; the exact test below decides.
+        // ceil(J + a) = J + ceil(a) for integer J, so the bounds are free of
+        // the rounding of large coordinates, and the window's offsets from J
+        // are the same for every thread.
+        const int xlo = JX + (int)ceilf(-2.0f + A.vlo_x[k] * A.dt);
+        const int xhi = JX + (int)ceilf(2.0f + A.vhi_x[k] * A.dt) - 1;
+        const int ylo = JY + (int)ceilf(-2.0f + A.vlo_y[l] * A.dt);
+        const int yhi = JY + (int)ceilf(2.0f + A.vhi_y[l] * A.dt) - 1;
+        // wrapped coordinates advance with the loop counters (one modulo
+        // per population, not per candidate)
+        const int tx0 = wrap_idx(xlo, A.nx);
+        int ty = wrap_idx(ylo, A.ny);
+        for (int yy = ylo; yy <= yhi; ++yy, ty = (ty + 1 == A.ny) ? 0 : ty + 1) {
+            const long long row = (long long)ty * A.nx;
+            int tx = tx0;
+            for (int xx = xlo; xx <= xhi; ++xx, tx = (tx + 1 == A.nx) ? 0 : tx + 1) {
+                const long long t = row + tx;
+                // the target's stencil origin for population q, as the
+                // target kernel found it
+                const long long o = (long long)q * A.N + t;
+                const int2 og = A.org[o];
+                const int jx = JX - (xx + og.x), jy = JY - (yy + og.y);
+                if (jx < 0 || jx > 3 || jy < 0 || jy > 3) continue;
+                const float4 th = A.gstar[t], tl = A.gstar[A.N + t];
+                const float wgt = A.lw[8 * o + jx] * A.lw[8 * o + 4 + jy];
+                const float coef = A.w[o] * wgt;
+                const float inv = A.inv_st[t];
+                const float r = sdiff(jh.x, jl.x, th.x, tl.x) * inv;
+                const float dx = sdiff(jh.y, jl.y, th.y, tl.y) * inv;
+                const float dy = sdiff(jh.z, jl.z, th.z, tl.z) * inv;
+                float gx[N1], gdx[N1], gy[N1], gdy[N1];
 #pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                lag_taylor_f(L, k, a, fmaf(L.c[a], r, dx), gx[a], gdx[a]);
-                lag_taylor_f(L, l, a, fmaf(L.c[a], r, dy), gy[a], gdy[a]);
-            }
-            float sux = 0.0f, suy = 0.0f, sst = 0.0f;
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                const float cgx = coef * gx[a];
-                float h = 0.0f, hp = 0.0f, hq = 0.0f;
-#pragma unroll
-                for (int b = 0; b < N1; ++b) {
-                    fb[N1 * a + b] = fmaf(cgx, gy[b], fb[N1 * a + b]);
-                    const float fv = fj[N1 * a + b];
-                    h = fmaf(gy[b], fv, h);
-                    hp = fmaf(gdy[b], fv, hp);
-                    hq = fmaf(gdy[b] * L.c[b], fv, hq);
+                for (int a = 0; a < N1; ++a) {
+                    lag_taylor_r<N1>(Rk, k, a, fmaf(L.c[a], r, dx), gx[a], gdx[a]);
+                    lag_taylor_r<N1>(Rl, l, a, fmaf(L.c[a], r, dy), gy[a], gdy[a]);
                 }
-                sux = fmaf(gdx[a], h, sux);
-                suy = fmaf(gx[a], hp, suy);
-                sst = fmaf(gdx[a] * L.c[a], h, fmaf(gx[a], hq, sst));
+                float sux = 0.0f, suy = 0.0f, sst = 0.0f;
+#pragma unroll
+                for (int a = 0; a < N1; ++a) {
+                    const float cgx = coef * gx[a];
+                    float h = 0.0f, hp = 0.0f, hq = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) {
+                        fb[N1 * a + b] = fmaf(cgx, gy[b], fb[N1 * a + b]);
+                        const float fv = fj[N1 * a + b];
+                        h = fmaf(gy[b], fv, h);
+                        hp = fmaf(gdy[b], fv, hp);
+                        hq = fmaf(gdy[b] * L.c[b], fv, hq);
+                    }
+                    sux = fmaf(gdx[a], h, sux);
+                    suy = fmaf(gx[a], hp, suy);
+                    sst = fmaf(gdx[a] * L.c[a], h, fmaf(gx[a], hq, sst));
+                }
+                const float ci = coef * inv;
+                bux = fmaf(ci, sux, bux);
+                buy = fmaf(ci, suy, buy);
+                bst = fmaf(ci, sst, bst);
             }
-            const float ci = coef * inv;
-            bux = fmaf(ci, sux, bux);
-            buy = fmaf(ci, suy, buy);
-            bst = fmaf(ci, sst, bst);
         }
     }
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) fb[i] += __shfl_xor_sync(0xffffffffu, fb[i], o);
-        bux += __shfl_xor_sync(0xffffffffu, bux, o);
-        buy += __shfl_xor_sync(0xffffffffu, buy, o);
-        bst += __shfl_xor_sync(0xffffffffu, bst, o);
-    }
-    if (lane < Q) {
-        float v = fb[0];
-#pragma unroll
-        for (int i = 1; i < Q; ++i)
-            if (lane == i) v = fb[i];
-        A.fbar_in[(long long)lane * A.N + src] = (double)v;
-    } else if (lane == 16) {
-        A.gbar_in[src] = (double)bux;
-    } else if (lane == 17) {
-        A.gbar_in[A.N + src] = (double)buy;
-    } else if (lane == 18) {
-        A.gbar_in[2 * A.N + src] = (double)bst / (2.0 * A.st_in[src] * (double)A.T_L);
-    }
+    for (int i = 0; i < Q; ++i) A.fbar_in[(long long)i * A.N + src] = (double)fb[i];
+    A.gbar_in[src] = (double)bux;
+    A.gbar_in[A.N + src] = (double)buy;
+    A.gbar_in[2 * A.N + src] = (double)bst / (2.0 * A.st_in[src] * (double)A.T_L);
 }
 
 }  // namespace pond
@@ -495,11 +525,11 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
         A.vlo_y[i] = (float)(slo + mm[2] - sl);
         A.vhi_y[i] = (float)(shi + mm[3] + sl);
     }
-    const unsigned nb = (unsigned)((N + ADJM_WARPS - 1) / ADJM_WARPS);
-    if (ctx->L.n1 == 3) k_adjoint_targets_mixed<3><<<nb, ADJM_WARPS * 32, 0, s>>>(A);
-    else k_adjoint_targets_mixed<4><<<nb, ADJM_WARPS * 32, 0, s>>>(A);
+    const unsigned nb = (unsigned)((N + ADJM_THREADS - 1) / ADJM_THREADS);
+    if (ctx->L.n1 == 3) k_adjoint_targets_mixed<3><<<nb, ADJM_THREADS, 0, s>>>(A);
+    else k_adjoint_targets_mixed<4><<<nb, ADJM_THREADS, 0, s>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (ctx->L.n1 == 3) k_adjoint_sources_mixed<3><<<nb, ADJM_WARPS * 32, 0, s>>>(A);
-    else k_adjoint_sources_mixed<4><<<nb, ADJM_WARPS * 32, 0, s>>>(A);
+    if (ctx->L.n1 == 3) k_adjoint_sources_mixed<3><<<nb, ADJM_THREADS, 0, s>>>(A);
+    else k_adjoint_sources_mixed<4><<<nb, ADJM_THREADS, 0, s>>>(A);
     return cudaGetLastError();
 }

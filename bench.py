@@ -53,10 +53,10 @@ BYTES_MIXED_Q9 = 2 * (9 * 4 + 3 * 8)
 # FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 flops x 2.07 GHz.
 PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes per k1_step_fp64 launch at 2048^2: the ncu capture of the same
-# kernel (two nodes per warp) at 1024^2 read 164.3 MB and wrote 124.8 MB;
-# traffic grows with the node count (4x).
-K1_TRAFFIC_BYTES_2048 = 4 * (164.3e6 + 124.8e6)
+# DRAM bytes per FP64 step launch at 2048^2: the ncu capture of the same
+# kernel (k1_step_fp64_node, one node per thread) at 1024^2 read 168.0 MB and
+# wrote 129.1 MB; traffic grows with the node count (4x).
+K1_TRAFFIC_BYTES_2048 = 4 * (167.97e6 + 129.12e6)
 
 
 def parse():
@@ -325,10 +325,10 @@ def run_pond(args, world, rank, local):
                      "frac": achieved / PEAK_FP64_TFLOPS,
                      "traffic": K1_TRAFFIC_BYTES_2048,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                       "k1_step_fp64<4, 2> launch at 1024^2 (289.1 MB), scaled "
+                                       "k1_step_fp64_node<4> launch at 1024^2 (297.1 MB), scaled "
                                        "x4 by nodes to the 2048^2 launch",
                      "peak_source": "nominal FP64 rate at 2070 MHz (profiling recipe)",
-                     "kernel": "k1_step_fp64", "kernel_ms": kernel_s * 1e3,
+                     "kernel": "k1_step_fp64_node", "kernel_ms": kernel_s * 1e3,
                      "hbm_gbs_algorithmic": nodes * BYTES_FP64 / kernel_s / 1e9,
                      "hbm_peak_gbs": peaks.get("hbm_gbs")},
         "clocks": clocks,

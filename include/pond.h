@@ -111,10 +111,13 @@ typedef struct pond_config {
                            seed {0, T_L}). */
     int32_t nodes_per_warp; /* FP64 form: target nodes per warp of the step
                            kernel, 1 (16 lanes per node, each lane half the
-                           stencil rows), 2 (each lane all rows) or, on D2Q9
-                           only, 3 (10 lanes per node); 0 = the library
-                           default.  They agree to rounding (the stencil
-                           rows and the moments are summed in other orders). */
+                           stencil rows), 2 (each lane all rows), on D2Q9
+                           only 3 (10 lanes per node), or 32 (one node per
+                           thread, looping over the populations); 0 = the
+                           library default.  Other values are rejected
+                           (POND_ERR_ARG).  They agree to rounding (the
+                           stencil rows and the moments are summed in other
+                           orders). */
 } pond_config;
 
 /* Counters accumulated over the steps of one pond_step call. */

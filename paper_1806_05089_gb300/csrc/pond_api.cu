@@ -291,8 +291,7 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
         cfg->tile_rows != -16)
         return POND_ERR_ARG;
     if (cfg->lattice != POND_D2Q16 && cfg->lattice != POND_D2Q9) return POND_ERR_ARG;
-    if (cfg->nodes_per_warp < 0 || cfg->nodes_per_warp > 3) return POND_ERR_ARG;
-    if (cfg->nodes_per_warp == 3 && cfg->lattice != POND_D2Q9) return POND_ERR_ARG;
+    if (!pond::fp64_npw_valid(cfg->nodes_per_warp, cfg->lattice)) return POND_ERR_ARG;
     if (cfg->lattice == POND_D2Q9 && cfg->tile_rows < 0) return POND_ERR_ARG;  // paired: D2Q16
     for (int g = 0; g < n_grids; ++g)
         if (nx[g] < 1 || ny[g] < 1) return POND_ERR_ARG;

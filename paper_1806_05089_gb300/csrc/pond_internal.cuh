@@ -111,11 +111,21 @@ cudaError_t upload_lattice_mixed();
 cudaError_t upload_lattice_adjoint();
 cudaError_t upload_lattice_adjoint_mixed();
 
-// FP64 step of a single grid, lattice L.n1, nodes_per_warp 1, 2 or (D2Q9) 3.
-constexpr int FP64_NODES_PER_WARP = 2;  // default mapping on D2Q16 (measured faster)
-constexpr int FP64_NODES_PER_WARP_Q9 = 3;  // default mapping on D2Q9 (measured faster)
+// FP64 step of a single grid, lattice L.n1, nodes_per_warp 1, 2, (D2Q9) 3, or 32
+// (one node per thread).
+constexpr int FP64_NODE_PER_THREAD = 32;  // nodes_per_warp value of the node-per-thread kernel
+// default mappings, measured fastest on both lattices at 2048^2 (D2Q16:
+// 1.31e7 node-updates/s against 1.23e7 with two nodes per warp; D2Q9: 3.63e7
+// against 2.66e7 with three)
+constexpr int FP64_NODES_PER_WARP = FP64_NODE_PER_THREAD;
+constexpr int FP64_NODES_PER_WARP_Q9 = FP64_NODE_PER_THREAD;
 constexpr int fp64_default_npw(int n1) {
     return n1 == 3 ? FP64_NODES_PER_WARP_Q9 : FP64_NODES_PER_WARP;
+}
+// accepted nodes_per_warp values: 0 (default), 1, 2, 3 (D2Q9 only), 32
+constexpr bool fp64_npw_valid(int npw, int lattice) {
+    return npw == 0 || npw == 1 || npw == 2 || npw == FP64_NODE_PER_THREAD ||
+           (npw == 3 && lattice == POND_D2Q9);
 }
 cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>& out,
                              int32_t* iters, DevStats* stats, int nx, int ny,

@@ -1,14 +1,19 @@
 // pond_step_fp64.cu -- FP64 PonD time step of one periodic grid.
 //
-// One or two target nodes per warp, 16 lanes per node (lane & 15 = the
-// population q).  With one node, the lane's other index (lane >> 4) halves
-// the four stencil rows and one shuffle sums the halves; with two, it picks
-// the node and each lane sweeps all four rows.  The moments of the Q
-// populations are butterfly-reduced within the 16 lanes, so every lane of a
-// node holds rho, u, T and takes the same convergence decision.  The step is
-// bound by the FP64 pipe; all source reads go through the read-only L1 path.
-// Templated on the lattice: D2Q16 (N1 = 4, all 16 lanes of a node busy) or
-// D2Q9 (N1 = 3: lanes with q >= 9 only join the shuffles).
+// Two kernels, both bound by the FP64 pipe, all source reads through the
+// read-only L1 path, templated on the lattice (D2Q16, N1 = 4, or D2Q9,
+// N1 = 3):
+//  * k1_step_fp64_node (the default): one node per thread, a rolled loop over
+//    the populations; the per-node scalar work of a pass runs once per node.
+//  * k1_step_fp64<N1, NPW>: one, two or (D2Q9) three target nodes per warp,
+//    16 (D2Q9 with three nodes: 10) lanes per node, lane = population q.
+//    With one node, the lane's other index (lane >> 4) halves the four
+//    stencil rows and one shuffle sums the halves; with two, it picks the
+//    node and each lane sweeps all four rows.  The moments of the Q
+//    populations are reduced by shuffles within the node's lanes, so every
+//    lane of a node holds rho, u, T and takes the same convergence decision;
+//    on D2Q9 with 16 lanes per node, lanes with q >= 9 only join the
+//    shuffles.
 //
 // Per predictor-corrector pass (Eqs. advection, vi, interpolation, transform):
 //   departure  y_q = x - (sqrt(theta) c_q + u) dt, origin floor(y_q) - 1
@@ -298,11 +303,238 @@ k1_step_fp64(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ it
     }
 }
 
+// One node per thread (nodes_per_warp = 32): a rolled loop over the
+// populations, each sweeping its 4 x 4 stencil, so the per-node scalar work
+// of a pass (the reciprocal, the moment sums, the square root and the
+// convergence test) is issued once per node instead of once per population
+// lane, and every lane of the FP64 pipe does pair work.  A warp holds 32
+// consecutive nodes on the same population (warp-uniform lattice constants);
+// it runs the largest pass count of its nodes, the finished ones idle.  The
+// pass's populations sit in shared memory for the closing re-gauge, one
+// column per thread (conflict-free).
+constexpr int K1N_THREADS = 128;
+
+template <int N1>
+__global__ void __launch_bounds__(K1N_THREADS, 3)
+k1_step_fp64_node(StateBuf<double> in, StateBuf<double> out, int32_t* __restrict__ iters,
+                  DevStats* __restrict__ stats, int nx, int ny, long long N, StepParams P) {
+    constexpr int Q = N1 * N1;
+    const Lattice& L = c_L[lattice_slot(N1)];
+    __shared__ double s_f[Q][K1N_THREADS];
+    __shared__ unsigned long long s_passes, s_nc, s_np;
+    __shared__ unsigned int s_max;
+    if (threadIdx.x == 0) {
+        s_passes = 0ull;
+        s_nc = 0ull;
+        s_np = 0ull;
+        s_max = 0u;
+    }
+    __syncthreads();
+
+    const int tid = threadIdx.x;
+    const long long node = (long long)blockIdx.x * K1N_THREADS + tid;
+    if (node < N) {
+        const int X = (int)(node % nx);
+        const int Y = (int)(node / nx);
+
+        // seed gauge (Eqs. seed_gauge, seed_gauge_T)
+        double ux = in.ux[node], uy = in.uy[node], st = in.st[node];
+        if (P.seed_mode == 1) {
+            ux = 0.0;
+            uy = 0.0;
+            st = 1.0;
+        } else if (P.seed_mode == 2) {
+            ux = -ux;
+            uy = -uy;
+        }
+
+        int pass = 0;
+        unsigned int flag = 0u;
+        double rho = 0.0;
+        double nux = ux, nuy = uy, nst = st;  // gauge the last pass's moments define
+        bool done = false;
+        while (!done) {
+            ++pass;
+            const double inv = 1.0 / st;
+            const double bx = -ux * inv, by = -uy * inv;
+            double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+#pragma unroll 1
+            for (int q = 0; q < Q; ++q) {
+                const int k = q / N1, l = q - N1 * k;
+                const double ck = L.c[k], cl = L.c[l];
+                double d1k[N1], d2k[N1], d1l[N1], d2l[N1];
+#pragma unroll
+                for (int a = 0; a < N1; ++a) {
+                    d1k[a] = L.d1[k][a];
+                    d2k[a] = L.d2[k][a];
+                    d1l[a] = L.d1[l][a];
+                    d2l[a] = L.d2[l][a];
+                }
+                const double d3k = L.d3[k], d3l = L.d3[l];
+                const double vx = fma(st, ck, ux), vy = fma(st, cl, uy);
+                const double depx = (double)X - vx * P.dt;
+                const double depy = (double)Y - vy * P.dt;
+                const double flx = floor(depx), fly = floor(depy);
+                double lx[4], ly[4];
+                lagrange4(depx - flx + 1.0, lx);
+                lagrange4(depy - fly + 1.0, ly);
+                const int x0 = wrap_idx((long long)flx - 1, nx);
+                const int y0 = wrap_idx((long long)fly - 1, ny);
+                double acc = 0.0;
+#pragma unroll
+                for (int jy = 0; jy < 4; ++jy) {
+                    const int sy = wrap_inc(y0, jy, ny);
+                    double rowacc = 0.0;
+#pragma unroll
+                    for (int jx = 0; jx < 4; ++jx) {
+                        const int sx = wrap_inc(x0, jx, nx);
+                        const long long s = (long long)sy * nx + sx;
+                        const double sts = __ldg(in.st + s);
+                        const double uxs = __ldg(in.ux + s);
+                        const double uys = __ldg(in.uy + s);
+                        const double r = fma(sts, inv, -1.0);  // st_s/st' - 1
+                        const double dx = fma(uxs, inv, bx);   // (u_s,x - u'_x)/st'
+                        const double dy = fma(uys, inv, by);
+                        double gx[N1], gy[N1];
+#pragma unroll
+                        for (int a = 0; a < N1; ++a) {
+                            const double de = fma(L.c[a], r, dx);
+                            gx[a] = gauge_poly<N1>(d3k, d2k[a], d1k[a], a == k ? 1.0 : 0.0, de);
+                        }
+#pragma unroll
+                        for (int b = 0; b < N1; ++b) {
+                            const double de = fma(L.c[b], r, dy);
+                            gy[b] = gauge_poly<N1>(d3l, d2l[b], d1l[b], b == l ? 1.0 : 0.0, de);
+                        }
+                        double g = 0.0;
+#pragma unroll
+                        for (int a = 0; a < N1; ++a) {
+                            double h = 0.0;
+#pragma unroll
+                            for (int b = 0; b < N1; ++b)
+                                h = fma(gy[b], __ldg(in.f + (long long)(N1 * a + b) * N + s), h);
+                            g = fma(gx[a], h, g);
+                        }
+                        rowacc = fma(lx[jx], g, rowacc);
+                    }
+                    acc = fma(ly[jy], rowacc, acc);
+                }
+                s_f[q][tid] = acc;
+                // moments of the pass (central form)
+                m0 += acc;
+                m1 = fma(ck, acc, m1);
+                m2 = fma(cl, acc, m2);
+                m3 = fma(ck * ck + cl * cl, acc, m3);
+            }
+
+            rho = m0;
+            const double ir = 1.0 / rho;
+            const double dux = st * m1 * ir, duy = st * m2 * ir;
+            const double ux1 = ux + dux, uy1 = uy + duy;
+            double st1 = st;
+            bool ok = (rho > 0.0) && isfinite(ux1) && isfinite(uy1);
+            if (P.thermal) {
+                const double T1 = 0.5 * (st * st * m3 * ir - (dux * dux + duy * duy));
+                ok = ok && (T1 > 0.0) && isfinite(T1);
+                st1 = sqrt(T1 / P.T_L);
+            }
+            if (!ok) {
+                flag |= 2u;
+                done = true;
+            } else {
+                nux = ux1;
+                nuy = uy1;
+                nst = st1;
+                const bool conv = fabs(ux1 - ux) < P.eps_abs + P.eps_rel * fabs(ux1) &&
+                                  fabs(uy1 - uy) < P.eps_abs + P.eps_rel * fabs(uy1) &&
+                                  fabs(st1 - st) < P.eps_abs + P.eps_rel * fabs(st1);
+                bool stop;
+                if (P.fixed_iter > 0) {
+                    stop = pass >= P.fixed_iter;
+                } else {
+                    stop = conv || pass >= P.max_iter;
+                    if (!conv && pass >= P.max_iter) flag |= 1u;
+                }
+                if (stop) {
+                    done = true;
+                } else {
+                    ux = ux1;
+                    uy = uy1;
+                    st = st1;
+                }
+            }
+        }
+
+        // Re-express f^{lambda_n} in the gauge lambda_{n+1} its moments define
+        // (Eq. transform at the node itself), then BGK toward rho W in that
+        // co-moving gauge (Eq. postcollision).  A node with non-physical
+        // moments keeps its populations and the gauge of its last pass.
+        const bool regauge = !(flag & 2u);
+        const double inv1 = 1.0 / nst;
+        const double r = fma(st, inv1, -1.0);
+        const double dx = (ux - nux) * inv1, dy = (uy - nuy) * inv1;
+#pragma unroll 1
+        for (int q = 0; q < Q; ++q) {
+            const int k = q / N1, l = q - N1 * k;
+            double total = s_f[q][tid];
+            if (regauge) {
+                double gx[N1], gy[N1];
+#pragma unroll
+                for (int a = 0; a < N1; ++a) {
+                    gx[a] = gauge_poly<N1>(L.d3[k], L.d2[k][a], L.d1[k][a], a == k ? 1.0 : 0.0,
+                                           fma(L.c[a], r, dx));
+                    gy[a] = gauge_poly<N1>(L.d3[l], L.d2[l][a], L.d1[l][a], a == l ? 1.0 : 0.0,
+                                           fma(L.c[a], r, dy));
+                }
+                double g = 0.0;
+#pragma unroll
+                for (int a = 0; a < N1; ++a) {
+                    double h = 0.0;
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) h = fma(gy[b], s_f[N1 * a + b][tid], h);
+                    g = fma(gx[a], h, g);
+                }
+                total = g;
+            }
+            const double feq = rho * L.w[k] * L.w[l];
+            out.f[(long long)q * N + node] = total + 2.0 * P.beta * (feq - total);
+        }
+        if (regauge) {
+            ux = nux;
+            uy = nuy;
+            st = nst;
+        }
+        out.ux[node] = ux;
+        out.uy[node] = uy;
+        out.st[node] = st;
+        if (iters) iters[node] = pass;
+        atomicAdd(&s_passes, (unsigned long long)pass);
+        atomicMax(&s_max, (unsigned int)pass);
+        if (flag & 1u) atomicAdd(&s_nc, 1ull);
+        if (flag & 2u) atomicAdd(&s_np, 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && stats) {
+        atomicAdd(&stats->passes, s_passes);
+        atomicMax(&stats->max_passes, s_max);
+        if (s_nc) atomicAdd(&stats->nonconverged, s_nc);
+        if (s_np) atomicAdd(&stats->nonphysical, s_np);
+    }
+}
+
 cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>& out,
                              int32_t* iters, DevStats* stats, int nx, int ny, const Lattice& L,
                              const StepParams& P, int nodes_per_warp, cudaStream_t s) {
     const long long N = (long long)nx * ny;
     if (N == 0) return cudaSuccess;
+    if (nodes_per_warp == FP64_NODE_PER_THREAD) {
+        const unsigned nbn = (unsigned)((N + K1N_THREADS - 1) / K1N_THREADS);
+        if (L.n1 == 3)
+            k1_step_fp64_node<3><<<nbn, K1N_THREADS, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+        else
+            k1_step_fp64_node<4><<<nbn, K1N_THREADS, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+        return cudaGetLastError();
+    }
     const int npw = (nodes_per_warp == 3 && L.n1 == 3) ? 3 : (nodes_per_warp == 1 ? 1 : 2);
     const long long per_cta = (long long)K1_WARPS * npw;
     const unsigned nb = (unsigned)((N + per_cta - 1) / per_cta);
@@ -391,8 +623,7 @@ extern "C" pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx
     if (cfg->precision != POND_FP64 || !(cfg->nu > 0.0) || !(cfg->T_ref > 0.0) ||
         !(cfg->dt > 0.0) || cfg->max_iter < 1 || cfg->fixed_iter < 0 || cfg->seed_mode < 0 ||
         cfg->seed_mode > 2 || (cfg->lattice != POND_D2Q16 && cfg->lattice != POND_D2Q9) ||
-        cfg->nodes_per_warp < 0 || cfg->nodes_per_warp > 3 ||
-        (cfg->nodes_per_warp == 3 && cfg->lattice != POND_D2Q9))
+        !fp64_npw_valid(cfg->nodes_per_warp, cfg->lattice))
         return POND_ERR_ARG;
     if (nx < 1 || ny < 1 || (int64_t)nx * ny > kNoAllocMaxNodes) return POND_ERR_ARG;
     int dev = 0;

@@ -29,7 +29,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="adjoint: precision of the rollout and its adjoint")
     ap.add_argument("--npw", type=int, default=0,
-                    help="fp64: nodes per warp of the step kernel (1 or 2; 0 = default)")
+                    help="fp64: nodes per warp of the step kernel (1, 2, 3 on d2q9, 32 = one per "
+                         "thread; 0 = default)")
     ap.add_argument("--lattice", choices=["d2q16", "d2q9"], default="d2q16",
                     help="fp64 / mixed / batched: lattice (d2q9 runs the same flow at "
                          "T_L = 1/3: T/3, u/sqrt 3)")

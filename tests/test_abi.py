@@ -66,9 +66,20 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
     bad = pond.pond_config_default(pond.POND_FP64)
     bad.nodes_per_warp = 3
     assert lib.pond_create(ctypes.byref(bad), 1, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
-    bad.nodes_per_warp = 4
     bad.lattice = pond.POND_D2Q9
-    assert lib.pond_create(ctypes.byref(bad), 1, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
+    for npw in (-1, 4, 16, 31, 33):
+        bad.nodes_per_warp = npw
+        assert lib.pond_create(ctypes.byref(bad), 1, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
+    # one node per thread (32) passes the argument check on both lattices;
+    # without a GPU the call then fails on the device, not on its arguments
+    for lattice in (pond.POND_D2Q16, pond.POND_D2Q9):
+        ok = pond.pond_config_default(pond.POND_FP64)
+        ok.lattice = lattice
+        ok.nodes_per_warp = 32
+        st = lib.pond_create(ctypes.byref(ok), 1, nx, ny, None, ctypes.byref(out))
+        assert st != pond.POND_ERR_ARG
+        if st == pond.POND_OK:
+            lib.pond_destroy(out)
 
 
 def test_no_cpu_fallback_without_gpu():

@@ -75,7 +75,7 @@ def rel_errors(g, grho, o, speed_scale=False):
     return e_rho, e_u, e_T, e_f
 
 
-@pytest.mark.parametrize("npw", [1, 2, 3])
+@pytest.mark.parametrize("npw", [1, 2, 3, 32])
 @pytest.mark.parametrize("name,nx,ny,steps", [("tg", 64, 64, 12), ("supersonic", 37, 29, 6),
                                               ("hot", 48, 40, 5), ("supersonic", 1, 1, 3),
                                               ("tg", 3, 5, 4), ("supersonic", 2, 7, 3)])
@@ -88,7 +88,7 @@ def test_d2q9_fp64_fixed_passes_matches_oracle(name, nx, ny, steps, npw):
     assert max(e) <= TOL64, e
 
 
-@pytest.mark.parametrize("npw", [2, 3])
+@pytest.mark.parametrize("npw", [2, 3, 32])
 @pytest.mark.parametrize("thermal", [1, 0])
 def test_d2q9_fp64_adaptive_matches_oracle(thermal, npw):
     fields = d2q9_fields("tg", 64, 64) if thermal else d2q9_fields("supersonic", 47, 41)

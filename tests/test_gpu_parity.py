@@ -77,7 +77,7 @@ def small_fields(name, nx, ny):
 
 # ------------------------------------------------------------------ FP64
 
-@pytest.mark.parametrize("npw", [1, 2])
+@pytest.mark.parametrize("npw", [1, 2, 32])
 @pytest.mark.parametrize("name,nx,ny,steps", [("tg", 64, 64, 12), ("supersonic", 37, 29, 6),
                                               ("hot", 48, 40, 5), ("supersonic", 1, 1, 3),
                                               ("tg", 3, 5, 4), ("supersonic", 2, 7, 3)])
@@ -90,10 +90,10 @@ def test_fp64_fixed_passes_matches_oracle(name, nx, ny, steps, npw):
     assert max(e) <= TOL64, e
 
 
-@pytest.mark.parametrize("npw", [1, 2])
+@pytest.mark.parametrize("npw", [1, 2, 32])
 def test_fp64_taylor_green_full_config_adaptive(npw):
     """64^2 Taylor-Green, u0 = 0.05, nu = 0.01, 100 steps, adaptive passes
-    (one and two nodes per warp)."""
+    (one and two nodes per warp, and one node per thread)."""
     fields = workloads.tg64()
     g, grho, git, stats = gpu_run(fields, 100, nodes_per_warp=npw)
     o, oit = oracle_run(fields, 100)
@@ -103,10 +103,11 @@ def test_fp64_taylor_green_full_config_adaptive(npw):
     assert max(e) <= 1e-9, e
 
 
-@pytest.mark.parametrize("npw", [1, 2])
+@pytest.mark.parametrize("npw", [1, 2, 32])
 def test_fp64_supersonic_adaptive_pass_map(npw):
     # 63 x 47: an odd node count leaves the last warp of the two-node mapping
-    # with one node
+    # with one node, and the last block of the node-per-thread mapping part
+    # filled
     fields = small_fields("supersonic", 63, 47)
     g, grho, git, stats = gpu_run(fields, 4, nodes_per_warp=npw)
     o, oit = oracle_run(fields, 4)

@@ -123,3 +123,60 @@ def test_header_is_plain_c_and_structs_match_the_binding(tmp_path):
         assert seen[(cname, "size")] == ctypes.sizeof(pyst), cname
         for field, _ in pyst._fields_:
             assert seen[(cname, field)] == getattr(pyst, field).offset, (cname, field)
+
+
+def test_plain_c_program_links_and_calls_the_library(tmp_path):
+    """A C99 program links against libpond.so by its exported names and calls
+    the argument checks of the boundary: the version string, the defaults,
+    rejections of bad arguments and, without a GPU, a CUDA status from a
+    valid pond_create (no CPU fallback)."""
+    import shutil
+    import subprocess
+    import torch
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pond.load()
+    libdir = os.path.dirname(pond._build.LIB)
+    src = tmp_path / "client.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "pond.h"
+
+int main(int argc, char** argv) {
+    int have_gpu = argc > 1 && strcmp(argv[1], "gpu") == 0;
+    pond_config cfg;
+    pond_config_default(&cfg, POND_FP64);
+    if (cfg.precision != POND_FP64 || !(cfg.nu > 0.0)) return 10;
+    if (strstr(pond_version(), "D2Q9") == NULL) return 11;
+    int32_t nx = 8, ny = 0;
+    pond_ctx* ctx = NULL;
+    if (pond_create(&cfg, 1, &nx, &ny, NULL, &ctx) != POND_ERR_ARG) return 12;
+    ny = 8;
+    cfg.nu = -1.0;
+    if (pond_create(&cfg, 1, &nx, &ny, NULL, &ctx) != POND_ERR_ARG) return 13;
+    pond_config_default(&cfg, POND_FP64);
+    cfg.nodes_per_warp = 5;
+    if (pond_create(&cfg, 1, &nx, &ny, NULL, &ctx) != POND_ERR_ARG) return 14;
+    if (pond_step(NULL, 1, NULL) != POND_ERR_ARG) return 15;
+    if (strcmp(pond_last_error(NULL), "no context") != 0) return 16;
+    pond_config_default(&cfg, POND_FP64);
+    pond_status st = pond_create(&cfg, 1, &nx, &ny, NULL, &ctx);
+    if (have_gpu) {
+        if (st != POND_OK) return 17;
+        pond_destroy(ctx);
+    } else if (st != POND_ERR_CUDA && st != POND_ERR_OOM) {
+        return 18;
+    }
+    printf("ok\n");
+    return 0;
+}
+''')
+    exe = tmp_path / "client"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-lpond", "-Wl,-rpath," + libdir], check=True)
+    args = [str(exe)] + (["gpu"] if torch.cuda.is_available() else [])
+    r = subprocess.run(args, capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)

@@ -244,3 +244,55 @@ def test_d2q16_thermal_diffusivity_is_bgk_prandtl_one():
     nu = 0.1
     alpha = _entropy_mode_decay(oracle.D2Q16, 64, nu, 1.0, 0.0, 700)
     assert abs(alpha / nu - 1) < 0.01, alpha
+
+
+@pytest.mark.parametrize("mach", [0.0, 1.5, 10.0])
+def test_d2q9_shear_wave_galilean_invariance(mach):
+    """Viscosity experiment on D2Q9: an isothermal shear wave u_y = A sin(2 pi
+    x/L) at T = T_L, advected along x at Mach Ma_a, decays at nu k^2 (within
+    3 %, independent of Ma_a) and moves with the flow."""
+    T = GOLD["d2q9_T_L"]["value"]
+    L, A, nu, steps = 64, 0.05 * np.sqrt(T), 0.05, 60
+    X = np.arange(L, dtype=float)[None, :]
+    U = mach * np.sqrt(T)
+    st = oracle.init_equilibrium(np.ones((1, L)), np.full((1, L), U),
+                                 A * np.sin(2 * np.pi * X / L), np.full((1, L), T), lattice=Q9)
+    p = oracle.Params(nu=nu, thermal=0, lattice=Q9, T_ref=T)
+    k = 2 * np.pi / L
+    amps = []
+    for _ in range(steps):
+        st, _, fl = oracle.step(st, p)
+        assert np.all(fl == 0)
+        amps.append((st.uy[0] * np.exp(-1j * k * X[0])).sum() * 2 / L)
+    amps = np.array(amps)
+    t = np.arange(1, steps + 1)
+    rate = -np.polyfit(t[10:], np.log(np.abs(amps[10:])), 1)[0]
+    assert abs(rate / (nu * k * k) - 1) < 0.03, rate
+    phase = np.unwrap(np.angle(amps))
+    speed = -np.polyfit(t[10:], phase[10:], 1)[0] / k
+    assert abs(speed - U) < 1e-3 * max(1.0, U), speed
+
+
+@pytest.mark.parametrize("T_over_TL", [0.5, 2.0])
+def test_d2q9_speed_of_sound(T_over_TL):
+    """Speed-of-sound experiment on D2Q9: a standing acoustic wave oscillates
+    at c_s = sqrt(gamma T), gamma = 2, within 1 %; the lattice's T_L = 1/3
+    does not enter (T at half and twice T_L)."""
+    T = T_over_TL * GOLD["d2q9_T_L"]["value"]
+    L, eps, steps = 64, 1e-3, 200
+    X = np.arange(L, dtype=float)[None, :]
+    st = oracle.init_equilibrium(1 + eps * np.cos(2 * np.pi * X / L), np.zeros((1, L)),
+                                 np.zeros((1, L)), np.full((1, L), T), lattice=Q9)
+    k = 2 * np.pi / L
+    basis = np.cos(k * X[0])
+    a = []
+    for _ in range(steps):
+        st, _, fl = oracle.step(st, oracle.Params(nu=0.01, lattice=Q9, T_ref=T))
+        assert np.all(fl == 0)
+        p = st.f.sum(axis=0)[0] * st.T[0]  # pressure p = rho T
+        a.append(((p - p.mean()) * basis).sum() * 2 / L)
+    a = np.array(a)
+    zc = [i + a[i] / (a[i] - a[i + 1]) for i in range(len(a) - 1) if a[i] * a[i + 1] < 0]
+    assert len(zc) >= 3
+    cs = np.pi / np.diff(zc).mean() / k
+    assert abs(cs / np.sqrt(GOLD["gamma_2d"]["value"] * T) - 1) < 0.01, cs

@@ -296,3 +296,27 @@ def test_d2q9_speed_of_sound(T_over_TL):
     assert len(zc) >= 3
     cs = np.pi / np.diff(zc).mean() / k
     assert abs(cs / np.sqrt(GOLD["gamma_2d"]["value"] * T) - 1) < 0.01, cs
+
+
+def test_d2q9_taylor_green_decay_rate():
+    """App. D on the paper's own lattice: the 64^2 Taylor-Green vortex at the
+    same Mach number as the D2Q16 pin (u0 = 0.05 sqrt(T_L), T = T_L,
+    nu = 0.01) decays at 2 nu k^2 within 5 %."""
+    from paper_1806_05089_gb300 import workloads
+    T_L = GOLD["d2q9_T_L"]["value"]
+    n, nu, steps = 64, 0.01, 100
+    tg = workloads.tg64(n)
+    st = oracle.init_equilibrium(tg.rho, tg.ux * np.sqrt(T_L), tg.uy * np.sqrt(T_L),
+                                 tg.T * T_L, lattice=Q9)
+    basis = tg.ux / np.abs(tg.ux).max()
+    amps = []
+    for _ in range(steps):
+        st, _, fl = oracle.step(st, oracle.Params(nu=nu, lattice=Q9, T_ref=T_L))
+        assert np.all(fl == 0)
+        amps.append((st.ux * basis).sum() / (basis * basis).sum())
+    t = np.arange(1, steps + 1)
+    sel = t >= 10
+    rate = -np.polyfit(t[sel], np.log(amps)[sel], 1)[0]
+    k = 2 * np.pi / n
+    theory = GOLD["tg_decay_factor"]["value"] * nu * k * k
+    assert abs(rate / theory - 1) < 0.05, (rate, theory)

@@ -194,8 +194,9 @@ pond_status pond_iterations(pond_ctx* ctx, int32_t grid, void* iters, int32_t on
  * is differentiated implicitly (the limit gauge of Eqs. density..T is a
  * function of the input state only; the seed gets no gradient).  All array
  * pointers are device pointers.  The state is left unchanged.  FP64 and
- * mixed contexts (the latter with FP32 pair arithmetic and an FP64 3 x 3
- * solve); single-grid, thermal mode, either lattice (POND_ERR_ARG otherwise).
+ * mixed contexts (the latter with FP32 pair arithmetic and an FP32 per-node
+ * 3 x 3 solve; the nu cotangent accumulates in FP64); single-grid, thermal
+ * mode, either lattice (POND_ERR_ARG otherwise).
  * Errors: POND_ERR_ARG, POND_ERR_STATE, POND_ERR_OOM, POND_ERR_CUDA. */
 pond_status pond_adjoint_step(pond_ctx* ctx, const void* f_bar_in, const void* gauge_bar_in,
                               void* f_bar_out, void* gauge_bar_out, double* nu_bar_accum);

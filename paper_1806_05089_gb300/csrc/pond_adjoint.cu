@@ -22,12 +22,11 @@
 // The seed gauge gets no gradient: the limit does not depend on it.
 //
 // Phase A (one warp per target node, lane = population, like the forward
-// step's warp mappings) forms A*, the
-// JVP A_lambda in three directions, the 3 x 3 solve and w.  Phase B (one warp
-// per source node) gathers the transpose: for every population it scans the
-// targets whose departure stencil can contain the source (a window bounded by
-// the particle-velocity range), so the result is deterministic and needs no
-// atomics.
+// step's warp mappings) forms A*, the JVP A_lambda in three directions, the
+// 3 x 3 solve and w.  Phase B (one warp per source node) gathers the
+// transpose: for every population it scans the targets whose departure
+// stencil can contain the source (a window bounded by the particle-velocity
+// range), so the result is deterministic and needs no atomics.
 #include <cmath>
 
 #include "pond_device.cuh"

@@ -49,8 +49,10 @@ BYTES_MIXED = 2 * (16 * 4 + 3 * 8)
 FLOP_PER_PASS_Q9 = 144 * 68 + 9 * 20 + 72
 BYTES_FP64_Q9 = 2 * (9 * 8 + 3 * 8)
 BYTES_MIXED_Q9 = 2 * (9 * 4 + 3 * 8)
-# Peaks of the arithmetic pipes (nominal, at the 2070 MHz maximum SM clock):
-# FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 flops x 2.07 GHz.
+# Nominal peaks of the arithmetic pipes at the 2070 MHz maximum SM clock
+# (FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 flops x 2.07 GHz).  The
+# roofline uses the rates the FMA-chain probe (pond_measure_peak) measures
+# at the start of every run instead; these are the fallback if it fails.
 PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per FP64 step launch at 2048^2: the ncu capture of the same
@@ -68,6 +70,10 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--precision-steps", type=int, default=1000,
+                    help="steps of the mixed-vs-FP64 moment-error leg")
+    ap.add_argument("--precision-full", action="store_true",
+                    help="run that leg on the full 4096^2 field (FP64 reference ~20 min)")
     return ap.parse_args()
 
 
@@ -195,6 +201,31 @@ def oracle_sample(fields, seconds: float, params=None):
     return out
 
 
+def measure_peaks(local):
+    """FP64 and FP32 FMA rates of this GPU, measured now by the library's
+    FMA-chain probe (pond_measure_peak; best of three launches of about
+    0.1 s each), with the clocks seen meanwhile.  The FP32 figure is the
+    packed fma.rn.f32x2 form, which reaches the pipe's rate with half the
+    issue slots; the scalar form is reported beside it."""
+    import torch
+    from paper_1806_05089_gb300 import pond
+    sink = torch.zeros(16, dtype=torch.float64, device="cuda")
+    out = {}
+    with ClockSampler(local) as clk:
+        for name, pipe, iters in (("fp64", pond.POND_PIPE_FP64, 2000),
+                                  ("fp32_scalar", pond.POND_PIPE_FP32, 100000),
+                                  ("fp32", pond.POND_PIPE_FP32X2, 50000)):
+            try:
+                out[name] = max(pond.pond_measure_peak(pipe, iters, sink)[0] for _ in range(3))
+            except Exception as e:  # keep the bench running on the nominal figure
+                out[name + "_error"] = str(e)
+    out["clocks"] = clk.summary()
+    out["how"] = ("pond_measure_peak: 8 independent FMA chains per thread, grid = SMs x resident "
+                  "CTAs of 256 threads, one launch of ~0.1 s timed with CUDA events after a "
+                  "warm-up launch, best of 3")
+    return out
+
+
 def time_steps(sim, stream, steps):
     """Time `steps` PonD steps on `stream` with CUDA events; returns (seconds,
     stats)."""
@@ -283,6 +314,11 @@ def run_pond(args, world, rank, local):
     fields = workloads.supersonic(2048)
     ny, nx = fields.shape
     nodes = nx * ny
+    probe = measure_peaks(local)
+    peak64 = probe.get("fp64", PEAK_FP64_TFLOPS)
+    peak32 = probe.get("fp32", PEAK_FP32_TFLOPS)
+    peak_src = ("measured in this run by the FMA-chain probe" if "fp64" in probe
+                else "nominal FP64 rate at 2070 MHz (probe failed)")
 
     # ---- headline: FP64 step, state resident in HBM (1.2 GB > L2)
     sim = pond.Sim(nx, ny, pond.POND_FP64, stream=stream.cuda_stream)
@@ -321,17 +357,20 @@ def run_pond(args, world, rank, local):
         "nonconverged": stats["nonconverged"],
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved,
-                     "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / PEAK_FP64_TFLOPS,
+                     "peak": peak64, "unit": "TFLOP/s",
+                     "frac": achieved / peak64,
                      "traffic": K1_TRAFFIC_BYTES_2048,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                        "k1_step_fp64_node<4> launch at 1024^2 (297.1 MB), scaled "
                                        "x4 by nodes to the 2048^2 launch",
-                     "peak_source": "nominal FP64 rate at 2070 MHz (profiling recipe)",
+                     "peak_source": peak_src,
+                     "peak_nominal": PEAK_FP64_TFLOPS,
+                     "flop_per_pass": FLOP_PER_PASS,
                      "kernel": "k1_step_fp64_node", "kernel_ms": kernel_s * 1e3,
                      "hbm_gbs_algorithmic": nodes * BYTES_FP64 / kernel_s / 1e9,
                      "hbm_peak_gbs": peaks.get("hbm_gbs")},
         "clocks": clocks,
+        "peaks_measured": probe,
     }
 
     # ---- end to end through the public API with host buffers
@@ -365,7 +404,7 @@ def run_pond(args, world, rank, local):
         msecs, mstats = time_steps(msim, stream, args.steps)
         rho32, ux32, uy32, T32 = msim.moments()
         forms["fp32_mixed_2048"] = form_line("supersonic-2048-mixed", nodes, args.steps, msecs,
-                                             mstats, PEAK_FP32_TFLOPS, BYTES_MIXED)
+                                             mstats, peak32, BYTES_MIXED)
         forms["fp32_mixed_2048"]["moment_err_vs_fp64"] = {
             "after_steps": args.warmup + args.steps,
             "rho": float(np.max(np.abs(rho32 - rho64)) / np.max(np.abs(rho64))),
@@ -383,7 +422,7 @@ def run_pond(args, world, rank, local):
         psim.step(args.warmup)
         psecs, pstats = time_steps(psim, stream, k2)
         forms["fp32_mixed_4096"] = form_line("precision-4096-mixed", 4096 * 4096, k2, psecs,
-                                             pstats, PEAK_FP32_TFLOPS, BYTES_MIXED)
+                                             pstats, peak32, BYTES_MIXED)
         psim.close()
         del pf
 
@@ -397,7 +436,7 @@ def run_pond(args, world, rank, local):
         bsim.step(args.warmup)
         bsecs, bstats = time_steps(bsim, stream, k2)
         forms["batched_256"] = form_line("ensemble-256-mixed", bnodes, k2, bsecs, bstats,
-                                         PEAK_FP32_TFLOPS, BYTES_MIXED)
+                                         peak32, BYTES_MIXED)
         bsim.close()
 
         # the paper's own D2Q9 lattice on the same supersonic flow, rescaled to
@@ -405,10 +444,10 @@ def run_pond(args, world, rank, local):
         q9 = workloads.supersonic(2048)
         q9.T, q9.ux, q9.uy = q9.T / 3.0, q9.ux / np.sqrt(3.0), q9.uy / np.sqrt(3.0)
         q9_out = {}
-        for key, prec, peak, nbytes in (("fp64_d2q9_2048", pond.POND_FP64, PEAK_FP64_TFLOPS,
+        for key, prec, peak, nbytes in (("fp64_d2q9_2048", pond.POND_FP64, peak64,
                                          BYTES_FP64_Q9),
                                         ("fp32_mixed_d2q9_2048", pond.POND_FP32_MIXED,
-                                         PEAK_FP32_TFLOPS, BYTES_MIXED_Q9)):
+                                         peak32, BYTES_MIXED_Q9)):
             extra = {"use_graph": 1, "autotune": 1} if prec == pond.POND_FP32_MIXED else {}
             qsim = pond.Sim(nx, ny, prec, stream=stream.cuda_stream, lattice=pond.POND_D2Q9,
                             T_ref=1.0 / 3.0, **extra)
@@ -431,47 +470,86 @@ def run_pond(args, world, rank, local):
             "T": float(np.max(np.abs(t32 - t64)) / np.max(np.abs(t64)))}
         del q9, q9_out
 
-        # adjoint / forward time on the 512^2 Taylor-Green + pulse workload
+        # adjoint / forward time on the 512^2 Taylor-Green + pulse workload.
+        # One short rollout with its backward runs first, untimed, so that
+        # one-time costs (first launches of the adjoint kernels and of
+        # torch's own loss kernels, first allocations) stay out of both
+        # legs.  The forward leg is the rollout call alone; the backward leg
+        # is the loss and its backward (segment recompute + adjoint steps).
         from paper_1806_05089_gb300.autograd import pond_rollout
         af, target = workloads.adjoint(512)
         dev = torch.device("cuda", local)
-        r = torch.tensor(af.rho, device=dev, requires_grad=True)
-        n = torch.tensor(0.01, dtype=torch.float64, device=dev, requires_grad=True)
         gauge = [torch.tensor(a, device=dev) for a in (af.ux, af.uy, af.T)]
         tgt = torch.tensor(target, device=dev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rho = pond_rollout(r, n, *gauge, 200, 20)
-        loss = 0.5 * ((rho - tgt) ** 2).sum()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        loss.backward()
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
+
+        def rollout_times(precision):
+            for steps, timed in ((4, False), (200, True)):
+                r = torch.tensor(af.rho, device=dev, requires_grad=True)
+                n = torch.tensor(0.01, dtype=torch.float64, device=dev, requires_grad=True)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rho = pond_rollout(r, n, *gauge, steps, 20 if timed else 2, precision=precision)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                loss = 0.5 * ((rho - tgt) ** 2).sum()
+                loss.backward()
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+            return r, n, loss, t1 - t0, t2 - t1
+
+        r, n, loss, fwd, bwd = rollout_times(pond.POND_FP64)
         forms["adjoint_512"] = {"workload": "adjoint-512-fp64", "steps": 200, "ckpt_every": 20,
-                                "forward_s": t1 - t0, "backward_s": t2 - t1,
-                                "adjoint_over_forward": (t2 - t1) / (t1 - t0),
+                                "forward_s": fwd, "backward_s": bwd,
+                                "adjoint_over_forward": bwd / fwd,
                                 "nu_grad": float(n.grad), "loss": float(loss.detach())}
         g64 = r.grad.detach().clone()
-        r32 = torch.tensor(af.rho, device=dev, requires_grad=True)
-        n32 = torch.tensor(0.01, dtype=torch.float64, device=dev, requires_grad=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rho32 = pond_rollout(r32, n32, *gauge, 200, 20, precision=pond.POND_FP32_MIXED)
-        loss32 = 0.5 * ((rho32 - tgt) ** 2).sum()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        loss32.backward()
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
+        nu64 = float(n.grad)
+        r32, n32, loss32, fwd32, bwd32 = rollout_times(pond.POND_FP32_MIXED)
         forms["adjoint_512_mixed"] = {
             "workload": "adjoint-512-mixed", "steps": 200, "ckpt_every": 20,
-            "forward_s": t1 - t0, "backward_s": t2 - t1,
-            "adjoint_over_forward": (t2 - t1) / (t1 - t0),
+            "forward_s": fwd32, "backward_s": bwd32,
+            "adjoint_over_forward": bwd32 / fwd32,
             "grad_rel_err_vs_fp64": float((r32.grad - g64).abs().max() / g64.abs().max()),
             "grad_max_abs": [float(g64.abs().max()), float(r32.grad.abs().max())],
-            "nu_grad_rel_err_vs_fp64": abs(float(n32.grad) - float(n.grad)) / abs(float(n.grad)),
-            "backward_speedup_vs_fp64": forms["adjoint_512"]["backward_s"] / (t2 - t1)}
+            "nu_grad_rel_err_vs_fp64": abs(float(n32.grad) - nu64) / abs(nu64),
+            "backward_speedup_vs_fp64": bwd / bwd32}
+
+        # moment error of the mixed form against the FP64 step after 1000
+        # steps on the temperature-ratio-4 precision field.  The FP64
+        # reference of the full 4096^2 field takes ~20 min on this part
+        # (--precision-full runs it); by default the same field recipe at
+        # 1024^2 (steeper gradients per cell, so no easier) is run in both
+        # forms for 1000 steps.
+        pn = 4096 if args.precision_full else 1024
+        pstate = workloads.precision(pn)
+        res = {}
+        for prec in (pond.POND_FP64, pond.POND_FP32_MIXED):
+            extra = {"use_graph": 1, "autotune": 1} if prec == pond.POND_FP32_MIXED else {}
+            with pond.Sim(pn, pn, prec, stream=stream.cuda_stream, **extra) as ps:
+                ps.set_state(pstate.rho, pstate.ux, pstate.uy, pstate.T)
+                ev = time_steps(ps, stream, args.precision_steps)
+                res[prec] = (ps.moments(), ev)
+        (r64_, x64_, y64_, t64_), (s64, st64) = res[pond.POND_FP64]
+        (r32_, x32_, y32_, t32_), (s32, st32) = res[pond.POND_FP32_MIXED]
+        forms["precision_%d_%dsteps" % (pn, args.precision_steps)] = {
+            "workload": "precision-%d" % pn, "steps": args.precision_steps,
+            "rho": float(np.max(np.abs(r32_ - r64_) / r64_)),
+            "u": float(max(np.abs(x32_ - x64_).max(), np.abs(y32_ - y64_).max())
+                       / np.hypot(x64_, y64_).max()),
+            "T": float(np.max(np.abs(t32_ - t64_) / t64_)),
+            "bound": 1e-5,
+            "fp64_s": s64, "mixed_s": s32,
+            "speedup_mixed_vs_fp64": s64 / s32,
+            "mean_passes": [st64["passes"] / st64["node_updates"],
+                            st32["passes"] / st32["node_updates"]],
+            "nonconverged": [st64["nonconverged"], st32["nonconverged"]],
+            "error_definition": "max over nodes: |d rho|/rho, |d u|/max|u_fp64|, |d T|/T"}
+        pkey = "precision_%d_%dsteps" % (pn, args.precision_steps)
+        forms["fp32_mixed_4096"]["moment_err_vs_fp64"] = {
+            "after_steps": args.precision_steps, "grid": "%dx%d" % (pn, pn),
+            "rho": forms[pkey]["rho"], "u": forms[pkey]["u"], "T": forms[pkey]["T"],
+            "see": pkey}
+        del pstate, res
         line["forms"] = forms
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1)

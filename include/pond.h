@@ -244,10 +244,16 @@ pond_status pond_adjoint_init(pond_ctx* ctx, const void* f_bar, void* rho_bar);
  * (2 x 8 x POND_NOALLOC_MAX_NODES + 256 bytes).  Every call on a device
  * shares that array and the counters are cleared at the start of each call,
  * so calls whose work can overlap on the GPU (different streams, or
- * different host threads) race and must be serialised by the caller.  The
- * first call on each device looks up the array's device address and uploads
- * the lattice constants (synchronous copies), so make it before any stream
- * capture.  No cudaMalloc, cudaFree or allocating library call is made.
+ * different host threads) race and must be serialised by the caller.  Every
+ * call looks up the array's device address (a lookup, not an allocation).
+ * The first call in each CUDA context also uploads the lattice constants (a
+ * synchronous copy), so make it before any stream capture; after a device
+ * reset the next call sees the new context and uploads them again.  With
+ * lazy module loading (the CUDA default) the driver loads this library's
+ * device code, and so places the array, at that first call: a caller that
+ * later reserves all free device memory should make one call first (a 1 x 1
+ * grid will do).  No cudaMalloc, cudaFree or allocating library call is
+ * made.
  *
  * Errors: POND_ERR_ARG (NULL pointer, bad config, nx * ny above
  * POND_NOALLOC_MAX_NODES), POND_ERR_CUDA, and with stats given
@@ -257,6 +263,25 @@ pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx, int32_t n
                                    const double* T_in, double* f_out, double* ux_out,
                                    double* uy_out, double* T_out, int32_t* iters,
                                    pond_stats* stats, void* cuda_stream);
+
+/* Arithmetic pipes pond_measure_peak can time. */
+enum { POND_PIPE_FP64 = 0, POND_PIPE_FP32 = 1, POND_PIPE_FP32X2 = 2 };
+
+/* Measurement utility; the paper has no counterpart.  The PonD step is
+ * bound by plain FMA arithmetic (FP64 pipe for the FP64 form, FP32 pipe for
+ * the mixed form), so its roofline denominators are FMA rates.  This times
+ * one launch (after a warm-up launch) of a kernel in which every thread of
+ * a grid of (SM count x resident CTAs per SM) CTAs of 256 threads runs eight
+ * independent FMA chains for iters x 16 steps, on the current device and
+ * cuda_stream, and returns the rate in *tflops (2 flops per FMA; the packed
+ * POND_PIPE_FP32X2 form, fma.rn.f32x2, counts two FMAs per instruction) and
+ * the launch time in *seconds (may be NULL).  sink is a device buffer of at
+ * least 8 bytes that is never written in practice (it keeps the chains
+ * alive).  Synchronises the stream.
+ * Errors: POND_ERR_ARG (NULL tflops or sink, iters < 1, unknown pipe),
+ * POND_ERR_CUDA. */
+pond_status pond_measure_peak(int32_t pipe, int32_t iters, void* sink, void* cuda_stream,
+                              double* tflops, double* seconds);
 
 void pond_destroy(pond_ctx* ctx);
 

@@ -29,6 +29,8 @@
 // pass's populations re-expressed in the gauge their moments define (so the
 // stored gauge is exactly their co-moving frame), and finally the BGK
 // relaxation f + 2 beta (rho W - f) (Eq. postcollision).
+#include <cuda.h>
+
 #include <mutex>
 
 #include "pond_device.cuh"
@@ -586,26 +588,61 @@ __global__ void k_noalloc_st_to_t(const double* __restrict__ st, double* __restr
     }
 }
 
+static_assert(sizeof(DevStats) <= 256 && alignof(DevStats) <= 256,
+              "the step counters must fit the 256-byte tail of the scratch array");
+static_assert(kNoAllocStatsOffset % 256 == 0, "the counters' tail must stay 256-byte aligned");
+
 namespace {
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[256] = {nullptr};  // device address of the scratch, per device
+// per device: id of the context whose constant bank holds the lattice
+unsigned long long g_noalloc_ctx[256] = {0};
+
+// Unique id of the calling thread's current context (0 if it cannot be
+// read).  A device reset or a released and re-created primary context gives
+// a new id, which tells the set-up below to upload the constants again.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                             nullptr) == cudaSuccess)
+            get_current = reinterpret_cast<GetCurrent>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault,
+                                             nullptr) == cudaSuccess)
+            get_id = reinterpret_cast<GetId>(p);
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c ||
+        get_id(c, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 }  // namespace
 
-// Once per device, with that device current: the device address of the
-// scratch array (its name in host code is only a host-side stand-in) and the
-// lattice constants of this translation unit.
+// Every call, with the device current: the device address of the scratch
+// array (its name in host code is only a host-side stand-in; the lookup
+// allocates nothing, but on the first call in a context it may make the
+// driver load this module, which places the array), and, once per context,
+// the lattice constants of this translation unit (a synchronous copy).
 static cudaError_t noalloc_setup(int dev, unsigned char** out) {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    const unsigned long long id = current_context_id();
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (id == 0 || g_noalloc_ctx[dev] != id) {
         e = upload_lattice_fp64();
         if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
+        g_noalloc_ctx[dev] = id;
     }
-    *out = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    *out = static_cast<unsigned char*>(p);
     return cudaSuccess;
 }
 

@@ -32,6 +32,9 @@ POND_FP64 = 0
 POND_FP32_MIXED = 1
 POND_D2Q16 = 0
 POND_D2Q9 = 1
+POND_PIPE_FP64 = 0
+POND_PIPE_FP32 = 1
+POND_PIPE_FP32X2 = 2
 N_SPEEDS = {POND_D2Q16: 4, POND_D2Q9: 3}  # speeds per dimension; Q = n1^2
 
 _STATUS = {0: "POND_OK", 1: "POND_ERR_ARG", 2: "POND_ERR_OOM", 3: "POND_ERR_CUDA",
@@ -88,7 +91,7 @@ _LIB = None
 EXPORTS = ["pond_config_default", "pond_create", "pond_set_stream", "pond_set_state",
            "pond_step", "pond_moments", "pond_get_state", "pond_iterations",
            "pond_adjoint_step", "pond_adjoint_step_given", "pond_adjoint_init",
-           "pond_step_fp64_noalloc", "pond_destroy",
+           "pond_step_fp64_noalloc", "pond_measure_peak", "pond_destroy",
            "pond_last_error", "pond_version"]
 
 POND_NOALLOC_MAX_NODES = 262144
@@ -141,6 +144,9 @@ def load(build_if_missing: bool = True, path: str | None = None):
                                            vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(pond_stats), vp]
     lib.pond_step_fp64_noalloc.restype = i32
+    lib.pond_measure_peak.argtypes = [i32, i32, vp, vp, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
+    lib.pond_measure_peak.restype = i32
     lib.pond_destroy.argtypes = [vp]
     lib.pond_destroy.restype = None
     lib.pond_last_error.argtypes = [vp]
@@ -280,10 +286,56 @@ def pond_adjoint_init(ctx, f_bar, rho_bar):
     _check(ctx, load().pond_adjoint_init(ctx, *[p for p, _ in ps]))
 
 
+def _check_noalloc_args(cfg, f_in, ux_in, uy_in, T_in, f_out, ux_out, uy_out, T_out, iters):
+    """The C entry point trusts its pointers (it has no context that knows the
+    grid), so the binding checks what the header requires before the call:
+    float64 populations of shape (Q, ny, nx) with Q from cfg.lattice,
+    float64 (ny, nx) gauges, an int32 (ny, nx) iteration map or None, all
+    contiguous CUDA tensors on the current device.  Raises ValueError or
+    TypeError; nothing reaches the GPU when a check fails."""
+    import torch
+    n1 = N_SPEEDS.get(int(cfg.lattice))
+    if n1 is None:
+        raise ValueError("unknown lattice %d" % int(cfg.lattice))
+    named = [("f_in", f_in), ("ux_in", ux_in), ("uy_in", uy_in), ("T_in", T_in),
+             ("f_out", f_out), ("ux_out", ux_out), ("uy_out", uy_out), ("T_out", T_out)]
+    for name, a in named + [("iters", iters)]:
+        if name == "iters" and a is None:
+            continue
+        if not isinstance(a, torch.Tensor):
+            raise TypeError("%s must be a torch tensor" % name)
+        if not a.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if ux_in.dim() != 2:
+        raise ValueError("ux_in must be (ny, nx), got %s" % (tuple(ux_in.shape),))
+    ny, nx = ux_in.shape
+    for name, a in named:
+        want = (n1 * n1, ny, nx) if name.startswith("f_") else (ny, nx)
+        if tuple(a.shape) != want:
+            raise ValueError("%s has shape %s; the lattice and grid need %s"
+                             % (name, tuple(a.shape), want))
+        if a.dtype != torch.float64:
+            raise TypeError("%s must be float64, got %s" % (name, a.dtype))
+    if iters is not None:
+        if tuple(iters.shape) != (ny, nx):
+            raise ValueError("iters has shape %s; the grid needs %s" % (tuple(iters.shape), (ny, nx)))
+        if iters.dtype != torch.int32:
+            raise TypeError("iters must be int32, got %s" % iters.dtype)
+    arrays = [a for _, a in named] + ([iters] if iters is not None else [])
+    if not all(a.is_cuda for a in arrays):
+        raise ValueError("pond_step_fp64_noalloc takes CUDA tensors only")
+    cur = torch.cuda.current_device()
+    for name, a in named + [("iters", iters)]:
+        if a is not None and a.device.index != cur:
+            raise ValueError("%s is on cuda:%d but the current device is cuda:%d"
+                             % (name, a.device.index, cur))
+
+
 def pond_step_fp64_noalloc(cfg, f_in, ux_in, uy_in, T_in, f_out, ux_out, uy_out, T_out,
                            iters=None, want_stats=True, stream=None):
     """One FP64 step without a context or any allocation (CUDA float64
     tensors; see include/pond.h).  Returns the step counters."""
+    _check_noalloc_args(cfg, f_in, ux_in, uy_in, T_in, f_out, ux_out, uy_out, T_out, iters)
     ny, nx = ux_in.shape
     ps = [_ptr(a, True) for a in (f_in, ux_in, uy_in, T_in, f_out, ux_out, uy_out, T_out, iters)]
     stats = pond_stats()
@@ -293,6 +345,20 @@ def pond_step_fp64_noalloc(cfg, f_in, ux_in, uy_in, T_in, f_out, ux_out, uy_out,
     if st != POND_OK:
         raise PondError(st, "pond_step_fp64_noalloc failed")
     return stats.as_dict() if want_stats else None
+
+
+def pond_measure_peak(pipe: int, iters: int, sink, stream=None):
+    """(TFLOP/s, seconds) of the FMA-chain probe of one arithmetic pipe
+    (POND_PIPE_FP64, POND_PIPE_FP32, POND_PIPE_FP32X2) on the current device;
+    ``sink`` is a CUDA tensor of at least 8 bytes."""
+    tf = ctypes.c_double(0.0)
+    secs = ctypes.c_double(0.0)
+    st = load().pond_measure_peak(int(pipe), int(iters), ctypes.c_void_p(sink.data_ptr()),
+                                  ctypes.c_void_p(stream or 0), ctypes.byref(tf),
+                                  ctypes.byref(secs))
+    if st != POND_OK:
+        raise PondError(st, "pond_measure_peak failed")
+    return tf.value, secs.value
 
 
 def pond_destroy(ctx):

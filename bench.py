@@ -49,6 +49,26 @@ BYTES_MIXED = 2 * (16 * 4 + 3 * 8)
 FLOP_PER_PASS_Q9 = 144 * 68 + 9 * 20 + 72
 BYTES_FP64_Q9 = 2 * (9 * 8 + 3 * 8)
 BYTES_MIXED_Q9 = 2 * (9 * 4 + 3 * 8)
+# The reference-gauge staged kernel (the default) does less arithmetic per
+# pass: the sources are re-expressed once per step in the tile's reference
+# gauge, and each pass, for every x-speed index k, sweeps the rows of the
+# union of the n1 y-stencils: per row, 4 sources x n1 x n1 FMAs of the x
+# interpolation, n1 x n1 of the x-map and n1 x n1 of the row's contribution
+# to the n1 populations (k, l).  The rows per sweep are 4 + (c_max - c_min)
+# sqrt(theta) on average (the spread of the y-departures plus the stencil).
+# Per (node, k) add the x-map's Taylor entries (5 n1 ops), the departure and
+# cubic weights (20), the y-map applied after the sweep (n1 x 6 n1 FMAs) and
+# the moments (8 n1); per pass the y-departures (20 n1) and the gauge update
+# (40).  The once-per-step staging (~500 flops per staged source) is left
+# out: the count is the per-pass work alone, so the fraction is a lower bound.
+def staged_flops_per_pass(n1: int, st_mean: float) -> float:
+    spread = 2 * 2.3344142183389773 if n1 == 4 else 2.0
+    rows = 4.0 + spread * st_mean
+    per_row = 2 * (4 * n1 * n1 + n1 * n1 + n1 * n1)
+    per_k = per_row * rows + 2 * 5 * n1 + 20 + n1 * 2 * 6 * n1 + 8 * n1
+    return n1 * per_k + 20 * n1 + 40
+
+
 # Nominal peaks of the arithmetic pipes at the 2070 MHz maximum SM clock
 # (FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 flops x 2.07 GHz).  The
 # roofline uses the rates the FMA-chain probe (pond_measure_peak) measures

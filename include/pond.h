@@ -66,6 +66,9 @@ enum { POND_FP64 = 0, POND_FP32_MIXED = 1 };
 /* Lattices (pond_config.lattice). */
 enum { POND_D2Q16 = 0, POND_D2Q9 = 1 };
 
+/* Step kernels (pond_config.kernel). */
+enum { POND_KERNEL_DEFAULT = 0, POND_KERNEL_STAGED = 1, POND_KERNEL_DIRECT = 2 };
+
 /* Run configuration.  Fill with pond_config_default() and override. */
 typedef struct pond_config {
     int32_t precision;  /* POND_FP64: all arithmetic and storage FP64.
@@ -93,19 +96,20 @@ typedef struct pond_config {
     int32_t use_graph;  /* 1: pond_step replays a CUDA graph of two steps
                            (captured on first use, re-captured after
                            set_state / set_stream) */
-    int32_t autotune;   /* 1 (mixed form): the first pond_step times the
-                           kernel's tile shapes (32 x 4, 32 x 8, 32 x 16
-                           nodes, and 32 x 16 with two stacked nodes per
-                           thread) on the current state, without advancing it,
-                           and keeps the fastest.  Results are cached per
+    int32_t autotune;   /* 1 (tile kernels): the first pond_step times the
+                           kernel's tile shapes (see tile_rows) on the
+                           current state, without advancing it, and keeps
+                           the fastest.  Results are cached per
                            process by grid-set signature and, when the
                            environment variable POND_AUTOTUNE_CACHE names a
                            file, in that JSON file across processes. */
-    int32_t tile_rows;  /* mixed form: 0 = default tile (32 x 8 nodes) or the
-                           autotuner's choice; 4, 8 or 16 force a 32-wide tile
-                           of that many rows, -16 the 32 x 16 tile with two
-                           stacked nodes per thread (disables autotune;
-                           D2Q16 only). */
+    int32_t tile_rows;  /* tile kernels (the mixed form, and the FP64 form's
+                           staged kernel): 0 = default tile (32 x 8 nodes)
+                           or the autotuner's choice; 4, 8 or 16 force a
+                           32-wide tile of that many rows (16: mixed only),
+                           -16 the direct mixed kernel's 32 x 16 tile with
+                           two stacked nodes per thread (D2Q16 only); a
+                           forced shape disables autotune. */
     int32_t lattice;    /* POND_D2Q16 (default) or POND_D2Q9.  Fixes Q and
                            T_L (so the meaning of theta = T / T_L and of the
                            seed {0, T_L}). */
@@ -118,6 +122,25 @@ typedef struct pond_config {
                            (POND_ERR_ARG).  They agree to rounding (the
                            stencil rows and the moments are summed in other
                            orders). */
+    int32_t kernel;     /* POND_KERNEL_STAGED (and POND_KERNEL_DEFAULT): the
+                           reference-gauge staged tile kernel, both forms.
+                           Eq. transform composes, M_t^-1 M_s =
+                           (M_t^-1 M_r)(M_r^-1 M_s), and the reconstruction
+                           of Eq. interpolation is linear, so each CTA
+                           stages the sources its tile's stencils reach
+                           once per step, re-expressed in a reference
+                           gauge r (the tile's first node), and each pass
+                           reconstructs in r and applies one map r -> target
+                           per population: the same f_q up to rounding, with
+                           a quarter of the per-pass arithmetic.  Tile
+                           shapes 32 x 4 and 32 x 8 nodes (FP64), 32 x 4,
+                           32 x 8, 32 x 16 (mixed).
+                           POND_KERNEL_DIRECT: the per-(population, source)
+                           kernels, G(s -> t) for every stencil node of
+                           every population (FP64 mappings by
+                           nodes_per_warp; mixed tiles by tile_rows,
+                           including the paired -16 shape).
+                           Other values: POND_ERR_ARG. */
 } pond_config;
 
 /* Counters accumulated over the steps of one pond_step call. */
@@ -220,6 +243,45 @@ pond_status pond_adjoint_step_given(pond_ctx* ctx, const void* ux_out, const voi
  * gauge cotangents pass through unchanged: set_state stores u and T as given.)
  * Errors: POND_ERR_ARG, POND_ERR_CUDA. */
 pond_status pond_adjoint_init(pond_ctx* ctx, const void* f_bar, void* rho_bar);
+
+/* Domain decomposition (spatial split of one grid over several contexts,
+ * typically one per GPU).  Eq. advection reads only the state at t - dt, so
+ * a sub-domain whose grid carries a halo at least as wide as the largest
+ * displacement plus the stencil reach (max(|u| + c_max sqrt(theta)) dt + 2
+ * nodes) can advance its interior for one step independently, after the
+ * halo has been refreshed from its neighbours.  These calls give a context
+ * that interior, move halo strips in and out of its state, and bound the
+ * displacement.
+ *
+ * pond_set_interior: from now on pond_step updates only the rectangle
+ * [x0, x0 + w) x [y0, y0 + h) of grid `grid` (the nodes outside it are read
+ * as sources but not written; after a step they hold stale values until
+ * the caller refreshes them).  The staged kernel only (POND_ERR_ARG for the
+ * direct kernels or a rectangle outside the grid).  pond_stats.node_updates
+ * then counts interior nodes. */
+pond_status pond_set_interior(pond_ctx* ctx, int32_t grid, int32_t x0, int32_t y0, int32_t w,
+                              int32_t h);
+
+/* Copy the rectangle [x0, x0 + w) x [y0, y0 + h) of grid `grid`'s current
+ * state to (pack) or from (unpack) a device buffer of (Q + 3) * w * h FP64
+ * values: the Q population planes [Q][h][w], then u_x, u_y and
+ * sqrt(T / T_L), each [h][w].  This is the stored representation
+ * (populations widened exactly from FP32 in the mixed form, the gauge as
+ * stored), meant for another context of the same configuration: a state
+ * split over sub-domains and reassembled this way is bit-identical.  Work is
+ * enqueued on the context's stream; the call does not synchronise.
+ * Errors: POND_ERR_ARG (NULL buffer, rectangle outside the grid), POND_ERR_CUDA. */
+pond_status pond_pack_rect(pond_ctx* ctx, int32_t grid, int32_t x0, int32_t y0, int32_t w,
+                           int32_t h, void* buf);
+pond_status pond_unpack_rect(pond_ctx* ctx, int32_t grid, int32_t x0, int32_t y0, int32_t w,
+                             int32_t h, const void* buf);
+
+/* Bound of the displacement of any particle of grid `grid` in one step from
+ * the current state: max over nodes of (|u_x| or |u_y|) + c_max sqrt(theta),
+ * times dt, in nodes (computed in FP32 on the device; synchronises the
+ * stream).  A decomposition's halo must exceed this plus the stencil reach.
+ * Errors: POND_ERR_ARG, POND_ERR_STATE (grid never set), POND_ERR_CUDA. */
+pond_status pond_max_displacement(pond_ctx* ctx, int32_t grid, double* out);
 
 /* Largest grid (nx * ny) pond_step_fp64_noalloc accepts. */
 #define POND_NOALLOC_MAX_NODES 262144

@@ -578,9 +578,7 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
                                 a->fwd.st, N, ctx->L.T_L, s),
             "adjoint given gauge");
     } else {
-        ACK(launch_step_fp64(in, a->fwd, a->iters, a->stats, G.nx, G.ny, ctx->L, ctx->P,
-                             fp64_npw(ctx), s),
-            "adjoint forward");
+        ACK(launch_ctx_step_fp64(ctx, in, a->fwd, a->iters, a->stats), "adjoint forward");
     }
     // 2. velocity bounds for the transpose gather
     ACK(launch_minmax3(a->fwd.ux, a->fwd.uy, a->fwd.st, N, a->minmax, s), "adjoint bounds");

@@ -472,9 +472,7 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
         e = launch_gauge_from_T(out_gauge[0], out_gauge[1], out_gauge[2], a->fwd.ux, a->fwd.uy,
                                 a->fwd.st, N, ctx->L.T_L, s);
     else
-        e = launch_step_mixed(in, a->fwd, a->iters, a->stats, ctx->grids_dev,
-                              ctx->tile_prefix_dev, 1, ctx->n_tiles, N, nullptr, ctx->win,
-                              ctx->persistent_ctas, ctx->L, ctx->P, s);
+        e = launch_ctx_step_mixed(ctx, in, a->fwd, a->iters, a->stats);
     if (e != cudaSuccess) return e;
     const unsigned nb256 = (unsigned)((N + 255) / 256);
     k_split_gauge<<<nb256, 256, 0, s>>>(in.ux, in.uy, in.st, a->gin, N);

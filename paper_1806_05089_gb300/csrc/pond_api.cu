@@ -8,6 +8,8 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <iterator>
+#include <vector>
 
 #include "pond_internal.cuh"
 
@@ -49,6 +51,9 @@ pond_status cuda_fail(pond_ctx* c, cudaError_t e, const char* where) {
 
 bool mixed(const pond_ctx* c) { return c->cfg.precision == POND_FP32_MIXED; }
 
+// contexts whose step runs a tile kernel (windows, tile shapes, autotune)
+bool tiled(const pond_ctx* c) { return mixed(c) || ctx_staged(c); }
+
 size_t real_size(const pond_ctx* c) { return mixed(c) ? sizeof(float) : sizeof(double); }
 
 template <typename Real>
@@ -59,6 +64,11 @@ StateBuf<Real> buf(pond_ctx* c, int which, int64_t offset) {
     b.uy = c->uy[which] + offset;
     b.st = c->st[which] + offset;
     return b;
+}
+
+template <typename Real>
+StateBuf<Real> buf_of(pond_ctx* c, int which, int64_t offset) {
+    return buf<Real>(c, which, offset);
 }
 
 // Staging buffer for host-side input/output (20 FP64 fields of one grid).
@@ -88,7 +98,7 @@ pond_status set_tile_rows(pond_ctx* ctx, int code) {
     for (int g = 0; g < ctx->n_grids; ++g) {
         prefix[g] = tiles;
         const GridDesc& G = ctx->grids_host[g];
-        tiles += (int64_t)((G.nx + MIXED_TX - 1) / MIXED_TX) * ((G.ny + ty - 1) / ty);
+        tiles += (int64_t)((G.iw + MIXED_TX - 1) / MIXED_TX) * ((G.ih + ty - 1) / ty);
     }
     prefix[ctx->n_grids] = tiles;
     CK(cudaMemcpyAsync(ctx->tile_prefix_dev, prefix.data(), sizeof(int64_t) * (ctx->n_grids + 1),
@@ -102,7 +112,7 @@ pond_status set_tile_rows(pond_ctx* ctx, int code) {
 
 // Window of the mixed kernel from the per-grid velocity spans.
 pond_status update_window(pond_ctx* ctx) {
-    if (!mixed(ctx)) return POND_OK;
+    if (!tiled(ctx)) return POND_OK;
     float sx = 0.f, sy = 0.f;
     for (int g = 0; g < ctx->n_grids; ++g) {
         if (!ctx->grid_set[g]) continue;
@@ -116,18 +126,28 @@ pond_status update_window(pond_ctx* ctx) {
     w.ty = ctx->tile_ty;
     w.pair = ctx->tile_pair ? 1 : 0;
     w.n1 = ctx->L.n1;
+    w.staged = ctx_staged(ctx) ? 1 : 0;
+    w.real_bytes = mixed(ctx) ? 4 : 8;
     w.ww = w.tx + (int)std::ceil(sx * dt + 2 * margin) + 5;
     w.wh = w.ty + (int)std::ceil(sy * dt + 2 * margin) + 5;
     // cap the staged window at the shared memory a CTA can have; stencils
     // beyond it take the global-memory path
+    auto bytes = [](const TileWindow& v) {
+        return v.staged ? staged_window_bytes(v) : mixed_smem_bytes(v);
+    };
     const size_t cap = 220 * 1024;
-    while (mixed_smem_bytes(w) > cap) {
+    while (bytes(w) > cap) {
         if (w.ww - w.tx >= w.wh - w.ty) --w.ww; else --w.wh;
     }
-    const size_t smem = mixed_smem_bytes(w);
+    const size_t smem = bytes(w);
     int per_sm = 0;
-    CK(mixed_prepare(w.ty, w.pair != 0, w.n1, smem, &per_sm), "mixed kernel set-up");
-    if (per_sm < 1) return fail(ctx, POND_ERR_CUDA, "mixed kernel does not fit on an SM");
+    if (!w.staged)
+        CK(mixed_prepare(w.ty, w.pair != 0, w.n1, smem, &per_sm), "mixed kernel set-up");
+    else if (mixed(ctx))
+        CK(staged_prepare_mixed(w.ty, w.n1, smem, &per_sm), "staged kernel set-up");
+    else
+        CK(staged_prepare_fp64(w.ty, w.n1, smem, &per_sm), "staged kernel set-up");
+    if (per_sm < 1) return fail(ctx, POND_ERR_CUDA, "tile kernel does not fit on an SM");
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "SM count");
     ctx->win = w;
@@ -143,21 +163,47 @@ pond_status check_grid(pond_ctx* ctx, int32_t grid) {
 
 }  // namespace
 
+cudaError_t launch_ctx_step_fp64(pond_ctx* ctx, const StateBuf<double>& in,
+                                 const StateBuf<double>& out, int32_t* iters, DevStats* stats) {
+    if (ctx_staged(ctx))
+        return launch_step_staged_fp64(in, out, iters, stats, ctx->grids_dev, ctx->tile_prefix_dev,
+                                       ctx->n_grids, ctx->n_tiles, ctx->N,
+                                       ctx->n_grids > 1 ? ctx->work_counter : nullptr, ctx->win,
+                                       ctx->persistent_ctas, ctx->L, ctx->P, ctx->stream);
+    const GridDesc& G = ctx->grids_host[0];
+    return launch_step_fp64(in, out, iters, stats, G.nx, G.ny, ctx->L, ctx->P, fp64_npw(ctx),
+                            ctx->stream);
+}
+
+cudaError_t launch_ctx_step_mixed(pond_ctx* ctx, const StateBuf<float>& in,
+                                  const StateBuf<float>& out, int32_t* iters, DevStats* stats) {
+    unsigned int* counter = ctx->n_grids > 1 ? ctx->work_counter : nullptr;
+    if (ctx_staged(ctx))
+        return launch_step_staged_mixed(in, out, iters, stats, ctx->grids_dev, ctx->tile_prefix_dev,
+                                        ctx->n_grids, ctx->n_tiles, ctx->N, counter, ctx->win,
+                                        ctx->persistent_ctas, ctx->L, ctx->P, ctx->stream);
+    return launch_step_mixed(in, out, iters, stats, ctx->grids_dev, ctx->tile_prefix_dev,
+                             ctx->n_grids, ctx->n_tiles, ctx->N, counter, ctx->win,
+                             ctx->persistent_ctas, ctx->L, ctx->P, ctx->stream);
+}
+
+// one step from buffer `in` into buffer `out` with the context's kernel
+static pond_status launch_step_into(pond_ctx* ctx, int in, int out) {
+    if (mixed(ctx))
+        CK(launch_ctx_step_mixed(ctx, buf<float>(ctx, in, 0), buf<float>(ctx, out, 0), ctx->iters,
+                                 ctx->stats),
+           "mixed step launch");
+    else
+        CK(launch_ctx_step_fp64(ctx, buf<double>(ctx, in, 0), buf<double>(ctx, out, 0), ctx->iters,
+                                ctx->stats),
+           "fp64 step launch");
+    return POND_OK;
+}
+
 static pond_status launch_one_step(pond_ctx* ctx) {
     const int in = ctx->cur, out = 1 - ctx->cur;
-    if (mixed(ctx)) {
-        const bool batched = ctx->n_grids > 1;
-        CK(launch_step_mixed(buf<float>(ctx, in, 0), buf<float>(ctx, out, 0), ctx->iters,
-                             ctx->stats, ctx->grids_dev, ctx->tile_prefix_dev, ctx->n_grids,
-                             ctx->n_tiles, ctx->N, batched ? ctx->work_counter : nullptr,
-                             ctx->win, ctx->persistent_ctas, ctx->L, ctx->P, ctx->stream),
-           "mixed step launch");
-    } else {
-        const GridDesc& G = ctx->grids_host[0];
-        CK(launch_step_fp64(buf<double>(ctx, in, 0), buf<double>(ctx, out, 0), ctx->iters,
-                            ctx->stats, G.nx, G.ny, ctx->L, ctx->P, fp64_npw(ctx), ctx->stream),
-           "fp64 step launch");
-    }
+    pond_status s = launch_step_into(ctx, in, out);
+    if (s != POND_OK) return s;
     ctx->cur = out;
     return POND_OK;
 }
@@ -290,15 +336,32 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
     if (cfg->tile_rows != 0 && cfg->tile_rows != 4 && cfg->tile_rows != 8 && cfg->tile_rows != 16 &&
         cfg->tile_rows != -16)
         return POND_ERR_ARG;
+    if (cfg->kernel < POND_KERNEL_DEFAULT || cfg->kernel > POND_KERNEL_DIRECT) return POND_ERR_ARG;
     if (cfg->lattice != POND_D2Q16 && cfg->lattice != POND_D2Q9) return POND_ERR_ARG;
     if (!pond::fp64_npw_valid(cfg->nodes_per_warp, cfg->lattice)) return POND_ERR_ARG;
     if (cfg->lattice == POND_D2Q9 && cfg->tile_rows < 0) return POND_ERR_ARG;  // paired: D2Q16
     for (int g = 0; g < n_grids; ++g)
         if (nx[g] < 1 || ny[g] < 1) return POND_ERR_ARG;
 
+    // the default kernel is the staged one, except where the config asks for
+    // a shape or mapping only the direct kernels have (the paired tile, an
+    // FP64 nodes-per-warp mapping)
+    int kernel = cfg->kernel;
+    if (kernel == POND_KERNEL_DEFAULT)
+        kernel = (cfg->tile_rows == -16 ||
+                  (cfg->precision == POND_FP64 && cfg->nodes_per_warp != 0))
+                     ? POND_KERNEL_DIRECT
+                     : POND_KERNEL_STAGED;
+    if (kernel == POND_KERNEL_STAGED &&
+        (cfg->tile_rows < 0 || (cfg->precision == POND_FP64 && cfg->tile_rows == 16)))
+        return POND_ERR_ARG;
+    if (kernel == POND_KERNEL_DIRECT && cfg->precision == POND_FP64 && cfg->tile_rows != 0)
+        return POND_ERR_ARG;  // the direct FP64 kernels have no tiles
+
     pond_ctx* ctx = new (std::nothrow) pond_ctx();
     if (!ctx) return POND_ERR_OOM;
     ctx->cfg = *cfg;
+    ctx->cfg.kernel = kernel;
     ctx->L = make_lattice(cfg->lattice);
     ctx->P.beta = 1.0 / (2.0 * cfg->nu / (cfg->T_ref * cfg->dt) + 1.0);
     ctx->P.dt = cfg->dt;
@@ -321,6 +384,10 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
         d.nx = nx[g];
         d.ny = ny[g];
         d.offset = off;
+        d.ix0 = 0;
+        d.iy0 = 0;
+        d.iw = nx[g];
+        d.ih = ny[g];
         ctx->grids_host.push_back(d);
         off += (int64_t)nx[g] * ny[g];
         prefix[g] = tiles;
@@ -328,6 +395,7 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
     }
     prefix[n_grids] = tiles;
     ctx->N = off;
+    ctx->N_active = off;
     ctx->n_tiles = tiles;
 
     pond_status st = POND_OK;
@@ -378,8 +446,9 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
         pond_destroy(ctx);
         return st == POND_OK ? POND_ERR_CUDA : st;
     }
-    if (mixed(ctx)) {
-        st = set_tile_rows(ctx, cfg->tile_rows ? cfg->tile_rows : MIXED_TY);
+    if (tiled(ctx)) {
+        const int ty0 = mixed(ctx) ? MIXED_TY : STAGED_TY_FP64[0];
+        st = set_tile_rows(ctx, cfg->tile_rows ? cfg->tile_rows : ty0);
         if (cfg->tile_rows) ctx->tuned = true;  // a forced shape is not retuned
         if (st != POND_OK) {
             pond_destroy(ctx);
@@ -512,7 +581,8 @@ std::string tune_key(const pond_ctx* ctx) {
         sy = std::fmax(sy, ctx->spans[4 * g + 3] - ctx->spans[4 * g + 2]);
     }
     char buf[256];
-    std::snprintf(buf, sizeof buf, "mixed|q%d|grids=%d|nodes=%lld|side=%lld-%lld|span=%d-%d",
+    std::snprintf(buf, sizeof buf, "%s|%s|q%d|grids=%d|nodes=%lld|side=%lld-%lld|span=%d-%d",
+                  mixed(ctx) ? "mixed" : "fp64", ctx_staged(ctx) ? "staged" : "direct",
                   ctx->L.q, ctx->n_grids, (long long)ctx->N, (long long)minside,
                   (long long)maxside, (int)std::ceil(sx), (int)std::ceil(sy));
     return buf;
@@ -562,16 +632,6 @@ void tune_file_store() {
 }
 }  // namespace
 
-static pond_status launch_step_into(pond_ctx* ctx, int in, int out) {
-    const bool batched = ctx->n_grids > 1;
-    CK(launch_step_mixed(buf<float>(ctx, in, 0), buf<float>(ctx, out, 0), ctx->iters, ctx->stats,
-                         ctx->grids_dev, ctx->tile_prefix_dev, ctx->n_grids, ctx->n_tiles, ctx->N,
-                         batched ? ctx->work_counter : nullptr, ctx->win, ctx->persistent_ctas,
-                         ctx->L, ctx->P, ctx->stream),
-       "mixed step launch");
-    return POND_OK;
-}
-
 static pond_status autotune(pond_ctx* ctx) {
     const std::string key = tune_key(ctx);
     {
@@ -591,8 +651,16 @@ static pond_status autotune(pond_ctx* ctx) {
     float best_ms = 1e30f;
     int best = ctx->tile_pair ? -ctx->tile_ty : ctx->tile_ty;
     pond_status s = POND_OK;
-    for (int ty : MIXED_TY_CHOICES) {
-        if (ty < 0 && ctx->L.n1 != 4) continue;  // the paired kernel is D2Q16-only
+    std::vector<int> choices;
+    if (!ctx_staged(ctx)) {
+        for (int ty : MIXED_TY_CHOICES)
+            if (ty > 0 || ctx->L.n1 == 4) choices.push_back(ty);  // paired: D2Q16 only
+    } else if (mixed(ctx)) {
+        choices.assign(std::begin(STAGED_TY_MIXED), std::end(STAGED_TY_MIXED));
+    } else {
+        choices.assign(std::begin(STAGED_TY_FP64), std::end(STAGED_TY_FP64));
+    }
+    for (int ty : choices) {
         s = set_tile_rows(ctx, ty);
         if (s == POND_OK) s = update_window(ctx);
         if (s != POND_OK) break;
@@ -632,7 +700,7 @@ pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats) {
     for (int g = 0; g < ctx->n_grids; ++g)
         if (!ctx->grid_set[g]) return fail(ctx, POND_ERR_STATE, "pond_step before pond_set_state");
     DeviceGuard dg(ctx->device);
-    if (ctx->cfg.autotune && mixed(ctx) && !ctx->tuned && nsteps > 0) {
+    if (ctx->cfg.autotune && tiled(ctx) && !ctx->tuned && nsteps > 0) {
         pond_status s = autotune(ctx);
         if (s != POND_OK) return s;
         drop_graphs(ctx);
@@ -657,10 +725,10 @@ pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats) {
            "D2H stats");
         CK(cudaStreamSynchronize(ctx->stream), "step sync");
         const DevStats& d = *ctx->stats_host;
-        stats->node_updates = (int64_t)nsteps * ctx->N;
+        stats->node_updates = (int64_t)nsteps * ctx->N_active;
         stats->passes = (int64_t)d.passes;
         stats->max_passes = (int32_t)d.max_passes;
-        stats->tile_rows = mixed(ctx) ? (ctx->tile_pair ? -ctx->tile_ty : ctx->tile_ty) : 0;
+        stats->tile_rows = tiled(ctx) ? (ctx->tile_pair ? -ctx->tile_ty : ctx->tile_ty) : 0;
         stats->nonconverged = (int64_t)d.nonconverged;
         stats->nonphysical = (int64_t)d.nonphysical;
         stats->halo_fallback = (int64_t)d.halo_fallback;
@@ -692,6 +760,88 @@ pond_status pond_iterations(pond_ctx* ctx, int32_t grid, void* iters, int32_t on
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream),
        "copy iters");
     if (!on_device) CK(cudaStreamSynchronize(ctx->stream), "iters sync");
+    return POND_OK;
+}
+
+pond_status pond_set_interior(pond_ctx* ctx, int32_t grid, int32_t x0, int32_t y0, int32_t w,
+                              int32_t h) {
+    pond_status s = check_grid(ctx, grid);
+    if (s != POND_OK) return s;
+    if (!ctx_staged(ctx)) return fail(ctx, POND_ERR_ARG, "set_interior: staged kernel only");
+    GridDesc& G = ctx->grids_host[grid];
+    if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || (int64_t)x0 + w > G.nx || (int64_t)y0 + h > G.ny)
+        return fail(ctx, POND_ERR_ARG, "set_interior: rectangle outside the grid");
+    DeviceGuard dg(ctx->device);
+    G.ix0 = x0;
+    G.iy0 = y0;
+    G.iw = w;
+    G.ih = h;
+    CK(cudaMemcpyAsync(ctx->grids_dev + grid, &G, sizeof(GridDesc), cudaMemcpyHostToDevice,
+                       ctx->stream),
+       "interior upload");
+    CK(cudaStreamSynchronize(ctx->stream), "interior sync");
+    s = set_tile_rows(ctx, ctx->tile_pair ? -ctx->tile_ty : ctx->tile_ty);
+    if (s != POND_OK) return s;
+    ctx->N_active = 0;
+    for (const GridDesc& d : ctx->grids_host) ctx->N_active += (int64_t)d.iw * d.ih;
+    drop_graphs(ctx);
+    return POND_OK;
+}
+
+static pond_status rect_io(pond_ctx* ctx, int32_t grid, int32_t x0, int32_t y0, int32_t w,
+                           int32_t h, double* buf, bool pack) {
+    pond_status s = check_grid(ctx, grid);
+    if (s != POND_OK) return s;
+    if (!buf) return fail(ctx, POND_ERR_ARG, "rect: NULL buffer");
+    const GridDesc& G = ctx->grids_host[grid];
+    if (x0 < 0 || y0 < 0 || w < 0 || h < 0 || (int64_t)x0 + w > G.nx || (int64_t)y0 + h > G.ny)
+        return fail(ctx, POND_ERR_ARG, "rect: rectangle outside the grid");
+    DeviceGuard dg(ctx->device);
+    const int q = ctx->L.q;
+    if (mixed(ctx)) {
+        StateBuf<float> b = buf_of<float>(ctx, ctx->cur, G.offset);
+        CK(pack ? launch_pack_rect<float>(b, G.nx, x0, y0, w, h, q, ctx->N, buf, ctx->stream)
+                : launch_unpack_rect<float>(b, G.nx, x0, y0, w, h, q, ctx->N, buf, ctx->stream),
+           "rect copy");
+    } else {
+        StateBuf<double> b = buf_of<double>(ctx, ctx->cur, G.offset);
+        CK(pack ? launch_pack_rect<double>(b, G.nx, x0, y0, w, h, q, ctx->N, buf, ctx->stream)
+                : launch_unpack_rect<double>(b, G.nx, x0, y0, w, h, q, ctx->N, buf, ctx->stream),
+           "rect copy");
+    }
+    return POND_OK;
+}
+
+pond_status pond_pack_rect(pond_ctx* ctx, int32_t grid, int32_t x0, int32_t y0, int32_t w,
+                           int32_t h, void* buf) {
+    return rect_io(ctx, grid, x0, y0, w, h, static_cast<double*>(buf), true);
+}
+
+pond_status pond_unpack_rect(pond_ctx* ctx, int32_t grid, int32_t x0, int32_t y0, int32_t w,
+                             int32_t h, const void* buf) {
+    return rect_io(ctx, grid, x0, y0, w, h, const_cast<double*>(static_cast<const double*>(buf)),
+                   false);
+}
+
+pond_status pond_max_displacement(pond_ctx* ctx, int32_t grid, double* out) {
+    pond_status s = check_grid(ctx, grid);
+    if (s != POND_OK) return s;
+    if (!out) return fail(ctx, POND_ERR_ARG, "max_displacement: NULL output");
+    if (!ctx->grid_set[grid]) return fail(ctx, POND_ERR_STATE, "grid state never set");
+    DeviceGuard dg(ctx->device);
+    const GridDesc& G = ctx->grids_host[grid];
+    const int64_t n = (int64_t)G.nx * G.ny;
+    CK(launch_disp_bounds(ctx->ux[ctx->cur] + G.offset, ctx->uy[ctx->cur] + G.offset,
+                          ctx->st[ctx->cur] + G.offset, n, ctx->L.c_max, ctx->bounds_dev,
+                          ctx->stream),
+       "bounds");
+    float b4[4];
+    CK(cudaMemcpyAsync(b4, ctx->bounds_dev, sizeof b4, cudaMemcpyDeviceToHost, ctx->stream),
+       "D2H bounds");
+    CK(cudaStreamSynchronize(ctx->stream), "bounds sync");
+    double m = 0.0;
+    for (int i = 0; i < 4; ++i) m = std::fmax(m, std::fabs((double)b4[i]));
+    *out = m * ctx->cfg.dt;
     return POND_OK;
 }
 

@@ -211,6 +211,63 @@ __global__ void k_bounds_reset(unsigned int* v) {
     if (i < 4) v[i] = (i & 1) ? 0u : 0xffffffffu;
 }
 
+// Halo strips of a domain decomposition: a rectangle of the state to or from
+// a contiguous device buffer.  The stored representation moves unchanged
+// (populations widened to FP64 exactly, the gauge as stored), so a state
+// split over sub-domains and reassembled is bit-identical.
+template <typename Real>
+__global__ void k_pack_rect(StateBuf<Real> st, int nx, int x0, int y0, int w, int h, int q,
+                            long long plane, double* __restrict__ buf) {
+    const long long n = (long long)w * h;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long node = (long long)(y0 + i / w) * nx + x0 + i % w;
+    for (int c = 0; c < q; ++c) buf[c * n + i] = (double)st.f[c * plane + node];
+    buf[q * n + i] = st.ux[node];
+    buf[(q + 1) * n + i] = st.uy[node];
+    buf[(q + 2) * n + i] = st.st[node];
+}
+
+template <typename Real>
+__global__ void k_unpack_rect(StateBuf<Real> st, int nx, int x0, int y0, int w, int h, int q,
+                              long long plane, const double* __restrict__ buf) {
+    const long long n = (long long)w * h;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long node = (long long)(y0 + i / w) * nx + x0 + i % w;
+    for (int c = 0; c < q; ++c) st.f[c * plane + node] = (Real)buf[c * n + i];
+    st.ux[node] = buf[q * n + i];
+    st.uy[node] = buf[(q + 1) * n + i];
+    st.st[node] = buf[(q + 2) * n + i];
+}
+
+template <typename Real>
+cudaError_t launch_pack_rect(StateBuf<Real> st, int nx, int x0, int y0, int w, int h, int q,
+                             int64_t plane, double* buf, cudaStream_t s) {
+    const long long n = (long long)w * h;
+    if (n == 0) return cudaSuccess;
+    k_pack_rect<Real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(st, nx, x0, y0, w, h, q, plane, buf);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_unpack_rect(StateBuf<Real> st, int nx, int x0, int y0, int w, int h, int q,
+                               int64_t plane, const double* buf, cudaStream_t s) {
+    const long long n = (long long)w * h;
+    if (n == 0) return cudaSuccess;
+    k_unpack_rect<Real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(st, nx, x0, y0, w, h, q, plane, buf);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_pack_rect<double>(StateBuf<double>, int, int, int, int, int, int,
+                                              int64_t, double*, cudaStream_t);
+template cudaError_t launch_pack_rect<float>(StateBuf<float>, int, int, int, int, int, int,
+                                             int64_t, double*, cudaStream_t);
+template cudaError_t launch_unpack_rect<double>(StateBuf<double>, int, int, int, int, int, int,
+                                                int64_t, const double*, cudaStream_t);
+template cudaError_t launch_unpack_rect<float>(StateBuf<float>, int, int, int, int, int, int,
+                                               int64_t, const double*, cudaStream_t);
+
 cudaError_t launch_disp_bounds(const double* ux, const double* uy, const double* st, int64_t N,
                                double c_max, float* out4, cudaStream_t s) {
     unsigned int* o = reinterpret_cast<unsigned int*>(out4);

@@ -25,6 +25,19 @@ __device__ __forceinline__ void lagrange4f(float t, float l[4]) {
     l[3] = (ab * c) * (1.0f / 6.0f);
 }
 
+// The same weights at t = s + 3/2, from the centred coordinate s in
+// [-1/2, 1/2): the factors t - j are then s + 3/2, s + 1/2, s - 1/2, s - 3/2,
+// each within half an FP32 unit of [1/2, 2) of its exact value, instead of
+// carrying the rounding of t in [1, 2).
+__device__ __forceinline__ void lagrange4f_centred(float s, float l[4]) {
+    const float a = s + 1.5f, b = s + 0.5f, c = s - 0.5f, d = s - 1.5f;
+    const float cd = c * d, ab = a * b;
+    l[0] = -(b * cd) * (1.0f / 6.0f);
+    l[1] = (a * cd) * 0.5f;
+    l[2] = -(ab * d) * 0.5f;
+    l[3] = (ab * c) * (1.0f / 6.0f);
+}
+
 // One entry of the 1D gauge transform in Taylor form around the identity,
 // G[k][a] = id + de (d1 + d2 de (+ d3 de^2 on D2Q16, where L_k is cubic; on
 // D2Q9 L_k is quadratic and d3 = 0)).  gauge_tail is the bracket, G - I

@@ -90,6 +90,9 @@ struct GridDesc {
     int32_t nx;
     int32_t ny;
     int64_t offset;
+    // interior rectangle the step updates (the whole grid unless
+    // pond_set_interior narrowed it; staged kernel only)
+    int32_t ix0, iy0, iw, ih;
 };
 
 // Device state of one context: packed over all grids, plane stride = N.
@@ -139,6 +142,8 @@ struct TileWindow {
     int ww, wh;       // maximum staged window (tile + halo)
     int pair;         // 1: each thread owns two vertically adjacent nodes
     int n1;           // speeds per dimension of the lattice (4 or 3)
+    int staged;       // 1: the reference-gauge staged kernel
+    int real_bytes;   // 8 (FP64 form) or 4 (mixed form)
 };
 
 // Mixed-precision step over one or many grids (one CTA per tile; batched
@@ -149,6 +154,31 @@ cudaError_t launch_step_mixed(const StateBuf<float>& in, const StateBuf<float>& 
                               int64_t n_tiles, int64_t plane, unsigned int* work_counter,
                               const TileWindow& win, int persistent_ctas,
                               const Lattice& L, const StepParams& P, cudaStream_t s);
+
+// The reference-gauge staged kernel (pond_staged.cuh), FP64 and mixed
+// forms, over one or many grids (tiles 32 x ty; ty 4 or 8 in FP64, 4, 8 or
+// 16 in the mixed form), its per-device set-up (returns resident CTAs per SM
+// for a dynamic shared-memory size) and that size for a window.
+cudaError_t launch_step_staged_fp64(const StateBuf<double>& in, const StateBuf<double>& out,
+                                    int32_t* iters, DevStats* stats, const GridDesc* grids_dev,
+                                    const int64_t* tile_prefix_dev, int n_grids, int64_t n_tiles,
+                                    int64_t plane, unsigned int* work_counter,
+                                    const TileWindow& win, int persistent_ctas, const Lattice& L,
+                                    const StepParams& P, cudaStream_t s);
+cudaError_t launch_step_staged_mixed(const StateBuf<float>& in, const StateBuf<float>& out,
+                                     int32_t* iters, DevStats* stats, const GridDesc* grids_dev,
+                                     const int64_t* tile_prefix_dev, int n_grids, int64_t n_tiles,
+                                     int64_t plane, unsigned int* work_counter,
+                                     const TileWindow& win, int persistent_ctas, const Lattice& L,
+                                     const StepParams& P, cudaStream_t s);
+cudaError_t staged_prepare_fp64(int ty, int n1, size_t smem, int* ctas_per_sm);
+cudaError_t staged_prepare_mixed(int ty, int n1, size_t smem, int* ctas_per_sm);
+inline size_t staged_window_bytes(const TileWindow& w) {
+    return (size_t)w.n1 * w.ww * w.wh * 4 * w.real_bytes +
+           (size_t)w.n1 * w.n1 * w.tx * w.ty * w.real_bytes;
+}
+constexpr int STAGED_TY_FP64[2] = {4, 8};
+constexpr int STAGED_TY_MIXED[3] = {4, 8, 16};
 
 // Tile shape of the mixed kernel, its shared-memory need for a window, and
 // the per-device attribute set-up (returns resident CTAs per SM).
@@ -170,6 +200,16 @@ template <typename Real>
 cudaError_t launch_read_state(StateBuf<Real> st, int64_t N, int64_t plane, double* rho,
                               double* ux, double* uy, double* T, double* f,
                               const Lattice& L, cudaStream_t s);
+
+// Rectangle [x0, x0 + w) x [y0, y0 + h) of one grid's state to or from a
+// device buffer of FP64 planes [Q + 3][h][w]: f (in its stored precision,
+// widened exactly), u_x, u_y, sqrt(theta) (the stored gauge, bit for bit).
+template <typename Real>
+cudaError_t launch_pack_rect(StateBuf<Real> st, int nx, int x0, int y0, int w, int h, int q,
+                             int64_t plane, double* buf, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_unpack_rect(StateBuf<Real> st, int nx, int x0, int y0, int w, int h, int q,
+                               int64_t plane, const double* buf, cudaStream_t s);
 
 // max over nodes of (|u_x| + c_max st, |u_y| + c_max st) and spread bounds.
 cudaError_t launch_disp_bounds(const double* ux, const double* uy, const double* st,
@@ -195,6 +235,7 @@ struct pond_ctx {
     std::vector<pond::GridDesc> grids_host;
     std::vector<float> spans;  // per grid: {min vx, max vx, min vy, max vy}
     int64_t N = 0;  // total nodes
+    int64_t N_active = 0;  // nodes a step updates (the interiors)
     int cur = 0;    // index of the current state buffer
     void* f[2] = {nullptr, nullptr};
     double* ux[2] = {nullptr, nullptr};
@@ -223,6 +264,19 @@ struct pond_ctx {
     pond::AdjointScratch* adj = nullptr;
     pond::AdjMixedScratch* adjm = nullptr;
 };
+
+// the context runs the reference-gauge staged kernel
+inline bool ctx_staged(const pond_ctx* ctx) { return ctx->cfg.kernel != POND_KERNEL_DIRECT; }
+
+// One step of the context's configured kernel from `in` to `out` (used by
+// pond_step and by the adjoints' forward recomputation, so both run the
+// same arithmetic).
+cudaError_t launch_ctx_step_fp64(pond_ctx* ctx, const pond::StateBuf<double>& in,
+                                 const pond::StateBuf<double>& out, int32_t* iters,
+                                 pond::DevStats* stats);
+cudaError_t launch_ctx_step_mixed(pond_ctx* ctx, const pond::StateBuf<float>& in,
+                                  const pond::StateBuf<float>& out, int32_t* iters,
+                                  pond::DevStats* stats);
 
 // nodes per warp of the context's FP64 step kernel
 inline int fp64_npw(const pond_ctx* ctx) {

@@ -34,6 +34,7 @@
 #include <mutex>
 
 #include "pond_device.cuh"
+#include "pond_staged.cuh"
 
 namespace pond {
 
@@ -548,6 +549,221 @@ cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>&
     } else {
         if (npw == 2) k1_step_fp64<4, 2><<<nb, T, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
         else k1_step_fp64<4, 1><<<nb, T, 0, s>>>(in, out, iters, stats, nx, ny, N, P);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The reference-gauge staged kernel (pond_staged.cuh) in FP64: gauges,
+// populations and every product in FP64; the moments of a pass in central
+// form, as k1_step_fp64_node; plain BGK (Eq. postcollision).
+
+struct StagedFP64 {
+    using Real = double;
+    struct __align__(32) Real4 {
+        double x, y, z, w;
+    };
+    static constexpr bool kUnrollK = true;
+    template <int NT>
+    static constexpr int min_blocks() {
+        return NT >= 256 ? 1 : 2;
+    }
+    template <int N1>
+    static __device__ __forceinline__ const Lattice& lat() {
+        return c_L[lattice_slot(N1)];
+    }
+    static __device__ __forceinline__ void lagrange(double t, double (&l)[4]) { lagrange4(t, l); }
+    // floor of the displacement d and the cubic weights at t = d - floor + 1
+    static __device__ __forceinline__ void departure(double d, double& fl, double (&l)[4]) {
+        fl = floor(d);
+        lagrange4(d - fl + 1.0, l);
+    }
+    static __device__ __forceinline__ void load4(const Real4* p, double (&v)[4]) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = b.x;
+        v[3] = b.y;
+    }
+    static __device__ __forceinline__ void store4(Real4* p, const double (&v)[4]) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+    // Moments of the pass -> the next gauge (Eqs. conservation_*, central
+    // form: u_{n+1} = u_n + st sum c f / rho, 2 T_{n+1} = st^2 sum |c|^2 f /
+    // rho - |u_{n+1} - u_n|^2) and the App. E test.  Returns true when the
+    // node stops.
+    static __device__ __forceinline__ bool update(const StepParams& P, PassGauge& g, double m0,
+                                                  double m1, double m2, double m3) {
+        ++g.pass;
+        g.rho = m0;
+        const double ir = 1.0 / m0;
+        const double dux = g.st * m1 * ir, duy = g.st * m2 * ir;
+        const double ux1 = g.ux + dux, uy1 = g.uy + duy;
+        double st1 = g.st;
+        bool ok = (m0 > 0.0) && isfinite(ux1) && isfinite(uy1);
+        if (P.thermal) {
+            const double T1 = 0.5 * (g.st * g.st * m3 * ir - (dux * dux + duy * duy));
+            ok = ok && (T1 > 0.0) && isfinite(T1);
+            st1 = sqrt(T1 / P.T_L);
+        }
+        if (!ok) {
+            g.flag |= 2u;
+            return true;
+        }
+        g.nux = ux1;
+        g.nuy = uy1;
+        g.nst = st1;
+        const bool conv = fabs(ux1 - g.ux) < P.eps_abs + P.eps_rel * fabs(ux1) &&
+                          fabs(uy1 - g.uy) < P.eps_abs + P.eps_rel * fabs(uy1) &&
+                          fabs(st1 - g.st) < P.eps_abs + P.eps_rel * fabs(st1);
+        bool stop;
+        if (P.fixed_iter > 0) {
+            stop = g.pass >= P.fixed_iter;
+        } else {
+            stop = conv || g.pass >= P.max_iter;
+            if (!conv && g.pass >= P.max_iter) g.flag |= 1u;
+        }
+        if (!stop) {
+            g.ux = ux1;
+            g.uy = uy1;
+            g.st = st1;
+        }
+        return stop;
+    }
+    // The last pass's populations (this thread's s_acc column) re-expressed
+    // in the gauge their moments define (Eq. transform at the node, in
+    // correction form f + (G - I) f), then BGK toward rho W in that co-moving
+    // gauge (Eq. postcollision) and the store.  A node with non-physical
+    // moments keeps its populations and the gauge of its last pass.
+    template <int N1>
+    static __device__ void finish(const StagedArgs<double>& A, double* s_acc, int NT, int tid,
+                                  long long node, const PassGauge& g) {
+        constexpr int Q = N1 * N1;
+        const Lattice& L = lat<N1>();
+        double f[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) f[q] = s_acc[q * NT + tid];
+        double ux = g.ux, uy = g.uy, st = g.st;
+        if (!(g.flag & 2u)) {
+            // xi_a = c_a + c_a (st_n / st_{n+1} - 1) + (u_n - u_{n+1}) / st_{n+1}
+            const double inv1 = 1.0 / g.nst;
+            const double r = (g.st - g.nst) * inv1;
+            const double dx = (g.ux - g.nux) * inv1, dy = (g.uy - g.nuy) * inv1;
+            double ex[N1][N1], ey[N1][N1];
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                const double dex = fma(L.c[a], r, dx), dey = fma(L.c[a], r, dy);
+#pragma unroll
+                for (int k = 0; k < N1; ++k) {
+                    ex[k][a] = gauge_tail<N1>(L.d3[k], L.d2[k][a], L.d1[k][a], dex) * dex;
+                    ey[k][a] = gauge_tail<N1>(L.d3[k], L.d2[k][a], L.d1[k][a], dey) * dey;
+                }
+            }
+            double H[Q];
+#pragma unroll
+            for (int a = 0; a < N1; ++a)
+#pragma unroll
+                for (int l = 0; l < N1; ++l) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) v = fma(ey[l][b], f[N1 * a + b], v);
+                    H[N1 * a + l] = v;
+                }
+            double o[Q];
+#pragma unroll
+            for (int k = 0; k < N1; ++k)
+#pragma unroll
+                for (int l = 0; l < N1; ++l) {
+                    double c = H[N1 * k + l];
+#pragma unroll
+                    for (int a = 0; a < N1; ++a) c = fma(ex[k][a], f[N1 * a + l] + H[N1 * a + l], c);
+                    o[N1 * k + l] = f[N1 * k + l] + c;
+                }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) f[q] = o[q];
+            ux = g.nux;
+            uy = g.nuy;
+            st = g.nst;
+        }
+        const double two_beta = 2.0 * A.P.beta;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const double feq = g.rho * L.w[q / N1] * L.w[q % N1];
+            A.out.f[q * A.plane + node] = f[q] + two_beta * (feq - f[q]);
+        }
+        A.out.ux[node] = ux;
+        A.out.uy[node] = uy;
+        A.out.st[node] = st;
+    }
+};
+
+template <int TY, int N1>
+static cudaError_t staged64_shape(size_t smem, int* per_sm, int* s_set) {
+    void (*kern)(StagedArgs<double>) = k_step_staged<StagedFP64, 32, TY, N1>;
+    if ((int)smem > *s_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        *s_set = (int)smem;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, 32 * TY, smem);
+}
+
+cudaError_t staged_prepare_fp64(int ty, int n1, size_t smem, int* ctas_per_sm) {
+    static int s_set[64][4] = {{0}};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const int slot = (n1 == 3 ? 2 : 0) + (ty == 8 ? 1 : 0);
+    if (ty != 4 && ty != 8) return cudaErrorInvalidValue;
+    if (n1 == 3)
+        return ty == 4 ? staged64_shape<4, 3>(smem, ctas_per_sm, &s_set[dev][slot])
+                       : staged64_shape<8, 3>(smem, ctas_per_sm, &s_set[dev][slot]);
+    return ty == 4 ? staged64_shape<4, 4>(smem, ctas_per_sm, &s_set[dev][slot])
+                   : staged64_shape<8, 4>(smem, ctas_per_sm, &s_set[dev][slot]);
+}
+
+cudaError_t launch_step_staged_fp64(const StateBuf<double>& in, const StateBuf<double>& out,
+                                    int32_t* iters, DevStats* stats, const GridDesc* grids_dev,
+                                    const int64_t* tile_prefix_dev, int n_grids, int64_t n_tiles,
+                                    int64_t plane, unsigned int* work_counter,
+                                    const TileWindow& win, int persistent_ctas, const Lattice& L,
+                                    const StepParams& P, cudaStream_t s) {
+    if (n_tiles == 0) return cudaSuccess;
+    if (win.n1 != L.n1 || (win.ty != 4 && win.ty != 8) || win.tx != 32) return cudaErrorInvalidValue;
+    StagedArgs<double> A{};
+    A.in = in;
+    A.out = out;
+    A.iters = iters;
+    A.stats = stats;
+    A.grids = grids_dev;
+    A.tile_prefix = tile_prefix_dev;
+    A.n_grids = n_grids;
+    A.n_tiles = n_tiles;
+    A.plane = plane;
+    A.work_counter = work_counter;
+    A.ww = win.ww;
+    A.wh = win.wh;
+    A.c_max = L.c_max;
+    A.margin = 1.0f;
+    A.P = P;
+    const size_t smem = staged_smem_bytes(L.n1, win.ww, win.wh, 32 * win.ty, sizeof(double));
+    unsigned int nb;
+    if (work_counter) {
+        cudaError_t e = cudaMemsetAsync(work_counter, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return e;
+        nb = (unsigned int)(persistent_ctas < n_tiles ? persistent_ctas : n_tiles);
+    } else {
+        nb = (unsigned int)n_tiles;
+    }
+    if (L.n1 == 3) {
+        if (win.ty == 4) k_step_staged<StagedFP64, 32, 4, 3><<<nb, 128, smem, s>>>(A);
+        else k_step_staged<StagedFP64, 32, 8, 3><<<nb, 256, smem, s>>>(A);
+    } else {
+        if (win.ty == 4) k_step_staged<StagedFP64, 32, 4, 4><<<nb, 128, smem, s>>>(A);
+        else k_step_staged<StagedFP64, 32, 8, 4><<<nb, 256, smem, s>>>(A);
     }
     return cudaGetLastError();
 }

@@ -25,6 +25,7 @@
 // CTAs take (grid, tile) work items from an atomic counter; the item -> grid
 // map is a prefix sum over the grids' tile counts.
 #include "pond_device.cuh"
+#include "pond_staged.cuh"
 
 namespace pond {
 
@@ -114,8 +115,8 @@ __device__ __noinline__ float stencil_global(const MixedArgs& A, const GridDesc&
 // that co-moving gauge (Eq. postcollision) and the store.  (r, dx, dy) are
 // the Taylor offsets of that transform: xi_a = c_a + c_a r + d.  Kept out of
 // line so the pass loop keeps its register budget.
-template <int N1>
-__device__ __noinline__ void finish_node(const MixedArgs& A, float* s_acc, int NT, int tid,
+template <int N1, class Args>
+__device__ __noinline__ void finish_node(const Args& A, float* s_acc, int NT, int tid,
                                          long long node, bool regauge, float r, float dx,
                                          float dy, double ux, double uy, double st, float rho) {
     constexpr int Q = N1 * N1;
@@ -939,6 +940,197 @@ __global__ void __launch_bounds__(TX* TY, 1) k2_step_mixed_pair(MixedArgs A) {
         if (s_np) atomicAdd(&A.stats->nonphysical, s_np);
         if (s_fb) atomicAdd(&A.stats->halo_fallback, s_fb);
     }
+}
+
+// ---------------------------------------------------------------------------
+// The reference-gauge staged kernel (pond_staged.cuh) in the mixed form: FP32
+// populations, staged sources and sweep; the gauge offsets of every map
+// formed from the FP64 gauges and rounded once; the moments and gauge
+// increments of a pass in FP32, accumulated into the FP64 gauge; the App. E
+// test in FP64; the exactly conservative FP32 collision of finish_node.
+
+struct StagedFP32 {
+    using Real = float;
+    using Real4 = float4;
+    static constexpr bool kUnrollK = false;
+    template <int NT>
+    static constexpr int min_blocks() {
+        return 512 / NT;
+    }
+    template <int N1>
+    static __device__ __forceinline__ const LatticeF& lat() {
+        return c_Lf[lattice_slot(N1)];
+    }
+    static __device__ __forceinline__ void lagrange(float t, float (&l)[4]) { lagrange4f(t, l); }
+    // floor of the displacement d and the cubic weights at its fraction,
+    // from the centred coordinate d - floor - 1/2, with the weight of the
+    // node nearest the departure point set to 1 minus the other three: the
+    // FP32 weights then sum to one to within one rounding, where each
+    // weight's own rounding would otherwise leave a sum off by a few units
+    // -- an error that an advected parcel, meeting the same departure
+    // fraction every step, would take on as a growth of its populations
+    // step after step.
+    static __device__ __forceinline__ void departure(float d, float& fl, float (&l)[4]) {
+        fl = floorf(d);
+        const float s = (d - fl) - 0.5f;
+        lagrange4f_centred(s, l);
+        if (s < 0.0f) l[1] = 1.0f - ((l[0] + l[2]) + l[3]);
+        else l[2] = 1.0f - ((l[0] + l[1]) + l[3]);
+    }
+    static __device__ __forceinline__ void load4(const float4* p, float (&v)[4]) {
+        const float4 a = *p;
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = a.z;
+        v[3] = a.w;
+    }
+    static __device__ __forceinline__ void store4(float4* p, const float (&v)[4]) {
+        *p = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    // FP32 moments -> FP32 increments of (u_x, u_y, sqrt(theta)) (central
+    // form of Eqs. conservation_*), added to the FP64 gauge; App. E test on
+    // the increments in FP64.
+    static __device__ __forceinline__ bool update(const StepParams& P, PassGauge& g, float m0,
+                                                  float m1, float m2, float m3) {
+        ++g.pass;
+        const float stf = (float)g.st;
+        const float invf = 1.0f / stf;
+        const float irf = 1.0f / m0;
+        const float dux = stf * m1 * irf, duy = stf * m2 * irf;
+        float dst = 0.0f;
+        bool ok = (m0 > 0.0f) && isfinite(dux) && isfinite(duy);
+        if (P.thermal) {
+            // theta_{n+1} / theta_n - 1
+            const float rm1 = (m3 * irf - (dux * dux + duy * duy) * invf * invf) *
+                                  (float)(0.5 / P.T_L) - 1.0f;
+            ok = ok && (rm1 > -1.0f) && isfinite(rm1);
+            dst = stf * rm1 / (sqrtf(1.0f + rm1) + 1.0f);
+        }
+        if (!ok) {
+            g.flag |= 2u;
+            g.rho = m0;
+            return true;
+        }
+        g.rho = m0;
+        const double ux1 = g.ux + (double)dux, uy1 = g.uy + (double)duy, st1 = g.st + (double)dst;
+        g.nux = ux1;
+        g.nuy = uy1;
+        g.nst = st1;
+        const bool conv = fabs((double)dux) < P.eps_abs + P.eps_rel * fabs(ux1) &&
+                          fabs((double)duy) < P.eps_abs + P.eps_rel * fabs(uy1) &&
+                          fabs((double)dst) < P.eps_abs + P.eps_rel * fabs(st1);
+        bool stop;
+        if (P.fixed_iter > 0) {
+            stop = g.pass >= P.fixed_iter;
+        } else {
+            stop = conv || g.pass >= P.max_iter;
+            if (!conv && g.pass >= P.max_iter) g.flag |= 1u;
+        }
+        if (!stop) {
+            g.ux = ux1;
+            g.uy = uy1;
+            g.st = st1;
+        }
+        return stop;
+    }
+    template <int N1>
+    static __device__ void finish(const StagedArgs<float>& A, float* s_acc, int NT, int tid,
+                                  long long node, const PassGauge& g) {
+        if (g.flag & 2u) {
+            // non-physical moments: keep the pass's populations and gauge
+            float r0 = 0.0f;
+#pragma unroll
+            for (int q = 0; q < N1 * N1; ++q) r0 += s_acc[q * NT + tid];
+            finish_node<N1>(A, s_acc, NT, tid, node, false, 0.0f, 0.0f, 0.0f, g.ux, g.uy, g.st, r0);
+        } else {
+            // re-gauge lambda_n -> lambda_{n+1}: xi_a = c_a + c_a r + d with
+            // r = st_n / st_{n+1} - 1, d = (u_n - u_{n+1}) / st_{n+1}
+            const double inv1 = 1.0 / g.nst;
+            finish_node<N1>(A, s_acc, NT, tid, node, true, (float)((g.st - g.nst) * inv1),
+                            (float)((g.ux - g.nux) * inv1), (float)((g.uy - g.nuy) * inv1), g.nux,
+                            g.nuy, g.nst, (float)g.rho);
+        }
+    }
+};
+
+template <int TY, int N1>
+static cudaError_t staged32_shape(size_t smem, int* per_sm, int* s_set) {
+    void (*kern)(StagedArgs<float>) = k_step_staged<StagedFP32, 32, TY, N1>;
+    if ((int)smem > *s_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        *s_set = (int)smem;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, 32 * TY, smem);
+}
+
+cudaError_t staged_prepare_mixed(int ty, int n1, size_t smem, int* ctas_per_sm) {
+    static int s_set[64][6] = {{0}};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const int t = ty == 4 ? 0 : ty == 8 ? 1 : ty == 16 ? 2 : -1;
+    if (t < 0) return cudaErrorInvalidValue;
+    int* set = &s_set[dev][(n1 == 3 ? 3 : 0) + t];
+    if (n1 == 3) {
+        if (ty == 4) return staged32_shape<4, 3>(smem, ctas_per_sm, set);
+        if (ty == 8) return staged32_shape<8, 3>(smem, ctas_per_sm, set);
+        return staged32_shape<16, 3>(smem, ctas_per_sm, set);
+    }
+    if (ty == 4) return staged32_shape<4, 4>(smem, ctas_per_sm, set);
+    if (ty == 8) return staged32_shape<8, 4>(smem, ctas_per_sm, set);
+    return staged32_shape<16, 4>(smem, ctas_per_sm, set);
+}
+
+cudaError_t launch_step_staged_mixed(const StateBuf<float>& in, const StateBuf<float>& out,
+                                     int32_t* iters, DevStats* stats, const GridDesc* grids_dev,
+                                     const int64_t* tile_prefix_dev, int n_grids, int64_t n_tiles,
+                                     int64_t plane, unsigned int* work_counter,
+                                     const TileWindow& win, int persistent_ctas, const Lattice& L,
+                                     const StepParams& P, cudaStream_t s) {
+    if (n_tiles == 0) return cudaSuccess;
+    if (win.n1 != L.n1 || win.tx != 32 || (win.ty != 4 && win.ty != 8 && win.ty != 16))
+        return cudaErrorInvalidValue;
+    StagedArgs<float> A{};
+    A.in = in;
+    A.out = out;
+    A.iters = iters;
+    A.stats = stats;
+    A.grids = grids_dev;
+    A.tile_prefix = tile_prefix_dev;
+    A.n_grids = n_grids;
+    A.n_tiles = n_tiles;
+    A.plane = plane;
+    A.work_counter = work_counter;
+    A.ww = win.ww;
+    A.wh = win.wh;
+    A.c_max = L.c_max;
+    A.margin = 1.0f;
+    A.P = P;
+    const size_t smem = staged_smem_bytes(L.n1, win.ww, win.wh, 32 * win.ty, sizeof(float));
+    unsigned int nb;
+    if (work_counter) {
+        cudaError_t e = cudaMemsetAsync(work_counter, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return e;
+        nb = (unsigned int)(persistent_ctas < n_tiles ? persistent_ctas : n_tiles);
+    } else {
+        nb = (unsigned int)n_tiles;
+    }
+    if (L.n1 == 3) {
+        switch (win.ty) {
+            case 4: k_step_staged<StagedFP32, 32, 4, 3><<<nb, 128, smem, s>>>(A); break;
+            case 8: k_step_staged<StagedFP32, 32, 8, 3><<<nb, 256, smem, s>>>(A); break;
+            default: k_step_staged<StagedFP32, 32, 16, 3><<<nb, 512, smem, s>>>(A); break;
+        }
+    } else {
+        switch (win.ty) {
+            case 4: k_step_staged<StagedFP32, 32, 4, 4><<<nb, 128, smem, s>>>(A); break;
+            case 8: k_step_staged<StagedFP32, 32, 8, 4><<<nb, 256, smem, s>>>(A); break;
+            default: k_step_staged<StagedFP32, 32, 16, 4><<<nb, 512, smem, s>>>(A); break;
+        }
+    }
+    return cudaGetLastError();
 }
 
 size_t mixed_smem_bytes(const TileWindow& w) {

@@ -32,6 +32,9 @@ POND_FP64 = 0
 POND_FP32_MIXED = 1
 POND_D2Q16 = 0
 POND_D2Q9 = 1
+POND_KERNEL_DEFAULT = 0
+POND_KERNEL_STAGED = 1
+POND_KERNEL_DIRECT = 2
 POND_PIPE_FP64 = 0
 POND_PIPE_FP32 = 1
 POND_PIPE_FP32X2 = 2
@@ -67,6 +70,7 @@ class pond_config(ctypes.Structure):
         ("tile_rows", ctypes.c_int32),
         ("lattice", ctypes.c_int32),
         ("nodes_per_warp", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
     ]
 
 
@@ -91,7 +95,8 @@ _LIB = None
 EXPORTS = ["pond_config_default", "pond_create", "pond_set_stream", "pond_set_state",
            "pond_step", "pond_moments", "pond_get_state", "pond_iterations",
            "pond_adjoint_step", "pond_adjoint_step_given", "pond_adjoint_init",
-           "pond_step_fp64_noalloc", "pond_measure_peak", "pond_destroy",
+           "pond_step_fp64_noalloc", "pond_measure_peak", "pond_set_interior",
+           "pond_pack_rect", "pond_unpack_rect", "pond_max_displacement", "pond_destroy",
            "pond_last_error", "pond_version"]
 
 POND_NOALLOC_MAX_NODES = 262144
@@ -147,6 +152,14 @@ def load(build_if_missing: bool = True, path: str | None = None):
     lib.pond_measure_peak.argtypes = [i32, i32, vp, vp, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]
     lib.pond_measure_peak.restype = i32
+    lib.pond_set_interior.argtypes = [vp, i32, i32, i32, i32, i32]
+    lib.pond_set_interior.restype = i32
+    lib.pond_pack_rect.argtypes = [vp, i32, i32, i32, i32, i32, vp]
+    lib.pond_pack_rect.restype = i32
+    lib.pond_unpack_rect.argtypes = [vp, i32, i32, i32, i32, i32, vp]
+    lib.pond_unpack_rect.restype = i32
+    lib.pond_max_displacement.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
+    lib.pond_max_displacement.restype = i32
     lib.pond_destroy.argtypes = [vp]
     lib.pond_destroy.restype = None
     lib.pond_last_error.argtypes = [vp]
@@ -359,6 +372,37 @@ def pond_measure_peak(pipe: int, iters: int, sink, stream=None):
     if st != POND_OK:
         raise PondError(st, "pond_measure_peak failed")
     return tf.value, secs.value
+
+
+def pond_set_interior(ctx, grid, x0, y0, w, h):
+    _check(ctx, load().pond_set_interior(ctx, int(grid), int(x0), int(y0), int(w), int(h)))
+
+
+def _rect_buffer(buf, ctx_q, w, h):
+    import torch
+    if not isinstance(buf, torch.Tensor) or not buf.is_cuda or buf.dtype != torch.float64:
+        raise TypeError("rectangle buffers are CUDA float64 tensors")
+    if not buf.is_contiguous() or buf.numel() < (ctx_q + 3) * w * h:
+        raise ValueError("rectangle buffer needs (Q + 3) * w * h contiguous values")
+    return ctypes.c_void_p(buf.data_ptr())
+
+
+def pond_pack_rect(ctx, grid, x0, y0, w, h, buf, q=16):
+    """Rectangle of the current state into a CUDA float64 buffer of
+    (q + 3) * w * h values (q = populations of the context's lattice)."""
+    _check(ctx, load().pond_pack_rect(ctx, int(grid), int(x0), int(y0), int(w), int(h),
+                                      _rect_buffer(buf, q, w, h)))
+
+
+def pond_unpack_rect(ctx, grid, x0, y0, w, h, buf, q=16):
+    _check(ctx, load().pond_unpack_rect(ctx, int(grid), int(x0), int(y0), int(w), int(h),
+                                        _rect_buffer(buf, q, w, h)))
+
+
+def pond_max_displacement(ctx, grid=0) -> float:
+    out = ctypes.c_double(0.0)
+    _check(ctx, load().pond_max_displacement(ctx, int(grid), ctypes.byref(out)))
+    return out.value
 
 
 def pond_destroy(ctx):

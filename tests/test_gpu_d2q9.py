@@ -75,37 +75,47 @@ def rel_errors(g, grho, o, speed_scale=False):
     return e_rho, e_u, e_T, e_f
 
 
-@pytest.mark.parametrize("npw", [1, 2, 3, 32])
+# the direct FP64 kernel's mappings (nodes per warp 1, 2, 3, or one node per
+# thread) and the staged tile kernel's two shapes
+Q9_FP64 = {"npw1": {"nodes_per_warp": 1}, "npw2": {"nodes_per_warp": 2},
+           "npw3": {"nodes_per_warp": 3}, "node": {"nodes_per_warp": 32},
+           "staged_32x4": {"kernel": pond.POND_KERNEL_STAGED, "tile_rows": 4},
+           "staged_32x8": {"kernel": pond.POND_KERNEL_STAGED, "tile_rows": 8}}
+
+
+@pytest.mark.parametrize("kern", list(Q9_FP64))
 @pytest.mark.parametrize("name,nx,ny,steps", [("tg", 64, 64, 12), ("supersonic", 37, 29, 6),
                                               ("hot", 48, 40, 5), ("supersonic", 1, 1, 3),
                                               ("tg", 3, 5, 4), ("supersonic", 2, 7, 3)])
-def test_d2q9_fp64_fixed_passes_matches_oracle(name, nx, ny, steps, npw):
+def test_d2q9_fp64_fixed_passes_matches_oracle(name, nx, ny, steps, kern):
     fields = d2q9_fields(name, nx, ny)
-    g, grho, git, _ = gpu_run(fields, steps, fixed_iter=4, nodes_per_warp=npw)
+    g, grho, git, _ = gpu_run(fields, steps, fixed_iter=4, **Q9_FP64[kern])
     o, oit = oracle_run(fields, steps, fixed_iter=4)
     assert np.all(git == 4) and np.all(oit == 4)
     e = rel_errors(g, grho, o)
     assert max(e) <= TOL64, e
 
 
-@pytest.mark.parametrize("npw", [2, 3, 32])
+@pytest.mark.parametrize("kern", ["npw2", "npw3", "node", "staged_32x4", "staged_32x8"])
 @pytest.mark.parametrize("thermal", [1, 0])
-def test_d2q9_fp64_adaptive_matches_oracle(thermal, npw):
+def test_d2q9_fp64_adaptive_matches_oracle(thermal, kern):
     fields = d2q9_fields("tg", 64, 64) if thermal else d2q9_fields("supersonic", 47, 41)
     steps = 60 if thermal else 8
-    g, grho, git, stats = gpu_run(fields, steps, thermal=thermal, nodes_per_warp=npw)
+    g, grho, git, stats = gpu_run(fields, steps, thermal=thermal, **Q9_FP64[kern])
     o, oit = oracle_run(fields, steps, thermal=thermal)
     assert stats["nonconverged"] == 0 and stats["nonphysical"] == 0
     assert np.mean(git == oit) >= 0.999
     assert max(rel_errors(g, grho, o)) <= 1e-9
 
 
+@pytest.mark.parametrize("kernel", [pond.POND_KERNEL_STAGED, pond.POND_KERNEL_DIRECT])
 @pytest.mark.parametrize("tile_rows", [4, 8, 16])
 @pytest.mark.parametrize("name,nx,ny,steps", [("supersonic", 64, 48, 10), ("hot", 45, 37, 6),
                                               ("tg", 5, 3, 4)])
-def test_d2q9_mixed_matches_oracle(name, nx, ny, steps, tile_rows):
+def test_d2q9_mixed_matches_oracle(name, nx, ny, steps, tile_rows, kernel):
     fields = d2q9_fields(name, nx, ny)
-    g, grho, git, stats = gpu_run(fields, steps, pond.POND_FP32_MIXED, tile_rows=tile_rows)
+    g, grho, git, stats = gpu_run(fields, steps, pond.POND_FP32_MIXED, tile_rows=tile_rows,
+                                  kernel=kernel)
     assert stats["tile_rows"] == tile_rows and stats["nonphysical"] == 0
     o, _ = oracle_run(fields, steps)
     e = rel_errors(g, grho, o, speed_scale=True)

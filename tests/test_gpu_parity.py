@@ -77,25 +77,37 @@ def small_fields(name, nx, ny):
 
 # ------------------------------------------------------------------ FP64
 
-@pytest.mark.parametrize("npw", [1, 2, 32])
+# FP64 kernels: the direct per-pair kernel in its three mappings (one and two
+# nodes per warp, one node per thread) and the reference-gauge staged tile
+# kernel (the default) with both tile shapes
+FP64_KERNELS = {
+    "direct_npw1": {"kernel": pond.POND_KERNEL_DIRECT, "nodes_per_warp": 1},
+    "direct_npw2": {"kernel": pond.POND_KERNEL_DIRECT, "nodes_per_warp": 2},
+    "direct_node": {"kernel": pond.POND_KERNEL_DIRECT, "nodes_per_warp": 32},
+    "staged_32x4": {"kernel": pond.POND_KERNEL_STAGED, "tile_rows": 4},
+    "staged_32x8": {"kernel": pond.POND_KERNEL_STAGED, "tile_rows": 8},
+}
+
+
+@pytest.mark.parametrize("kern", list(FP64_KERNELS))
 @pytest.mark.parametrize("name,nx,ny,steps", [("tg", 64, 64, 12), ("supersonic", 37, 29, 6),
                                               ("hot", 48, 40, 5), ("supersonic", 1, 1, 3),
                                               ("tg", 3, 5, 4), ("supersonic", 2, 7, 3)])
-def test_fp64_fixed_passes_matches_oracle(name, nx, ny, steps, npw):
+def test_fp64_fixed_passes_matches_oracle(name, nx, ny, steps, kern):
     fields = small_fields(name, nx, ny)
-    g, grho, git, _ = gpu_run(fields, steps, fixed_iter=4, nodes_per_warp=npw)
+    g, grho, git, _ = gpu_run(fields, steps, fixed_iter=4, **FP64_KERNELS[kern])
     o, oit = oracle_run(fields, steps, fixed_iter=4)
     assert np.all(git == 4) and np.all(oit == 4)
     e = rel_errors(g, grho, o)
     assert max(e) <= TOL64, e
 
 
-@pytest.mark.parametrize("npw", [1, 2, 32])
-def test_fp64_taylor_green_full_config_adaptive(npw):
-    """64^2 Taylor-Green, u0 = 0.05, nu = 0.01, 100 steps, adaptive passes
-    (one and two nodes per warp, and one node per thread)."""
+@pytest.mark.parametrize("kern", list(FP64_KERNELS))
+def test_fp64_taylor_green_full_config_adaptive(kern):
+    """64^2 Taylor-Green, u0 = 0.05, nu = 0.01, 100 steps, adaptive passes,
+    every FP64 kernel."""
     fields = workloads.tg64()
-    g, grho, git, stats = gpu_run(fields, 100, nodes_per_warp=npw)
+    g, grho, git, stats = gpu_run(fields, 100, **FP64_KERNELS[kern])
     o, oit = oracle_run(fields, 100)
     assert stats["nonconverged"] == 0 and stats["nonphysical"] == 0
     assert np.mean(git == oit) >= 0.999
@@ -103,13 +115,13 @@ def test_fp64_taylor_green_full_config_adaptive(npw):
     assert max(e) <= 1e-9, e
 
 
-@pytest.mark.parametrize("npw", [1, 2, 32])
-def test_fp64_supersonic_adaptive_pass_map(npw):
+@pytest.mark.parametrize("kern", list(FP64_KERNELS))
+def test_fp64_supersonic_adaptive_pass_map(kern):
     # 63 x 47: an odd node count leaves the last warp of the two-node mapping
-    # with one node, and the last block of the node-per-thread mapping part
-    # filled
+    # with one node, the last block of the node-per-thread mapping part
+    # filled, and the last tiles of the staged kernel ragged in x and y
     fields = small_fields("supersonic", 63, 47)
-    g, grho, git, stats = gpu_run(fields, 4, nodes_per_warp=npw)
+    g, grho, git, stats = gpu_run(fields, 4, **FP64_KERNELS[kern])
     o, oit = oracle_run(fields, 4)
     assert np.mean(git == oit) >= 0.999
     assert max(rel_errors(g, grho, o)) <= 1e-9
@@ -219,13 +231,20 @@ def test_strict_mode_reports_nonconvergence():
 
 # ------------------------------------------------------------------ mixed
 
-@pytest.mark.parametrize("tile_rows", [4, 8, 16, -16])
+MIXED_KERNELS = [(pond.POND_KERNEL_STAGED, 4), (pond.POND_KERNEL_STAGED, 8),
+                 (pond.POND_KERNEL_STAGED, 16), (pond.POND_KERNEL_DIRECT, 4),
+                 (pond.POND_KERNEL_DIRECT, 8), (pond.POND_KERNEL_DIRECT, 16),
+                 (pond.POND_KERNEL_DIRECT, -16)]
+
+
+@pytest.mark.parametrize("kernel,tile_rows", MIXED_KERNELS)
 @pytest.mark.parametrize("name,nx,ny,steps", [("tg", 64, 64, 20), ("supersonic", 70, 45, 8),
                                               ("hot", 40, 33, 6), ("supersonic", 5, 3, 3),
                                               ("tg", 1, 1, 2)])
-def test_mixed_matches_oracle(name, nx, ny, steps, tile_rows):
+def test_mixed_matches_oracle(name, nx, ny, steps, kernel, tile_rows):
     fields = small_fields(name, nx, ny)
-    g, grho, git, stats = gpu_run(fields, steps, pond.POND_FP32_MIXED, tile_rows=tile_rows)
+    g, grho, git, stats = gpu_run(fields, steps, pond.POND_FP32_MIXED, tile_rows=tile_rows,
+                                  kernel=kernel)
     assert stats["tile_rows"] == tile_rows
     o, _ = oracle_run(fields, steps)
     assert stats["nonconverged"] == 0
@@ -243,19 +262,23 @@ def test_mixed_halo_fallback_path():
     assert max(rel_errors(g, grho, o, speed_scale=True)[:3]) <= TOL32
 
 
-@pytest.mark.parametrize("tile_rows", [8, -16])
-def test_batched_matches_single_grid_runs(tile_rows):
+@pytest.mark.parametrize("kernel,tile_rows", [(pond.POND_KERNEL_STAGED, 8),
+                                              (pond.POND_KERNEL_STAGED, 16),
+                                              (pond.POND_KERNEL_DIRECT, 8),
+                                              (pond.POND_KERNEL_DIRECT, -16)])
+def test_batched_matches_single_grid_runs(kernel, tile_rows):
     sizes = [(37, 23), (64, 40), (33, 70), (32, 32), (50, 45), (96, 17), (1, 1), (5, 9)]
     members = [workloads.ensemble_member(i, nx, ny) for i, (nx, ny) in enumerate(sizes)]
     nxs = [s[0] for s in sizes]
     nys = [s[1] for s in sizes]
-    with pond.Sim(nxs, nys, pond.POND_FP32_MIXED, tile_rows=tile_rows) as b:
+    with pond.Sim(nxs, nys, pond.POND_FP32_MIXED, tile_rows=tile_rows, kernel=kernel) as b:
         for i, m in enumerate(members):
             b.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
         b.step(3)
         batched = [b.state(i) for i in range(len(sizes))]
     for i, m in enumerate(members):
-        with pond.Sim(nxs[i], nys[i], pond.POND_FP32_MIXED, tile_rows=tile_rows) as s:
+        with pond.Sim(nxs[i], nys[i], pond.POND_FP32_MIXED, tile_rows=tile_rows,
+                      kernel=kernel) as s:
             s.set_state(m.rho, m.ux, m.uy, m.T)
             s.step(3)
             single = s.state()

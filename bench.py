@@ -75,10 +75,10 @@ def staged_flops_per_pass(n1: int, st_mean: float) -> float:
 # at the start of every run instead; these are the fallback if it fails.
 PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes per FP64 step launch at 2048^2: the ncu capture of the same
-# kernel (k1_step_fp64_node, one node per thread) at 1024^2 read 168.0 MB and
-# wrote 129.1 MB; traffic grows with the node count (4x).
-K1_TRAFFIC_BYTES_2048 = 4 * (167.97e6 + 129.12e6)
+# DRAM bytes per FP64 step launch at 2048^2 of the staged kernel, from an ncu
+# capture of the same kernel (None until one is taken of the current code).
+K_STAGED64_TRAFFIC_2048 = None
+K_STAGED64_TRAFFIC_SOURCE = "no ncu capture of the current kernel yet"
 
 
 def parse():
@@ -93,7 +93,7 @@ def parse():
     ap.add_argument("--precision-steps", type=int, default=1000,
                     help="steps of the mixed-vs-FP64 moment-error leg")
     ap.add_argument("--precision-full", action="store_true",
-                    help="run that leg on the full 4096^2 field (FP64 reference ~20 min)")
+                    help="run that leg on the full 4096^2 field (FP64 reference ~8 min)")
     return ap.parse_args()
 
 
@@ -262,6 +262,9 @@ def time_steps(sim, stream, steps):
 
 def form_line(name, nodes, steps, secs, stats, precision_peak_tflops, bytes_per_update,
               flop_per_pass=FLOP_PER_PASS):
+    """One form's throughput and roofline; flop_per_pass is the count of the
+    kernel that ran (staged_flops_per_pass for the staged kernel, the
+    per-pair count FLOP_PER_PASS for the direct ones)."""
     passes = stats["passes"] / max(stats["node_updates"], 1)
     achieved = flop_per_pass * stats["passes"] / secs / 1e12
     return {
@@ -340,11 +343,14 @@ def run_pond(args, world, rank, local):
     peak_src = ("measured in this run by the FMA-chain probe" if "fp64" in probe
                 else "nominal FP64 rate at 2070 MHz (probe failed)")
 
-    # ---- headline: FP64 step, state resident in HBM (1.2 GB > L2)
-    sim = pond.Sim(nx, ny, pond.POND_FP64, stream=stream.cuda_stream)
+    # ---- headline: FP64 step (the staged kernel, tile shape autotuned during
+    # the warm-up), state resident in HBM (1.2 GB > L2)
+    sim = pond.Sim(nx, ny, pond.POND_FP64, stream=stream.cuda_stream, autotune=1)
     sim.set_state(fields.rho, fields.ux, fields.uy, fields.T)
     torch.cuda.synchronize()
     sim.step(args.warmup)
+    st_mean = float(np.sqrt(fields.T).mean())
+    flop_pass = staged_flops_per_pass(4, st_mean)
     barrier(world)
     with ClockSampler(local) as clk:
         secs, stats = time_steps(sim, stream, args.steps)
@@ -354,7 +360,7 @@ def run_pond(args, world, rank, local):
     rho64, ux64, uy64, T64 = sim.moments()
     mean_passes = stats["passes"] / stats["node_updates"]
     kernel_s = secs / args.steps
-    achieved = FLOP_PER_PASS * (stats["passes"] / args.steps) / kernel_s / 1e12
+    achieved = flop_pass * (stats["passes"] / args.steps) / kernel_s / 1e12
     line = {
         "metric": METRIC,
         "value": world * nodes * args.steps / secs_max,
@@ -379,14 +385,16 @@ def run_pond(args, world, rank, local):
         "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved,
                      "peak": peak64, "unit": "TFLOP/s",
                      "frac": achieved / peak64,
-                     "traffic": K1_TRAFFIC_BYTES_2048,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                       "k1_step_fp64_node<4> launch at 1024^2 (297.1 MB), scaled "
-                                       "x4 by nodes to the 2048^2 launch",
+                     "traffic": K_STAGED64_TRAFFIC_2048,
+                     "traffic_source": K_STAGED64_TRAFFIC_SOURCE,
                      "peak_source": peak_src,
                      "peak_nominal": PEAK_FP64_TFLOPS,
-                     "flop_per_pass": FLOP_PER_PASS,
-                     "kernel": "k1_step_fp64_node", "kernel_ms": kernel_s * 1e3,
+                     "flop_per_pass": flop_pass,
+                     "flop_count": "staged kernel, per-pass sweep only (staging excluded)",
+                     "direct_equivalent_tflops": FLOP_PER_PASS * (stats["passes"] / args.steps)
+                                                 / kernel_s / 1e12,
+                     "tile": [32, stats.get("tile_rows", 0)],
+                     "kernel": "k_step_staged<StagedFP64>", "kernel_ms": kernel_s * 1e3,
                      "hbm_gbs_algorithmic": nodes * BYTES_FP64 / kernel_s / 1e9,
                      "hbm_peak_gbs": peaks.get("hbm_gbs")},
         "clocks": clocks,
@@ -424,7 +432,7 @@ def run_pond(args, world, rank, local):
         msecs, mstats = time_steps(msim, stream, args.steps)
         rho32, ux32, uy32, T32 = msim.moments()
         forms["fp32_mixed_2048"] = form_line("supersonic-2048-mixed", nodes, args.steps, msecs,
-                                             mstats, peak32, BYTES_MIXED)
+                                             mstats, peak32, BYTES_MIXED, flop_pass)
         forms["fp32_mixed_2048"]["moment_err_vs_fp64"] = {
             "after_steps": args.warmup + args.steps,
             "rho": float(np.max(np.abs(rho32 - rho64)) / np.max(np.abs(rho64))),
@@ -435,6 +443,19 @@ def run_pond(args, world, rank, local):
             nodes * args.steps / secs)
         msim.close()
 
+        # the direct per-pair kernels on the same field, for comparison
+        for key, prec, peak, nb, kw in (
+                ("fp64_direct_2048", pond.POND_FP64, peak64, BYTES_FP64, {}),
+                ("fp32_mixed_direct_2048", pond.POND_FP32_MIXED, peak32, BYTES_MIXED,
+                 {"use_graph": 1, "autotune": 1})):
+            with pond.Sim(nx, ny, prec, stream=stream.cuda_stream, kernel=pond.POND_KERNEL_DIRECT,
+                          **kw) as dsim:
+                dsim.set_state(fields.rho, fields.ux, fields.uy, fields.T)
+                dsim.step(2)
+                dsteps = 4 if prec == pond.POND_FP64 else args.steps
+                dsecs, dstats = time_steps(dsim, stream, dsteps)
+            forms[key] = form_line(key.replace("_", "-"), nodes, dsteps, dsecs, dstats, peak, nb)
+
         pf = workloads.precision(4096)
         psim = pond.Sim(4096, 4096, pond.POND_FP32_MIXED, stream=stream.cuda_stream, use_graph=1,
                         autotune=1)
@@ -442,21 +463,37 @@ def run_pond(args, world, rank, local):
         psim.step(args.warmup)
         psecs, pstats = time_steps(psim, stream, k2)
         forms["fp32_mixed_4096"] = form_line("precision-4096-mixed", 4096 * 4096, k2, psecs,
-                                             pstats, peak32, BYTES_MIXED)
+                                             pstats, peak32, BYTES_MIXED,
+                                             staged_flops_per_pass(4, float(np.sqrt(pf.T).mean())))
         psim.close()
         del pf
 
-        nxs, nys = workloads.ensemble_sizes(256)
+        # the ensemble: whole grids sharded over the ranks (largest first to
+        # the least loaded rank), each rank's share as one batched context
+        from paper_1806_05089_gb300 import decomp
+        nxs_all, nys_all = workloads.ensemble_sizes(256)
+        mine = decomp.ensemble_shards(nxs_all, nys_all, world)[rank]
         members = workloads.ensemble(256)
+        nxs = [nxs_all[i] for i in mine]
+        nys = [nys_all[i] for i in mine]
         bsim = pond.Sim(nxs, nys, pond.POND_FP32_MIXED, stream=stream.cuda_stream, use_graph=1,
                         autotune=1)
-        for i, m in enumerate(members):
-            bsim.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
+        for j, i in enumerate(mine):
+            m = members[i]
+            bsim.set_state(m.rho, m.ux, m.uy, m.T, grid=j)
         bnodes = int(sum(a * b for a, b in zip(nxs, nys)))
+        st_b = float(np.average([np.sqrt(members[i].T).mean() for i in mine],
+                                weights=[nxs_all[i] * nys_all[i] for i in mine]))
         bsim.step(args.warmup)
+        barrier(world)
         bsecs, bstats = time_steps(bsim, stream, k2)
+        barrier(world)
+        bsecs_max = max_over_ranks(world, bsecs)
         forms["batched_256"] = form_line("ensemble-256-mixed", bnodes, k2, bsecs, bstats,
-                                         peak32, BYTES_MIXED)
+                                         peak32, BYTES_MIXED, staged_flops_per_pass(4, st_b))
+        forms["batched_256"]["grids_on_this_rank"] = len(mine)
+        forms["batched_256"]["all_ranks_value"] = (int(sum(a * b for a, b in zip(nxs_all, nys_all)))
+                                                   * k2 / bsecs_max)
         bsim.close()
 
         # the paper's own D2Q9 lattice on the same supersonic flow, rescaled to
@@ -468,7 +505,7 @@ def run_pond(args, world, rank, local):
                                          BYTES_FP64_Q9),
                                         ("fp32_mixed_d2q9_2048", pond.POND_FP32_MIXED,
                                          peak32, BYTES_MIXED_Q9)):
-            extra = {"use_graph": 1, "autotune": 1} if prec == pond.POND_FP32_MIXED else {}
+            extra = {"use_graph": 1, "autotune": 1}
             qsim = pond.Sim(nx, ny, prec, stream=stream.cuda_stream, lattice=pond.POND_D2Q9,
                             T_ref=1.0 / 3.0, **extra)
             qsim.set_state(q9.rho, q9.ux, q9.uy, q9.T)
@@ -477,7 +514,7 @@ def run_pond(args, world, rank, local):
             forms[key] = form_line("supersonic-2048-d2q9-" + ("fp64" if prec == pond.POND_FP64
                                                               else "mixed"),
                                    nodes, args.steps, qsecs, qstats, peak, nbytes,
-                                   FLOP_PER_PASS_Q9)
+                                   staged_flops_per_pass(3, float(np.sqrt(q9.T * 3.0).mean())))
             q9_out[key] = qsim.moments()
             qsim.close()
         r64, u64x, u64y, t64 = q9_out["fp64_d2q9_2048"]
@@ -489,6 +526,25 @@ def run_pond(args, world, rank, local):
                        / np.max(np.hypot(u64x, u64y))),
             "T": float(np.max(np.abs(t32 - t64)) / np.max(np.abs(t64)))}
         del q9, q9_out
+
+        # the paper's hardest flow: an isentropic vortex advected through the
+        # periodic box, over a small (Ma_a, Ma_v) sweep, mixed form (staged
+        # kernel), with the pass counts of its iteration map
+        vortex = {}
+        for ma, mv in ((0.0, 0.5), (1.0, 0.5), (3.0, 0.5), (1.0, 0.8)):
+            vf = workloads.vortex(1024, 64.0, mv, ma, angle=0.6)
+            with pond.Sim(1024, 1024, pond.POND_FP32_MIXED, stream=stream.cuda_stream,
+                          use_graph=1, autotune=1) as vsim:
+                vsim.set_state(vf.rho, vf.ux, vf.uy, vf.T)
+                vsim.step(args.warmup)
+                vsecs, vstats = time_steps(vsim, stream, k2)
+            line_v = form_line("vortex-1024-mixed", 1024 * 1024, k2, vsecs, vstats, peak32,
+                               BYTES_MIXED, staged_flops_per_pass(4, float(np.sqrt(vf.T).mean())))
+            vortex["Ma_a=%g,Ma_v=%g" % (ma, mv)] = {
+                k: line_v[k] for k in ("value", "ms_per_step", "mean_passes", "max_passes",
+                                       "nonconverged", "halo_fallback", "alu_frac", "tile")}
+        forms["vortex_mixed_1024"] = {"workload": "vortex-1024-mixed", "unit": UNIT,
+                                      "radius": 64.0, "steps": k2, "sweep": vortex}
 
         # adjoint / forward time on the 512^2 Taylor-Green + pulse workload.
         # One short rollout with its backward runs first, untimed, so that
@@ -536,15 +592,14 @@ def run_pond(args, world, rank, local):
 
         # moment error of the mixed form against the FP64 step after 1000
         # steps on the temperature-ratio-4 precision field.  The FP64
-        # reference of the full 4096^2 field takes ~20 min on this part
-        # (--precision-full runs it); by default the same field recipe at
-        # 1024^2 (steeper gradients per cell, so no easier) is run in both
-        # forms for 1000 steps.
-        pn = 4096 if args.precision_full else 1024
+        # reference of the full 4096^2 field takes ~8 min (--precision-full
+        # runs it); by default the same field recipe at 2048^2 (steeper
+        # gradients per cell, so no easier) is run in both forms.
+        pn = 4096 if args.precision_full else 2048
         pstate = workloads.precision(pn)
         res = {}
         for prec in (pond.POND_FP64, pond.POND_FP32_MIXED):
-            extra = {"use_graph": 1, "autotune": 1} if prec == pond.POND_FP32_MIXED else {}
+            extra = {"use_graph": 1, "autotune": 1}
             with pond.Sim(pn, pn, prec, stream=stream.cuda_stream, **extra) as ps:
                 ps.set_state(pstate.rho, pstate.ux, pstate.uy, pstate.T)
                 ev = time_steps(ps, stream, args.precision_steps)

@@ -154,7 +154,11 @@ typedef struct pond_stats {
     int64_t nonconverged;  /* node updates that hit max_iter unconverged */
     int64_t nonphysical;   /* node updates that met rho <= 0, T <= 0 or NaN */
     int64_t halo_fallback; /* stencils read from global memory instead of the
-                              shared-memory halo tile (mixed form only) */
+                              shared-memory window (tile kernels) */
+    int64_t index_faults;  /* debug builds of the library (compiled with
+                              POND_DEBUG): accesses of the staged kernel that
+                              failed their index check and were skipped; 0
+                              in release builds, which have no checks */
 } pond_stats;
 
 /* Defaults for a precision (POND_FP64 or POND_FP32_MIXED). */

@@ -18,6 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libpond.so")
 BUILD_DIR = os.path.join(HERE, "_build")
+# debug build: the staged kernel's index checks compiled in (POND_DEBUG)
+DEBUG_LIB = os.path.join(HERE, "libpond_debug.so")
+DEBUG_BUILD_DIR = os.path.join(HERE, "_build_debug")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
@@ -44,9 +47,18 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str | None = None,
-          build_dir: str | None = None) -> str:
+          build_dir: str | None = None, debug: bool = False) -> str:
     """Compile and link; ``extra_flags``/``out``/``build_dir`` build a variant
-    library elsewhere (tuning experiments) without touching the default one."""
+    library elsewhere (tuning experiments) without touching the default one;
+    ``debug`` builds libpond_debug.so with the index checks (POND_DEBUG)."""
+    if debug:
+        extra_flags = tuple(extra_flags) + ("-DPOND_DEBUG",)
+        out = out or DEBUG_LIB
+        build_dir = build_dir or DEBUG_BUILD_DIR
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= max(
+                os.path.getmtime(d) for d in sources() + glob.glob(os.path.join(CSRC, "*.cuh"))
+                + [os.path.join(INCLUDE, "pond.h")]):
+            return out
     lib = out or LIB
     if not force and out is None and not _stale():
         return LIB

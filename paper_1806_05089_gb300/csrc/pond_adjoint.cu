@@ -460,6 +460,7 @@ void destroy_adjoint(pond_ctx* ctx) {
 
 static pond_status adj_fail(pond_ctx* ctx, cudaError_t e, const char* where) {
     ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();  // clear a non-sticky error (a failed allocation) for the next call
     return e == cudaErrorMemoryAllocation ? POND_ERR_OOM : POND_ERR_CUDA;
 }
 
@@ -571,6 +572,7 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
     in.st = ctx->st[ctx->cur];
     cudaStream_t s = ctx->stream;
 
+    NvtxRange nv("pond_adjoint_step (FP64)");
     // 1. the fixed point lambda*: the gauge the forward step stores, given by
     //    the caller or recomputed into scratch
     if (out_gauge[0]) {
@@ -618,11 +620,13 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
         A.vhi_y[i] = shi + mm[3];
     }
     const unsigned nb = (unsigned)((N + ADJ_WARPS - 1) / ADJ_WARPS);
+    nvtxRangePushA("adjoint targets + transpose gather");
     if (ctx->L.n1 == 3) k_adjoint_targets<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
     else k_adjoint_targets<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
     ACK(cudaGetLastError(), "adjoint targets");
     if (ctx->L.n1 == 3) k_adjoint_sources<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
     else k_adjoint_sources<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    nvtxRangePop();
     ACK(cudaGetLastError(), "adjoint sources");
     double bb = 0.0;
     ACK(cudaMemcpyAsync(&bb, a->beta_bar, sizeof(double), cudaMemcpyDeviceToHost, s), "adjoint copy");

@@ -440,6 +440,7 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
                                const double* fbar, const double* gbar, double* fbar_out,
                                double* gbar_out, double* beta_bar_dev, double* minmax_dev,
                                double* minmax_host) {
+    NvtxRange nv("pond_adjoint_step (FP32)");
     const int64_t N = ctx->N;
     cudaStream_t s = ctx->stream;
     cudaError_t e;

@@ -40,6 +40,10 @@ pond_status cuda_fail(pond_ctx* c, cudaError_t e, const char* where) {
     if (c) {
         c->err = std::string(where) + ": " + cudaGetErrorString(e);
     }
+    // a failed allocation (like any non-sticky error) is also left as the
+    // runtime's last error, where the next launch check would find it and
+    // report it again; clear it so the caller can carry on
+    (void)cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? POND_ERR_OOM : POND_ERR_CUDA;
 }
 
@@ -494,6 +498,7 @@ pond_status pond_set_state(pond_ctx* ctx, int32_t grid, const void* rho, const v
     if (!ux || !uy || !T || (!f && !rho))
         return fail(ctx, POND_ERR_ARG, "set_state: ux, uy, T and one of rho / f are required");
     DeviceGuard dg(ctx->device);
+    NvtxRange nv("pond_set_state");
     const GridDesc& G = ctx->grids_host[grid];
     const int64_t n = (int64_t)G.nx * G.ny;
     const double *d_rho, *d_ux, *d_uy, *d_T, *d_f;
@@ -633,6 +638,7 @@ void tune_file_store() {
 }  // namespace
 
 static pond_status autotune(pond_ctx* ctx) {
+    NvtxRange nv("pond_autotune");
     const std::string key = tune_key(ctx);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -696,6 +702,7 @@ static pond_status autotune(pond_ctx* ctx) {
 
 pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats) {
     if (!ctx) return POND_ERR_ARG;
+    NvtxRange nv("pond_step");
     if (nsteps < 0) return fail(ctx, POND_ERR_ARG, "nsteps < 0");
     for (int g = 0; g < ctx->n_grids; ++g)
         if (!ctx->grid_set[g]) return fail(ctx, POND_ERR_STATE, "pond_step before pond_set_state");
@@ -732,6 +739,7 @@ pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats) {
         stats->nonconverged = (int64_t)d.nonconverged;
         stats->nonphysical = (int64_t)d.nonphysical;
         stats->halo_fallback = (int64_t)d.halo_fallback;
+        stats->index_faults = (int64_t)d.index_faults;
         if (d.nonphysical) return fail(ctx, POND_ERR_NONPHYSICAL, "rho <= 0, T <= 0 or NaN met");
         if (ctx->cfg.strict && d.nonconverged)
             return fail(ctx, POND_ERR_NOT_CONVERGED, "a node hit max_iter without converging");
@@ -797,6 +805,7 @@ static pond_status rect_io(pond_ctx* ctx, int32_t grid, int32_t x0, int32_t y0, 
     if (x0 < 0 || y0 < 0 || w < 0 || h < 0 || (int64_t)x0 + w > G.nx || (int64_t)y0 + h > G.ny)
         return fail(ctx, POND_ERR_ARG, "rect: rectangle outside the grid");
     DeviceGuard dg(ctx->device);
+    NvtxRange nv(pack ? "pond_pack_rect" : "pond_unpack_rect");
     const int q = ctx->L.q;
     if (mixed(ctx)) {
         StateBuf<float> b = buf_of<float>(ctx, ctx->cur, G.offset);

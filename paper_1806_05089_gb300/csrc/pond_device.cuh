@@ -5,6 +5,21 @@
 
 namespace pond {
 
+// Debug builds (-DPOND_DEBUG, build.build(debug=True)): index checks on the
+// staged kernel's global and shared-memory accesses.  A failed check adds
+// one to the step counters' index_faults and the access is skipped (a
+// zero is read, nothing is written); nothing traps.  Release builds compile
+// the checks away.
+#ifdef POND_DEBUG
+__device__ __forceinline__ bool pond_index_ok(bool ok, DevStats* st) {
+    if (!ok && st) atomicAdd(&st->index_faults, 1ull);
+    return ok;
+}
+#define POND_INDEX_OK(cond, stats) ::pond::pond_index_ok((cond), (stats))
+#else
+#define POND_INDEX_OK(cond, stats) true
+#endif
+
 // Cubic Lagrange weights on the nodes 0, 1, 2, 3 at local coordinate t
 // (App. C: a_n(t) = prod_{k != n} (t - k)/(n - k)).
 __device__ __forceinline__ void lagrange4(double t, double l[4]) {

@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -16,6 +17,15 @@
 #include "../../include/pond.h"
 
 namespace pond {
+
+// NVTX range over a host-side phase (a step, an adjoint phase, a halo
+// copy): header-only NVTX v3, a no-op unless a profiler is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Lattice constants, computed on the host from their closed forms and passed
 // to kernels by value (they land in the constant bank).
@@ -81,6 +91,7 @@ struct DevStats {
     unsigned long long nonconverged;
     unsigned long long nonphysical;
     unsigned long long halo_fallback;
+    unsigned long long index_faults;  // debug builds: accesses skipped by a failed index check
     unsigned int max_passes;
     unsigned int pad;
 };

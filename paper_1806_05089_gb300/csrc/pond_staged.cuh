@@ -151,6 +151,7 @@ __device__ __noinline__ typename Tr::Real staged_fallback(const StagedArgs<typen
         for (int jx = 0; jx < 4; ++jx) {
             const int sx = wrap_inc(x0, jx, G.nx);
             const long long s = base + (long long)sy * G.nx + sx;
+            if (!POND_INDEX_OK(sx >= 0 && sx < G.nx && sy >= 0 && sy < G.ny, A.stats)) continue;
             const Real r = (Real)((A.in.st[s] - st) * inv);
             const Real dx = (Real)((A.in.ux[s] - ux) * inv);
             const Real dy = (Real)((A.in.uy[s] - uy) * inv);
@@ -293,6 +294,8 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
             const int gx = wrap_idx((long long)wx0 + cx, G.nx);
             const int gy = wrap_idx((long long)wy0 + cy, G.ny);
             const long long gi = base + (long long)gy * G.nx + gx;
+            if (!POND_INDEX_OK(gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny && i < WN, A.stats))
+                continue;
             // xi_a = c_a + c_a (st_s/st_r - 1) + (u_s - u_r)/st_r, in FP64
             const Real r = (Real)((__ldg(A.in.st + gi) - rst) * inv_rst);
             const Real dx = (Real)((__ldg(A.in.ux + gi) - rux) * inv_rst);
@@ -367,9 +370,9 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
             }
             Real m0 = 0, m1 = 0, m2 = 0, m3 = 0;
             unsigned int offwin = 0u;
-            // FP64 unrolls the x-speed loop (the identity term is then a
-            // register, fr[k][b]); FP32 keeps it rolled within its register
-            // budget and forms that term exactly as sum_a [a == k] fr[a][b]
+            // The x-speed loop is unrolled where the register budget allows
+            // (the identity term of the x-map is then a register, Fi[k][b]);
+            // rolled, that term is formed exactly as sum_a [a == k] Fi[a][b]
             constexpr int KU = Tr::kUnrollK ? N1 : 1;
 #pragma unroll KU
             for (int k = 0; k < N1; ++k) {
@@ -425,11 +428,21 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
 #pragma unroll
                             for (int b = 0; b < N1; ++b) Fi[a][b] = (Real)0;
                         const Real4* src = s_f + y * ww + col;
+                        const bool rowok = POND_INDEX_OK(y >= 0 && col >= 0 && y < wh &&
+                                                             col + 3 < ww && y * ww + col + 3 < WN,
+                                                         A.stats);
 #pragma unroll
                         for (int jx = 0; jx < 4; ++jx) {
                             Real fr[N1][4];
 #pragma unroll
-                            for (int a = 0; a < N1; ++a) Tr::load4(src + (size_t)a * WN + jx, fr[a]);
+                            for (int a = 0; a < N1; ++a) {
+                                if (rowok) {
+                                    Tr::load4(src + (size_t)a * WN + jx, fr[a]);
+                                } else {
+#pragma unroll
+                                    for (int b = 0; b < 4; ++b) fr[a][b] = (Real)0;
+                                }
+                            }
 #pragma unroll
                             for (int a = 0; a < N1; ++a)
 #pragma unroll
@@ -500,7 +513,7 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
             }
             if (work) done = Tr::update(A.P, pg, m0, m1, m2, m3);
         }
-        if (valid) {
+        if (valid && POND_INDEX_OK(node >= base && node < base + (long long)G.nx * G.ny, A.stats)) {
             Tr::template finish<N1>(A, s_acc, NT, tid, node, pg);
             if (A.iters) A.iters[node] = pg.pass;
             atomicAdd(&s_passes, (unsigned long long)pg.pass);

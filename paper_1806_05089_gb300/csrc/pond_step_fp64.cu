@@ -936,6 +936,7 @@ extern "C" pond_status pond_step_fp64_noalloc(const pond_config* cfg, int32_t nx
         stats->nonconverged = (int64_t)h.nonconverged;
         stats->nonphysical = (int64_t)h.nonphysical;
         stats->halo_fallback = 0;
+        stats->index_faults = (int64_t)h.index_faults;
         if (h.nonphysical) return POND_ERR_NONPHYSICAL;
         if (cfg->strict && h.nonconverged) return POND_ERR_NOT_CONVERGED;
     }

@@ -952,7 +952,7 @@ __global__ void __launch_bounds__(TX* TY, 1) k2_step_mixed_pair(MixedArgs A) {
 struct StagedFP32 {
     using Real = float;
     using Real4 = float4;
-    static constexpr bool kUnrollK = false;
+    static constexpr bool kUnrollK = true;
     template <int NT>
     static constexpr int min_blocks() {
         return 512 / NT;

@@ -83,6 +83,7 @@ class pond_stats(ctypes.Structure):
         ("nonconverged", ctypes.c_int64),
         ("nonphysical", ctypes.c_int64),
         ("halo_fallback", ctypes.c_int64),
+        ("index_faults", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -1,6 +1,6 @@
 """Run one small PonD case for profiling (e.g. under ncu).
 
-  python -m paper_1806_05089_gb300.profile_case --form fp64 --n 1024 --steps 2
+  python -m paper_1806_05089_gb300.profile_case --form fp64 --n 1024 --steps 2 [--kernel direct]
   python -m paper_1806_05089_gb300.profile_case --form mixed --n 2048 --steps 3
   python -m paper_1806_05089_gb300.profile_case --form batched --grids 64 --steps 2
   python -m paper_1806_05089_gb300.profile_case --form adjoint --n 256 --steps 2
@@ -25,12 +25,16 @@ def main():
     ap.add_argument("--grids", type=int, default=64)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--tile", type=int, default=0,
-                    help="mixed forms: tile rows (4, 8, 16; -16 = two nodes per thread)")
+                    help="tile kernels: tile rows (4, 8, 16 mixed only; -16 = the direct mixed "
+                         "kernel's two nodes per thread)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="adjoint: precision of the rollout and its adjoint")
     ap.add_argument("--npw", type=int, default=0,
                     help="fp64: nodes per warp of the step kernel (1, 2, 3 on d2q9, 32 = one per "
                          "thread; 0 = default)")
+    ap.add_argument("--kernel", choices=["staged", "direct"], default="staged",
+                    help="fp64 / mixed / batched: the reference-gauge staged tile kernel (the "
+                         "default) or the direct per-pair kernels")
     ap.add_argument("--lattice", choices=["d2q16", "d2q9"], default="d2q16",
                     help="fp64 / mixed / batched: lattice (d2q9 runs the same flow at "
                          "T_L = 1/3: T/3, u/sqrt 3)")
@@ -54,7 +58,8 @@ def main():
         prec = pond.POND_FP64 if a.form == "fp64" else pond.POND_FP32_MIXED
         f = scaled(workloads.supersonic(a.n))
         cfg = dict(lat)
-        if prec == pond.POND_FP32_MIXED:
+        cfg["kernel"] = pond.POND_KERNEL_STAGED if a.kernel == "staged" else pond.POND_KERNEL_DIRECT
+        if prec == pond.POND_FP32_MIXED or a.kernel == "staged":
             cfg["tile_rows"] = a.tile
         else:
             cfg["nodes_per_warp"] = a.npw
@@ -71,7 +76,8 @@ def main():
     elif a.form == "batched":
         nxs, nys = workloads.ensemble_sizes(256)
         nxs, nys = nxs[:a.grids], nys[:a.grids]
-        with pond.Sim(nxs, nys, pond.POND_FP32_MIXED, tile_rows=a.tile, **lat) as s:
+        kern = pond.POND_KERNEL_STAGED if a.kernel == "staged" else pond.POND_KERNEL_DIRECT
+        with pond.Sim(nxs, nys, pond.POND_FP32_MIXED, tile_rows=a.tile, kernel=kern, **lat) as s:
             for i in range(a.grids):
                 m = scaled(workloads.ensemble_member(i, nxs[i], nys[i]))
                 s.set_state(m.rho, m.ux, m.uy, m.T, grid=i)

@@ -1,0 +1,31 @@
+"""GPU tests of the failure paths that need no GPU fault: a device
+allocation larger than the GPU's memory is refused with POND_ERR_OOM by
+pond_create (the CUDA allocator's own refusal, provoked on the host side by
+the size asked for), partial allocations are released, and the process
+stays usable for the next context."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1806_05089_gb300 import pond, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", [pond.POND_FP64, pond.POND_FP32_MIXED])
+def test_create_larger_than_device_memory_reports_oom(precision):
+    free, total = torch.cuda.mem_get_info()
+    # populations alone: 2 buffers x 16 x nodes x (8 or 4) bytes > 4 x total
+    side = int(np.sqrt(4 * total / (2 * 16 * 4))) + 1
+    with pytest.raises(pond.PondError) as e:
+        pond.Sim(side, side, precision)
+    assert e.value.status == pond.POND_ERR_OOM
+    # nothing leaked: the free memory is back where it was (within the
+    # allocator's granularity), and a normal context still works
+    free2, _ = torch.cuda.mem_get_info()
+    assert free2 >= free - (64 << 20)
+    f = workloads.supersonic(nx=32, ny=24)
+    with pond.Sim(32, 24, precision) as s:
+        s.set_state(f.rho, f.ux, f.uy, f.T)
+        st = s.step(2)
+    assert st["nonphysical"] == 0 and st["node_updates"] == 2 * 32 * 24

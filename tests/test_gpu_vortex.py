@@ -56,3 +56,78 @@ def test_advected_vortex_keeps_its_shape(traversals, steps):
     # the swirl is unchanged too (velocity relative to the flow)
     du = np.hypot(out[1][1] - U - out[0][1], out[1][2] - out[0][2]).max()
     assert du <= 0.02 * mach_v * np.sqrt(2.0)
+
+
+def _vortex64(mach_a=1.0, mach_v=0.5):
+    # diagonal advection, so both departure directions carry the flow
+    return workloads.vortex(64, 8.0, mach_v, mach_a, angle=0.6)
+
+
+@pytest.mark.parametrize("kernel", [pond.POND_KERNEL_STAGED, pond.POND_KERNEL_DIRECT])
+def test_vortex_fp64_matches_oracle(kernel):
+    """64^2 advected vortex (Ma_a 1, Ma_v 0.5), 3 steps with 4 passes each:
+    the GPU FP64 step against the FP64 CPU oracle at 1e-12."""
+    import oracle
+    f = _vortex64()
+    cfg = {"kernel": kernel}
+    if kernel == pond.POND_KERNEL_DIRECT:
+        cfg["nodes_per_warp"] = 32
+    with pond.Sim(64, 64, pond.POND_FP64, fixed_iter=4, **cfg) as s:
+        s.set_state(f.rho, f.ux, f.uy, f.T)
+        s.step(3)
+        g = s.state()
+        rho = g.f.sum(axis=0)
+    st = oracle.init_equilibrium(f.rho, f.ux, f.uy, f.T)
+    for _ in range(3):
+        st, it, fl = oracle.step(st, oracle.Params(fixed_iter=4))
+        assert not fl.any()
+    orho = st.f.sum(axis=0)
+    umax = np.hypot(st.ux, st.uy).max()
+    assert np.max(np.abs(rho - orho) / orho) <= 1e-12
+    assert np.max(np.abs(g.T - st.T) / st.T) <= 1e-12
+    assert max(np.abs(g.ux - st.ux).max(), np.abs(g.uy - st.uy).max()) <= 1e-12 * umax
+    assert np.abs(g.f - st.f).max() <= 1e-12 * np.abs(st.f).max()
+
+
+@pytest.mark.parametrize("kernel", [pond.POND_KERNEL_STAGED, pond.POND_KERNEL_DIRECT])
+def test_vortex_mixed_matches_oracle(kernel):
+    """The same vortex in the mixed form with adaptive passes, 6 steps,
+    against the oracle at the mixed form's 1e-5."""
+    import oracle
+    f = _vortex64()
+    with pond.Sim(64, 64, pond.POND_FP32_MIXED, kernel=kernel) as s:
+        s.set_state(f.rho, f.ux, f.uy, f.T)
+        stats = s.step(6)
+        rho, ux, uy, T = s.moments()
+    assert stats["nonconverged"] == 0
+    st = oracle.init_equilibrium(f.rho, f.ux, f.uy, f.T)
+    for _ in range(6):
+        st, it, fl = oracle.step(st)
+    orho = st.f.sum(axis=0)
+    speed = max(np.hypot(st.ux, st.uy).max(), np.sqrt(st.T.mean()))
+    assert np.max(np.abs(rho - orho) / orho) <= 1e-5
+    assert np.max(np.abs(T - st.T) / st.T) <= 1e-5
+    assert max(np.abs(ux - st.ux).max(), np.abs(uy - st.uy).max()) <= 1e-5 * speed
+
+
+@pytest.mark.parametrize("kernel", [pond.POND_KERNEL_STAGED, pond.POND_KERNEL_DIRECT])
+def test_vortex_mixed_halo_fallback_run_matches_fp64(kernel):
+    """A fast vortex (Ma_a 3) seeded with {-u, T}: every tile plans its staged
+    window around departures on the wrong side, so stencils leave the window
+    and take the global-memory path (halo_fallback > 0).  The mixed run still
+    matches the FP64 run of the same steps to the mixed form's 1e-5."""
+    f = _vortex64(mach_a=3.0)
+    out = {}
+    for prec in (pond.POND_FP64, pond.POND_FP32_MIXED):
+        with pond.Sim(64, 64, prec, seed_mode=2, max_iter=60, kernel=kernel) as s:
+            s.set_state(f.rho, f.ux, f.uy, f.T)
+            stats = s.step(2)
+            out[prec] = (s.moments(), stats)
+    (r64, x64, y64, t64), s64 = out[pond.POND_FP64]
+    (r32, x32, y32, t32), s32 = out[pond.POND_FP32_MIXED]
+    assert s32["halo_fallback"] > 0
+    assert s32["nonconverged"] == 0 and s64["nonconverged"] == 0
+    speed = max(np.hypot(x64, y64).max(), np.sqrt(t64.mean()))
+    assert np.max(np.abs(r32 - r64) / r64) <= 1e-5
+    assert np.max(np.abs(t32 - t64) / t64) <= 1e-5
+    assert max(np.abs(x32 - x64).max(), np.abs(y32 - y64).max()) <= 1e-5 * speed

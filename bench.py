@@ -75,10 +75,13 @@ def staged_flops_per_pass(n1: int, st_mean: float) -> float:
 # at the start of every run instead; these are the fallback if it fails.
 PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes per FP64 step launch at 2048^2 of the staged kernel, from an ncu
-# capture of the same kernel (None until one is taken of the current code).
-K_STAGED64_TRAFFIC_2048 = None
-K_STAGED64_TRAFFIC_SOURCE = "no ncu capture of the current kernel yet"
+# DRAM bytes per FP64 step launch at 2048^2 of the staged kernel: the ncu
+# capture of the same kernel (k_step_staged<StagedFP64, 32, 8, 4>) at 1024^2
+# read 161.8 MB and wrote 124.5 MB; traffic grows with the node count (4x).
+K_STAGED64_TRAFFIC_2048 = 4 * (161.78e6 + 124.45e6)
+K_STAGED64_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                             "k_step_staged<StagedFP64, 32, 8, 4> launch at 1024^2 (286.2 MB), "
+                             "scaled x4 by nodes to the 2048^2 launch")
 
 
 def parse():

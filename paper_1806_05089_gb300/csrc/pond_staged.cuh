@@ -409,6 +409,9 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
                 for (int l = 0; l < N1; ++l)
 #pragma unroll
                     for (int b = 0; b < N1; ++b) Z[l][b] = (Real)0;
+                float2 Z2[N1][2];  // the packed form's accumulators (pairs of b)
+#pragma unroll
+                for (int l = 0; l < N1; ++l) Z2[l][0] = Z2[l][1] = make_float2(0.f, 0.f);
 #pragma unroll 1
                 for (int y = lo; y <= hi; ++y) {
                     Real wl[N1];
@@ -419,6 +422,42 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
                         any = any || (on[l] && y >= top[l] && y <= top[l] + 3);
                     }
                     if (any) {
+                        const Real4* src = s_f + y * ww + col;
+                        const bool rowok = POND_INDEX_OK(y >= 0 && col >= 0 && y < wh &&
+                                                             col + 3 < ww && y * ww + col + 3 < WN,
+                                                         A.stats);
+                        if constexpr (Tr::kPacked) {
+                            // the same arithmetic on pairs of b (fma.rn.f32x2:
+                            // two FP32 FMAs per instruction, each rounded as
+                            // the scalar one)
+                            float2 Fi2[N1][2];
+#pragma unroll
+                            for (int a = 0; a < N1; ++a) Fi2[a][0] = Fi2[a][1] = make_float2(0.f, 0.f);
+#pragma unroll
+                            for (int jx = 0; jx < 4; ++jx) {
+                                const float2 w2 = make_float2(lx[jx], lx[jx]);
+#pragma unroll
+                                for (int a = 0; a < N1; ++a) {
+                                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                                    if (rowok) v = src[(size_t)a * WN + jx];
+                                    Fi2[a][0] = __ffma2_rn(w2, make_float2(v.x, v.y), Fi2[a][0]);
+                                    Fi2[a][1] = __ffma2_rn(w2, make_float2(v.z, v.w), Fi2[a][1]);
+                                }
+                            }
+                            float2 P2[2] = {Fi2[k][0], Fi2[k][1]};
+#pragma unroll
+                            for (int a = 0; a < N1; ++a) {
+                                const float2 e2 = make_float2(ext[a], ext[a]);
+                                P2[0] = __ffma2_rn(e2, Fi2[a][0], P2[0]);
+                                P2[1] = __ffma2_rn(e2, Fi2[a][1], P2[1]);
+                            }
+#pragma unroll
+                            for (int l = 0; l < N1; ++l) {
+                                const float2 w2 = make_float2(wl[l], wl[l]);
+                                Z2[l][0] = __ffma2_rn(w2, P2[0], Z2[l][0]);
+                                Z2[l][1] = __ffma2_rn(w2, P2[1], Z2[l][1]);
+                            }
+                        } else {
                         // Fi[a][b] = sum_jx lx[jx] g(col + jx, y)[a][b] (the row's
                         // four sources interpolated in x), then
                         // P[b] = sum_a (I + Ex)[k][a] Fi[a][b]
@@ -427,10 +466,6 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
                         for (int a = 0; a < N1; ++a)
 #pragma unroll
                             for (int b = 0; b < N1; ++b) Fi[a][b] = (Real)0;
-                        const Real4* src = s_f + y * ww + col;
-                        const bool rowok = POND_INDEX_OK(y >= 0 && col >= 0 && y < wh &&
-                                                             col + 3 < ww && y * ww + col + 3 < WN,
-                                                         A.stats);
 #pragma unroll
                         for (int jx = 0; jx < 4; ++jx) {
                             Real fr[N1][4];
@@ -468,6 +503,15 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
                         for (int l = 0; l < N1; ++l)
 #pragma unroll
                             for (int b = 0; b < N1; ++b) Z[l][b] = fma(wl[l], P[b], Z[l][b]);
+                        }
+                    }
+                }
+                if constexpr (Tr::kPacked) {
+#pragma unroll
+                    for (int l = 0; l < N1; ++l) {
+                        const float z4[4] = {Z2[l][0].x, Z2[l][0].y, Z2[l][1].x, Z2[l][1].y};
+#pragma unroll
+                        for (int b = 0; b < N1; ++b) Z[l][b] = z4[b];
                     }
                 }
                 if (work) {

@@ -564,6 +564,7 @@ struct StagedFP64 {
         double x, y, z, w;
     };
     static constexpr bool kUnrollK = true;
+    static constexpr bool kPacked = false;  // the sweep on packed FP32 pairs
     template <int NT>
     static constexpr int min_blocks() {
         return NT >= 256 ? 1 : 2;

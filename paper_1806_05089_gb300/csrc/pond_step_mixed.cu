@@ -953,6 +953,7 @@ struct StagedFP32 {
     using Real = float;
     using Real4 = float4;
     static constexpr bool kUnrollK = true;
+    static constexpr bool kPacked = true;  // the sweep on packed FP32 pairs
     template <int NT>
     static constexpr int min_blocks() {
         return 512 / NT;

@@ -112,11 +112,15 @@ def test_vortex_mixed_matches_oracle(kernel):
 
 @pytest.mark.parametrize("kernel", [pond.POND_KERNEL_STAGED, pond.POND_KERNEL_DIRECT])
 def test_vortex_mixed_halo_fallback_run_matches_fp64(kernel):
-    """A fast vortex (Ma_a 3) seeded with {-u, T}: every tile plans its staged
-    window around departures on the wrong side, so stencils leave the window
-    and take the global-memory path (halo_fallback > 0).  The mixed run still
-    matches the FP64 run of the same steps to the mixed form's 1e-5."""
-    f = _vortex64(mach_a=3.0)
+    """An advected vortex (Ma_a 1.2, |u| about 1.7) seeded with {-u, T}: every
+    tile plans its staged window around departures 2|u| dt on the wrong
+    side, so stencils leave the window and take the global-memory path
+    (halo_fallback > 0).  The mixed run still matches the FP64 run of the
+    same steps to the mixed form's 1e-5.  (At Ma_a 3 that seed is so far
+    from the fixed point that the first pass's moments are non-physical, in
+    FP64 as well: the seed-independence the paper reports holds near the
+    limit, not from any seed.)"""
+    f = _vortex64(mach_a=1.2)
     out = {}
     for prec in (pond.POND_FP64, pond.POND_FP32_MIXED):
         with pond.Sim(64, 64, prec, seed_mode=2, max_iter=60, kernel=kernel) as s:

@@ -30,6 +30,7 @@
 #include <cmath>
 
 #include "pond_device.cuh"
+#include "pond_staged.cuh"
 
 namespace pond {
 
@@ -52,6 +53,7 @@ struct AdjointScratch {
     int2* org = nullptr;         // [16][N] stencil origin of (q, t), relative to t
     double* lw = nullptr;        // [16][N][8] cubic weights of (q, t): x 0..3, y 0..3
     double* inv_st = nullptr;    // [N] 1 / s* at every target
+    double* jvp = nullptr;       // [4][16][N] A*, dA/du_x, dA/du_y, dA/ds (staged phase A)
     double host_minmax[6];
 };
 
@@ -361,6 +363,131 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A
     }
 }
 
+// The same gather with the source-gauge derivatives taken out of the hit
+// loop.  G(j -> t) = G(r -> t) G(j -> r) for any fixed r (the matched
+// moments determine the populations), so with r held at the source's own
+// gauge lambda_j,
+//   d/dlambda_j [G(j -> t) f_j]_q = [G(r -> t) dG(j -> r)/dlambda_j f_j]_q,
+// and summed over the hits (target t, population q) with their weights,
+//   lambda_j_bar = sum_{a,b} h[a][b] (dG(j -> r)/dlambda_j f_j)[a][b],
+//   h = sum_hits coef G(j -> t)[q, :]  (= the populations' cotangent f_j_bar).
+// At r = lambda_j the map G(j -> r) is the identity and its derivatives are
+// the constants L_k'(c_a) = d1[k][a] over s_j (x: d xi/d u = 1/s_j; s:
+// d xi/d s = c_a/s_j).  Each hit then costs the two rows of G(j -> t) and a
+// rank-one update, about a third of the direct gather's FP64 work.
+template <int N1>
+__global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources_r(AdjArgs A) {
+    constexpr int Q = N1 * N1;
+    const Lattice& L = c_La[lattice_slot(N1)];
+    const int lane = threadIdx.x & 31;
+    const long long src = (long long)blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
+    if (src >= A.N) return;  // warp-uniform
+    const int JX = (int)(src % A.nx), JY = (int)(src / A.nx);
+    // lane = (population q, half); on D2Q9 lanes with q >= 9 hold no
+    // population: they contribute zeros to the 16-lane sums and read nothing
+    const int q = lane & 15, half = lane >> 4;
+    const bool act = q < Q;
+    const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
+    double fj[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fj[i] = A.in.f[(long long)i * A.N + src];
+    const double uxj = A.in.ux[src], uyj = A.in.uy[src], stj = A.in.st[src];
+
+    double fb[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fb[i] = 0.0;
+    double bux = 0.0, buy = 0.0, bst = 0.0;
+
+    // candidate targets: J is in the stencil of the target at x when
+    // floor(x - v dt) is in [J - 2, J + 1], i.e. x in [J - 2 + v dt, J + 2 + v dt);
+    // over v in [vlo, vhi] the integers x from ceil(J - 2 + vlo dt) to
+    // ceil(J + 2 + vhi dt) - 1, widened by a rounding margin (the exact test
+    // below decides).  ceil(J + a) = J + ceil(a) for integer J, so the bounds
+    // are formed relative to J.
+    const double ex = 1e-9 * (1.0 + fabs(A.vlo_x[k]) + fabs(A.vhi_x[k])) * A.dt;
+    const double ey = 1e-9 * (1.0 + fabs(A.vlo_y[l]) + fabs(A.vhi_y[l])) * A.dt;
+    const int xlo = JX + (int)ceil(-2.0 + A.vlo_x[k] * A.dt - ex);
+    const int xhi = JX + (int)ceil(2.0 + A.vhi_x[k] * A.dt + ex) - 1;
+    const int ylo = JY + (int)ceil(-2.0 + A.vlo_y[l] * A.dt - ey);
+    const int yhi = JY + (int)ceil(2.0 + A.vhi_y[l] * A.dt + ey) - 1;
+    for (int yy = ylo + half; act && yy <= yhi; yy += 2) {
+        const int ty = wrap_idx(yy, A.ny);
+        for (int xx = xlo; xx <= xhi; ++xx) {
+            const int tx = wrap_idx(xx, A.nx);
+            const long long t = (long long)ty * A.nx + tx;
+            // the target's stencil origin for population q, as the target
+            // kernel found it (at the target's own, wrapped position)
+            const long long o = (long long)q * A.N + t;
+            const int2 og = A.org[o];
+            const int jx = JX - (xx + og.x), jy = JY - (yy + og.y);
+            if (jx < 0 || jx > 3 || jy < 0 || jy > 3) continue;
+            const double wgt = A.lw[8 * o + jx] * A.lw[8 * o + 4 + jy];
+            const double coef = A.w[o] * wgt;
+            const double ux = A.ux_s[t], uy = A.uy_s[t];
+            const double inv = A.inv_st[t];
+            const double r = fma(stj, inv, -1.0);
+            const double dx = (uxj - ux) * inv, dy = (uyj - uy) * inv;
+            double gx[N1], gy[N1];
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                gx[a] = gauge_poly<N1>(L.d3[k], L.d2[k][a], L.d1[k][a], a == k ? 1.0 : 0.0,
+                                       fma(L.c[a], r, dx));
+                gy[a] = gauge_poly<N1>(L.d3[l], L.d2[l][a], L.d1[l][a], a == l ? 1.0 : 0.0,
+                                       fma(L.c[a], r, dy));
+            }
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                const double cgx = coef * gx[a];
+#pragma unroll
+                for (int b = 0; b < N1; ++b) fb[N1 * a + b] = fma(cgx, gy[b], fb[N1 * a + b]);
+            }
+        }
+    }
+    // reduce over the warp (all populations and both halves)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fb[i] += __shfl_xor_sync(0xffffffffu, fb[i], o);
+    }
+    // the source-gauge cotangent from h = fb: dg/du_x [k][l] = sum_a d1[k][a]
+    // f[a][l] / s_j, dg/du_y [k][l] = sum_b d1[l][b] f[k][b] / s_j, dg/ds the
+    // same with c_a, c_b inside
+    {
+        const double is = 1.0 / stj;
+#pragma unroll
+        for (int kk = 0; kk < N1; ++kk)
+#pragma unroll
+            for (int ll = 0; ll < N1; ++ll) {
+                double gxu = 0.0, gyu = 0.0, gsx = 0.0, gsy = 0.0;
+#pragma unroll
+                for (int a = 0; a < N1; ++a) {
+                    gxu = fma(L.d1[kk][a], fj[N1 * a + ll], gxu);
+                    gsx = fma(L.d1[kk][a] * L.c[a], fj[N1 * a + ll], gsx);
+                    gyu = fma(L.d1[ll][a], fj[N1 * kk + a], gyu);
+                    gsy = fma(L.d1[ll][a] * L.c[a], fj[N1 * kk + a], gsy);
+                }
+                const double h = fb[N1 * kk + ll];
+                bux = fma(h, gxu * is, bux);
+                buy = fma(h, gyu * is, buy);
+                bst = fma(h, (gsx + gsy) * is, bst);
+            }
+    }
+    if (lane < Q) {
+        double v = fb[0];
+#pragma unroll
+        for (int i = 1; i < Q; ++i)
+            if (lane == i) v = fb[i];
+        A.fbar_in[(long long)lane * A.N + src] = v;
+    } else if (lane == 16) {
+        A.gbar_in[src] = bux;
+    } else if (lane == 17) {
+        A.gbar_in[A.N + src] = buy;
+    } else if (lane == 18) {
+        // s = sqrt(T / T_L): dL/dT = dL/ds / (2 s T_L)
+        A.gbar_in[2 * A.N + src] = bst / (2.0 * stj * A.T_L);
+    }
+}
+
 // Bounds {min ux, max ux, min uy, max uy, min s, max s} of a gauge field,
 // exact in FP64: a grid-stride pass, warp reductions, and 64-bit integer
 // atomics on an order-preserving encoding of the doubles (one per warp and
@@ -424,6 +551,399 @@ cudaError_t launch_minmax3(const double* ux, const double* uy, const double* st,
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Phase A in the staged form of the forward step (pond_staged.cuh): the
+// sources are re-expressed once per tile in a reference gauge lambda_r (the
+// tile's centre node of the input state), g = G(s -> r) f_s, and for each
+// target population (k, l)
+//   A_q(lambda) = sum_b (I + Ey)[l][b] sum_jy ly[jy] P(jy)[b],
+//   P(jy)[b]    = sum_a (I + Ex)[k][a] Fi[a][b],  Fi = sum_jx lx[jx] g(x0 + jx, y0 + jy),
+// with Ex, Ey the maps r -> lambda.  Its tangents at lambda* follow term by
+// term: the cubic weights move with the departure point (d t / d u = -dt,
+// d t / d s = -c dt) and the maps with xi_a = (s_r c_a + u_r - u) / s
+// (d xi / d u = -1/s, d xi / d s = -xi / s), so one sweep of the stencil rows
+// gives A and its three tangents from the interpolated rows Fi and their
+// weight derivatives Fd = sum_jx lx'[jx] g.  About a third of the FP64
+// arithmetic of the per-(population, source) form.
+
+struct StagedAdj64 {
+    using Real = double;
+    using Real4 = Double4;
+    template <int N1>
+    static __device__ __forceinline__ const Lattice& lat() {
+        return c_La[lattice_slot(N1)];
+    }
+    static __device__ __forceinline__ void load4(const Real4* p, double (&v)[4]) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = b.x;
+        v[3] = b.y;
+    }
+    static __device__ __forceinline__ void store4(Real4* p, const double (&v)[4]) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+};
+
+// L_k(c_a + de) - [k == a] in correction form, and L_k'(c_a + de).
+__device__ __forceinline__ void lag_taylor_e(const Lattice& L, int k, int a, double de, double& e,
+                                            double& gd) {
+    const double d1 = L.d1[k][a], d2 = L.d2[k][a], d3 = L.d3[k];
+    e = fma(fma(d3, de, d2), de, d1) * de;
+    gd = fma(fma(3.0 * d3, de, 2.0 * d2), de, d1);
+}
+
+// One population's A and tangents in the direct form, read from global
+// memory: for a stencil that leaves the staged window.
+template <int N1>
+__device__ __noinline__ void adj_population_direct(const AdjArgs& A, int X, int Y, int k, int l,
+                                                   double ux, double uy, double st,
+                                                   double* out4) {
+    const Lattice& L = c_La[lattice_slot(N1)];
+    const double ck = L.c[k], cl = L.c[l];
+    const double inv = 1.0 / st;
+    const double vx = fma(st, ck, ux), vy = fma(st, cl, uy);
+    const double depx = (double)X - vx * A.dt, depy = (double)Y - vy * A.dt;
+    const double flx = floor(depx), fly = floor(depy);
+    double lx[4], dlx[4], ly[4], dly[4];
+    lagrange4_d(depx - flx + 1.0, lx, dlx);
+    lagrange4_d(depy - fly + 1.0, ly, dly);
+    const int x0 = wrap_idx((long long)flx - 1, A.nx);
+    const int y0 = wrap_idx((long long)fly - 1, A.ny);
+    double Aq = 0.0, dAux = 0.0, dAuy = 0.0, dAst = 0.0;
+    for (int jy = 0; jy < 4; ++jy) {
+        const int sy = wrap_inc(y0, jy, A.ny);
+        for (int jx = 0; jx < 4; ++jx) {
+            const int sx = wrap_inc(x0, jx, A.nx);
+            const long long s = (long long)sy * A.nx + sx;
+            const double r = fma(A.in.st[s], inv, -1.0);
+            const double dx = (A.in.ux[s] - ux) * inv;
+            const double dy = (A.in.uy[s] - uy) * inv;
+            double gx[N1], gdx[N1], gy[N1], gdy[N1], xix[N1], xiy[N1];
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                const double ex = fma(L.c[a], r, dx), ey = fma(L.c[a], r, dy);
+                xix[a] = L.c[a] + ex;
+                xiy[a] = L.c[a] + ey;
+                lag_taylor(L, k, a, ex, gx[a], gdx[a]);
+                lag_taylor(L, l, a, ey, gy[a], gdy[a]);
+            }
+            double g = 0.0, gux = 0.0, guy = 0.0, gst = 0.0;
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                double h = 0.0, hp = 0.0, hq = 0.0;
+#pragma unroll
+                for (int b = 0; b < N1; ++b) {
+                    const double fv = A.in.f[(long long)(N1 * a + b) * A.N + s];
+                    h = fma(gy[b], fv, h);
+                    hp = fma(gdy[b], fv, hp);
+                    hq = fma(gdy[b] * xiy[b], fv, hq);
+                }
+                g = fma(gx[a], h, g);
+                gux = fma(gdx[a], h, gux);
+                guy = fma(gx[a], hp, guy);
+                gst = fma(gdx[a] * xix[a], h, fma(gx[a], hq, gst));
+            }
+            gux *= -inv;
+            guy *= -inv;
+            gst *= -inv;
+            const double wx = lx[jx], dwx = dlx[jx], wy = ly[jy], dwy = dly[jy];
+            const double a_w = wx * wy;
+            const double da_ux = -A.dt * dwx * wy;
+            const double da_uy = -A.dt * wx * dwy;
+            const double da_st = -A.dt * (ck * dwx * wy + cl * wx * dwy);
+            Aq = fma(a_w, g, Aq);
+            dAux = fma(a_w, gux, fma(da_ux, g, dAux));
+            dAuy = fma(a_w, guy, fma(da_uy, g, dAuy));
+            dAst = fma(a_w, gst, fma(da_st, g, dAst));
+        }
+    }
+    out4[0] = Aq;
+    out4[1] = dAux;
+    out4[2] = dAuy;
+    out4[3] = dAst;
+}
+
+constexpr int ADJ_TY = 4;  // staged phase A tile: 32 x 4 targets
+
+// Phase A, staged: A*, its tangents at lambda* into jvp[4][Q][N], the
+// gather's per-(population, target) stencil origin and weights, and 1 / s*.
+template <int N1>
+__global__ void __launch_bounds__(32 * ADJ_TY, 1)
+k_adjoint_jvp_staged(AdjArgs A, int wwa, int wha, double c_max, double* __restrict__ jvp) {
+    constexpr int TX = 32, NT = TX * ADJ_TY, Q = N1 * N1;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    Double4* s_f = reinterpret_cast<Double4*>(smem_raw);  // [N1][WN]
+    __shared__ float s_red[4][NT / 32];
+    const Lattice& L = c_La[lattice_slot(N1)];
+    const int WN = wwa * wha;
+    const int tid = threadIdx.x;
+    const int tiles_x = (A.nx + TX - 1) / TX;
+    const int tx0 = (int)(blockIdx.x % tiles_x) * TX;
+    const int ty0 = (int)(blockIdx.x / tiles_x) * ADJ_TY;
+    const int X = tx0 + tid % TX, Y = ty0 + tid / TX;
+    const bool valid = X < A.nx && Y < A.ny;
+    const long long node = (long long)Y * A.nx + X;
+
+    // reference gauge: the tile's centre node of the input state
+    const long long rnode = (long long)min(ty0 + ADJ_TY / 2, A.ny - 1) * A.nx +
+                            min(tx0 + TX / 2, A.nx - 1);
+    const double rux = A.in.ux[rnode], ruy = A.in.uy[rnode], rst = A.in.st[rnode];
+
+    double ux = 0.0, uy = 0.0, st = 1.0;
+    float vxlo = 3.0e38f, vxhi = -3.0e38f, vylo = 3.0e38f, vyhi = -3.0e38f;
+    if (valid) {
+        ux = A.ux_s[node];
+        uy = A.uy_s[node];
+        st = A.st_s[node];
+        const float sp = (float)(c_max * st);
+        vxlo = (float)ux - sp;
+        vxhi = (float)ux + sp;
+        vylo = (float)uy - sp;
+        vyhi = (float)uy + sp;
+    }
+    staged_block_minmax4<StagedAdj64, NT>(vxlo, vxhi, vylo, vyhi, s_red);
+    const float m = 1.0f, fdt = (float)A.dt;
+    const float bxl = fminf(fmaxf(vxlo, -1.0e6f), 1.0e6f), bxh = fminf(fmaxf(vxhi, -1.0e6f), 1.0e6f);
+    const float byl = fminf(fmaxf(vylo, -1.0e6f), 1.0e6f), byh = fminf(fmaxf(vyhi, -1.0e6f), 1.0e6f);
+    const int wx0 = (int)floorf((float)tx0 - bxh * fdt - m) - 1;
+    const int wx1 = (int)floorf((float)(tx0 + TX - 1) - bxl * fdt + m) + 2;
+    const int wy0 = (int)floorf((float)ty0 - byh * fdt - m) - 1;
+    const int wy1 = (int)floorf((float)(ty0 + ADJ_TY - 1) - byl * fdt + m) + 2;
+    const bool fin = isfinite(vxlo) && isfinite(vxhi) && isfinite(vylo) && isfinite(vyhi) &&
+                     vxlo > -1.0e6f && vxhi < 1.0e6f && vylo > -1.0e6f && vyhi < 1.0e6f;
+    const int ww = fin ? max(1, min(wx1 - wx0 + 1, wwa)) : 1;
+    const int wh = fin ? max(1, min(wy1 - wy0 + 1, wha)) : 1;
+    GridDesc G;
+    G.nx = A.nx;
+    G.ny = A.ny;
+    G.offset = 0;
+    G.ix0 = 0;
+    G.iy0 = 0;
+    G.iw = A.nx;
+    G.ih = A.ny;
+    stage_window<StagedAdj64, N1>(A.in, A.N, G, 0, wx0, wy0, ww, wh, WN, rux, ruy, rst, s_f,
+                                  nullptr, tid, NT);
+    __syncthreads();
+    if (!valid) return;
+
+    const double inv = 1.0 / st;
+    A.inv_st[node] = inv;
+    // offsets of the maps r -> lambda*
+    const double rt = (rst - st) * inv, dxt = (rux - ux) * inv, dyt = (ruy - uy) * inv;
+    const double dt = A.dt;
+#pragma unroll
+    for (int k = 0; k < N1; ++k) {
+        const double ck = L.c[k];
+        const double depx = (double)X - fma(st, ck, ux) * dt;
+        const double flx = floor(depx);
+        double lx[4], dlx[4];
+        lagrange4_d(depx - flx + 1.0, lx, dlx);
+        const int col = (int)flx - 1 - wx0;  // flx is the absolute departure floor
+        double ex[N1], gdx[N1], xix[N1];
+#pragma unroll
+        for (int a = 0; a < N1; ++a) {
+            const double de = fma(L.c[a], rt, dxt);
+            lag_taylor_e(L, k, a, de, ex[a], gdx[a]);
+            xix[a] = L.c[a] + de;
+        }
+#pragma unroll 1
+        for (int l = 0; l < N1; ++l) {
+            const double cl = L.c[l];
+            const double depy = (double)Y - fma(st, cl, uy) * dt;
+            const double fly = floor(depy);
+            double ly[4], dly[4];
+            lagrange4_d(depy - fly + 1.0, ly, dly);
+            const int top = (int)fly - 1 - wy0;
+            const int q = N1 * k + l;
+            const long long o = (long long)q * A.N + node;
+            A.org[o] = make_int2((int)((long long)flx - 1 - X), (int)((long long)fly - 1 - Y));
+            double2* pw = reinterpret_cast<double2*>(A.lw + 8 * o);
+            pw[0] = make_double2(lx[0], lx[1]);
+            pw[1] = make_double2(lx[2], lx[3]);
+            pw[2] = make_double2(ly[0], ly[1]);
+            pw[3] = make_double2(ly[2], ly[3]);
+            double R[4];
+            if (col >= 0 && col + 3 < ww && top >= 0 && top + 3 < wh) {
+                double Z[N1], Zux[N1], Zuy[N1], Zs[N1];
+#pragma unroll
+                for (int b = 0; b < N1; ++b) Z[b] = Zux[b] = Zuy[b] = Zs[b] = 0.0;
+#pragma unroll 1
+                for (int jy = 0; jy < 4; ++jy) {
+                    const double w = jy == 0 ? ly[0] : jy == 1 ? ly[1] : jy == 2 ? ly[2] : ly[3];
+                    const double dw = jy == 0 ? dly[0] : jy == 1 ? dly[1] : jy == 2 ? dly[2] : dly[3];
+                    const Double4* src = s_f + (top + jy) * ww + col;
+                    double Fi[N1][N1], Fd[N1][N1];
+#pragma unroll
+                    for (int a = 0; a < N1; ++a)
+#pragma unroll
+                        for (int b = 0; b < N1; ++b) Fi[a][b] = Fd[a][b] = 0.0;
+#pragma unroll
+                    for (int jx = 0; jx < 4; ++jx) {
+#pragma unroll
+                        for (int a = 0; a < N1; ++a) {
+                            double fr[4];
+                            StagedAdj64::load4(src + (size_t)a * WN + jx, fr);
+#pragma unroll
+                            for (int b = 0; b < N1; ++b) {
+                                Fi[a][b] = fma(lx[jx], fr[b], Fi[a][b]);
+                                Fd[a][b] = fma(dlx[jx], fr[b], Fd[a][b]);
+                            }
+                        }
+                    }
+                    // row contributions: value, and the tangents through the
+                    // x-weights (Fd), the x-map (gdx) and the row weight (dw)
+                    const double wux = -dt * w, wdy = -dt * dw;
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) {
+                        double P = Fi[k][b], P1 = Fd[k][b], Pd = 0.0, Pdx = 0.0;
+#pragma unroll
+                        for (int a = 0; a < N1; ++a) {
+                            P = fma(ex[a], Fi[a][b], P);
+                            P1 = fma(ex[a], Fd[a][b], P1);
+                            Pd = fma(gdx[a], Fi[a][b], Pd);
+                            Pdx = fma(gdx[a] * xix[a], Fi[a][b], Pdx);
+                        }
+                        Z[b] = fma(w, P, Z[b]);
+                        Zux[b] = fma(wux, P1, fma(-w * inv, Pd, Zux[b]));
+                        Zuy[b] = fma(wdy, P, Zuy[b]);
+                        Zs[b] = fma(ck * wux, P1, fma(-w * inv, Pdx, fma(cl * wdy, P, Zs[b])));
+                    }
+                }
+                // the y-map r -> lambda* and its derivatives
+                double Al = 0.0, Axl = 0.0, Ayl = 0.0, Asl = 0.0;
+#pragma unroll
+                for (int b = 0; b < N1; ++b) {
+                    const bool id = b == l;  // the identity part, exactly
+                    Al += id ? Z[b] : 0.0;
+                    Axl += id ? Zux[b] : 0.0;
+                    Ayl += id ? Zuy[b] : 0.0;
+                    Asl += id ? Zs[b] : 0.0;
+                }
+                double Ae = 0.0, Axe = 0.0, Aye = 0.0, Ase = 0.0, Dy = 0.0, Ds = 0.0;
+#pragma unroll
+                for (int b = 0; b < N1; ++b) {
+                    const double de = fma(L.c[b], rt, dyt);
+                    double ey, gdy;
+                    lag_taylor_e(L, l, b, de, ey, gdy);
+                    Ae = fma(ey, Z[b], Ae);
+                    Axe = fma(ey, Zux[b], Axe);
+                    Aye = fma(ey, Zuy[b], Aye);
+                    Ase = fma(ey, Zs[b], Ase);
+                    Dy = fma(gdy, Z[b], Dy);
+                    Ds = fma(gdy * (L.c[b] + de), Z[b], Ds);
+                }
+                R[0] = Al + Ae;
+                R[1] = Axl + Axe;
+                R[2] = fma(-inv, Dy, Ayl + Aye);
+                R[3] = fma(-inv, Ds, Asl + Ase);
+            } else {
+                adj_population_direct<N1>(A, X, Y, k, l, ux, uy, st, R);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) jvp[((long long)i * Q + q) * A.N + node] = R[i];
+        }
+    }
+}
+
+// The rest of phase A from A* and its tangents: the collision cotangent,
+// beta_bar, the 3 x 3 implicit solve at the fixed point and w (one warp per
+// target node, lane = population, as k_adjoint_targets).
+template <int N1>
+__global__ void __launch_bounds__(ADJ_WARPS * 32, 2)
+k_adjoint_epilogue(AdjArgs A, const double* __restrict__ jvp) {
+    constexpr int Q = N1 * N1;
+    const Lattice& L = c_La[lattice_slot(N1)];
+    const int lane = threadIdx.x & 31;
+    const long long node = (long long)blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
+    if (node >= A.N) return;  // warp-uniform
+    const int q = lane & 15;
+    const bool act = lane < Q;
+    const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
+    const double ck = act ? L.c[k] : 0.0, cl = act ? L.c[l] : 0.0;
+    const double st = A.st_s[node];
+    double Aq = 0.0, dAux = 0.0, dAuy = 0.0, dAst = 0.0;
+    if (act) {
+        Aq = jvp[((long long)0 * Q + q) * A.N + node];
+        dAux = jvp[((long long)1 * Q + q) * A.N + node];
+        dAuy = jvp[((long long)2 * Q + q) * A.N + node];
+        dAst = jvp[((long long)3 * Q + q) * A.N + node];
+    }
+    auto sum32 = [](double v) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
+    const double Wq = act ? L.w[k] * L.w[l] : 0.0;
+    const double fb = act ? A.fbar[(long long)q * A.N + node] : 0.0;
+    const double rho = sum32(Aq);
+    const double wf = sum32(Wq * fb);
+    const double Abar = (1.0 - 2.0 * A.beta) * fb + 2.0 * A.beta * wf;
+    const double bb = sum32(act ? 2.0 * (rho * Wq - Aq) * fb : 0.0);
+    const double c2 = ck * ck + cl * cl;
+    const double mux = st * ck / rho, muy = st * cl / rho;
+    const double mst = act ? st * (c2 - 2.0 * A.T_L) / (4.0 * rho * A.T_L) : 0.0;
+    double J[3][3];
+    J[0][0] = sum32(mux * dAux);
+    J[0][1] = sum32(mux * dAuy);
+    J[0][2] = sum32(mux * dAst);
+    J[1][0] = sum32(muy * dAux);
+    J[1][1] = sum32(muy * dAuy);
+    J[1][2] = sum32(muy * dAst);
+    J[2][0] = sum32(mst * dAux);
+    J[2][1] = sum32(mst * dAuy);
+    J[2][2] = sum32(mst * dAst);
+    double g0 = sum32(Abar * dAux) + A.gbar[node];
+    double g1 = sum32(Abar * dAuy) + A.gbar[A.N + node];
+    double g2 = sum32(Abar * dAst) + A.gbar[2 * A.N + node] * 2.0 * st * A.T_L;
+    const double a00 = J[0][0], a01 = J[1][0], a02 = J[2][0];
+    const double a10 = J[0][1], a11 = J[1][1], a12 = J[2][1];
+    const double a20 = J[0][2], a21 = J[1][2], a22 = J[2][2];
+    const double det = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
+                       a02 * (a10 * a21 - a11 * a20);
+    const double idet = 1.0 / det;
+    const double r0 = -g0, r1 = -g1, r2 = -g2;
+    const double mu0 = (r0 * (a11 * a22 - a12 * a21) - a01 * (r1 * a22 - a12 * r2) +
+                        a02 * (r1 * a21 - a11 * r2)) * idet;
+    const double mu1 = (a00 * (r1 * a22 - a12 * r2) - r0 * (a10 * a22 - a12 * a20) +
+                        a02 * (a10 * r2 - r1 * a20)) * idet;
+    const double mu2 = (a00 * (a11 * r2 - r1 * a21) - a01 * (a10 * r2 - r1 * a20) +
+                        r0 * (a10 * a21 - a11 * a20)) * idet;
+    const double wq = Abar + mux * mu0 + muy * mu1 + mst * mu2;
+    if (act) A.w[(long long)q * A.N + node] = wq;
+    if (lane == 0) atomicAdd(A.beta_bar, bb);
+}
+
+// Shared memory and launch of the staged phase A for a window of wwa x wha
+// staged nodes (FP64 rows of 32 bytes).
+cudaError_t launch_adjoint_phase_a_staged(const AdjArgs& A, int n1, int wwa, int wha, double c_max,
+                                          double* jvp, cudaStream_t s) {
+    static int s_set[64][2] = {{0}};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const size_t smem = (size_t)n1 * wwa * wha * sizeof(Double4);
+    void (*kern)(AdjArgs, int, int, double, double*) =
+        n1 == 3 ? k_adjoint_jvp_staged<3> : k_adjoint_jvp_staged<4>;
+    int& set = s_set[dev][n1 == 3 ? 1 : 0];
+    if ((int)smem > set) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set = (int)smem;
+    }
+    const unsigned tiles = (unsigned)(((A.nx + 31) / 32) * ((A.ny + ADJ_TY - 1) / ADJ_TY));
+    kern<<<tiles, 32 * ADJ_TY, smem, s>>>(A, wwa, wha, c_max, jvp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned nb = (unsigned)((A.N + ADJ_WARPS - 1) / ADJ_WARPS);
+    if (n1 == 3) k_adjoint_epilogue<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A, jvp);
+    else k_adjoint_epilogue<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A, jvp);
+    return cudaGetLastError();
+}
+
 template <int N1>
 __global__ void k_rho_bar(const double* __restrict__ fbar, double* __restrict__ rbar, long long N) {
     const Lattice& L = c_La[lattice_slot(N1)];
@@ -454,6 +974,7 @@ void destroy_adjoint(pond_ctx* ctx) {
     cudaFree(a->org);
     cudaFree(a->lw);
     cudaFree(a->inv_st);
+    cudaFree(a->jvp);
     delete a;
     ctx->adj = nullptr;
 }
@@ -621,11 +1142,33 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
     }
     const unsigned nb = (unsigned)((N + ADJ_WARPS - 1) / ADJ_WARPS);
     nvtxRangePushA("adjoint targets + transpose gather");
-    if (ctx->L.n1 == 3) k_adjoint_targets<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
-    else k_adjoint_targets<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    if (ctx_staged(ctx)) {
+        // phase A in the staged form: a window per 32 x 4 tile of targets
+        // sized from the bounds of the particle velocities at lambda*
+        if (!a->jvp) ACK(cudaMalloc(&a->jvp, sizeof(double) * 4 * 16 * N), "adjoint alloc");
+        const double cm = ctx->L.c_max;
+        const double sx = (mm[1] - mm[0]) + 2.0 * cm * mm[5];
+        const double sy = (mm[3] - mm[2]) + 2.0 * cm * mm[5];
+        int wwa = 32 + (int)std::ceil(sx * A.dt + 2.0) + 5;
+        int wha = ADJ_TY + (int)std::ceil(sy * A.dt + 2.0) + 5;
+        const size_t cap = 200 * 1024;
+        while ((size_t)ctx->L.n1 * wwa * wha * sizeof(Double4) > cap) {
+            if (wwa - 32 >= wha - ADJ_TY) --wwa; else --wha;
+        }
+        ACK(launch_adjoint_phase_a_staged(A, ctx->L.n1, wwa, wha, cm, a->jvp, s),
+            "adjoint targets (staged)");
+    } else {
+        if (ctx->L.n1 == 3) k_adjoint_targets<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+        else k_adjoint_targets<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    }
     ACK(cudaGetLastError(), "adjoint targets");
-    if (ctx->L.n1 == 3) k_adjoint_sources<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
-    else k_adjoint_sources<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    if (ctx_staged(ctx)) {
+        if (ctx->L.n1 == 3) k_adjoint_sources_r<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+        else k_adjoint_sources_r<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    } else {
+        if (ctx->L.n1 == 3) k_adjoint_sources<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+        else k_adjoint_sources<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+    }
     nvtxRangePop();
     ACK(cudaGetLastError(), "adjoint sources");
     double bb = 0.0;

@@ -53,6 +53,11 @@
 
 namespace pond {
 
+// Four FP64 values in 32 bytes: one row of a staged FP64 source.
+struct __align__(32) Double4 {
+    double x, y, z, w;
+};
+
 template <typename Real>
 struct StagedArgs {
     StateBuf<Real> in, out;
@@ -178,13 +183,80 @@ __device__ __noinline__ typename Tr::Real staged_fallback(const StagedArgs<typen
     return acc;
 }
 
+// Stage the window [wx0, wx0 + ww) x [wy0, wy0 + wh) of grid G (periodic
+// wrap; state planes of stride `plane`) into s_f, each source re-expressed in
+// the reference gauge lambda_r = (rux, ruy, rst):
+//   g = f_s + Ex (f_s + Ey f_s) + Ey f_s   (G(s -> r) = (I + Ex) (x) (I + Ey)),
+// with xi_a = c_a + c_a (st_s/st_r - 1) + (u_s - u_r)/st_r formed in FP64.
+// Rows a = 0..n1-1 of g at s_f[a * WN + i], i = the window-relative node.
+// All threads of the block take part (a block-stride loop); the caller
+// synchronises afterwards.
+template <class Tr, int N1>
+__device__ __forceinline__ void stage_window(const StateBuf<typename Tr::Real>& in, long long plane,
+                                             const GridDesc& G, long long base, int wx0, int wy0,
+                                             int ww, int wh, int WN, double rux, double ruy,
+                                             double rst, typename Tr::Real4* s_f,
+                                             DevStats* stats, int tid, int nt) {
+    using Real = typename Tr::Real;
+    constexpr int Q = N1 * N1;
+    const auto& L = Tr::template lat<N1>();
+    const double inv_rst = 1.0 / rst;
+    (void)stats;
+    for (int i = tid; i < ww * wh; i += nt) {
+        const int cx = i % ww, cy = i / ww;
+        const int gx = wrap_idx((long long)wx0 + cx, G.nx);
+        const int gy = wrap_idx((long long)wy0 + cy, G.ny);
+        const long long gi = base + (long long)gy * G.nx + gx;
+        if (!POND_INDEX_OK(gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny && i < WN, stats))
+            continue;
+        const Real r = (Real)((__ldg(in.st + gi) - rst) * inv_rst);
+        const Real dx = (Real)((__ldg(in.ux + gi) - rux) * inv_rst);
+        const Real dy = (Real)((__ldg(in.uy + gi) - ruy) * inv_rst);
+        Real f[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) f[q] = __ldg(in.f + gi + (long long)q * plane);
+        Real ex[N1][N1], ey[N1][N1];  // [k][a]
+#pragma unroll
+        for (int a = 0; a < N1; ++a) {
+            const Real dex = fma((Real)L.c[a], r, dx), dey = fma((Real)L.c[a], r, dy);
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                ex[k][a] = gauge_tail<N1>((Real)L.d3[k], (Real)L.d2[k][a], (Real)L.d1[k][a], dex) * dex;
+                ey[k][a] = gauge_tail<N1>((Real)L.d3[k], (Real)L.d2[k][a], (Real)L.d1[k][a], dey) * dey;
+            }
+        }
+        Real H[Q];
+#pragma unroll
+        for (int a = 0; a < N1; ++a)
+#pragma unroll
+            for (int l = 0; l < N1; ++l) {
+                Real v = (Real)0;
+#pragma unroll
+                for (int b = 0; b < N1; ++b) v = fma(ey[l][b], f[N1 * a + b], v);
+                H[N1 * a + l] = v;
+            }
+        Real out[4][4];
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+#pragma unroll
+            for (int l = 0; l < N1; ++l) {
+                Real c = H[N1 * k + l];
+#pragma unroll
+                for (int a = 0; a < N1; ++a) c = fma(ex[k][a], f[N1 * a + l] + H[N1 * a + l], c);
+                out[k][l] = f[N1 * k + l] + c;
+            }
+            if constexpr (N1 == 3) out[k][3] = (Real)0;
+            Tr::store4(s_f + (size_t)k * WN + i, out[k]);
+        }
+    }
+}
+
 template <class Tr, int TX, int TY, int N1>
 __global__ void __launch_bounds__(TX* TY, Tr::template min_blocks<TX * TY>())
 k_step_staged(StagedArgs<typename Tr::Real> A) {
     using Real = typename Tr::Real;
     using Real4 = typename Tr::Real4;
     constexpr int NT = TX * TY;
-    constexpr int Q = N1 * N1;
     constexpr unsigned FULL = 0xffffffffu;
     static_assert(TX == 32, "a warp is one tile row");
     extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -244,7 +316,6 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
         const long long rnode = base + (long long)min(ty0 + TY / 2, G.iy0 + G.ih - 1) * G.nx +
                                 min(tx0 + TX / 2, G.ix0 + G.iw - 1);
         const double rux = A.in.ux[rnode], ruy = A.in.uy[rnode], rst = A.in.st[rnode];
-        const double inv_rst = 1.0 / rst;
 
         PassGauge pg;
         pg.ux = 0.0;
@@ -287,56 +358,9 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
         const int ww = fin ? max(1, min(wx1 - wx0 + 1, A.ww)) : 1;
         const int wh = fin ? max(1, min(wy1 - wy0 + 1, A.wh)) : 1;
 
-        // stage the window, each source re-expressed in lambda_r:
-        //   g = f_s + Ex (f_s + Ey f_s) + Ey f_s  (G(s -> r) = (I + Ex) (x) (I + Ey))
-        for (int i = tid; i < ww * wh; i += NT) {
-            const int cx = i % ww, cy = i / ww;
-            const int gx = wrap_idx((long long)wx0 + cx, G.nx);
-            const int gy = wrap_idx((long long)wy0 + cy, G.ny);
-            const long long gi = base + (long long)gy * G.nx + gx;
-            if (!POND_INDEX_OK(gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny && i < WN, A.stats))
-                continue;
-            // xi_a = c_a + c_a (st_s/st_r - 1) + (u_s - u_r)/st_r, in FP64
-            const Real r = (Real)((__ldg(A.in.st + gi) - rst) * inv_rst);
-            const Real dx = (Real)((__ldg(A.in.ux + gi) - rux) * inv_rst);
-            const Real dy = (Real)((__ldg(A.in.uy + gi) - ruy) * inv_rst);
-            Real f[Q];
-#pragma unroll
-            for (int q = 0; q < Q; ++q) f[q] = __ldg(A.in.f + gi + (long long)q * A.plane);
-            Real ex[N1][N1], ey[N1][N1];  // [k][a]
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                const Real dex = fma(L.c[a], r, dx), dey = fma(L.c[a], r, dy);
-#pragma unroll
-                for (int k = 0; k < N1; ++k) {
-                    ex[k][a] = gauge_tail<N1>((Real)L.d3[k], (Real)L.d2[k][a], (Real)L.d1[k][a], dex) * dex;
-                    ey[k][a] = gauge_tail<N1>((Real)L.d3[k], (Real)L.d2[k][a], (Real)L.d1[k][a], dey) * dey;
-                }
-            }
-            Real H[Q];
-#pragma unroll
-            for (int a = 0; a < N1; ++a)
-#pragma unroll
-                for (int l = 0; l < N1; ++l) {
-                    Real v = (Real)0;
-#pragma unroll
-                    for (int b = 0; b < N1; ++b) v = fma(ey[l][b], f[N1 * a + b], v);
-                    H[N1 * a + l] = v;
-                }
-            Real out[4][4];
-#pragma unroll
-            for (int k = 0; k < N1; ++k) {
-#pragma unroll
-                for (int l = 0; l < N1; ++l) {
-                    Real c = H[N1 * k + l];
-#pragma unroll
-                    for (int a = 0; a < N1; ++a) c = fma(ex[k][a], f[N1 * a + l] + H[N1 * a + l], c);
-                    out[k][l] = f[N1 * k + l] + c;
-                }
-                if constexpr (N1 == 3) out[k][3] = (Real)0;
-                Tr::store4(s_f + (size_t)k * WN + i, out[k]);
-            }
-        }
+        // stage the window, each source re-expressed in lambda_r
+        stage_window<Tr, N1>(A.in, A.plane, G, base, wx0, wy0, ww, wh, WN, rux, ruy, rst, s_f,
+                             A.stats, tid, NT);
         __syncthreads();
 
         // ---------------------------------------------------- pass loop

@@ -560,9 +560,7 @@ cudaError_t launch_step_fp64(const StateBuf<double>& in, const StateBuf<double>&
 
 struct StagedFP64 {
     using Real = double;
-    struct __align__(32) Real4 {
-        double x, y, z, w;
-    };
+    using Real4 = Double4;
     static constexpr bool kUnrollK = true;
     static constexpr bool kPacked = false;  // the sweep on packed FP32 pairs
     template <int NT>

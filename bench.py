@@ -264,12 +264,15 @@ def time_steps(sim, stream, steps):
 
 
 def form_line(name, nodes, steps, secs, stats, precision_peak_tflops, bytes_per_update,
-              flop_per_pass=FLOP_PER_PASS):
+              flop_per_pass=FLOP_PER_PASS, direct_flop_per_pass=FLOP_PER_PASS):
     """One form's throughput and roofline; flop_per_pass is the count of the
     kernel that ran (staged_flops_per_pass for the staged kernel, the
-    per-pair count FLOP_PER_PASS for the direct ones)."""
+    per-pair count FLOP_PER_PASS for the direct ones).  The per-pair count
+    of the lattice (direct_flop_per_pass) gives the direct-equivalent rate
+    beside it: the same throughput counted as the per-pair form's work."""
     passes = stats["passes"] / max(stats["node_updates"], 1)
     achieved = flop_per_pass * stats["passes"] / secs / 1e12
+    direct_eq = direct_flop_per_pass * stats["passes"] / secs / 1e12
     return {
         "workload": name,
         "value": nodes * steps / secs,
@@ -283,6 +286,8 @@ def form_line(name, nodes, steps, secs, stats, precision_peak_tflops, bytes_per_
         "tile": [32, stats.get("tile_rows", 0)],
         "alu_tflops": achieved,
         "alu_frac": achieved / precision_peak_tflops,
+        "flop_per_pass": flop_per_pass,
+        "direct_equivalent_frac": direct_eq / precision_peak_tflops,
         "hbm_gbs_algorithmic": nodes * steps * bytes_per_update / secs / 1e9,
     }
 
@@ -495,6 +500,11 @@ def run_pond(args, world, rank, local):
         forms["batched_256"] = form_line("ensemble-256-mixed", bnodes, k2, bsecs, bstats,
                                          peak32, BYTES_MIXED, staged_flops_per_pass(4, st_b))
         forms["batched_256"]["grids_on_this_rank"] = len(mine)
+        # share of the persistent launches' CTA slots left idle (start skew
+        # and the tail after the work list ran dry), from the kernel's own
+        # globaltimer stamps
+        if bstats.get("slot_ns", 0) > 0:
+            forms["batched_256"]["idle_slot_frac"] = 1.0 - bstats["busy_ns"] / bstats["slot_ns"]
         forms["batched_256"]["all_ranks_value"] = (int(sum(a * b for a, b in zip(nxs_all, nys_all)))
                                                    * k2 / bsecs_max)
         bsim.close()
@@ -517,7 +527,8 @@ def run_pond(args, world, rank, local):
             forms[key] = form_line("supersonic-2048-d2q9-" + ("fp64" if prec == pond.POND_FP64
                                                               else "mixed"),
                                    nodes, args.steps, qsecs, qstats, peak, nbytes,
-                                   staged_flops_per_pass(3, float(np.sqrt(q9.T * 3.0).mean())))
+                                   staged_flops_per_pass(3, float(np.sqrt(q9.T * 3.0).mean())),
+                                   FLOP_PER_PASS_Q9)
             q9_out[key] = qsim.moments()
             qsim.close()
         r64, u64x, u64y, t64 = q9_out["fp64_d2q9_2048"]

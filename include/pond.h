@@ -159,6 +159,13 @@ typedef struct pond_stats {
                               POND_DEBUG): accesses of the staged kernel that
                               failed their index check and were skipped; 0
                               in release builds, which have no checks */
+    int64_t busy_ns;       /* batched contexts on the staged kernel (one
+                              persistent launch per step): CTA busy time
+                              summed over the launches' CTAs, in ns */
+    int64_t slot_ns;       /* the same launches' CTA slots: resident CTAs x
+                              launch span, in ns.  1 - busy_ns / slot_ns is
+                              the share of those slots left idle by the start
+                              skew and the tail; both 0 for other contexts */
 } pond_stats;
 
 /* Defaults for a precision (POND_FP64 or POND_FP32_MIXED). */
@@ -169,8 +176,11 @@ void pond_config_default(pond_config* cfg, int32_t precision);
  * together by one launch per step).  cuda_stream is a cudaStream_t (NULL =
  * legacy default stream).  Allocates all device state; nothing else
  * allocates afterwards except pond_adjoint_step's first call.
+ * Ensembles run on the staged kernel in either precision, and on the
+ * direct mixed kernel; the direct FP64 kernels step one grid.
  * Errors: POND_ERR_ARG (NULL pointers, n_grids < 1, a side < 1, bad
- * precision), POND_ERR_OOM, POND_ERR_CUDA. */
+ * precision, n_grids > 1 with the direct FP64 kernels), POND_ERR_OOM,
+ * POND_ERR_CUDA. */
 pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* nx,
                         const int32_t* ny, void* cuda_stream, pond_ctx** out);
 

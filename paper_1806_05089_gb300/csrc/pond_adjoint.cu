@@ -21,12 +21,15 @@
 //                       populations f_j and source gauges lambda_j)
 // The seed gauge gets no gradient: the limit does not depend on it.
 //
-// Phase A (one warp per target node, lane = population, like the forward
-// step's warp mappings) forms A*, the JVP A_lambda in three directions, the
-// 3 x 3 solve and w.  Phase B (one warp per source node) gathers the
-// transpose: for every population it scans the targets whose departure
-// stencil can contain the source (a window bounded by the particle-velocity
-// range), so the result is deterministic and needs no atomics.
+// Phase A forms A*, the JVP A_lambda in three directions, the 3 x 3 solve
+// and w.  Contexts on the staged forward kernel run it staged
+// (k_adjoint_jvp_staged: one thread per target node, the sources staged per
+// tile in a reference gauge, then k_adjoint_epilogue); contexts on the
+// direct kernels run k_adjoint_targets (one warp per target node, lane =
+// population).  Phase B (one warp per source node) gathers the transpose:
+// for every population it scans the targets whose departure stencil can
+// contain the source (a window bounded by the particle-velocity range), so
+// the result is deterministic and needs no atomics.
 #include <cmath>
 
 #include "pond_device.cuh"
@@ -255,6 +258,24 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_targets(AdjArgs A
     if (lane == 0) atomicAdd(A.beta_bar, bb);
 }
 
+// Warp reduce-scatter of 16 per-lane partial sums by recursive halving: at
+// distance 2h each lane keeps the h slots its lane bit selects and adds its
+// partner's copy of them.  Returns, in lanes 2p and 2p + 1, the warp total of
+// slot p (16 additions per lane, against 16 x 5 for a full all-reduce).
+__device__ __forceinline__ double warp_reduce_scatter16(double (&v)[16], int lane) {
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+        const bool up = (lane & (2 * h)) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double keep = up ? v[i + h] : v[i];
+            const double send = up ? v[i] : v[i + h];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * h);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 // Transpose of the reconstruction, gathered at each source node.
 template <int N1>
 __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A) {
@@ -338,26 +359,23 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A
             bst = fma(ci, sst, bst);
         }
     }
-    // reduce over the warp (all populations and both halves)
+    // reduce over the warp (all populations and both halves): lanes 2p and
+    // 2p + 1 get population p's total, every lane the gauge cotangents
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = i < Q ? fb[i] : 0.0;
+    const double tot = warp_reduce_scatter16(v, lane);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) fb[i] += __shfl_xor_sync(0xffffffffu, fb[i], o);
         bux += __shfl_xor_sync(0xffffffffu, bux, o);
         buy += __shfl_xor_sync(0xffffffffu, buy, o);
         bst += __shfl_xor_sync(0xffffffffu, bst, o);
     }
-    if (lane < Q) {
-        double v = fb[0];
-#pragma unroll
-        for (int i = 1; i < Q; ++i)
-            if (lane == i) v = fb[i];
-        A.fbar_in[(long long)lane * A.N + src] = v;
-    } else if (lane == 16) {
+    const int p = lane >> 1;
+    if ((lane & 1) == 0 && p < Q) A.fbar_in[(long long)p * A.N + src] = tot;
+    if (lane == 1) {
         A.gbar_in[src] = bux;
-    } else if (lane == 17) {
         A.gbar_in[A.N + src] = buy;
-    } else if (lane == 18) {
         // s = sqrt(T / T_L): dL/dT = dL/ds / (2 s T_L)
         A.gbar_in[2 * A.N + src] = bst / (2.0 * stj * A.T_L);
     }
@@ -388,9 +406,6 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources_r(AdjArgs
     const int q = lane & 15, half = lane >> 4;
     const bool act = q < Q;
     const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
-    double fj[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) fj[i] = A.in.f[(long long)i * A.N + src];
     const double uxj = A.in.ux[src], uyj = A.in.uy[src], stj = A.in.st[src];
 
     double fb[Q];
@@ -443,48 +458,47 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources_r(AdjArgs
             }
         }
     }
-    // reduce over the warp (all populations and both halves)
+    // reduce over the warp: lanes 2p and 2p + 1 get population p's total
+    constexpr unsigned FULL = 0xffffffffu;
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = i < Q ? fb[i] : 0.0;
+    const double tot = warp_reduce_scatter16(v, lane);
+    // the source-gauge cotangent from h = fb, one population per even lane:
+    // dg/du_x [k][l] = sum_a d1[k][a] f[a][l] / s_j, dg/du_y [k][l] =
+    // sum_b d1[l][b] f[k][b] / s_j, dg/ds the same with c_a, c_b inside
+    const int p = lane >> 1;
+    double pux = 0.0, puy = 0.0, pst = 0.0;
+    if ((lane & 1) == 0 && p < Q) {
+        const int kk = p / N1, ll = p % N1;
+        double gxu = 0.0, gyu = 0.0, gsx = 0.0, gsy = 0.0;
+#pragma unroll
+        for (int a = 0; a < N1; ++a) {
+            // the source's populations f_j[a][ll] and f_j[kk][a]
+            const double fx = A.in.f[(long long)(N1 * a + ll) * A.N + src];
+            const double fy = A.in.f[(long long)(N1 * kk + a) * A.N + src];
+            gxu = fma(L.d1[kk][a], fx, gxu);
+            gsx = fma(L.d1[kk][a] * L.c[a], fx, gsx);
+            gyu = fma(L.d1[ll][a], fy, gyu);
+            gsy = fma(L.d1[ll][a] * L.c[a], fy, gsy);
+        }
+        pux = tot * gxu;
+        puy = tot * gyu;
+        pst = tot * (gsx + gsy);
+        A.fbar_in[(long long)p * A.N + src] = tot;
+    }
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) fb[i] += __shfl_xor_sync(0xffffffffu, fb[i], o);
+        pux += __shfl_xor_sync(FULL, pux, o);
+        puy += __shfl_xor_sync(FULL, puy, o);
+        pst += __shfl_xor_sync(FULL, pst, o);
     }
-    // the source-gauge cotangent from h = fb: dg/du_x [k][l] = sum_a d1[k][a]
-    // f[a][l] / s_j, dg/du_y [k][l] = sum_b d1[l][b] f[k][b] / s_j, dg/ds the
-    // same with c_a, c_b inside
-    {
+    if (lane == 0) {
         const double is = 1.0 / stj;
-#pragma unroll
-        for (int kk = 0; kk < N1; ++kk)
-#pragma unroll
-            for (int ll = 0; ll < N1; ++ll) {
-                double gxu = 0.0, gyu = 0.0, gsx = 0.0, gsy = 0.0;
-#pragma unroll
-                for (int a = 0; a < N1; ++a) {
-                    gxu = fma(L.d1[kk][a], fj[N1 * a + ll], gxu);
-                    gsx = fma(L.d1[kk][a] * L.c[a], fj[N1 * a + ll], gsx);
-                    gyu = fma(L.d1[ll][a], fj[N1 * kk + a], gyu);
-                    gsy = fma(L.d1[ll][a] * L.c[a], fj[N1 * kk + a], gsy);
-                }
-                const double h = fb[N1 * kk + ll];
-                bux = fma(h, gxu * is, bux);
-                buy = fma(h, gyu * is, buy);
-                bst = fma(h, (gsx + gsy) * is, bst);
-            }
-    }
-    if (lane < Q) {
-        double v = fb[0];
-#pragma unroll
-        for (int i = 1; i < Q; ++i)
-            if (lane == i) v = fb[i];
-        A.fbar_in[(long long)lane * A.N + src] = v;
-    } else if (lane == 16) {
-        A.gbar_in[src] = bux;
-    } else if (lane == 17) {
-        A.gbar_in[A.N + src] = buy;
-    } else if (lane == 18) {
+        A.gbar_in[src] = pux * is;
+        A.gbar_in[A.N + src] = puy * is;
         // s = sqrt(T / T_L): dL/dT = dL/ds / (2 s T_L)
-        A.gbar_in[2 * A.N + src] = bst / (2.0 * stj * A.T_L);
+        A.gbar_in[2 * A.N + src] = pst * is / (2.0 * stj * A.T_L);
     }
 }
 
@@ -849,71 +863,93 @@ k_adjoint_jvp_staged(AdjArgs A, int wwa, int wha, double c_max, double* __restri
 }
 
 // The rest of phase A from A* and its tangents: the collision cotangent,
-// beta_bar, the 3 x 3 implicit solve at the fixed point and w (one warp per
-// target node, lane = population, as k_adjoint_targets).
+// beta_bar, the 3 x 3 implicit solve at the fixed point and w, one thread
+// per target node.  Every sum the solve needs is linear in the populations'
+// values, so the node's populations are read once and folded into running
+// sums (tangent d^i, i = u_x, u_y, s; e_q = |c_q|^2 - 2 T_L):
+//   rho = sum A_q,  wf = sum W_q fbar_q,  af = sum A_q fbar_q,
+//   sk_i = sum c_k d^i_q,  sl_i = sum c_l d^i_q,  se_i = sum e_q d^i_q,
+//   sf_i = sum fbar_q d^i_q,  s1_i = sum d^i_q.
+// Then J = M_A A_lambda has rows (s/rho) sk, (s/rho) sl, s/(4 rho T_L) se;
+// g_i = (1 - 2 beta) sf_i + 2 beta wf s1_i + lambdabar_i (the s component
+// of lambdabar taken from T: dT/ds = 2 s T_L); betabar = 2 rho wf - 2 af;
+// and w_q = Abar_q + (M_A^T mu)_q.
 template <int N1>
-__global__ void __launch_bounds__(ADJ_WARPS * 32, 2)
-k_adjoint_epilogue(AdjArgs A, const double* __restrict__ jvp) {
+__global__ void __launch_bounds__(256) k_adjoint_epilogue(AdjArgs A, const double* __restrict__ jvp) {
     constexpr int Q = N1 * N1;
     const Lattice& L = c_La[lattice_slot(N1)];
-    const int lane = threadIdx.x & 31;
-    const long long node = (long long)blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
-    if (node >= A.N) return;  // warp-uniform
-    const int q = lane & 15;
-    const bool act = lane < Q;
-    const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
-    const double ck = act ? L.c[k] : 0.0, cl = act ? L.c[l] : 0.0;
-    const double st = A.st_s[node];
-    double Aq = 0.0, dAux = 0.0, dAuy = 0.0, dAst = 0.0;
-    if (act) {
-        Aq = jvp[((long long)0 * Q + q) * A.N + node];
-        dAux = jvp[((long long)1 * Q + q) * A.N + node];
-        dAuy = jvp[((long long)2 * Q + q) * A.N + node];
-        dAst = jvp[((long long)3 * Q + q) * A.N + node];
-    }
-    auto sum32 = [](double v) {
+    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = node < A.N;
+    double bb = 0.0;
+    if (valid) {
+        const long long N = A.N;
+        double rho = 0.0, wf = 0.0, af = 0.0;
+        double sk[3], sl[3], se[3], sf[3], s1[3];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        return v;
-    };
-    const double Wq = act ? L.w[k] * L.w[l] : 0.0;
-    const double fb = act ? A.fbar[(long long)q * A.N + node] : 0.0;
-    const double rho = sum32(Aq);
-    const double wf = sum32(Wq * fb);
-    const double Abar = (1.0 - 2.0 * A.beta) * fb + 2.0 * A.beta * wf;
-    const double bb = sum32(act ? 2.0 * (rho * Wq - Aq) * fb : 0.0);
-    const double c2 = ck * ck + cl * cl;
-    const double mux = st * ck / rho, muy = st * cl / rho;
-    const double mst = act ? st * (c2 - 2.0 * A.T_L) / (4.0 * rho * A.T_L) : 0.0;
-    double J[3][3];
-    J[0][0] = sum32(mux * dAux);
-    J[0][1] = sum32(mux * dAuy);
-    J[0][2] = sum32(mux * dAst);
-    J[1][0] = sum32(muy * dAux);
-    J[1][1] = sum32(muy * dAuy);
-    J[1][2] = sum32(muy * dAst);
-    J[2][0] = sum32(mst * dAux);
-    J[2][1] = sum32(mst * dAuy);
-    J[2][2] = sum32(mst * dAst);
-    double g0 = sum32(Abar * dAux) + A.gbar[node];
-    double g1 = sum32(Abar * dAuy) + A.gbar[A.N + node];
-    double g2 = sum32(Abar * dAst) + A.gbar[2 * A.N + node] * 2.0 * st * A.T_L;
-    const double a00 = J[0][0], a01 = J[1][0], a02 = J[2][0];
-    const double a10 = J[0][1], a11 = J[1][1], a12 = J[2][1];
-    const double a20 = J[0][2], a21 = J[1][2], a22 = J[2][2];
-    const double det = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
-                       a02 * (a10 * a21 - a11 * a20);
-    const double idet = 1.0 / det;
-    const double r0 = -g0, r1 = -g1, r2 = -g2;
-    const double mu0 = (r0 * (a11 * a22 - a12 * a21) - a01 * (r1 * a22 - a12 * r2) +
-                        a02 * (r1 * a21 - a11 * r2)) * idet;
-    const double mu1 = (a00 * (r1 * a22 - a12 * r2) - r0 * (a10 * a22 - a12 * a20) +
-                        a02 * (a10 * r2 - r1 * a20)) * idet;
-    const double mu2 = (a00 * (a11 * r2 - r1 * a21) - a01 * (a10 * r2 - r1 * a20) +
-                        r0 * (a10 * a21 - a11 * a20)) * idet;
-    const double wq = Abar + mux * mu0 + muy * mu1 + mst * mu2;
-    if (act) A.w[(long long)q * A.N + node] = wq;
-    if (lane == 0) atomicAdd(A.beta_bar, bb);
+        for (int i = 0; i < 3; ++i) sk[i] = sl[i] = se[i] = sf[i] = s1[i] = 0.0;
+        double fb[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int k = q / N1, l = q % N1;
+            const double ck = L.c[k], cl = L.c[l];
+            const double e = fma(ck, ck, cl * cl) - 2.0 * A.T_L;
+            const double a = jvp[(long long)q * N + node];
+            fb[q] = A.fbar[(long long)q * N + node];
+            rho += a;
+            wf = fma(L.w[k] * L.w[l], fb[q], wf);
+            af = fma(a, fb[q], af);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double d = jvp[((long long)(1 + i) * Q + q) * N + node];
+                sk[i] = fma(ck, d, sk[i]);
+                sl[i] = fma(cl, d, sl[i]);
+                se[i] = fma(e, d, se[i]);
+                sf[i] = fma(fb[q], d, sf[i]);
+                s1[i] += d;
+            }
+        }
+        const double st = A.st_s[node];
+        const double sr = st / rho, ss = st / (4.0 * rho * A.T_L);
+        bb = 2.0 * (rho * wf - af);
+        // J[m][i]: moment m (u_x, u_y, s), tangent i
+        double J[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            J[0][i] = sr * sk[i];
+            J[1][i] = sr * sl[i];
+            J[2][i] = ss * se[i];
+        }
+        const double b1 = 1.0 - 2.0 * A.beta, b2 = 2.0 * A.beta * wf;
+        const double g0 = fma(b1, sf[0], b2 * s1[0]) + A.gbar[node];
+        const double g1 = fma(b1, sf[1], b2 * s1[1]) + A.gbar[N + node];
+        const double g2 = fma(b1, sf[2], b2 * s1[2]) + A.gbar[2 * N + node] * 2.0 * st * A.T_L;
+        // solve J^T mu = -g by Cramer's rule (a = J^T)
+        const double a00 = J[0][0], a01 = J[1][0], a02 = J[2][0];
+        const double a10 = J[0][1], a11 = J[1][1], a12 = J[2][1];
+        const double a20 = J[0][2], a21 = J[1][2], a22 = J[2][2];
+        const double det = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
+                           a02 * (a10 * a21 - a11 * a20);
+        const double idet = 1.0 / det;
+        const double r0 = -g0, r1 = -g1, r2 = -g2;
+        const double mu0 = (r0 * (a11 * a22 - a12 * a21) - a01 * (r1 * a22 - a12 * r2) +
+                            a02 * (r1 * a21 - a11 * r2)) * idet;
+        const double mu1 = (a00 * (r1 * a22 - a12 * r2) - r0 * (a10 * a22 - a12 * a20) +
+                            a02 * (a10 * r2 - r1 * a20)) * idet;
+        const double mu2 = (a00 * (a11 * r2 - r1 * a21) - a01 * (a10 * r2 - r1 * a20) +
+                            r0 * (a10 * a21 - a11 * a20)) * idet;
+        const double m0 = sr * mu0, m1 = sr * mu1, m2 = ss * mu2;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int k = q / N1, l = q % N1;
+            const double ck = L.c[k], cl = L.c[l];
+            const double e = fma(ck, ck, cl * cl) - 2.0 * A.T_L;
+            A.w[(long long)q * N + node] = fma(b1, fb[q], b2) + fma(ck, m0, fma(cl, m1, e * m2));
+        }
+    }
+    // beta_bar: one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bb += __shfl_xor_sync(0xffffffffu, bb, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(A.beta_bar, bb);
 }
 
 // Shared memory and launch of the staged phase A for a window of wwa x wha
@@ -938,9 +974,9 @@ cudaError_t launch_adjoint_phase_a_staged(const AdjArgs& A, int n1, int wwa, int
     kern<<<tiles, 32 * ADJ_TY, smem, s>>>(A, wwa, wha, c_max, jvp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const unsigned nb = (unsigned)((A.N + ADJ_WARPS - 1) / ADJ_WARPS);
-    if (n1 == 3) k_adjoint_epilogue<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A, jvp);
-    else k_adjoint_epilogue<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A, jvp);
+    const unsigned nb = (unsigned)((A.N + 255) / 256);
+    if (n1 == 3) k_adjoint_epilogue<3><<<nb, 256, 0, s>>>(A, jvp);
+    else k_adjoint_epilogue<4><<<nb, 256, 0, s>>>(A, jvp);
     return cudaGetLastError();
 }
 

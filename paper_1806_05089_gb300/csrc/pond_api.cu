@@ -336,7 +336,6 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
     if (!(cfg->nu > 0.0) || !(cfg->T_ref > 0.0) || !(cfg->dt > 0.0) || cfg->max_iter < 1 ||
         cfg->fixed_iter < 0 || cfg->seed_mode < 0 || cfg->seed_mode > 2)
         return POND_ERR_ARG;
-    if (cfg->precision == POND_FP64 && n_grids != 1) return POND_ERR_ARG;
     if (cfg->tile_rows != 0 && cfg->tile_rows != 4 && cfg->tile_rows != 8 && cfg->tile_rows != 16 &&
         cfg->tile_rows != -16)
         return POND_ERR_ARG;
@@ -361,6 +360,8 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
         return POND_ERR_ARG;
     if (kernel == POND_KERNEL_DIRECT && cfg->precision == POND_FP64 && cfg->tile_rows != 0)
         return POND_ERR_ARG;  // the direct FP64 kernels have no tiles
+    if (kernel == POND_KERNEL_DIRECT && cfg->precision == POND_FP64 && n_grids != 1)
+        return POND_ERR_ARG;  // ... and step one grid
 
     pond_ctx* ctx = new (std::nothrow) pond_ctx();
     if (!ctx) return POND_ERR_OOM;
@@ -740,6 +741,8 @@ pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats) {
         stats->nonphysical = (int64_t)d.nonphysical;
         stats->halo_fallback = (int64_t)d.halo_fallback;
         stats->index_faults = (int64_t)d.index_faults;
+        stats->busy_ns = (int64_t)d.busy_ns;
+        stats->slot_ns = (int64_t)d.slot_ns;
         if (d.nonphysical) return fail(ctx, POND_ERR_NONPHYSICAL, "rho <= 0, T <= 0 or NaN met");
         if (ctx->cfg.strict && d.nonconverged)
             return fail(ctx, POND_ERR_NOT_CONVERGED, "a node hit max_iter without converging");

@@ -20,6 +20,39 @@ __device__ __forceinline__ bool pond_index_ok(bool ok, DevStats* st) {
 #define POND_INDEX_OK(cond, stats) true
 #endif
 
+// The GPU's global nanosecond timer (PTX %globaltimer).
+__device__ __forceinline__ unsigned long long pond_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Exit of one CTA of a persistent launch (one thread per CTA): adds its busy
+// time and widens the launch's span; the launch's last CTA to exit folds the
+// launch into busy_ns and slot_ns (gridDim.x x span) and zeroes the scratch
+// for the next launch.  1 - busy/slot is the share of the launch's CTA slots
+// left idle, by the start skew and the tail after the work list ran dry.
+// No CTA waits on another.
+__device__ __forceinline__ void persistent_exit(DevStats* st, unsigned long long t_begin) {
+    const unsigned long long t_end = pond_globaltimer();
+    atomicAdd(&st->l_busy, t_end - t_begin);
+    atomicMax(&st->l_begin_inv, ~t_begin);
+    atomicMax(&st->l_end, t_end);
+    __threadfence();
+    if (atomicAdd(&st->l_done, 1u) == gridDim.x - 1) {
+        __threadfence();
+        const unsigned long long busy = atomicAdd(&st->l_busy, 0ull);
+        const unsigned long long b = ~atomicAdd(&st->l_begin_inv, 0ull);
+        const unsigned long long e = atomicAdd(&st->l_end, 0ull);
+        st->busy_ns += busy;
+        st->slot_ns += (unsigned long long)gridDim.x * (e > b ? e - b : 0ull);
+        st->l_busy = 0ull;
+        st->l_begin_inv = 0ull;
+        st->l_end = 0ull;
+        st->l_done = 0u;
+    }
+}
+
 // Cubic Lagrange weights on the nodes 0, 1, 2, 3 at local coordinate t
 // (App. C: a_n(t) = prod_{k != n} (t - k)/(n - k)).
 __device__ __forceinline__ void lagrange4(double t, double l[4]) {

@@ -94,6 +94,17 @@ struct DevStats {
     unsigned long long index_faults;  // debug builds: accesses skipped by a failed index check
     unsigned int max_passes;
     unsigned int pad;
+    // persistent (batched) launches of the staged kernel: summed CTA busy
+    // time, and resident CTAs x launch span, in globaltimer nanoseconds
+    unsigned long long busy_ns;
+    unsigned long long slot_ns;
+    // per-launch scratch of those launches, folded into busy_ns / slot_ns
+    // and zeroed by the launch's last CTA
+    unsigned long long l_begin_inv;  // max of ~(CTA start time) = ~(earliest start)
+    unsigned long long l_end;        // latest CTA exit
+    unsigned long long l_busy;       // summed CTA busy time
+    unsigned int l_done;             // CTAs exited
+    unsigned int pad2;
 };
 
 // Per-grid descriptor of a batched context (node offset into packed arrays).

@@ -278,6 +278,7 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
     }
     const int lxi = tid % TX, lyi = tid / TX;
     const Real dt = (Real)A.P.dt;
+    const unsigned long long t_begin = (A.work_counter && tid == 0) ? pond_globaltimer() : 0ull;
 
     long long item = blockIdx.x;
     for (;;) {
@@ -600,6 +601,7 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
         if (s_nc) atomicAdd(&A.stats->nonconverged, s_nc);
         if (s_np) atomicAdd(&A.stats->nonphysical, s_np);
         if (s_fb) atomicAdd(&A.stats->halo_fallback, s_fb);
+        if (A.work_counter) persistent_exit(A.stats, t_begin);
     }
 }
 

@@ -84,6 +84,8 @@ class pond_stats(ctypes.Structure):
         ("nonphysical", ctypes.c_int64),
         ("halo_fallback", ctypes.c_int64),
         ("index_faults", ctypes.c_int64),
+        ("busy_ns", ctypes.c_int64),
+        ("slot_ns", ctypes.c_int64),
     ]
 
     def as_dict(self):

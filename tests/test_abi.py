@@ -49,10 +49,15 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
     bad = pond.pond_config_default(pond.POND_FP64)
     bad.nu = -1.0
     assert lib.pond_create(ctypes.byref(bad), 1, nx, ny, None, ctypes.byref(out)) == pond.POND_ERR_ARG
-    # FP64 contexts are single-grid; batched ensembles use the mixed form
+    # the direct FP64 kernels step one grid; FP64 ensembles run staged
     nx2 = (ctypes.c_int32 * 2)(8, 8)
     ny2 = (ctypes.c_int32 * 2)(8, 8)
-    assert lib.pond_create(ctypes.byref(cfg), 2, nx2, ny2, None, ctypes.byref(out)) == pond.POND_ERR_ARG
+    direct = pond.pond_config_default(pond.POND_FP64)
+    direct.kernel = pond.POND_KERNEL_DIRECT
+    assert lib.pond_create(ctypes.byref(direct), 2, nx2, ny2, None, ctypes.byref(out)) == pond.POND_ERR_ARG
+    direct.kernel = pond.POND_KERNEL_DEFAULT
+    direct.nodes_per_warp = 2  # a direct-only mapping
+    assert lib.pond_create(ctypes.byref(direct), 2, nx2, ny2, None, ctypes.byref(out)) == pond.POND_ERR_ARG
     assert lib.pond_step(None, 1, None) == pond.POND_ERR_ARG
     assert lib.pond_last_error(None) == b"no context"
     # lattice: D2Q16 or D2Q9 only; the paired tile shape is D2Q16-only

@@ -291,6 +291,31 @@ def test_batched_matches_single_grid_runs(kernel, tile_rows):
         assert np.max(np.abs(batched[i].f.sum(0) - o.f.sum(0)) / o.f.sum(0)) <= TOL32
 
 
+@pytest.mark.parametrize("tile_rows", [4, 8])
+def test_fp64_batched_matches_single_grid_runs(tile_rows):
+    """FP64 ensembles on the staged kernel's persistent work list: every
+    grid bit-identical to its own single-grid run (which the FP64 parity
+    tests pin to the oracle)."""
+    sizes = [(37, 23), (64, 40), (33, 70), (1, 1), (50, 45), (5, 9)]
+    members = [workloads.ensemble_member(i, nx, ny) for i, (nx, ny) in enumerate(sizes)]
+    nxs = [s[0] for s in sizes]
+    nys = [s[1] for s in sizes]
+    with pond.Sim(nxs, nys, pond.POND_FP64, tile_rows=tile_rows) as b:
+        for i, m in enumerate(members):
+            b.set_state(m.rho, m.ux, m.uy, m.T, grid=i)
+        st = b.step(2)
+        batched = [b.state(i) for i in range(len(sizes))]
+    assert st["nonphysical"] == 0
+    for i, m in enumerate(members):
+        with pond.Sim(nxs[i], nys[i], pond.POND_FP64, tile_rows=tile_rows) as s:
+            s.set_state(m.rho, m.ux, m.uy, m.T)
+            s.step(2)
+            single = s.state()
+        assert np.array_equal(batched[i].f, single.f), i
+        assert np.array_equal(batched[i].ux, single.ux), i
+        assert np.array_equal(batched[i].T, single.T), i
+
+
 def test_graph_replay_matches_plain_launches():
     fields = small_fields("supersonic", 80, 40)
     out = []

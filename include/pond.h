@@ -227,7 +227,10 @@ pond_status pond_iterations(pond_ctx* ctx, int32_t grid, void* iters, int32_t on
  * current state is the step's INPUT state s; given the cotangents of the
  * step's output, f_bar_in [Q][ny][nx] and gauge_bar_in [3][ny][nx]
  * (ux, uy, T), writes the cotangents of s to f_bar_out and gauge_bar_out
- * (same layouts) and adds d(loss)/d(nu) to *nu_bar_accum.  The fixed point
+ * (same layouts) and adds d(loss)/d(nu) to *nu_bar_accum (a host double;
+ * the call then waits for the step's kernels), or, when nu_bar_accum is NULL,
+ * to an accumulator the context keeps on the device (the call then returns
+ * without waiting; read it with pond_adjoint_nu_bar).  The fixed point
  * is differentiated implicitly (the limit gauge of Eqs. density..T is a
  * function of the input state only; the seed gets no gradient).  All array
  * pointers are device pointers.  The state is left unchanged.  FP64 and
@@ -250,6 +253,13 @@ pond_status pond_adjoint_step_given(pond_ctx* ctx, const void* ux_out, const voi
                                     const void* T_out, const void* f_bar_in,
                                     const void* gauge_bar_in, void* f_bar_out,
                                     void* gauge_bar_out, double* nu_bar_accum);
+
+/* The nu cotangent accumulated on the device by the adjoint calls made
+ * with nu_bar_accum == NULL since the last read: written to *nu_bar (host),
+ * and the accumulator cleared.  Waits for the context's stream.  0 before
+ * the first adjoint call.
+ * Errors: POND_ERR_ARG (NULL pointer), POND_ERR_CUDA. */
+pond_status pond_adjoint_nu_bar(pond_ctx* ctx, double* nu_bar);
 
 /* VJP of the equilibrium initialisation of pond_set_state (f = rho W,
  * Eq. equilibrium): rho_bar[x] = sum_q W_q f_bar[q][x].  Single-grid

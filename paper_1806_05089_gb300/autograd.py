@@ -75,7 +75,6 @@ class PondRollout(torch.autograd.Function):
         gbar = torch.zeros((3, ny, nx), dtype=torch.float64, device=dev)
         fbar_new = torch.empty_like(fbar)
         gbar_new = torch.empty_like(gbar)
-        nu_bar = 0.0
         steps, every = ctx.steps, ctx.ckpt_every
         for seg in reversed(range(len(ctx.ckpts))):
             start = seg * every
@@ -94,13 +93,15 @@ class PondRollout(torch.autograd.Function):
                 else:
                     nxt = ctx.final
                 _set_state(sim, states[t - start])
-                nu_bar += pond.pond_adjoint_step_given(sim.ctx, nxt[1], nxt[2], nxt[3], fbar, gbar,
-                                                       fbar_new, gbar_new)
+                # the nu cotangent accumulates on the device: no wait per step
+                pond.pond_adjoint_step_given(sim.ctx, nxt[1], nxt[2], nxt[3], fbar, gbar,
+                                             fbar_new, gbar_new, nu_on_device=True)
                 fbar, fbar_new = fbar_new, fbar
                 gbar, gbar_new = gbar_new, gbar
             del states
         rho_bar = torch.empty((ny, nx), dtype=torch.float64, device=dev)
         pond.pond_adjoint_init(sim.ctx, fbar, rho_bar)
+        nu_bar = pond.pond_adjoint_nu_bar(sim.ctx)
         torch.cuda.current_stream(dev).synchronize()
         sim.close()
         nu_grad = torch.tensor(nu_bar, dtype=torch.float64, device=dev)

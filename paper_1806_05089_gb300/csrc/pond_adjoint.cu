@@ -57,6 +57,7 @@ struct AdjointScratch {
     double* lw = nullptr;        // [16][N][8] cubic weights of (q, t): x 0..3, y 0..3
     double* inv_st = nullptr;    // [N] 1 / s* at every target
     double* jvp = nullptr;       // [4][16][N] A*, dA/du_x, dA/du_y, dA/ds (staged phase A)
+    double* nu_dev = nullptr;    // nu cotangent of calls with nu_bar_accum == NULL
     double host_minmax[6];
 };
 
@@ -529,14 +530,28 @@ __global__ void k_minmax3(const double* __restrict__ ux, const double* __restric
         v[4] = fmin(v[4], c);
         v[5] = fmax(v[5], c);
     }
+    // warp, then block reduction: one atomic per block and value
+    __shared__ double s_b[6][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
+        for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            const double u = __shfl_xor_sync(0xffffffffu, v[j], off);
-            v[j] = (j & 1) ? fmax(v[j], u) : fmin(v[j], u);
-        }
-    if ((threadIdx.x & 31) == 0)
+            for (int j = 0; j < 6; ++j) {
+                const double u = __shfl_xor_sync(0xffffffffu, v[j], off);
+                v[j] = (j & 1) ? fmax(v[j], u) : fmin(v[j], u);
+            }
+        if (pass == 1) break;
+        if (lane == 0)
+#pragma unroll
+            for (int j = 0; j < 6; ++j) s_b[j][warp] = v[j];
+        __syncthreads();
+        if (warp != 0) return;
+        const bool in = lane < (int)(blockDim.x >> 5);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) v[j] = in ? s_b[j][lane] : ((j & 1) ? -1e300 : 1e300);
+    }
+    if (lane == 0)
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
             if (j & 1) atomicMax(o + j, d2ord(v[j]));
@@ -558,7 +573,7 @@ cudaError_t launch_minmax3(const double* ux, const double* uy, const double* st,
     unsigned long long* o = reinterpret_cast<unsigned long long*>(out6);
     k_minmax3_reset<<<1, 32, 0, s>>>(o);
     long long nb = (N + 255) / 256;
-    if (nb > 1024) nb = 1024;
+    if (nb > 256) nb = 256;
     if (nb < 1) nb = 1;
     k_minmax3<<<(unsigned)nb, 256, 0, s>>>(ux, uy, st, N, o);
     k_minmax3_decode<<<1, 32, 0, s>>>(o);
@@ -1011,6 +1026,7 @@ void destroy_adjoint(pond_ctx* ctx) {
     cudaFree(a->lw);
     cudaFree(a->inv_st);
     cudaFree(a->jvp);
+    cudaFree(a->nu_dev);
     delete a;
     ctx->adj = nullptr;
 }
@@ -1054,6 +1070,31 @@ cudaError_t launch_gauge_from_T(const double* ux, const double* uy, const double
 
 }  // namespace pond
 
+// d(loss)/d(nu) of one adjoint step from its beta cotangent on the device:
+// beta = 1 / (2 nu / (T_ref dt) + 1)  =>  d beta / d nu = -2 beta^2 / (T_ref dt).
+// To the host accumulator when one is given (a copy and a synchronisation),
+// else to the context's device accumulator (stream-ordered, no
+// synchronisation), which pond_adjoint_nu_bar reads.
+__global__ void k_nu_accum(const double* __restrict__ beta_bar, double* __restrict__ nu_dev,
+                           double dbeta_dnu) {
+    if (threadIdx.x == 0) *nu_dev += *beta_bar * dbeta_dnu;
+}
+
+static cudaError_t accumulate_nu_bar(pond_ctx* ctx, AdjointScratch* a, double* nu_bar_accum) {
+    const double beta = ctx->P.beta;
+    const double dbeta = -2.0 * beta * beta / (ctx->cfg.T_ref * ctx->cfg.dt);
+    if (!nu_bar_accum) {
+        k_nu_accum<<<1, 32, 0, ctx->stream>>>(a->beta_bar, a->nu_dev, dbeta);
+        return cudaGetLastError();
+    }
+    double bb = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&bb, a->beta_bar, sizeof(double), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) *nu_bar_accum += bb * dbeta;
+    return e;
+}
+
 // Both entry points: out_gauge = {u_x, u_y, T} of the step's output when
 // the caller has it (pond_adjoint_step_given), else NULLs and the forward
 // step is recomputed here.
@@ -1062,7 +1103,7 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
                                      void* f_bar_out, void* gauge_bar_out,
                                      double* nu_bar_accum) {
     if (!ctx) return POND_ERR_ARG;
-    if (!f_bar_in || !gauge_bar_in || !f_bar_out || !gauge_bar_out || !nu_bar_accum) {
+    if (!f_bar_in || !gauge_bar_in || !f_bar_out || !gauge_bar_out) {
         ctx->err = "adjoint: NULL argument";
         return POND_ERR_ARG;
     }
@@ -1091,6 +1132,8 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
         ctx->adj = a;
         a->N = N;
         ACK(cudaMalloc(&a->beta_bar, sizeof(double)), "adjoint alloc");
+        ACK(cudaMalloc(&a->nu_dev, sizeof(double)), "adjoint alloc");
+        ACK(cudaMemsetAsync(a->nu_dev, 0, sizeof(double), ctx->stream), "adjoint alloc");
         ACK(cudaMalloc(&a->minmax, sizeof(double) * 6), "adjoint alloc");
         ACK(cudaMalloc(&a->org, sizeof(int2) * 16 * N), "adjoint alloc");
         ACK(cudaMalloc(&a->lw, sizeof(double) * 8 * 16 * N), "adjoint alloc");
@@ -1111,14 +1154,9 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
         ACK(adjoint_step_mixed(ctx, out_gauge, static_cast<const double*>(f_bar_in),
                                static_cast<const double*>(gauge_bar_in),
                                static_cast<double*>(f_bar_out), static_cast<double*>(gauge_bar_out),
-                               a->beta_bar, a->minmax, a->host_minmax),
+                               a->beta_bar, a->minmax),
             "adjoint (mixed)");
-        double bbm = 0.0;
-        ACK(cudaMemcpyAsync(&bbm, a->beta_bar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
-            "adjoint copy");
-        ACK(cudaStreamSynchronize(ctx->stream), "adjoint sync");
-        const double beta = ctx->P.beta;
-        *nu_bar_accum += bbm * (-2.0 * beta * beta / (ctx->cfg.T_ref * ctx->cfg.dt));
+        ACK(accumulate_nu_bar(ctx, a, nu_bar_accum), "adjoint nu cotangent");
         return POND_OK;
     }
     const GridDesc& G = ctx->grids_host[0];
@@ -1207,12 +1245,23 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
     }
     nvtxRangePop();
     ACK(cudaGetLastError(), "adjoint sources");
-    double bb = 0.0;
-    ACK(cudaMemcpyAsync(&bb, a->beta_bar, sizeof(double), cudaMemcpyDeviceToHost, s), "adjoint copy");
-    ACK(cudaStreamSynchronize(s), "adjoint sync");
-    // beta = 1 / (2 nu / (T_ref dt) + 1)  =>  d beta / d nu = -2 beta^2 / (T_ref dt)
-    const double beta = ctx->P.beta;
-    *nu_bar_accum += bb * (-2.0 * beta * beta / (ctx->cfg.T_ref * ctx->cfg.dt));
+    ACK(accumulate_nu_bar(ctx, a, nu_bar_accum), "adjoint nu cotangent");
+    return POND_OK;
+}
+
+extern "C" pond_status pond_adjoint_nu_bar(pond_ctx* ctx, double* nu_bar) {
+    if (!ctx || !nu_bar) {
+        if (ctx) ctx->err = "adjoint_nu_bar: NULL argument";
+        return POND_ERR_ARG;
+    }
+    *nu_bar = 0.0;
+    AdjointScratch* a = ctx->adj;
+    if (!a) return POND_OK;
+    DeviceGuard dg(ctx->device);
+    ACK(cudaMemcpyAsync(nu_bar, a->nu_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+        "adjoint_nu_bar copy");
+    ACK(cudaMemsetAsync(a->nu_dev, 0, sizeof(double), ctx->stream), "adjoint_nu_bar reset");
+    ACK(cudaStreamSynchronize(ctx->stream), "adjoint_nu_bar sync");
     return POND_OK;
 }
 

@@ -35,7 +35,31 @@ struct AdjMixedScratch {
     int2* org = nullptr;      // [16][N] stencil origin of (q, t), relative to t
     float* lw = nullptr;      // [16][N][8] cubic weights of (q, t): x 0..3, y 0..3
     float* inv_st = nullptr;  // [N] 1 / s* at every target
+    float* vb = nullptr;      // [16] per-speed velocity bounds of lambda* (k_speed_bounds)
 };
+
+// Velocity bounds of every speed index from the bounds of lambda*
+// (bounds6 = {min ux*, max ux*, min uy*, max uy*, min s*, max s*}, on the
+// device), each widened by a slack for the FP32 departures (their rounding
+// is ~1e-6 cells): vb = {vlo_x[4], vhi_x[4], vlo_y[4], vhi_y[4]}.  One
+// thread, so the gathers need no host round trip for their candidate
+// windows.
+struct SpeedsD {
+    double c[4];
+};
+__global__ void k_speed_bounds(const double* __restrict__ mm, SpeedsD sp, double slack,
+                               float* __restrict__ vb) {
+    if (threadIdx.x != 0) return;
+    for (int i = 0; i < 4; ++i) {
+        const double c = sp.c[i];
+        const double slo = c >= 0 ? c * mm[4] : c * mm[5];
+        const double shi = c >= 0 ? c * mm[5] : c * mm[4];
+        vb[i] = (float)(slo + mm[0] - slack);
+        vb[4 + i] = (float)(shi + mm[1] + slack);
+        vb[8 + i] = (float)(slo + mm[2] - slack);
+        vb[12 + i] = (float)(shi + mm[3] + slack);
+    }
+}
 
 __global__ void k_split_gauge(const double* __restrict__ ux, const double* __restrict__ uy,
                               const double* __restrict__ st, float4* __restrict__ out,
@@ -105,7 +129,7 @@ struct AdjMixedArgs {
     int nx, ny;
     long long N;
     float beta, dt, T_L;
-    float vlo_x[4], vhi_x[4], vlo_y[4], vhi_y[4];
+    const float* vb;  // {vlo_x[4], vhi_x[4], vlo_y[4], vhi_y[4]} (device)
 };
 
 // One thread per node, a rolled loop over the populations: a warp holds 32
@@ -346,10 +370,10 @@ __global__ void __launch_bounds__(ADJM_THREADS) k_adjoint_sources_mixed(AdjMixed
         // ceil(J + a) = J + ceil(a) for integer J, so the bounds are free of
         // the rounding of large coordinates, and the window's offsets from J
         // are the same for every thread.
-        const int xlo = JX + (int)ceilf(-2.0f + A.vlo_x[k] * A.dt);
-        const int xhi = JX + (int)ceilf(2.0f + A.vhi_x[k] * A.dt) - 1;
-        const int ylo = JY + (int)ceilf(-2.0f + A.vlo_y[l] * A.dt);
-        const int yhi = JY + (int)ceilf(2.0f + A.vhi_y[l] * A.dt) - 1;
+        const int xlo = JX + (int)ceilf(-2.0f + A.vb[k] * A.dt);
+        const int xhi = JX + (int)ceilf(2.0f + A.vb[4 + k] * A.dt) - 1;
+        const int ylo = JY + (int)ceilf(-2.0f + A.vb[8 + l] * A.dt);
+        const int yhi = JY + (int)ceilf(2.0f + A.vb[12 + l] * A.dt) - 1;
         // wrapped coordinates advance with the loop counters (one modulo
         // per population, not per candidate)
         const int tx0 = wrap_idx(xlo, A.nx);
@@ -442,10 +466,10 @@ __global__ void __launch_bounds__(ADJM_THREADS) k_adjoint_sources_mixed_r(AdjMix
         // ceil(J + a) = J + ceil(a) for integer J, so the bounds are free of
         // the rounding of large coordinates, and the window's offsets from J
         // are the same for every thread.
-        const int xlo = JX + (int)ceilf(-2.0f + A.vlo_x[k] * A.dt);
-        const int xhi = JX + (int)ceilf(2.0f + A.vhi_x[k] * A.dt) - 1;
-        const int ylo = JY + (int)ceilf(-2.0f + A.vlo_y[l] * A.dt);
-        const int yhi = JY + (int)ceilf(2.0f + A.vhi_y[l] * A.dt) - 1;
+        const int xlo = JX + (int)ceilf(-2.0f + A.vb[k] * A.dt);
+        const int xhi = JX + (int)ceilf(2.0f + A.vb[4 + k] * A.dt) - 1;
+        const int ylo = JY + (int)ceilf(-2.0f + A.vb[8 + l] * A.dt);
+        const int yhi = JY + (int)ceilf(2.0f + A.vb[12 + l] * A.dt) - 1;
         // wrapped coordinates advance with the loop counters (one modulo
         // per population, not per candidate)
         const int tx0 = wrap_idx(xlo, A.nx);
@@ -535,17 +559,18 @@ void destroy_adjoint_mixed(pond_ctx* ctx) {
     cudaFree(a->org);
     cudaFree(a->lw);
     cudaFree(a->inv_st);
+    cudaFree(a->vb);
     delete a;
     ctx->adjm = nullptr;
 }
 
 // Mixed-precision adjoint step; arguments already validated by
-// pond_adjoint_step.  bounds6 = {min ux*, max ux*, min uy*, max uy*, min s*,
-// max s*} of the forward gauge is filled by the caller's bounds pass.
+// pond_adjoint_step.  minmax_dev receives the bounds {min ux*, max ux*,
+// min uy*, max uy*, min s*, max s*} of the forward gauge; everything stays on
+// the stream (no host synchronisation).
 cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
                                const double* fbar, const double* gbar, double* fbar_out,
-                               double* gbar_out, double* beta_bar_dev, double* minmax_dev,
-                               double* minmax_host) {
+                               double* gbar_out, double* beta_bar_dev, double* minmax_dev) {
     NvtxRange nv("pond_adjoint_step (FP32)");
     const int64_t N = ctx->N;
     cudaStream_t s = ctx->stream;
@@ -566,6 +591,7 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
         if ((e = cudaMalloc(&a->org, sizeof(int2) * 16 * N)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&a->lw, sizeof(float) * 8 * 16 * N)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&a->inv_st, sizeof(float) * N)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a->vb, sizeof(float) * 16)) != cudaSuccess) return e;
     }
     AdjMixedScratch* a = ctx->adjm;
     StateBuf<float> in;
@@ -589,11 +615,12 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_minmax3(a->fwd.ux, a->fwd.uy, a->fwd.st, N, minmax_dev, s)) != cudaSuccess)
         return e;
-    if ((e = cudaMemcpyAsync(minmax_host, minmax_dev, sizeof(double) * 6, cudaMemcpyDeviceToHost,
-                             s)) != cudaSuccess)
-        return e;
+    {
+        SpeedsD sp;
+        for (int i = 0; i < 4; ++i) sp.c[i] = ctx->L.c[i];
+        k_speed_bounds<<<1, 32, 0, s>>>(minmax_dev, sp, 1e-3 / ctx->P.dt, a->vb);
+    }
     if ((e = cudaMemsetAsync(beta_bar_dev, 0, sizeof(double), s)) != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
 
     const GridDesc& G = ctx->grids_host[0];
     AdjMixedArgs A{};
@@ -618,18 +645,7 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
     A.beta = (float)ctx->P.beta;
     A.dt = (float)ctx->P.dt;
     A.T_L = (float)ctx->L.T_L;
-    const double* mm = minmax_host;
-    for (int i = 0; i < 4; ++i) {
-        const double c = ctx->L.c[i];
-        const double slo = c >= 0 ? c * mm[4] : c * mm[5];
-        const double shi = c >= 0 ? c * mm[5] : c * mm[4];
-        // slack for the FP32 departures (their rounding is ~1e-6 cells)
-        const double sl = 1e-3 / ctx->P.dt;
-        A.vlo_x[i] = (float)(slo + mm[0] - sl);
-        A.vhi_x[i] = (float)(shi + mm[1] + sl);
-        A.vlo_y[i] = (float)(slo + mm[2] - sl);
-        A.vhi_y[i] = (float)(shi + mm[3] + sl);
-    }
+    A.vb = a->vb;
     const unsigned nb = (unsigned)((N + ADJM_THREADS - 1) / ADJM_THREADS);
     if (ctx->L.n1 == 3) k_adjoint_targets_mixed<3><<<nb, ADJM_THREADS, 0, s>>>(A);
     else k_adjoint_targets_mixed<4><<<nb, ADJM_THREADS, 0, s>>>(A);

@@ -19,18 +19,6 @@ namespace {
 
 const char* kVersion = "pond-gb300 0.2 (D2Q16 and D2Q9, sm_103a)";
 
-// Keep the caller's current device across a call.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-        else if (prev == dev) prev = -1;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
 pond_status fail(pond_ctx* c, pond_status s, const char* msg) {
     if (c) c->err = msg;
     return s;

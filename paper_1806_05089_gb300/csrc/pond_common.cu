@@ -183,13 +183,33 @@ __global__ void k_disp_bounds(const double* __restrict__ ux, const double* __res
         lo_y = fminf(lo_y, (float)(uy[i] - s));
         hi_y = fmaxf(hi_y, (float)(uy[i] + s));
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        lo_x = fminf(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, o));
-        hi_x = fmaxf(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, o));
-        lo_y = fminf(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
-        hi_y = fmaxf(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
+    // warp, then block reduction: one atomic per block and value (atomics on
+    // one address serialise, so one per warp would dominate the pass)
+    __shared__ float s_b[4][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo_x = fminf(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, o));
+            hi_x = fmaxf(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, o));
+            lo_y = fminf(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
+            hi_y = fmaxf(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
+        }
+        if (pass == 1) break;
+        if (lane == 0) {
+            s_b[0][warp] = lo_x;
+            s_b[1][warp] = hi_x;
+            s_b[2][warp] = lo_y;
+            s_b[3][warp] = hi_y;
+        }
+        __syncthreads();
+        if (warp != 0) return;
+        const bool in = lane < (int)(blockDim.x >> 5);
+        lo_x = in ? s_b[0][lane] : 3.0e38f;
+        hi_x = in ? s_b[1][lane] : -3.0e38f;
+        lo_y = in ? s_b[2][lane] : 3.0e38f;
+        hi_y = in ? s_b[3][lane] : -3.0e38f;
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         atomicMin(out4 + 0, f2ord(lo_x));
         atomicMax(out4 + 1, f2ord(hi_x));
         atomicMin(out4 + 2, f2ord(lo_y));
@@ -274,7 +294,7 @@ cudaError_t launch_disp_bounds(const double* ux, const double* uy, const double*
     k_bounds_reset<<<1, 32, 0, s>>>(o);
     const int bs = 256;
     int64_t nb = (N + bs - 1) / bs;
-    if (nb > 1024) nb = 1024;
+    if (nb > 256) nb = 256;
     if (nb < 1) nb = 1;
     k_disp_bounds<<<(unsigned)nb, bs, 0, s>>>(ux, uy, st, N, c_max, o);
     k_ord_to_float<<<1, 32, 0, s>>>(o);

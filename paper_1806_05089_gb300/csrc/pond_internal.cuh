@@ -27,6 +27,20 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Keep the caller's current device across a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else if (prev == dev) prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 // Lattice constants, computed on the host from their closed forms and passed
 // to kernels by value (they land in the constant bank).
 //
@@ -310,5 +324,4 @@ void destroy_adjoint_mixed(pond_ctx* ctx);
 // out_gauge: {u_x, u_y, T} of the step's output, or NULLs to recompute it
 cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
                                const double* fbar, const double* gbar, double* fbar_out,
-                               double* gbar_out, double* beta_bar_dev, double* minmax_dev,
-                               double* minmax_host);
+                               double* gbar_out, double* beta_bar_dev, double* minmax_dev);

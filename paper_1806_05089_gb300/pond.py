@@ -98,6 +98,7 @@ _LIB = None
 EXPORTS = ["pond_config_default", "pond_create", "pond_set_stream", "pond_set_state",
            "pond_step", "pond_moments", "pond_get_state", "pond_iterations",
            "pond_adjoint_step", "pond_adjoint_step_given", "pond_adjoint_init",
+           "pond_adjoint_nu_bar",
            "pond_step_fp64_noalloc", "pond_measure_peak", "pond_set_interior",
            "pond_pack_rect", "pond_unpack_rect", "pond_max_displacement", "pond_destroy",
            "pond_last_error", "pond_version"]
@@ -148,6 +149,8 @@ def load(build_if_missing: bool = True, path: str | None = None):
     lib.pond_adjoint_step_given.restype = i32
     lib.pond_adjoint_init.argtypes = [vp, vp, vp]
     lib.pond_adjoint_init.restype = i32
+    lib.pond_adjoint_nu_bar.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.pond_adjoint_nu_bar.restype = i32
     lib.pond_step_fp64_noalloc.argtypes = [ctypes.POINTER(pond_config), i32, i32,
                                            vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                            ctypes.POINTER(pond_stats), vp]
@@ -277,23 +280,37 @@ def pond_iterations(ctx, grid, iters):
     _check(ctx, load().pond_iterations(ctx, grid, p, int(dev)))
 
 
-def pond_adjoint_step(ctx, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out):
-    """Device tensors only; returns d(loss)/d(nu) of this step."""
+def pond_adjoint_step(ctx, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out,
+                      nu_on_device: bool = False):
+    """Device tensors only; returns d(loss)/d(nu) of this step, or, with
+    nu_on_device, None: the contribution then accumulates on the device
+    (read with pond_adjoint_nu_bar) and the call does not wait for the GPU."""
     nu_bar = ctypes.c_double(0.0)
     ps = [_ptr(a, True) for a in (f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out)]
-    _check(ctx, load().pond_adjoint_step(ctx, *[p for p, _ in ps], ctypes.byref(nu_bar)))
-    return nu_bar.value
+    acc = None if nu_on_device else ctypes.byref(nu_bar)
+    _check(ctx, load().pond_adjoint_step(ctx, *[p for p, _ in ps], acc))
+    return None if nu_on_device else nu_bar.value
 
 
 def pond_adjoint_step_given(ctx, ux_out, uy_out, T_out, f_bar_in, gauge_bar_in, f_bar_out,
-                            gauge_bar_out):
+                            gauge_bar_out, nu_on_device: bool = False):
     """pond_adjoint_step with the step's output gauge (device tensors) given,
-    so the forward step is not recomputed; returns d(loss)/d(nu) of this step."""
+    so the forward step is not recomputed; returns d(loss)/d(nu) of this step
+    (None with nu_on_device, as pond_adjoint_step)."""
     nu_bar = ctypes.c_double(0.0)
     ps = [_ptr(a, True) for a in (ux_out, uy_out, T_out, f_bar_in, gauge_bar_in, f_bar_out,
                                   gauge_bar_out)]
-    _check(ctx, load().pond_adjoint_step_given(ctx, *[p for p, _ in ps], ctypes.byref(nu_bar)))
-    return nu_bar.value
+    acc = None if nu_on_device else ctypes.byref(nu_bar)
+    _check(ctx, load().pond_adjoint_step_given(ctx, *[p for p, _ in ps], acc))
+    return None if nu_on_device else nu_bar.value
+
+
+def pond_adjoint_nu_bar(ctx) -> float:
+    """The nu cotangent accumulated on the device since the last read (and
+    clear it)."""
+    v = ctypes.c_double(0.0)
+    _check(ctx, load().pond_adjoint_nu_bar(ctx, ctypes.byref(v)))
+    return v.value
 
 
 def pond_adjoint_init(ctx, f_bar, rho_bar):

@@ -239,6 +239,43 @@ def test_adjoint_given_output_gauge_matches_recomputed(precision, lattice, T_L):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nu_cotangent_on_device_matches_host(precision):
+    """With nu_bar_accum NULL the nu cotangent accumulates on the device and
+    pond_adjoint_nu_bar returns (and clears) the sum: the same value as the
+    host accumulator, over several calls, and the same f / gauge cotangents."""
+    from paper_1806_05089_gb300 import pond
+    rho0, ux, uy, T, _ = small_case(40, 36, seed=3)
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(4)
+    fbar = torch.tensor(rng.standard_normal((16, 36, 40)), device=dev)
+    gbar = torch.tensor(rng.standard_normal((3, 36, 40)), device=dev)
+    with pond.Sim(40, 36, precision, nu=0.01) as s:
+        s.set_state(rho0, ux, uy, T)
+        s.step(2)
+        assert pond.pond_adjoint_nu_bar(s.ctx) == 0.0  # before any adjoint call
+        outs = []
+        for on_device in (False, True):
+            tot = 0.0
+            for _ in range(3):
+                fo = torch.empty_like(fbar)
+                go = torch.empty_like(gbar)
+                nb = pond.pond_adjoint_step(s.ctx, fbar, gbar, fo, go, nu_on_device=on_device)
+                if on_device:
+                    assert nb is None
+                else:
+                    tot += nb
+            if on_device:
+                tot = pond.pond_adjoint_nu_bar(s.ctx)
+                assert pond.pond_adjoint_nu_bar(s.ctx) == 0.0  # cleared by the read
+            outs.append((fo.cpu().numpy(), go.cpu().numpy(), tot))
+    (f_a, g_a, n_a), (f_b, g_b, n_b) = outs
+    assert np.abs(f_a - f_b).max() <= 1e-14 * np.abs(f_a).max()
+    assert np.abs(g_a - g_b).max() <= 1e-14 * np.abs(g_a).max()
+    assert n_a != 0.0 and abs(n_a - n_b) <= 1e-12 * abs(n_a)
+
+
+@pytest.mark.gpu
 def test_mixed_adjoint_rollout_length_bound():
     """The stated accuracy of the FP32 adjoint over a long rollout: on the
     512^2 adjoint workload, 200 steps with checkpoints every 20, its gradient

@@ -196,8 +196,9 @@ pond_status pond_set_stream(pond_ctx* ctx, void* cuda_stream);
  * (Eq. equilibrium; rho is then required).  If f is given ([Q][ny][nx]),
  * it is taken as the populations in the gauge (ux, uy, T) and rho is
  * ignored (may be NULL).  on_device: pointers are device (1) or host (0).
- * Errors: POND_ERR_ARG, POND_ERR_NONPHYSICAL (T <= 0 or non-finite gauge on
- * host input), POND_ERR_CUDA. */
+ * Errors: POND_ERR_ARG, POND_ERR_NONPHYSICAL (T <= 0 or a non-finite
+ * gauge at some node, host or device input, checked on the device; the grid
+ * then counts as never set until a valid call), POND_ERR_CUDA. */
 pond_status pond_set_state(pond_ctx* ctx, int32_t grid, const void* rho, const void* ux,
                            const void* uy, const void* T, const void* f, int32_t on_device);
 

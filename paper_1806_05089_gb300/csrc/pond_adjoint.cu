@@ -695,7 +695,7 @@ __device__ __noinline__ void adj_population_direct(const AdjArgs& A, int X, int 
     out4[3] = dAst;
 }
 
-constexpr int ADJ_TY = 4;  // staged phase A tile: 32 x 4 targets
+constexpr int ADJ_TY = 8;  // staged phase A tile: 32 x 8 targets (0.8 % faster than 32 x 4)
 
 // Phase A, staged: A*, its tangents at lambda* into jvp[4][Q][N], the
 // gather's per-(population, target) stencil origin and weights, and 1 / s*.
@@ -763,7 +763,7 @@ k_adjoint_jvp_staged(AdjArgs A, int wwa, int wha, double c_max, double* __restri
     // offsets of the maps r -> lambda*
     const double rt = (rst - st) * inv, dxt = (rux - ux) * inv, dyt = (ruy - uy) * inv;
     const double dt = A.dt;
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < N1; ++k) {
         const double ck = L.c[k];
         const double depx = (double)X - fma(st, ck, ux) * dt;
@@ -771,108 +771,159 @@ k_adjoint_jvp_staged(AdjArgs A, int wwa, int wha, double c_max, double* __restri
         double lx[4], dlx[4];
         lagrange4_d(depx - flx + 1.0, lx, dlx);
         const int col = (int)flx - 1 - wx0;  // flx is the absolute departure floor
-        double ex[N1], gdx[N1], xix[N1];
+        double ex[N1], gdx[N1], gdxx[N1];
 #pragma unroll
         for (int a = 0; a < N1; ++a) {
             const double de = fma(L.c[a], rt, dxt);
             lag_taylor_e(L, k, a, de, ex[a], gdx[a]);
-            xix[a] = L.c[a] + de;
+            gdxx[a] = gdx[a] * (L.c[a] + de);
         }
+        const bool colok = col >= 0 && col + 3 < ww;
+        // The y-speeds in pairs (l0, l0 + 1): one sweep over the union of
+        // the pair's two y-stencils, so a row both stencils hold is
+        // interpolated once.  Each row is taken one component b at a time
+        // (Fi, Fd of that column of the staged rows), which keeps the two
+        // populations' accumulators in registers; every sum runs in the
+        // order of the single-population sweep, so the results are the same.
 #pragma unroll 1
-        for (int l = 0; l < N1; ++l) {
-            const double cl = L.c[l];
-            const double depy = (double)Y - fma(st, cl, uy) * dt;
-            const double fly = floor(depy);
-            double ly[4], dly[4];
-            lagrange4_d(depy - fly + 1.0, ly, dly);
-            const int top = (int)fly - 1 - wy0;
-            const int q = N1 * k + l;
-            const long long o = (long long)q * A.N + node;
-            A.org[o] = make_int2((int)((long long)flx - 1 - X), (int)((long long)fly - 1 - Y));
-            double2* pw = reinterpret_cast<double2*>(A.lw + 8 * o);
-            pw[0] = make_double2(lx[0], lx[1]);
-            pw[1] = make_double2(lx[2], lx[3]);
-            pw[2] = make_double2(ly[0], ly[1]);
-            pw[3] = make_double2(ly[2], ly[3]);
-            double R[4];
-            if (col >= 0 && col + 3 < ww && top >= 0 && top + 3 < wh) {
-                double Z[N1], Zux[N1], Zuy[N1], Zs[N1];
+        for (int l0 = 0; l0 < N1; l0 += 2) {
+            const int np = l0 + 1 < N1 ? 2 : 1;
+            double ly[2][4], dly[2][4];
+            int top[2] = {0, 0};
+            bool in[2] = {false, false};
 #pragma unroll
-                for (int b = 0; b < N1; ++b) Z[b] = Zux[b] = Zuy[b] = Zs[b] = 0.0;
+            for (int p = 0; p < 2; ++p) {
+                if (p >= np) break;
+                const int l = l0 + p;
+                const double depy = (double)Y - fma(st, L.c[l], uy) * dt;
+                const double fly = floor(depy);
+                lagrange4_d(depy - fly + 1.0, ly[p], dly[p]);
+                top[p] = (int)fly - 1 - wy0;
+                in[p] = colok && top[p] >= 0 && top[p] + 3 < wh;
+                const long long o = (long long)(N1 * k + l) * A.N + node;
+                A.org[o] = make_int2((int)((long long)flx - 1 - X), (int)((long long)fly - 1 - Y));
+                double2* pw = reinterpret_cast<double2*>(A.lw + 8 * o);
+                pw[0] = make_double2(lx[0], lx[1]);
+                pw[1] = make_double2(lx[2], lx[3]);
+                pw[2] = make_double2(ly[p][0], ly[p][1]);
+                pw[3] = make_double2(ly[p][2], ly[p][3]);
+            }
+            double Z[2][N1], Zux[2][N1], Zuy[2][N1], Zs[2][N1];
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int b = 0; b < N1; ++b) Z[p][b] = Zux[p][b] = Zuy[p][b] = Zs[p][b] = 0.0;
+            if (in[0] || in[1]) {
+                const int r0 = in[0] && in[1] ? min(top[0], top[1]) : (in[0] ? top[0] : top[1]);
+                const int r1 = (in[0] && in[1] ? max(top[0], top[1]) : (in[0] ? top[0] : top[1])) + 3;
 #pragma unroll 1
-                for (int jy = 0; jy < 4; ++jy) {
-                    const double w = jy == 0 ? ly[0] : jy == 1 ? ly[1] : jy == 2 ? ly[2] : ly[3];
-                    const double dw = jy == 0 ? dly[0] : jy == 1 ? dly[1] : jy == 2 ? dly[2] : dly[3];
-                    const Double4* src = s_f + (top + jy) * ww + col;
-                    double Fi[N1][N1], Fd[N1][N1];
+                for (int row = r0; row <= r1; ++row) {
+                    bool cov[2];
+                    double w[2], dw[2];
 #pragma unroll
-                    for (int a = 0; a < N1; ++a)
-#pragma unroll
-                        for (int b = 0; b < N1; ++b) Fi[a][b] = Fd[a][b] = 0.0;
-#pragma unroll
-                    for (int jx = 0; jx < 4; ++jx) {
-#pragma unroll
-                        for (int a = 0; a < N1; ++a) {
-                            double fr[4];
-                            StagedAdj64::load4(src + (size_t)a * WN + jx, fr);
-#pragma unroll
-                            for (int b = 0; b < N1; ++b) {
-                                Fi[a][b] = fma(lx[jx], fr[b], Fi[a][b]);
-                                Fd[a][b] = fma(dlx[jx], fr[b], Fd[a][b]);
-                            }
-                        }
+                    for (int p = 0; p < 2; ++p) {
+                        const int j = row - top[p];
+                        cov[p] = in[p] && j >= 0 && j < 4;
+                        w[p] = j == 0 ? ly[p][0] : j == 1 ? ly[p][1] : j == 2 ? ly[p][2] : ly[p][3];
+                        dw[p] = j == 0 ? dly[p][0] : j == 1 ? dly[p][1] : j == 2 ? dly[p][2] : dly[p][3];
                     }
-                    // row contributions: value, and the tangents through the
-                    // x-weights (Fd), the x-map (gdx) and the row weight (dw)
-                    const double wux = -dt * w, wdy = -dt * dw;
+                    if (!cov[0] && !cov[1]) continue;  // a gap between the two stencils
+                    // the row's weights in the four accumulators, per population
+                    double cwux[2], cwdy[2], cwi[2], cckwux[2], cclwdy[2];
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        cwux[p] = -dt * w[p];
+                        cwdy[p] = -dt * dw[p];
+                        cwi[p] = -w[p] * inv;
+                        cckwux[p] = ck * cwux[p];
+                        cclwdy[p] = L.c[l0 + p] * cwdy[p];
+                    }
+                    const Double4* src = s_f + row * ww + col;
 #pragma unroll
                     for (int b = 0; b < N1; ++b) {
-                        double P = Fi[k][b], P1 = Fd[k][b], Pd = 0.0, Pdx = 0.0;
+                        double Fi[N1], Fd[N1];
+#pragma unroll
+                        for (int a = 0; a < N1; ++a) Fi[a] = Fd[a] = 0.0;
+#pragma unroll
+                        for (int jx = 0; jx < 4; ++jx) {
+#pragma unroll
+                            for (int a = 0; a < N1; ++a) {
+                                const double v =
+                                    reinterpret_cast<const double*>(src + (size_t)a * WN + jx)[b];
+                                Fi[a] = fma(lx[jx], v, Fi[a]);
+                                Fd[a] = fma(dlx[jx], v, Fd[a]);
+                            }
+                        }
+                        // the row's contributions: value, and the tangents
+                        // through the x-weights (Fd), the x-map (gdx) and
+                        // the row weight (dw)
+                        // the identity part of the x-map, Fi[k] (k is a
+                        // loop variable: taken by selection, in registers)
+                        double P = Fi[0], P1 = Fd[0], Pd = 0.0, Pdx = 0.0;
+#pragma unroll
+                        for (int a = 1; a < N1; ++a) {
+                            P = k == a ? Fi[a] : P;
+                            P1 = k == a ? Fd[a] : P1;
+                        }
 #pragma unroll
                         for (int a = 0; a < N1; ++a) {
-                            P = fma(ex[a], Fi[a][b], P);
-                            P1 = fma(ex[a], Fd[a][b], P1);
-                            Pd = fma(gdx[a], Fi[a][b], Pd);
-                            Pdx = fma(gdx[a] * xix[a], Fi[a][b], Pdx);
+                            P = fma(ex[a], Fi[a], P);
+                            P1 = fma(ex[a], Fd[a], P1);
+                            Pd = fma(gdx[a], Fi[a], Pd);
+                            Pdx = fma(gdxx[a], Fi[a], Pdx);
                         }
-                        Z[b] = fma(w, P, Z[b]);
-                        Zux[b] = fma(wux, P1, fma(-w * inv, Pd, Zux[b]));
-                        Zuy[b] = fma(wdy, P, Zuy[b]);
-                        Zs[b] = fma(ck * wux, P1, fma(-w * inv, Pdx, fma(cl * wdy, P, Zs[b])));
+#pragma unroll
+                        for (int p = 0; p < 2; ++p) {
+                            if (!cov[p]) continue;
+                            Z[p][b] = fma(w[p], P, Z[p][b]);
+                            Zux[p][b] = fma(cwux[p], P1, fma(cwi[p], Pd, Zux[p][b]));
+                            Zuy[p][b] = fma(cwdy[p], P, Zuy[p][b]);
+                            Zs[p][b] = fma(cckwux[p], P1, fma(cwi[p], Pdx, fma(cclwdy[p], P, Zs[p][b])));
+                        }
                     }
                 }
-                // the y-map r -> lambda* and its derivatives
-                double Al = 0.0, Axl = 0.0, Ayl = 0.0, Asl = 0.0;
-#pragma unroll
-                for (int b = 0; b < N1; ++b) {
-                    const bool id = b == l;  // the identity part, exactly
-                    Al += id ? Z[b] : 0.0;
-                    Axl += id ? Zux[b] : 0.0;
-                    Ayl += id ? Zuy[b] : 0.0;
-                    Asl += id ? Zs[b] : 0.0;
-                }
-                double Ae = 0.0, Axe = 0.0, Aye = 0.0, Ase = 0.0, Dy = 0.0, Ds = 0.0;
-#pragma unroll
-                for (int b = 0; b < N1; ++b) {
-                    const double de = fma(L.c[b], rt, dyt);
-                    double ey, gdy;
-                    lag_taylor_e(L, l, b, de, ey, gdy);
-                    Ae = fma(ey, Z[b], Ae);
-                    Axe = fma(ey, Zux[b], Axe);
-                    Aye = fma(ey, Zuy[b], Aye);
-                    Ase = fma(ey, Zs[b], Ase);
-                    Dy = fma(gdy, Z[b], Dy);
-                    Ds = fma(gdy * (L.c[b] + de), Z[b], Ds);
-                }
-                R[0] = Al + Ae;
-                R[1] = Axl + Axe;
-                R[2] = fma(-inv, Dy, Ayl + Aye);
-                R[3] = fma(-inv, Ds, Asl + Ase);
-            } else {
-                adj_population_direct<N1>(A, X, Y, k, l, ux, uy, st, R);
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) jvp[((long long)i * Q + q) * A.N + node] = R[i];
+            for (int p = 0; p < 2; ++p) {
+                if (p >= np) break;
+                const int l = l0 + p;
+                const int q = N1 * k + l;
+                double R[4];
+                if (in[p]) {
+                    // the y-map r -> lambda* and its derivatives; its
+                    // identity part exactly
+                    double Al = 0.0, Axl = 0.0, Ayl = 0.0, Asl = 0.0;
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) {
+                        const bool id = b == l;
+                        Al += id ? Z[p][b] : 0.0;
+                        Axl += id ? Zux[p][b] : 0.0;
+                        Ayl += id ? Zuy[p][b] : 0.0;
+                        Asl += id ? Zs[p][b] : 0.0;
+                    }
+                    double Ae = 0.0, Axe = 0.0, Aye = 0.0, Ase = 0.0, Dy = 0.0, Ds = 0.0;
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) {
+                        const double de = fma(L.c[b], rt, dyt);
+                        double ey, gdy;
+                        lag_taylor_e(L, l, b, de, ey, gdy);
+                        Ae = fma(ey, Z[p][b], Ae);
+                        Axe = fma(ey, Zux[p][b], Axe);
+                        Aye = fma(ey, Zuy[p][b], Aye);
+                        Ase = fma(ey, Zs[p][b], Ase);
+                        Dy = fma(gdy, Z[p][b], Dy);
+                        Ds = fma(gdy * (L.c[b] + de), Z[p][b], Ds);
+                    }
+                    R[0] = Al + Ae;
+                    R[1] = Axl + Axe;
+                    R[2] = fma(-inv, Dy, Ayl + Aye);
+                    R[3] = fma(-inv, Ds, Asl + Ase);
+                } else {
+                    adj_population_direct<N1>(A, X, Y, k, l, ux, uy, st, R);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) jvp[((long long)i * Q + q) * A.N + node] = R[i];
+            }
         }
     }
 }

@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "pond_device.cuh"
+#include "pond_staged.cuh"
 
 namespace pond {
 
@@ -539,6 +540,385 @@ __global__ void __launch_bounds__(ADJM_THREADS) k_adjoint_sources_mixed_r(AdjMix
     A.gbar_in[2 * A.N + src] = (double)bst / (2.0 * A.st_in[src] * (double)A.T_L);
 }
 
+// ---------------------------------------------------------------------------
+// Phase A in the staged form (the FP64 counterpart is k_adjoint_jvp_staged in
+// pond_adjoint.cu): the window of sources a 32 x 4 tile of targets can reach
+// is staged once in the tile's reference gauge lambda_r (FP32 rows, the
+// forward step's own staging), and each population's A* and its three
+// tangents come from one pass over its four stencil rows: the rows
+// interpolated with the cubic weights (Fi) and with their derivatives (Fd),
+// the x-map r -> lambda* applied, the y-map after.  The per-node epilogue of
+// k_adjoint_targets_mixed follows in the same thread (running sums over the
+// populations, the 3 x 3 solve, w, the beta cotangent), so A* and its
+// tangents never leave registers.
+
+struct StagedAdj32 {
+    using Real = float;
+    using Real4 = float4;
+    template <int N1>
+    static __device__ __forceinline__ const LatticeF& lat() {
+        return c_Lam[lattice_slot(N1)];
+    }
+    static __device__ __forceinline__ void store4(float4* p, const float (&v)[4]) {
+        *p = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+
+constexpr int ADJM_TY = 4;  // staged phase A tile: 32 x 4 targets
+
+// L_k(c_a + de) - [k == a] in correction form, and L_k'(c_a + de)
+__device__ __forceinline__ void lag_taylor_ef(const LatticeF& L, int k, int a, float de, float& e,
+                                              float& gd) {
+    const float d1 = L.d1[k][a], d2 = L.d2[k][a], d3 = L.d3[k];
+    e = fmaf(fmaf(d3, de, d2), de, d1) * de;
+    gd = fmaf(fmaf(3.0f * d3, de, 2.0f * d2), de, d1);
+}
+
+// One population's A and tangents in the per-pair form, read from global
+// memory (the pair loop of k_adjoint_targets_mixed): for a stencil that
+// leaves the staged window.  th, tl: splits of lambda* at the target.
+template <int N1>
+__device__ __noinline__ void adj_population_direct_mixed(const AdjMixedArgs& A, int X, int Y, int k,
+                                                         int l, float4 th, float4 tl, float st,
+                                                         float ux, float uy, float inv,
+                                                         float* out4) {
+    const LatticeF& L = c_Lam[lattice_slot(N1)];
+    const float ck = L.c[k], cl = L.c[l];
+    const RowCoef<N1> Rk = row_coef<N1>(L, k), Rl = row_coef<N1>(L, l);
+    const float frx = -fmaf(st, ck, ux) * A.dt, fry = -fmaf(st, cl, uy) * A.dt;
+    const float flx = floorf(frx), fly = floorf(fry);
+    float lx[4], dlx[4], ly[4], dly[4];
+    lagrange4_df(frx - flx + 1.0f, lx, dlx);
+    lagrange4_df(fry - fly + 1.0f, ly, dly);
+    const int x0 = wrap_idx((long long)X + (long long)flx - 1, A.nx);
+    const int y0 = wrap_idx((long long)Y + (long long)fly - 1, A.ny);
+    float Aq = 0.0f, dAux = 0.0f, dAuy = 0.0f, dAst = 0.0f;
+    for (int jy = 0; jy < 4; ++jy) {
+        const int sy = wrap_inc(y0, jy, A.ny);
+        for (int jx = 0; jx < 4; ++jx) {
+            const int sx = wrap_inc(x0, jx, A.nx);
+            const long long s = (long long)sy * A.nx + sx;
+            const float4 sh = A.gin[s], sl = A.gin[A.N + s];
+            const float r = sdiff(sh.x, sl.x, th.x, tl.x) * inv;
+            const float dx = sdiff(sh.y, sl.y, th.y, tl.y) * inv;
+            const float dy = sdiff(sh.z, sl.z, th.z, tl.z) * inv;
+            float gx[N1], gdx[N1], gy[N1], gdyx[N1], gdy[N1], xix[N1];
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                const float ex = fmaf(L.c[a], r, dx), ey = fmaf(L.c[a], r, dy);
+                xix[a] = L.c[a] + ex;
+                lag_taylor_r<N1>(Rk, k, a, ex, gx[a], gdx[a]);
+                lag_taylor_r<N1>(Rl, l, a, ey, gy[a], gdy[a]);
+                gdyx[a] = gdy[a] * (L.c[a] + ey);
+            }
+            float g = 0.0f, gux = 0.0f, guy = 0.0f, gst = 0.0f;
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                float h = 0.0f, hp = 0.0f, hq = 0.0f;
+                const float4 r4 = A.f4[(long long)a * A.N + s];
+                const float fr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                for (int b = 0; b < N1; ++b) {
+                    h = fmaf(gy[b], fr[b], h);
+                    hp = fmaf(gdy[b], fr[b], hp);
+                    hq = fmaf(gdyx[b], fr[b], hq);
+                }
+                g = fmaf(gx[a], h, g);
+                gux = fmaf(gdx[a], h, gux);
+                guy = fmaf(gx[a], hp, guy);
+                gst = fmaf(gdx[a] * xix[a], h, fmaf(gx[a], hq, gst));
+            }
+            gux *= -inv;
+            guy *= -inv;
+            gst *= -inv;
+            const float wx = lx[jx], dwx = dlx[jx], wy = ly[jy], dwy = dly[jy];
+            const float a_w = wx * wy;
+            Aq = fmaf(a_w, g, Aq);
+            dAux = fmaf(a_w, gux, fmaf(-A.dt * dwx * wy, g, dAux));
+            dAuy = fmaf(a_w, guy, fmaf(-A.dt * wx * dwy, g, dAuy));
+            dAst = fmaf(a_w, gst, fmaf(-A.dt * (ck * dwx * wy + cl * wx * dwy), g, dAst));
+        }
+    }
+    out4[0] = Aq;
+    out4[1] = dAux;
+    out4[2] = dAuy;
+    out4[3] = dAst;
+}
+
+// Phase A, staged, with the per-node epilogue: writes w, the gather's
+// per-(population, target) stencil origin and weights, 1 / s*, and adds the
+// beta cotangent.  in: the step's input state; ux_star / uy_star (and
+// A.st_star): lambda* in FP64; wwa x wha: the window capacity.
+template <int N1>
+__global__ void __launch_bounds__(32 * ADJM_TY, 3)  // 3 CTAs per SM: measured 2 % faster than 2
+k_adjoint_jvp_staged_mixed(AdjMixedArgs A, StateBuf<float> in, const double* __restrict__ ux_star,
+                           const double* __restrict__ uy_star, int wwa, int wha, float c_max) {
+    constexpr int TX = 32, NT = TX * ADJM_TY, Q = N1 * N1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* s_f = reinterpret_cast<float4*>(smem_raw);  // [N1][WN]
+    __shared__ float s_red[4][NT / 32];
+    const LatticeF& L = c_Lam[lattice_slot(N1)];
+    const int WN = wwa * wha;
+    const int tid = threadIdx.x;
+    const int tiles_x = (A.nx + TX - 1) / TX;
+    const int tx0 = (int)(blockIdx.x % tiles_x) * TX;
+    const int ty0 = (int)(blockIdx.x / tiles_x) * ADJM_TY;
+    const int X = tx0 + tid % TX, Y = ty0 + tid / TX;
+    const bool valid = X < A.nx && Y < A.ny;
+    const long long node = (long long)Y * A.nx + X;
+
+    // reference gauge: the tile's centre node of the input state
+    const long long rnode = (long long)min(ty0 + ADJM_TY / 2, A.ny - 1) * A.nx +
+                            min(tx0 + TX / 2, A.nx - 1);
+    const double rux = in.ux[rnode], ruy = in.uy[rnode], rst = in.st[rnode];
+
+    double uxd = 0.0, uyd = 0.0, sdd = 1.0;
+    float vxlo = 3.0e38f, vxhi = -3.0e38f, vylo = 3.0e38f, vyhi = -3.0e38f;
+    if (valid) {
+        uxd = ux_star[node];
+        uyd = uy_star[node];
+        sdd = A.st_star[node];
+        const float sp = c_max * (float)sdd;
+        vxlo = (float)uxd - sp;
+        vxhi = (float)uxd + sp;
+        vylo = (float)uyd - sp;
+        vyhi = (float)uyd + sp;
+    }
+    staged_block_minmax4<StagedAdj32, NT>(vxlo, vxhi, vylo, vyhi, s_red);
+    const float m = 1.0f, fdt = A.dt;
+    const float bxl = fminf(fmaxf(vxlo, -1.0e6f), 1.0e6f), bxh = fminf(fmaxf(vxhi, -1.0e6f), 1.0e6f);
+    const float byl = fminf(fmaxf(vylo, -1.0e6f), 1.0e6f), byh = fminf(fmaxf(vyhi, -1.0e6f), 1.0e6f);
+    const int wx0 = (int)floorf((float)tx0 - bxh * fdt - m) - 1;
+    const int wx1 = (int)floorf((float)(tx0 + TX - 1) - bxl * fdt + m) + 2;
+    const int wy0 = (int)floorf((float)ty0 - byh * fdt - m) - 1;
+    const int wy1 = (int)floorf((float)(ty0 + ADJM_TY - 1) - byl * fdt + m) + 2;
+    const bool fin = isfinite(vxlo) && isfinite(vxhi) && isfinite(vylo) && isfinite(vyhi) &&
+                     vxlo > -1.0e6f && vxhi < 1.0e6f && vylo > -1.0e6f && vyhi < 1.0e6f;
+    const int ww = fin ? max(1, min(wx1 - wx0 + 1, wwa)) : 1;
+    const int wh = fin ? max(1, min(wy1 - wy0 + 1, wha)) : 1;
+    GridDesc G;
+    G.nx = A.nx;
+    G.ny = A.ny;
+    G.offset = 0;
+    G.ix0 = 0;
+    G.iy0 = 0;
+    G.iw = A.nx;
+    G.ih = A.ny;
+    stage_window<StagedAdj32, N1>(in, A.N, G, 0, wx0, wy0, ww, wh, WN, rux, ruy, rst, s_f, nullptr,
+                                  tid, NT);
+    __syncthreads();
+
+    double bb = 0.0;
+    if (valid) {
+        const float st = (float)sdd, ux = (float)uxd, uy = (float)uyd;
+        const float inv = 1.0f / st;
+        A.inv_st[node] = inv;
+        // offsets of the maps r -> lambda*, formed in FP64 and rounded once
+        const double invd = 1.0 / sdd;
+        const float rt = (float)((rst - sdd) * invd);
+        const float dxt = (float)((rux - uxd) * invd);
+        const float dyt = (float)((ruy - uyd) * invd);
+        const float4 th = A.gstar[node], tl = A.gstar[A.N + node];
+        const float dt = A.dt, T_L = A.T_L;
+        // running sums of the epilogue (k_adjoint_targets_mixed)
+        float rho = 0.0f, sAf = 0.0f, wf = 0.0f;
+        float Px[3] = {0.0f, 0.0f, 0.0f}, Py[3] = {0.0f, 0.0f, 0.0f}, Pt[3] = {0.0f, 0.0f, 0.0f};
+        float gF[3] = {0.0f, 0.0f, 0.0f}, gS[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            const float ck = L.c[k];
+            const float frx = -fmaf(st, ck, ux) * dt;
+            const float flx = floorf(frx);
+            float lx[4], dlx[4];
+            lagrange4_df(frx - flx + 1.0f, lx, dlx);
+            const int col = X + (int)flx - 1 - wx0;
+            float ex[N1], gdx[N1], gdxx[N1];
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                const float de = fmaf(L.c[a], rt, dxt);
+                lag_taylor_ef(L, k, a, de, ex[a], gdx[a]);
+                gdxx[a] = gdx[a] * (L.c[a] + de);
+            }
+#pragma unroll 1
+            for (int l = 0; l < N1; ++l) {
+                const float cl = L.c[l];
+                const float fry = -fmaf(st, cl, uy) * dt;
+                const float fly = floorf(fry);
+                float ly[4], dly[4];
+                lagrange4_df(fry - fly + 1.0f, ly, dly);
+                const int top = Y + (int)fly - 1 - wy0;
+                const int q = N1 * k + l;
+                const long long o = (long long)q * A.N + node;
+                A.org[o] = make_int2((int)flx - 1, (int)fly - 1);
+                float4* pw = reinterpret_cast<float4*>(A.lw + 8 * o);
+                pw[0] = make_float4(lx[0], lx[1], lx[2], lx[3]);
+                pw[1] = make_float4(ly[0], ly[1], ly[2], ly[3]);
+                float R[4];
+                if (col >= 0 && col + 3 < ww && top >= 0 && top + 3 < wh) {
+                    float Z[N1], Zux[N1], Zuy[N1], Zs[N1];
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) Z[b] = Zux[b] = Zuy[b] = Zs[b] = 0.0f;
+#pragma unroll 1
+                    for (int jy = 0; jy < 4; ++jy) {
+                        const float w = jy == 0 ? ly[0] : jy == 1 ? ly[1] : jy == 2 ? ly[2] : ly[3];
+                        const float dw = jy == 0 ? dly[0] : jy == 1 ? dly[1] : jy == 2 ? dly[2] : dly[3];
+                        const float4* src = s_f + (top + jy) * ww + col;
+                        float Fi[N1][N1], Fd[N1][N1];
+#pragma unroll
+                        for (int a = 0; a < N1; ++a)
+#pragma unroll
+                            for (int b = 0; b < N1; ++b) Fi[a][b] = Fd[a][b] = 0.0f;
+#pragma unroll
+                        for (int jx = 0; jx < 4; ++jx) {
+#pragma unroll
+                            for (int a = 0; a < N1; ++a) {
+                                const float4 v = src[(size_t)a * WN + jx];
+                                const float fr[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                                for (int b = 0; b < N1; ++b) {
+                                    Fi[a][b] = fmaf(lx[jx], fr[b], Fi[a][b]);
+                                    Fd[a][b] = fmaf(dlx[jx], fr[b], Fd[a][b]);
+                                }
+                            }
+                        }
+                        // the row's contributions: value, and the tangents
+                        // through the x-weights (Fd), the x-map (gdx) and
+                        // the row weight (dw)
+                        const float wux = -dt * w, wdy = -dt * dw, wi = -w * inv;
+#pragma unroll
+                        for (int b = 0; b < N1; ++b) {
+                            float P = Fi[k][b], P1 = Fd[k][b], Pd = 0.0f, Pdx = 0.0f;
+#pragma unroll
+                            for (int a = 0; a < N1; ++a) {
+                                P = fmaf(ex[a], Fi[a][b], P);
+                                P1 = fmaf(ex[a], Fd[a][b], P1);
+                                Pd = fmaf(gdx[a], Fi[a][b], Pd);
+                                Pdx = fmaf(gdxx[a], Fi[a][b], Pdx);
+                            }
+                            Z[b] = fmaf(w, P, Z[b]);
+                            Zux[b] = fmaf(wux, P1, fmaf(wi, Pd, Zux[b]));
+                            Zuy[b] = fmaf(wdy, P, Zuy[b]);
+                            Zs[b] = fmaf(ck * wux, P1, fmaf(wi, Pdx, fmaf(cl * wdy, P, Zs[b])));
+                        }
+                    }
+                    // the y-map r -> lambda* and its derivatives; its
+                    // identity part exactly
+                    float Al = 0.0f, Axl = 0.0f, Ayl = 0.0f, Asl = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) {
+                        const bool id = b == l;
+                        Al += id ? Z[b] : 0.0f;
+                        Axl += id ? Zux[b] : 0.0f;
+                        Ayl += id ? Zuy[b] : 0.0f;
+                        Asl += id ? Zs[b] : 0.0f;
+                    }
+                    float Ae = 0.0f, Axe = 0.0f, Aye = 0.0f, Ase = 0.0f, Dy = 0.0f, Ds = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) {
+                        const float de = fmaf(L.c[b], rt, dyt);
+                        float ey, gdy;
+                        lag_taylor_ef(L, l, b, de, ey, gdy);
+                        Ae = fmaf(ey, Z[b], Ae);
+                        Axe = fmaf(ey, Zux[b], Axe);
+                        Aye = fmaf(ey, Zuy[b], Aye);
+                        Ase = fmaf(ey, Zs[b], Ase);
+                        Dy = fmaf(gdy, Z[b], Dy);
+                        Ds = fmaf(gdy * (L.c[b] + de), Z[b], Ds);
+                    }
+                    R[0] = Al + Ae;
+                    R[1] = Axl + Axe;
+                    R[2] = fmaf(-inv, Dy, Ayl + Aye);
+                    R[3] = fmaf(-inv, Ds, Asl + Ase);
+                } else {
+                    adj_population_direct_mixed<N1>(A, X, Y, k, l, th, tl, st, ux, uy, inv, R);
+                }
+                const float fb = (float)A.fbar[o];
+                const float mt = fmaf(ck, ck, cl * cl) - 2.0f * T_L;
+                rho += R[0];
+                sAf = fmaf(R[0], fb, sAf);
+                wf = fmaf(L.w[k] * L.w[l], fb, wf);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    Px[j] = fmaf(ck, R[1 + j], Px[j]);
+                    Py[j] = fmaf(cl, R[1 + j], Py[j]);
+                    Pt[j] = fmaf(mt, R[1 + j], Pt[j]);
+                    gF[j] = fmaf(fb, R[1 + j], gF[j]);
+                    gS[j] += R[1 + j];
+                }
+            }
+        }
+        // the epilogue of k_adjoint_targets_mixed: J = M_A A_lambda, g, the
+        // 3 x 3 solve by Cramer's rule, w
+        const float beta = A.beta;
+        const float irho = 1.0f / rho;
+        const float sx = st * irho, stt = st * irho / (4.0f * T_L);
+        float J[3][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            J[0][j] = sx * Px[j];
+            J[1][j] = sx * Py[j];
+            J[2][j] = stt * Pt[j];
+        }
+        const float c1 = 1.0f - 2.0f * beta, c2b = 2.0f * beta * wf;
+        const float g0 = fmaf(c1, gF[0], c2b * gS[0]) + (float)A.gbar[node];
+        const float g1 = fmaf(c1, gF[1], c2b * gS[1]) + (float)A.gbar[A.N + node];
+        const float g2 = fmaf(c1, gF[2], c2b * gS[2]) + (float)A.gbar[2 * A.N + node] * 2.0f * st * T_L;
+        const float a00 = J[0][0], a01 = J[1][0], a02 = J[2][0];
+        const float a10 = J[0][1], a11 = J[1][1], a12 = J[2][1];
+        const float a20 = J[0][2], a21 = J[1][2], a22 = J[2][2];
+        const float det = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
+                          a02 * (a10 * a21 - a11 * a20);
+        const float idet = 1.0f / det;
+        const float r0 = -g0, r1 = -g1, r2 = -g2;
+        const float mu0 = (r0 * (a11 * a22 - a12 * a21) - a01 * (r1 * a22 - a12 * r2) +
+                           a02 * (r1 * a21 - a11 * r2)) * idet;
+        const float mu1 = (a00 * (r1 * a22 - a12 * r2) - r0 * (a10 * a22 - a12 * a20) +
+                           a02 * (a10 * r2 - r1 * a20)) * idet;
+        const float mu2 = (a00 * (a11 * r2 - r1 * a21) - a01 * (a10 * r2 - r1 * a20) +
+                           r0 * (a10 * a21 - a11 * a20)) * idet;
+        const float m0 = sx * mu0, m1 = sx * mu1, m2 = stt * mu2;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int k = q / N1, l = q % N1;
+            const float ck = L.c[k], cl = L.c[l];
+            const float mt = fmaf(ck, ck, cl * cl) - 2.0f * T_L;
+            const long long o = (long long)q * A.N + node;
+            const float Abar = fmaf(c1, (float)A.fbar[o], c2b);
+            A.w[o] = fmaf(ck, m0, fmaf(cl, m1, fmaf(mt, m2, Abar)));
+        }
+        bb = 2.0 * ((double)rho * (double)wf - (double)sAf);
+    }
+    // beta cotangent sum 2 (rho W_q - A_q) fb_q, reduced over the warp in FP64
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bb += __shfl_xor_sync(0xffffffffu, bb, o);
+    if ((tid & 31) == 0) atomicAdd(A.beta_bar, bb);
+}
+// Shared memory and launch of the staged phase A for a window capacity of
+// wwa x wha staged nodes (FP32 rows of 16 bytes).
+static cudaError_t launch_adjoint_phase_a_staged_mixed(const AdjMixedArgs& A,
+                                                       const StateBuf<float>& in,
+                                                       const double* ux_star,
+                                                       const double* uy_star, int n1, int wwa,
+                                                       int wha, float c_max, cudaStream_t s) {
+    static int s_set[64][2] = {{0}};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const size_t smem = (size_t)n1 * wwa * wha * sizeof(float4);
+    void (*kern)(AdjMixedArgs, StateBuf<float>, const double*, const double*, int, int, float) =
+        n1 == 3 ? k_adjoint_jvp_staged_mixed<3> : k_adjoint_jvp_staged_mixed<4>;
+    int& set = s_set[dev][n1 == 3 ? 1 : 0];
+    if ((int)smem > set) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set = (int)smem;
+    }
+    const unsigned tiles = (unsigned)(((A.nx + 31) / 32) * ((A.ny + ADJM_TY - 1) / ADJM_TY));
+    kern<<<tiles, 32 * ADJM_TY, smem, s>>>(A, in, ux_star, uy_star, wwa, wha, c_max);
+    return cudaGetLastError();
+}
+
 }  // namespace pond
 
 using namespace pond;
@@ -647,9 +1027,31 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
     A.T_L = (float)ctx->L.T_L;
     A.vb = a->vb;
     const unsigned nb = (unsigned)((N + ADJM_THREADS - 1) / ADJM_THREADS);
-    if (ctx->L.n1 == 3) k_adjoint_targets_mixed<3><<<nb, ADJM_THREADS, 0, s>>>(A);
-    else k_adjoint_targets_mixed<4><<<nb, ADJM_THREADS, 0, s>>>(A);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ctx_staged(ctx)) {
+        // phase A in the staged form.  Its window capacity comes from the
+        // input state's particle-velocity spans (on the host since
+        // pond_set_state, so no synchronisation), widened by two cells for
+        // lambda*'s departure from the input gauge; the kernel sizes each
+        // tile's window from lambda* itself, and a stencil beyond the
+        // capacity takes the per-pair path from global memory.
+        const float* sp = &ctx->spans[0];
+        const double sx = (double)sp[1] - sp[0], sy = (double)sp[3] - sp[2];
+        const double dt = ctx->P.dt;
+        int wwa = 32 + (int)std::ceil(sx * dt + 2.0) + 7;
+        int wha = ADJM_TY + (int)std::ceil(sy * dt + 2.0) + 7;
+        if (!(wwa > 0 && wha > 0) || wwa > 4096 || wha > 4096) wwa = wha = 1;  // non-finite spans
+        const size_t cap = 160 * 1024;
+        while ((size_t)ctx->L.n1 * wwa * wha * sizeof(float4) > cap) {
+            if (wwa - 32 >= wha - ADJM_TY) --wwa; else --wha;
+        }
+        e = launch_adjoint_phase_a_staged_mixed(A, in, a->fwd.ux, a->fwd.uy, ctx->L.n1, wwa, wha,
+                                                (float)ctx->L.c_max, s);
+        if (e != cudaSuccess) return e;
+    } else {
+        if (ctx->L.n1 == 3) k_adjoint_targets_mixed<3><<<nb, ADJM_THREADS, 0, s>>>(A);
+        else k_adjoint_targets_mixed<4><<<nb, ADJM_THREADS, 0, s>>>(A);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (ctx_staged(ctx)) {
         if (ctx->L.n1 == 3) k_adjoint_sources_mixed_r<3><<<nb, ADJM_THREADS, 0, s>>>(A);
         else k_adjoint_sources_mixed_r<4><<<nb, ADJM_THREADS, 0, s>>>(A);

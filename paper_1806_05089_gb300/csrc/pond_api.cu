@@ -413,7 +413,7 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
     ok = ok && alloc((void**)&ctx->grids_dev, sizeof(GridDesc) * n_grids, "alloc grids");
     ok = ok && alloc((void**)&ctx->tile_prefix_dev, sizeof(int64_t) * (n_grids + 1), "alloc prefix");
     ok = ok && alloc((void**)&ctx->work_counter, sizeof(unsigned int), "alloc counter");
-    ok = ok && alloc((void**)&ctx->bounds_dev, 4 * sizeof(float), "alloc bounds");
+    ok = ok && alloc((void**)&ctx->bounds_dev, 8 * sizeof(float), "alloc bounds");
     if (ok) {
         cudaError_t e = cudaMallocHost((void**)&ctx->stats_host, sizeof(DevStats));
         if (e != cudaSuccess) {
@@ -498,13 +498,6 @@ pond_status pond_set_state(pond_ctx* ctx, int32_t grid, const void* rho, const v
         d_T = static_cast<const double*>(T);
         d_f = static_cast<const double*>(f);
     } else {
-        const double* hT = static_cast<const double*>(T);
-        const double* hx = static_cast<const double*>(ux);
-        const double* hy = static_cast<const double*>(uy);
-        for (int64_t i = 0; i < n; ++i)
-            if (!(hT[i] > 0.0) || !std::isfinite(hT[i]) || !std::isfinite(hx[i]) ||
-                !std::isfinite(hy[i]))
-                return fail(ctx, POND_ERR_NONPHYSICAL, "set_state: T <= 0 or non-finite gauge");
         s = ensure_staging(ctx, n);
         if (s != POND_OK) return s;
         double* sb = static_cast<double*>(ctx->staging);
@@ -535,17 +528,26 @@ pond_status pond_set_state(pond_ctx* ctx, int32_t grid, const void* rho, const v
                                      ctx->stream),
            "init state");
     }
-    // velocity spans of this grid, for the mixed kernel's halo window
+    // velocity spans of this grid, for the tile kernels' windows, and the
+    // count of nodes with T <= 0 or a non-finite gauge (the gauge is checked
+    // on the device, in the same pass, for host and device input alike)
     CK(launch_disp_bounds(ctx->ux[ctx->cur] + G.offset, ctx->uy[ctx->cur] + G.offset,
                           ctx->st[ctx->cur] + G.offset, n, ctx->L.c_max, ctx->bounds_dev,
                           ctx->stream),
        "bounds");
-    float b4[4];
-    CK(cudaMemcpyAsync(b4, ctx->bounds_dev, sizeof b4, cudaMemcpyDeviceToHost, ctx->stream), "D2H bounds");
+    float b5[5];
+    CK(cudaMemcpyAsync(b5, ctx->bounds_dev, sizeof b5, cudaMemcpyDeviceToHost, ctx->stream), "D2H bounds");
     CK(cudaStreamSynchronize(ctx->stream), "set_state sync");
-    for (int i = 0; i < 4; ++i) ctx->spans[4 * grid + i] = b4[i];
-    if (!(std::isfinite(b4[0]) && std::isfinite(b4[1]) && std::isfinite(b4[2]) && std::isfinite(b4[3])))
-        return fail(ctx, POND_ERR_NONPHYSICAL, "set_state: non-finite gauge");
+    unsigned int bad = 0;
+    std::memcpy(&bad, &b5[4], sizeof bad);
+    if (bad != 0 || !(std::isfinite(b5[0]) && std::isfinite(b5[1]) && std::isfinite(b5[2]) &&
+                      std::isfinite(b5[3]))) {
+        // the grid's buffers now hold the refused state: no step runs on it
+        // until a valid pond_set_state
+        ctx->grid_set[grid] = 0;
+        return fail(ctx, POND_ERR_NONPHYSICAL, "set_state: T <= 0 or non-finite gauge");
+    }
+    for (int i = 0; i < 4; ++i) ctx->spans[4 * grid + i] = b5[i];
     ctx->grid_set[grid] = 1;
     const TileWindow before = ctx->win;
     s = update_window(ctx);

@@ -173,19 +173,23 @@ __device__ __forceinline__ unsigned int f2ord(float f) {
 
 __global__ void k_disp_bounds(const double* __restrict__ ux, const double* __restrict__ uy,
                               const double* __restrict__ st, int64_t N, double cmax,
-                              unsigned int* out4) {
+                              unsigned int* out5) {
     float lo_x = 3.0e38f, hi_x = -3.0e38f, lo_y = 3.0e38f, hi_y = -3.0e38f;
+    unsigned int bad = 0u;  // nodes with s <= 0 or a non-finite gauge
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double s = cmax * st[i];
-        lo_x = fminf(lo_x, (float)(ux[i] - s));
-        hi_x = fmaxf(hi_x, (float)(ux[i] + s));
-        lo_y = fminf(lo_y, (float)(uy[i] - s));
-        hi_y = fmaxf(hi_y, (float)(uy[i] + s));
+        const double x = ux[i], y = uy[i], t = st[i];
+        bad += (t > 0.0 && isfinite(t) && isfinite(x) && isfinite(y)) ? 0u : 1u;
+        const double s = cmax * t;
+        lo_x = fminf(lo_x, (float)(x - s));
+        hi_x = fmaxf(hi_x, (float)(x + s));
+        lo_y = fminf(lo_y, (float)(y - s));
+        hi_y = fmaxf(hi_y, (float)(y + s));
     }
     // warp, then block reduction: one atomic per block and value (atomics on
     // one address serialise, so one per warp would dominate the pass)
     __shared__ float s_b[4][32];
+    __shared__ unsigned int s_bad[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int pass = 0; pass < 2; ++pass) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -194,12 +198,14 @@ __global__ void k_disp_bounds(const double* __restrict__ ux, const double* __res
             lo_y = fminf(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
             hi_y = fmaxf(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
         }
+        bad = __reduce_add_sync(0xffffffffu, bad);
         if (pass == 1) break;
         if (lane == 0) {
             s_b[0][warp] = lo_x;
             s_b[1][warp] = hi_x;
             s_b[2][warp] = lo_y;
             s_b[3][warp] = hi_y;
+            s_bad[warp] = bad;
         }
         __syncthreads();
         if (warp != 0) return;
@@ -208,12 +214,14 @@ __global__ void k_disp_bounds(const double* __restrict__ ux, const double* __res
         hi_x = in ? s_b[1][lane] : -3.0e38f;
         lo_y = in ? s_b[2][lane] : 3.0e38f;
         hi_y = in ? s_b[3][lane] : -3.0e38f;
+        bad = in ? s_bad[lane] : 0u;
     }
     if (lane == 0) {
-        atomicMin(out4 + 0, f2ord(lo_x));
-        atomicMax(out4 + 1, f2ord(hi_x));
-        atomicMin(out4 + 2, f2ord(lo_y));
-        atomicMax(out4 + 3, f2ord(hi_y));
+        atomicMin(out5 + 0, f2ord(lo_x));
+        atomicMax(out5 + 1, f2ord(hi_x));
+        atomicMin(out5 + 2, f2ord(lo_y));
+        atomicMax(out5 + 3, f2ord(hi_y));
+        if (bad) atomicAdd(out5 + 4, bad);
     }
 }
 
@@ -229,6 +237,7 @@ __global__ void k_ord_to_float(unsigned int* v) {
 __global__ void k_bounds_reset(unsigned int* v) {
     const int i = threadIdx.x;
     if (i < 4) v[i] = (i & 1) ? 0u : 0xffffffffu;
+    if (i == 4) v[4] = 0u;
 }
 
 // Halo strips of a domain decomposition: a rectangle of the state to or from
@@ -289,8 +298,8 @@ template cudaError_t launch_unpack_rect<float>(StateBuf<float>, int, int, int, i
                                                int64_t, const double*, cudaStream_t);
 
 cudaError_t launch_disp_bounds(const double* ux, const double* uy, const double* st, int64_t N,
-                               double c_max, float* out4, cudaStream_t s) {
-    unsigned int* o = reinterpret_cast<unsigned int*>(out4);
+                               double c_max, float* out5, cudaStream_t s) {
+    unsigned int* o = reinterpret_cast<unsigned int*>(out5);
     k_bounds_reset<<<1, 32, 0, s>>>(o);
     const int bs = 256;
     int64_t nb = (N + bs - 1) / bs;

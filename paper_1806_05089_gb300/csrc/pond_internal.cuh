@@ -247,9 +247,12 @@ template <typename Real>
 cudaError_t launch_unpack_rect(StateBuf<Real> st, int nx, int x0, int y0, int w, int h, int q,
                                int64_t plane, const double* buf, cudaStream_t s);
 
-// max over nodes of (|u_x| + c_max st, |u_y| + c_max st) and spread bounds.
+// Bounds of the particle velocities over the nodes, {min (u_x - c_max st),
+// max (u_x + c_max st), min (u_y - c_max st), max (u_y + c_max st)} as
+// floats in out5[0..3], and in out5[4] (read as an unsigned int) the number
+// of nodes with st <= 0 or a non-finite gauge.
 cudaError_t launch_disp_bounds(const double* ux, const double* uy, const double* st,
-                               int64_t N, double c_max, float* out4, cudaStream_t s);
+                               int64_t N, double c_max, float* out5, cudaStream_t s);
 
 // Adjoint (pond_adjoint.cu, pond_adjoint_mixed.cu).
 struct AdjointScratch;

@@ -322,3 +322,43 @@ def test_staged_adjoint_matches_direct_adjoint(nx, ny, lattice, T_L):
     assert np.abs(f_a - f_b).max() <= 1e-11 * np.abs(f_b).max()
     assert np.abs(g_a - g_b).max() <= 1e-11 * np.abs(g_b).max()
     assert abs(n_a - n_b) <= 1e-11 * abs(n_b)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("lattice,T_L", LATTICES)
+@pytest.mark.parametrize("nx,ny", [(40, 36), (37, 29), (3, 5)])
+def test_staged_mixed_adjoint_matches_direct_mixed_adjoint(nx, ny, lattice, T_L):
+    """The FP32 adjoint step with the staged phase A (sources staged in the
+    tile's reference gauge, epilogue fused) and with the per-pair phase A,
+    both handed the same input state and output gauge, agree to FP32
+    rounding, and both with the FP64 adjoint step, on a full, a ragged and a
+    tiny grid."""
+    from paper_1806_05089_gb300 import pond
+    rho0, ux, uy, T, _ = small_case(nx, ny, seed=13, T_L=T_L)
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(14)
+    Q = 16 if lattice == 0 else 9
+    fbar = torch.tensor(rng.standard_normal((Q, ny, nx)), device=dev)
+    gbar = torch.tensor(rng.standard_normal((3, ny, nx)), device=dev)
+    with pond.Sim(nx, ny, pond.POND_FP64, nu=0.01, lattice=lattice, T_ref=T_L) as s:
+        s.set_state(rho0, ux, uy, T)
+        s.step(2)
+        st0 = s.state()
+        s.step(1)
+        st1 = s.state()
+    g1 = [torch.tensor(a, device=dev) for a in (st1.ux, st1.uy, st1.T)]
+    outs = {}
+    for name, prec, kernel in (("staged", pond.POND_FP32_MIXED, pond.POND_KERNEL_STAGED),
+                               ("direct", pond.POND_FP32_MIXED, pond.POND_KERNEL_DIRECT),
+                               ("fp64", pond.POND_FP64, pond.POND_KERNEL_STAGED)):
+        with pond.Sim(nx, ny, prec, nu=0.01, lattice=lattice, T_ref=T_L, kernel=kernel) as s:
+            s.set_state(None, st0.ux, st0.uy, st0.T, st0.f)
+            fo = torch.empty_like(fbar)
+            go = torch.empty_like(gbar)
+            nb = pond.pond_adjoint_step_given(s.ctx, *g1, fbar, gbar, fo, go)
+            outs[name] = (fo.cpu().numpy(), go.cpu().numpy(), nb)
+    for a, b in (("staged", "direct"), ("staged", "fp64"), ("direct", "fp64")):
+        (f_a, g_a, n_a), (f_b, g_b, n_b) = outs[a], outs[b]
+        assert np.abs(f_a - f_b).max() <= 1e-4 * np.abs(f_b).max(), (a, b)
+        assert np.abs(g_a - g_b).max() <= 1e-4 * np.abs(g_b).max(), (a, b)
+        assert abs(n_a - n_b) <= 1e-4 * abs(n_b), (a, b)

@@ -220,6 +220,35 @@ def test_errors_are_reported_not_trapped():
         assert s.step(1)["nonphysical"] == 0
 
 
+@pytest.mark.parametrize("on_device", [False, True])
+def test_set_state_refuses_bad_gauges(on_device):
+    """T <= 0 or a non-finite gauge at any node is refused (checked on the
+    device in the set_state bounds pass, for host and device input); the
+    refused grid takes no step until a valid set_state."""
+    import torch
+    fields = small_fields("tg", 24, 16)
+    dev = torch.device("cuda")
+
+    def side(a):
+        return torch.tensor(a, device=dev) if on_device else a
+
+    cases = [("T", 0.0), ("T", -2.0), ("T", np.nan), ("ux", np.inf), ("uy", np.nan)]
+    with pond.Sim(24, 16) as s:
+        for name, v in cases:
+            s.set_state(side(fields.rho), side(fields.ux), side(fields.uy), side(fields.T))
+            s.step(1)
+            arrs = {"ux": fields.ux.copy(), "uy": fields.uy.copy(), "T": fields.T.copy()}
+            arrs[name][7, 13] = v
+            with pytest.raises(pond.PondError) as e:
+                s.set_state(side(fields.rho), side(arrs["ux"]), side(arrs["uy"]), side(arrs["T"]))
+            assert e.value.status == pond.POND_ERR_NONPHYSICAL, (name, v)
+            with pytest.raises(pond.PondError) as e:
+                s.step(1)
+            assert e.value.status == pond.POND_ERR_STATE, (name, v)
+        s.set_state(side(fields.rho), side(fields.ux), side(fields.uy), side(fields.T))
+        assert s.step(1)["nonphysical"] == 0
+
+
 def test_strict_mode_reports_nonconvergence():
     fields = small_fields("supersonic", 16, 16)
     with pond.Sim(16, 16, max_iter=1, strict=1) as s:

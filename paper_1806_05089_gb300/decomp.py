@@ -163,6 +163,11 @@ class LocalTransport:
     """All blocks live in this process: a receive takes the matching send's
     buffer (same source, destination and tag)."""
 
+    def reduce_max(self, value: float) -> float:
+        """The maximum over all blocks of a per-process value: this process
+        holds every block."""
+        return float(value)
+
     def run(self, ops):
         """ops: list of (rank, phase, send_buffers, recv_buffers) for every
         block; fills the receive buffers."""
@@ -183,6 +188,17 @@ class TorchDistTransport:
         import torch.distributed as dist
         self.dist = dist
         self.group = group
+
+    def reduce_max(self, value: float) -> float:
+        """The maximum of a per-rank value over the ranks (an all-reduce;
+        on the GPU for NCCL, on the host for gloo), so that every rank takes
+        the same decision from it."""
+        import torch
+        backend = self.dist.get_backend(self.group)
+        dev = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else None
+        t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX, group=self.group)
+        return float(t.item())
 
     def run(self, ops):
         dist = self.dist
@@ -285,13 +301,16 @@ class DecomposedSim:
         return self.torch.empty((self.Q + 3) * n, dtype=self.torch.float64, device="cuda")
 
     def max_displacement(self) -> float:
-        return max(self.pond.pond_max_displacement(s.ctx, 0) for s in self.sims.values())
+        """The largest displacement of one step over the whole grid: the
+        local blocks' bound, reduced over the ranks by the transport."""
+        local = max(self.pond.pond_max_displacement(s.ctx, 0) for s in self.sims.values())
+        return self.transport.reduce_max(local)
 
     def step(self, nsteps: int = 1, check: bool = True):
         """nsteps steps, each one halo exchange then one step of every local
-        block.  With check, the displacement bound is verified against the
-        halo before each step (the local maximum; under torch.distributed
-        the caller reduces it across ranks with max_displacement())."""
+        block.  With check, the displacement bound (reduced over all ranks,
+        so that every rank refuses the same step) is verified against the
+        halo before each step."""
         stats = []
         for _ in range(nsteps):
             if check:

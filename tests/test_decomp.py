@@ -102,6 +102,10 @@ def test_local_exchange_fills_every_halo(nx, ny, px, py, halo):
         assert torch.equal(st["f"], ref["f"]) and torch.equal(st["g"], ref["g"]), r
 
 
+def test_local_transport_max_is_the_local_value():
+    assert decomp.LocalTransport().reduce_max(3.75) == 3.75
+
+
 def test_halo_width_covers_the_stencil_reach():
     # displacement d moves a departure point at most d nodes; the cubic
     # stencil reaches from floor(departure) - 1 to floor(departure) + 2
@@ -124,9 +128,13 @@ def _gloo_rank(rank, world, port, px, py, out):
         part = decomp.Partition(80, 48, px, py, halo=5, align_x=1, align_y=1)
         f, g = global_state(80, 48, seed=3)
         blocks = {rank: block_state(part, rank, f, g)}
-        decomp.exchange(part, blocks, pack, unpack, decomp.TorchDistTransport(), alloc)
+        tr = decomp.TorchDistTransport()
+        decomp.exchange(part, blocks, pack, unpack, tr, alloc)
         ref = block_state(part, rank, f, g, blank=False)
         ok = torch.equal(blocks[rank]["f"], ref["f"]) and torch.equal(blocks[rank]["g"], ref["g"])
+        # the displacement bound every rank checks its halo against is the
+        # maximum over the ranks
+        ok = ok and tr.reduce_max(1.5 + 2.25 * rank) == 1.5 + 2.25 * (world - 1)
         out[rank] = int(ok)
     finally:
         dist.destroy_process_group()

@@ -53,19 +53,23 @@ BYTES_MIXED_Q9 = 2 * (9 * 4 + 3 * 8)
 # pass: the sources are re-expressed once per step in the tile's reference
 # gauge, and each pass, for every x-speed index k, sweeps the rows of the
 # union of the n1 y-stencils: per row, 4 sources x n1 x n1 FMAs of the x
-# interpolation, n1 x n1 of the x-map and n1 x n1 of the row's contribution
-# to the n1 populations (k, l).  The rows per sweep are 4 + (c_max - c_min)
-# sqrt(theta) on average (the spread of the y-departures plus the stencil).
-# Per (node, k) add the x-map's Taylor entries (5 n1 ops), the departure and
-# cubic weights (20), the y-map applied after the sweep (n1 x 6 n1 FMAs) and
-# the moments (8 n1); per pass the y-departures (20 n1) and the gauge update
-# (40).  The once-per-step staging (~500 flops per staged source) is left
-# out: the count is the per-pass work alone, so the fraction is a lower bound.
-def staged_flops_per_pass(n1: int, st_mean: float) -> float:
+# interpolation and n1 x n1 of the x-map; in the FP64 form each population
+# (k, l) then takes its four rows once (4 x n1 FMAs), while the mixed form's
+# packed sweep adds every row to the n1 populations (n1 x n1 FMAs per row,
+# zero weights outside a stencil; every_row=True).  The rows per sweep are
+# 4 + (c_max - c_min) sqrt(theta) on average (the spread of the
+# y-departures plus the stencil).  Per (node, k) add the x-map's Taylor
+# entries (5 n1 ops), the departure and cubic weights (20), the y-map
+# applied after the sweep (n1 x 6 n1 FMAs) and the moments (8 n1); per pass
+# the y-departures (20 n1) and the gauge update (40).  The once-per-step
+# staging (~500 flops per staged source) is left out: the count is the
+# per-pass work alone, so the fraction is a lower bound.
+def staged_flops_per_pass(n1: int, st_mean: float, every_row: bool = False) -> float:
     spread = 2 * 2.3344142183389773 if n1 == 4 else 2.0
     rows = 4.0 + spread * st_mean
-    per_row = 2 * (4 * n1 * n1 + n1 * n1 + n1 * n1)
-    per_k = per_row * rows + 2 * 5 * n1 + 20 + n1 * 2 * 6 * n1 + 8 * n1
+    per_row = 2 * (4 * n1 * n1 + n1 * n1 + (n1 * n1 if every_row else 0))
+    accumulate = 0 if every_row else 2 * 4 * n1 * n1
+    per_k = per_row * rows + accumulate + 2 * 5 * n1 + 20 + n1 * 2 * 6 * n1 + 8 * n1
     return n1 * per_k + 20 * n1 + 40
 
 
@@ -77,10 +81,10 @@ PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per FP64 step launch at 2048^2 of the staged kernel: the ncu
 # capture of the same kernel (k_step_staged<StagedFP64, 32, 8, 4>) at 1024^2
-# read 161.8 MB and wrote 124.5 MB; traffic grows with the node count (4x).
-K_STAGED64_TRAFFIC_2048 = 4 * (161.78e6 + 124.45e6)
+# read 163.3 MB and wrote 124.9 MB; traffic grows with the node count (4x).
+K_STAGED64_TRAFFIC_2048 = 4 * (163.25e6 + 124.93e6)
 K_STAGED64_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                             "k_step_staged<StagedFP64, 32, 8, 4> launch at 1024^2 (286.2 MB), "
+                             "k_step_staged<StagedFP64, 32, 8, 4> launch at 1024^2 (288.2 MB), "
                              "scaled x4 by nodes to the 2048^2 launch")
 
 
@@ -440,7 +444,8 @@ def run_pond(args, world, rank, local):
         msecs, mstats = time_steps(msim, stream, args.steps)
         rho32, ux32, uy32, T32 = msim.moments()
         forms["fp32_mixed_2048"] = form_line("supersonic-2048-mixed", nodes, args.steps, msecs,
-                                             mstats, peak32, BYTES_MIXED, flop_pass)
+                                             mstats, peak32, BYTES_MIXED,
+                                             staged_flops_per_pass(4, st_mean, every_row=True))
         forms["fp32_mixed_2048"]["moment_err_vs_fp64"] = {
             "after_steps": args.warmup + args.steps,
             "rho": float(np.max(np.abs(rho32 - rho64)) / np.max(np.abs(rho64))),
@@ -472,7 +477,7 @@ def run_pond(args, world, rank, local):
         psecs, pstats = time_steps(psim, stream, k2)
         forms["fp32_mixed_4096"] = form_line("precision-4096-mixed", 4096 * 4096, k2, psecs,
                                              pstats, peak32, BYTES_MIXED,
-                                             staged_flops_per_pass(4, float(np.sqrt(pf.T).mean())))
+                                             staged_flops_per_pass(4, float(np.sqrt(pf.T).mean()), every_row=True))
         psim.close()
         del pf
 
@@ -498,7 +503,8 @@ def run_pond(args, world, rank, local):
         barrier(world)
         bsecs_max = max_over_ranks(world, bsecs)
         forms["batched_256"] = form_line("ensemble-256-mixed", bnodes, k2, bsecs, bstats,
-                                         peak32, BYTES_MIXED, staged_flops_per_pass(4, st_b))
+                                         peak32, BYTES_MIXED,
+                                         staged_flops_per_pass(4, st_b, every_row=True))
         forms["batched_256"]["grids_on_this_rank"] = len(mine)
         # share of the persistent launches' CTA slots left idle (start skew
         # and the tail after the work list ran dry), from the kernel's own
@@ -527,7 +533,8 @@ def run_pond(args, world, rank, local):
             forms[key] = form_line("supersonic-2048-d2q9-" + ("fp64" if prec == pond.POND_FP64
                                                               else "mixed"),
                                    nodes, args.steps, qsecs, qstats, peak, nbytes,
-                                   staged_flops_per_pass(3, float(np.sqrt(q9.T * 3.0).mean())),
+                                   staged_flops_per_pass(3, float(np.sqrt(q9.T * 3.0).mean()),
+                                                         every_row=prec != pond.POND_FP64),
                                    FLOP_PER_PASS_Q9)
             q9_out[key] = qsim.moments()
             qsim.close()
@@ -553,7 +560,8 @@ def run_pond(args, world, rank, local):
                 vsim.step(args.warmup)
                 vsecs, vstats = time_steps(vsim, stream, k2)
             line_v = form_line("vortex-1024-mixed", 1024 * 1024, k2, vsecs, vstats, peak32,
-                               BYTES_MIXED, staged_flops_per_pass(4, float(np.sqrt(vf.T).mean())))
+                               BYTES_MIXED,
+                               staged_flops_per_pass(4, float(np.sqrt(vf.T).mean()), every_row=True))
             vortex["Ma_a=%g,Ma_v=%g" % (ma, mv)] = {
                 k: line_v[k] for k in ("value", "ms_per_step", "mean_passes", "max_passes",
                                        "nonconverged", "halo_fallback", "alu_frac", "tile")}

@@ -115,6 +115,7 @@ __device__ __forceinline__ void staged_block_minmax4(float& a, float& b, float& 
     __syncthreads();
 }
 
+
 // Row weight of a stencil whose top row is `top`, for grid row y: the cubic
 // weight ly[y - top] inside the stencil, zero outside it (or when the
 // stencil is not swept).
@@ -427,62 +428,87 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
                 }
                 lo = __reduce_min_sync(FULL, lo);
                 hi = __reduce_max_sync(FULL, hi);
-                // Z_l[b] = sum_y ly_l(y) P(y)[b]; the y-map is applied after
-                // the sweep: f_(k,l) = Z_l[l] + sum_b Ey[l][b] Z_l[b]
+                // Z_l[b] = sum_y ly_l(y) P(y)[b] over population l's four
+                // stencil rows; the y-map is applied after the sweep:
+                // f_(k,l) = Z_l[l] + sum_b Ey[l][b] Z_l[b].
+                // Scalar form: the sweep keeps the P of its last four rows
+                // (Pb[3] the newest), and population l takes its four rows
+                // when the sweep reaches its last one, y = top[l] + 3, with
+                // the fused multiply-adds in row order -- the same result as
+                // adding ly_l(y) P(y) on every row with zero weights outside
+                // the stencil, without those zero-weight FMAs.
+                // Packed form (at its 128-register budget the four-row
+                // buffer costs more than it saves: measured 45 % slower):
+                // every row adds w_l(y) P(y) to the n1 populations, with the
+                // row's weights selected per population.
                 Real Z[N1][N1];
 #pragma unroll
                 for (int l = 0; l < N1; ++l)
 #pragma unroll
                     for (int b = 0; b < N1; ++b) Z[l][b] = (Real)0;
+                int last[N1];  // the row that completes population l's stencil
+                bool anyon = false;
+#pragma unroll
+                for (int l = 0; l < N1; ++l) {
+                    last[l] = on[l] ? top[l] + 3 : -1;
+                    anyon = anyon || on[l];
+                }
                 float2 Z2[N1][2];  // the packed form's accumulators (pairs of b)
+                Real Pb[4][N1];    // the scalar form's row buffer
 #pragma unroll
                 for (int l = 0; l < N1; ++l) Z2[l][0] = Z2[l][1] = make_float2(0.f, 0.f);
+                // the rows of the warp's union [lo, hi] lie in the window for
+                // every thread with a population on it; a thread with none
+                // skips the sweep
 #pragma unroll 1
-                for (int y = lo; y <= hi; ++y) {
-                    Real wl[N1];
-                    bool any = false;
+                for (int y = anyon ? lo : hi + 1; y <= hi; ++y) {
+                    const Real4* src = s_f + y * ww + col;
+                    const bool rowok = POND_INDEX_OK(y >= 0 && col >= 0 && y < wh && col + 3 < ww &&
+                                                         y * ww + col + 3 < WN,
+                                                     A.stats);
+                    if constexpr (Tr::kPacked) {
+                        // pairs of b on fma.rn.f32x2: two FP32 FMAs per
+                        // instruction, each rounded as the scalar one
+                        Real wl[N1];
+                        bool any = false;
 #pragma unroll
-                    for (int l = 0; l < N1; ++l) {
-                        wl[l] = row_weight<Real>(y, top[l], on[l], ly[l]);
-                        any = any || (on[l] && y >= top[l] && y <= top[l] + 3);
-                    }
-                    if (any) {
-                        const Real4* src = s_f + y * ww + col;
-                        const bool rowok = POND_INDEX_OK(y >= 0 && col >= 0 && y < wh &&
-                                                             col + 3 < ww && y * ww + col + 3 < WN,
-                                                         A.stats);
-                        if constexpr (Tr::kPacked) {
-                            // the same arithmetic on pairs of b (fma.rn.f32x2:
-                            // two FP32 FMAs per instruction, each rounded as
-                            // the scalar one)
-                            float2 Fi2[N1][2];
+                        for (int l = 0; l < N1; ++l) {
+                            wl[l] = row_weight<Real>(y, top[l], on[l], ly[l]);
+                            any = any || (on[l] && y >= top[l] && y <= top[l] + 3);
+                        }
+                        if (!any) continue;
+                        float2 Fi2[N1][2];
 #pragma unroll
-                            for (int a = 0; a < N1; ++a) Fi2[a][0] = Fi2[a][1] = make_float2(0.f, 0.f);
+                        for (int a = 0; a < N1; ++a) Fi2[a][0] = Fi2[a][1] = make_float2(0.f, 0.f);
 #pragma unroll
-                            for (int jx = 0; jx < 4; ++jx) {
-                                const float2 w2 = make_float2(lx[jx], lx[jx]);
-#pragma unroll
-                                for (int a = 0; a < N1; ++a) {
-                                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                                    if (rowok) v = src[(size_t)a * WN + jx];
-                                    Fi2[a][0] = __ffma2_rn(w2, make_float2(v.x, v.y), Fi2[a][0]);
-                                    Fi2[a][1] = __ffma2_rn(w2, make_float2(v.z, v.w), Fi2[a][1]);
-                                }
-                            }
-                            float2 P2[2] = {Fi2[k][0], Fi2[k][1]};
+                        for (int jx = 0; jx < 4; ++jx) {
+                            const float2 w2 = make_float2(lx[jx], lx[jx]);
 #pragma unroll
                             for (int a = 0; a < N1; ++a) {
-                                const float2 e2 = make_float2(ext[a], ext[a]);
-                                P2[0] = __ffma2_rn(e2, Fi2[a][0], P2[0]);
-                                P2[1] = __ffma2_rn(e2, Fi2[a][1], P2[1]);
+                                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                                if (rowok) v = src[(size_t)a * WN + jx];
+                                Fi2[a][0] = __ffma2_rn(w2, make_float2(v.x, v.y), Fi2[a][0]);
+                                Fi2[a][1] = __ffma2_rn(w2, make_float2(v.z, v.w), Fi2[a][1]);
                             }
+                        }
+                        float2 P2[2] = {Fi2[k][0], Fi2[k][1]};
 #pragma unroll
-                            for (int l = 0; l < N1; ++l) {
-                                const float2 w2 = make_float2(wl[l], wl[l]);
-                                Z2[l][0] = __ffma2_rn(w2, P2[0], Z2[l][0]);
-                                Z2[l][1] = __ffma2_rn(w2, P2[1], Z2[l][1]);
-                            }
-                        } else {
+                        for (int a = 0; a < N1; ++a) {
+                            const float2 e2 = make_float2(ext[a], ext[a]);
+                            P2[0] = __ffma2_rn(e2, Fi2[a][0], P2[0]);
+                            P2[1] = __ffma2_rn(e2, Fi2[a][1], P2[1]);
+                        }
+#pragma unroll
+                        for (int l = 0; l < N1; ++l) {
+                            const float2 w2 = make_float2(wl[l], wl[l]);
+                            Z2[l][0] = __ffma2_rn(w2, P2[0], Z2[l][0]);
+                            Z2[l][1] = __ffma2_rn(w2, P2[1], Z2[l][1]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+#pragma unroll
+                            for (int b = 0; b < N1; ++b) Pb[i][b] = Pb[i + 1][b];
                         // Fi[a][b] = sum_jx lx[jx] g(col + jx, y)[a][b] (the row's
                         // four sources interpolated in x), then
                         // P[b] = sum_a (I + Ex)[k][a] Fi[a][b]
@@ -508,7 +534,6 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
 #pragma unroll
                                 for (int b = 0; b < N1; ++b) Fi[a][b] = fma(lx[jx], fr[a][b], Fi[a][b]);
                         }
-                        Real P[N1];
 #pragma unroll
                         for (int b = 0; b < N1; ++b) {
                             Real v = (Real)0;
@@ -522,12 +547,15 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
                             }
 #pragma unroll
                             for (int a = 0; a < N1; ++a) v = fma(ext[a], Fi[a][b], v);
-                            P[b] = v;
+                            Pb[3][b] = v;
                         }
 #pragma unroll
-                        for (int l = 0; l < N1; ++l)
+                        for (int l = 0; l < N1; ++l) {
+                            if (y != last[l]) continue;
 #pragma unroll
-                            for (int b = 0; b < N1; ++b) Z[l][b] = fma(wl[l], P[b], Z[l][b]);
+                            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                                for (int b = 0; b < N1; ++b) Z[l][b] = fma(ly[l][j], Pb[j][b], Z[l][b]);
                         }
                     }
                 }

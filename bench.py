@@ -52,24 +52,27 @@ BYTES_MIXED_Q9 = 2 * (9 * 4 + 3 * 8)
 # The reference-gauge staged kernel (the default) does less arithmetic per
 # pass: the sources are re-expressed once per step in the tile's reference
 # gauge, and each pass, for every x-speed index k, sweeps the rows of the
-# union of the n1 y-stencils: per row, 4 sources x n1 x n1 FMAs of the x
-# interpolation and n1 x n1 of the x-map; in the FP64 form each population
-# (k, l) then takes its four rows once (4 x n1 FMAs), while the mixed form's
-# packed sweep adds every row to the n1 populations (n1 x n1 FMAs per row,
-# zero weights outside a stencil; every_row=True).  The rows per sweep are
-# 4 + (c_max - c_min) sqrt(theta) on average (the spread of the
-# y-departures plus the stencil).  Per (node, k) add the x-map's Taylor
-# entries (5 n1 ops), the departure and cubic weights (20), the y-map
-# applied after the sweep (n1 x 6 n1 FMAs) and the moments (8 n1); per pass
-# the y-departures (20 n1) and the gauge update (40).  The once-per-step
-# staging (~500 flops per staged source) is left out: the count is the
-# per-pass work alone, so the fraction is a lower bound.
+# union of the n1 y-stencils.  FP64 form: per row, 4 sources x n1 x n1 FMAs
+# (the x-interpolation with the x-map folded into its weights, formed once
+# per k: 4 n1 products), and each population (k, l) takes its four rows once
+# (4 x n1 FMAs).  Mixed form (every_row=True): per row the x-interpolation
+# (4 n1^2), the x-map (n1^2) and the row added to the n1 populations (n1^2,
+# zero weights outside a stencil).  The rows per sweep are
+# 4 + (c_max - c_min) sqrt(theta) on average (the spread of the y-departures
+# plus the stencil).  Per (node, k) add the x-map's Taylor entries (5 n1
+# ops), the departure and cubic weights (20), the y-map applied after the
+# sweep (n1 x 6 n1 FMAs) and the moments (8 n1); per pass the y-departures
+# (20 n1) and the gauge update (40).  The once-per-step staging (~500 flops
+# per staged source) is left out: the count is the per-pass work alone, so
+# the fraction is a lower bound.
 def staged_flops_per_pass(n1: int, st_mean: float, every_row: bool = False) -> float:
     spread = 2 * 2.3344142183389773 if n1 == 4 else 2.0
     rows = 4.0 + spread * st_mean
-    per_row = 2 * (4 * n1 * n1 + n1 * n1 + (n1 * n1 if every_row else 0))
-    accumulate = 0 if every_row else 2 * 4 * n1 * n1
-    per_k = per_row * rows + accumulate + 2 * 5 * n1 + 20 + n1 * 2 * 6 * n1 + 8 * n1
+    if every_row:
+        sweep = 2 * (4 * n1 * n1 + n1 * n1 + n1 * n1) * rows
+    else:
+        sweep = 2 * (4 * n1 * n1) * rows + 4 * n1 + 2 * 4 * n1 * n1
+    per_k = sweep + 2 * 5 * n1 + 20 + n1 * 2 * 6 * n1 + 8 * n1
     return n1 * per_k + 20 * n1 + 40
 
 
@@ -81,10 +84,10 @@ PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per FP64 step launch at 2048^2 of the staged kernel: the ncu
 # capture of the same kernel (k_step_staged<StagedFP64, 32, 8, 4>) at 1024^2
-# read 163.3 MB and wrote 124.9 MB; traffic grows with the node count (4x).
-K_STAGED64_TRAFFIC_2048 = 4 * (163.25e6 + 124.93e6)
+# read 164.1 MB and wrote 125.2 MB; traffic grows with the node count (4x).
+K_STAGED64_TRAFFIC_2048 = 4 * (164.13e6 + 125.25e6)
 K_STAGED64_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                             "k_step_staged<StagedFP64, 32, 8, 4> launch at 1024^2 (288.2 MB), "
+                             "k_step_staged<StagedFP64, 32, 8, 4> launch at 1024^2 (289.4 MB), "
                              "scaled x4 by nodes to the 2048^2 launch")
 
 

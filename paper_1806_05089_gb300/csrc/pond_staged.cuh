@@ -455,6 +455,18 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
                 }
                 float2 Z2[N1][2];  // the packed form's accumulators (pairs of b)
                 Real Pb[4][N1];    // the scalar form's row buffer
+                // The scalar (FP64) form folds the x-map into the x-weights,
+                // cxa[jx][a] = lx[jx] (I + Ex)[k][a], once per x-speed and
+                // pass: a row then costs the interpolation alone.  (The packed
+                // FP32 form keeps the correction form P = Fi[k] + Ex Fi, whose
+                // identity term is exact: there 1 + Ex would round in FP32.)
+                Real cxa[4][N1];
+                if constexpr (!Tr::kPacked) {
+#pragma unroll
+                    for (int jx = 0; jx < 4; ++jx)
+#pragma unroll
+                        for (int a = 0; a < N1; ++a) cxa[jx][a] = lx[jx] * (ik[a] + ext[a]);
+                }
 #pragma unroll
                 for (int l = 0; l < N1; ++l) Z2[l][0] = Z2[l][1] = make_float2(0.f, 0.f);
                 // the rows of the warp's union [lo, hi] lie in the window for
@@ -509,14 +521,12 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
                         for (int i = 0; i < 3; ++i)
 #pragma unroll
                             for (int b = 0; b < N1; ++b) Pb[i][b] = Pb[i + 1][b];
-                        // Fi[a][b] = sum_jx lx[jx] g(col + jx, y)[a][b] (the row's
-                        // four sources interpolated in x), then
-                        // P[b] = sum_a (I + Ex)[k][a] Fi[a][b]
-                        Real Fi[N1][N1];
+                        // P[b] = sum_{jx, a} cxa[jx][a] g(col + jx, y)[a][b]:
+                        // the row's four sources interpolated in x and mapped
+                        // r -> lambda in one contraction (n1^2 FMAs per source)
+                        Real P[N1];
 #pragma unroll
-                        for (int a = 0; a < N1; ++a)
-#pragma unroll
-                            for (int b = 0; b < N1; ++b) Fi[a][b] = (Real)0;
+                        for (int b = 0; b < N1; ++b) P[b] = (Real)0;
 #pragma unroll
                         for (int jx = 0; jx < 4; ++jx) {
                             Real fr[N1][4];
@@ -532,23 +542,10 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
 #pragma unroll
                             for (int a = 0; a < N1; ++a)
 #pragma unroll
-                                for (int b = 0; b < N1; ++b) Fi[a][b] = fma(lx[jx], fr[a][b], Fi[a][b]);
+                                for (int b = 0; b < N1; ++b) P[b] = fma(cxa[jx][a], fr[a][b], P[b]);
                         }
 #pragma unroll
-                        for (int b = 0; b < N1; ++b) {
-                            Real v = (Real)0;
-                            if constexpr (Tr::kUnrollK) {
-                                v = Fi[k][b];
-                            } else {
-                                // the identity part Fi[k][b], exactly: products
-                                // with the 0/1 entries of I and sums of zeros
-#pragma unroll
-                                for (int a = 0; a < N1; ++a) v = fma(ik[a], Fi[a][b], v);
-                            }
-#pragma unroll
-                            for (int a = 0; a < N1; ++a) v = fma(ext[a], Fi[a][b], v);
-                            Pb[3][b] = v;
-                        }
+                        for (int b = 0; b < N1; ++b) Pb[3][b] = P[b];
 #pragma unroll
                         for (int l = 0; l < N1; ++l) {
                             if (y != last[l]) continue;

@@ -503,6 +503,203 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources_r(AdjArgs
     }
 }
 
+// The same gather organised by target.  For a source j and a candidate
+// target t, population (k, l) hits when j lies in both its x-stencil and its
+// y-stencil; the x-stencil's origin depends on k alone and the y-stencil's
+// on l alone, so the hits of (j, t) are a product set K x L.  The rows
+// G(j -> t)_x[k][.] (k in K) and G_y[l][.] (l in L) are then evaluated once
+// per target, not once per hit, and a hit costs its weight and a rank-one
+// update.  Each round, every lane of the source's warp takes one candidate
+// target and writes its gauge offsets and stencil positions to a
+// shared-memory slot, its rows to a job queue and its hits to a hit queue
+// (offsets by a warp prefix sum); the warp then evaluates the rows and does
+// the hits 32 at a time.  Work per lane thus does not depend on how many
+// rows and hits its own target has: the FP64 pipe serves full warps.
+constexpr int ADJ_GATHER_WARPS = 2;
+
+struct GatherSlot {
+    double gx[4][4];   // G_x(j -> t)[k][a]
+    double gy[4][4];   // G_y(j -> t)[l][b]
+    double lx[4];      // x-weight of j in the stencil of x-speed k
+    double ly[4];      // y-weight of j in the stencil of y-speed l
+    double r, dx, dy;  // gauge offsets of j from t (r: s_j / s_t - 1)
+    long long t;
+    signed char jx[4], jy[4];  // j's position in the x- and y-stencils
+};
+
+template <int N1>
+__global__ void __launch_bounds__(ADJ_GATHER_WARPS * 32) k_adjoint_sources_t(AdjArgs A) {
+    constexpr int Q = N1 * N1;
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ GatherSlot s_slot[ADJ_GATHER_WARPS][32];
+    __shared__ unsigned short s_hit[ADJ_GATHER_WARPS][32 * Q];
+    __shared__ unsigned short s_job[ADJ_GATHER_WARPS][32 * 2 * N1];
+    const Lattice& L = c_La[lattice_slot(N1)];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long src = (long long)blockIdx.x * ADJ_GATHER_WARPS + wid;
+    if (src >= A.N) return;  // warp-uniform
+    const int JX = (int)(src % A.nx), JY = (int)(src / A.nx);
+    const double uxj = A.in.ux[src], uyj = A.in.uy[src], stj = A.in.st[src];
+    GatherSlot& my = s_slot[wid][lane];
+    unsigned short* hitq = s_hit[wid];
+    unsigned short* jobq = s_job[wid];
+
+    // candidate targets: the union over the speeds of the windows of
+    // k_adjoint_sources (J in the stencil of the target at x when
+    // floor(x - v dt) is in [J - 2, J + 1], v within the speed's bounds)
+    int xlo = 0x7fffffff, xhi = -0x7fffffff, ylo = 0x7fffffff, yhi = -0x7fffffff;
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+        const double ex = 1e-9 * (1.0 + fabs(A.vlo_x[i]) + fabs(A.vhi_x[i])) * A.dt;
+        const double ey = 1e-9 * (1.0 + fabs(A.vlo_y[i]) + fabs(A.vhi_y[i])) * A.dt;
+        xlo = min(xlo, (int)ceil(-2.0 + A.vlo_x[i] * A.dt - ex));
+        xhi = max(xhi, (int)ceil(2.0 + A.vhi_x[i] * A.dt + ex) - 1);
+        ylo = min(ylo, (int)ceil(-2.0 + A.vlo_y[i] * A.dt - ey));
+        yhi = max(yhi, (int)ceil(2.0 + A.vhi_y[i] * A.dt + ey) - 1);
+    }
+    const int wx = xhi - xlo + 1;
+    const int nc = wx * (yhi - ylo + 1);
+
+    double fb[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fb[i] = 0.0;
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+        // 1. this lane's candidate: its hit set K x L and gauge offsets
+        const int c = c0 + lane;
+        unsigned kmask = 0u, lmask = 0u;
+        if (c < nc) {
+            const int xx = JX + xlo + c % wx, yy = JY + ylo + c / wx;
+            const long long t = (long long)wrap_idx(yy, A.ny) * A.nx + wrap_idx(xx, A.nx);
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                const int jx = JX - (xx + A.org[(long long)(N1 * i) * A.N + t].x);
+                const int jy = JY - (yy + A.org[(long long)i * A.N + t].y);
+                my.jx[i] = (signed char)jx;
+                my.jy[i] = (signed char)jy;
+                kmask |= (jx >= 0 && jx <= 3) ? 1u << i : 0u;
+                lmask |= (jy >= 0 && jy <= 3) ? 1u << i : 0u;
+            }
+            if (kmask && lmask) {
+                my.t = t;
+                const double inv = A.inv_st[t];
+                my.r = fma(stj, inv, -1.0);
+                my.dx = (uxj - A.ux_s[t]) * inv;
+                my.dy = (uyj - A.uy_s[t]) * inv;
+            } else {
+                kmask = lmask = 0u;
+            }
+        }
+        // 2. the round's row jobs and hits into the warp's queues: one scan
+        //    of (jobs << 16 | hits)
+        const int nk = __popc(kmask), nl = __popc(lmask);
+        const int mine = ((nk + nl) << 16) | (nk * nl);
+        int incl = mine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int tot = __shfl_sync(FULL, incl, 31);
+        const int ex = incl - mine;
+        int hoff = ex & 0xffff, joff = ex >> 16;
+        const int nhit = tot & 0xffff, njob = tot >> 16;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            if (!(kmask >> k & 1u)) continue;
+            jobq[joff++] = (unsigned short)((lane << 3) | k);
+#pragma unroll
+            for (int l = 0; l < N1; ++l)
+                if (lmask >> l & 1u) hitq[hoff++] = (unsigned short)((lane << 4) | (k << 2) | l);
+        }
+#pragma unroll
+        for (int l = 0; l < N1; ++l)
+            if (lmask >> l & 1u) jobq[joff++] = (unsigned short)((lane << 3) | 4 | l);
+        __syncwarp();
+        // 3. the rows on full warps: G_x[k][.] or G_y[l][.] and the weight
+        for (int j = lane; j < njob; j += 32) {
+            const unsigned code = jobq[j];
+            GatherSlot& g = s_slot[wid][code >> 3];
+            const int i = (int)code & 3;
+            const bool yrow = (code & 4u) != 0;
+            const double base = yrow ? g.dy : g.dx, r = g.r;
+            double row[N1];
+#pragma unroll
+            for (int a = 0; a < N1; ++a)
+                row[a] = gauge_poly<N1>(L.d3[i], L.d2[i][a], L.d1[i][a], a == i ? 1.0 : 0.0,
+                                        fma(L.c[a], r, base));
+            if (yrow) {
+                g.ly[i] = A.lw[8 * ((long long)i * A.N + g.t) + 4 + g.jy[i]];
+#pragma unroll
+                for (int a = 0; a < N1; ++a) g.gy[i][a] = row[a];
+            } else {
+                g.lx[i] = A.lw[8 * ((long long)(N1 * i) * A.N + g.t) + g.jx[i]];
+#pragma unroll
+                for (int a = 0; a < N1; ++a) g.gx[i][a] = row[a];
+            }
+        }
+        __syncwarp();
+        // 4. the hits on full warps: weight, then the rank-one update
+        for (int h = lane; h < nhit; h += 32) {
+            const unsigned code = hitq[h];
+            const GatherSlot& g = s_slot[wid][code >> 4];
+            const int k = (int)(code >> 2) & 3, l = (int)code & 3;
+            const double coef = A.w[(long long)(N1 * k + l) * A.N + g.t] * g.lx[k] * g.ly[l];
+            double gy[N1];
+#pragma unroll
+            for (int b = 0; b < N1; ++b) gy[b] = g.gy[l][b];
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                const double cgx = coef * g.gx[k][a];
+#pragma unroll
+                for (int b = 0; b < N1; ++b) fb[N1 * a + b] = fma(cgx, gy[b], fb[N1 * a + b]);
+            }
+        }
+        __syncwarp();  // the slots and the queues are rewritten next round
+    }
+
+    // reduce over the warp: lanes 2p and 2p + 1 get population p's total
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = i < Q ? fb[i] : 0.0;
+    const double tot = warp_reduce_scatter16(v, lane);
+    // the source-gauge cotangent from h = fb, one population per even lane:
+    // dg/du_x [k][l] = sum_a d1[k][a] f[a][l] / s_j, dg/du_y [k][l] =
+    // sum_b d1[l][b] f[k][b] / s_j, dg/ds the same with c_a, c_b inside
+    const int p = lane >> 1;
+    double pux = 0.0, puy = 0.0, pst = 0.0;
+    if ((lane & 1) == 0 && p < Q) {
+        const int kk = p / N1, ll = p % N1;
+        double gxu = 0.0, gyu = 0.0, gsx = 0.0, gsy = 0.0;
+#pragma unroll
+        for (int a = 0; a < N1; ++a) {
+            // the source's populations f_j[a][ll] and f_j[kk][a]
+            const double fx = A.in.f[(long long)(N1 * a + ll) * A.N + src];
+            const double fy = A.in.f[(long long)(N1 * kk + a) * A.N + src];
+            gxu = fma(L.d1[kk][a], fx, gxu);
+            gsx = fma(L.d1[kk][a] * L.c[a], fx, gsx);
+            gyu = fma(L.d1[ll][a], fy, gyu);
+            gsy = fma(L.d1[ll][a] * L.c[a], fy, gsy);
+        }
+        pux = tot * gxu;
+        puy = tot * gyu;
+        pst = tot * (gsx + gsy);
+        A.fbar_in[(long long)p * A.N + src] = tot;
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        pux += __shfl_xor_sync(FULL, pux, o);
+        puy += __shfl_xor_sync(FULL, puy, o);
+        pst += __shfl_xor_sync(FULL, pst, o);
+    }
+    if (lane == 0) {
+        const double is = 1.0 / stj;
+        A.gbar_in[src] = pux * is;
+        A.gbar_in[A.N + src] = puy * is;
+        // s = sqrt(T / T_L): dL/dT = dL/ds / (2 s T_L)
+        A.gbar_in[2 * A.N + src] = pst * is / (2.0 * stj * A.T_L);
+    }
+}
+
 // Bounds {min ux, max ux, min uy, max uy, min s, max s} of a gauge field,
 // exact in FP64: a grid-stride pass, warp reductions, and 64-bit integer
 // atomics on an order-preserving encoding of the doubles (one per warp and
@@ -1288,8 +1485,9 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
     }
     ACK(cudaGetLastError(), "adjoint targets");
     if (ctx_staged(ctx)) {
-        if (ctx->L.n1 == 3) k_adjoint_sources_r<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
-        else k_adjoint_sources_r<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
+        const unsigned nbt = (unsigned)((N + ADJ_GATHER_WARPS - 1) / ADJ_GATHER_WARPS);
+        if (ctx->L.n1 == 3) k_adjoint_sources_t<3><<<nbt, ADJ_GATHER_WARPS * 32, 0, s>>>(A);
+        else k_adjoint_sources_t<4><<<nbt, ADJ_GATHER_WARPS * 32, 0, s>>>(A);
     } else {
         if (ctx->L.n1 == 3) k_adjoint_sources<3><<<nb, ADJ_WARPS * 32, 0, s>>>(A);
         else k_adjoint_sources<4><<<nb, ADJ_WARPS * 32, 0, s>>>(A);

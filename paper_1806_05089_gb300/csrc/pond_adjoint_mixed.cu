@@ -540,6 +540,131 @@ __global__ void __launch_bounds__(ADJM_THREADS) k_adjoint_sources_mixed_r(AdjMix
     A.gbar_in[2 * A.N + src] = (double)bst / (2.0 * A.st_in[src] * (double)A.T_L);
 }
 
+// The same gather organised by target (see k_adjoint_sources_t in
+// pond_adjoint.cu): the hits of a (source, target) pair are a product set
+// K x L, since the x-stencil's origin depends on the x-speed alone and the
+// y-stencil's on the y-speed alone.  Each thread walks the union of its
+// source's candidate windows once, evaluates a hit target's rows G_x[k][.]
+// (k in K) and G_y[l][.] (l in L) once, then does each hit's weight and
+// rank-one update.
+template <int N1>
+__global__ void __launch_bounds__(ADJM_THREADS) k_adjoint_sources_mixed_t(AdjMixedArgs A) {
+    constexpr int Q = N1 * N1;
+    const LatticeF& L = c_Lam[lattice_slot(N1)];
+    const long long src0 = (long long)blockIdx.x * ADJM_THREADS + threadIdx.x;
+    if (src0 >= A.N) return;  // no warp-wide operation follows
+    const long long src = src0;
+    const int JX = (int)(src % A.nx), JY = (int)(src / A.nx);
+    float fj[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fj[i] = A.f_in[(long long)i * A.N + src];
+    const float4 jh = A.gin[src], jl = A.gin[A.N + src];
+
+    float fb[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fb[i] = 0.0f;
+    float bux = 0.0f, buy = 0.0f, bst = 0.0f;
+    // the union over the speeds of the candidate windows of
+    // k_adjoint_sources_mixed (bounds with the FP32 departures' margin)
+    int wxl = 0x7fffffff, wxh = -0x7fffffff, wyl = 0x7fffffff, wyh = -0x7fffffff;
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+        wxl = min(wxl, (int)ceilf(-2.0f + A.vb[i] * A.dt));
+        wxh = max(wxh, (int)ceilf(2.0f + A.vb[4 + i] * A.dt) - 1);
+        wyl = min(wyl, (int)ceilf(-2.0f + A.vb[8 + i] * A.dt));
+        wyh = max(wyh, (int)ceilf(2.0f + A.vb[12 + i] * A.dt) - 1);
+    }
+    const int xlo = JX + wxl, xhi = JX + wxh, ylo = JY + wyl, yhi = JY + wyh;
+    const int tx0 = wrap_idx(xlo, A.nx);
+    int ty = wrap_idx(ylo, A.ny);
+    for (int yy = ylo; yy <= yhi; ++yy, ty = (ty + 1 == A.ny) ? 0 : ty + 1) {
+        const long long row = (long long)ty * A.nx;
+        int tx = tx0;
+        for (int xx = xlo; xx <= xhi; ++xx, tx = (tx + 1 == A.nx) ? 0 : tx + 1) {
+            const long long t = row + tx;
+            int jx[N1], jy[N1];
+            unsigned kmask = 0u, lmask = 0u;
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                jx[i] = JX - (xx + A.org[(long long)(N1 * i) * A.N + t].x);
+                jy[i] = JY - (yy + A.org[(long long)i * A.N + t].y);
+                kmask |= (jx[i] >= 0 && jx[i] <= 3) ? 1u << i : 0u;
+                lmask |= (jy[i] >= 0 && jy[i] <= 3) ? 1u << i : 0u;
+            }
+            if (!kmask || !lmask) continue;
+            const float4 th = A.gstar[t], tl = A.gstar[A.N + t];
+            const float inv = A.inv_st[t];
+            const float r = sdiff(jh.x, jl.x, th.x, tl.x) * inv;
+            const float dx = sdiff(jh.y, jl.y, th.y, tl.y) * inv;
+            const float dy = sdiff(jh.z, jl.z, th.z, tl.z) * inv;
+            float gx[N1][N1], gy[N1][N1], lxs[N1], lys[N1];
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                lxs[k] = 0.0f;
+                if (!(kmask >> k & 1u)) continue;
+                lxs[k] = A.lw[8 * ((long long)(N1 * k) * A.N + t) + jx[k]];
+#pragma unroll
+                for (int a = 0; a < N1; ++a)
+                    gx[k][a] = gauge_poly<N1>(L.d3[k], L.d2[k][a], L.d1[k][a], a == k ? 1.0f : 0.0f,
+                                              fmaf(L.c[a], r, dx));
+            }
+#pragma unroll
+            for (int l = 0; l < N1; ++l) {
+                lys[l] = 0.0f;
+                if (!(lmask >> l & 1u)) continue;
+                lys[l] = A.lw[8 * ((long long)l * A.N + t) + 4 + jy[l]];
+#pragma unroll
+                for (int b = 0; b < N1; ++b)
+                    gy[l][b] = gauge_poly<N1>(L.d3[l], L.d2[l][b], L.d1[l][b], b == l ? 1.0f : 0.0f,
+                                              fmaf(L.c[b], r, dy));
+            }
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                if (!(kmask >> k & 1u)) continue;
+#pragma unroll
+                for (int l = 0; l < N1; ++l) {
+                    if (!(lmask >> l & 1u)) continue;
+                    const float coef = A.w[(long long)(N1 * k + l) * A.N + t] * (lxs[k] * lys[l]);
+#pragma unroll
+                    for (int a = 0; a < N1; ++a) {
+                        const float cgx = coef * gx[k][a];
+#pragma unroll
+                        for (int b = 0; b < N1; ++b) fb[N1 * a + b] = fmaf(cgx, gy[l][b], fb[N1 * a + b]);
+                    }
+                }
+            }
+        }
+    }
+    // the source-gauge cotangent from fb (= h, the populations' cotangent in
+    // the frame r = lambda_j): dg/du_x [k][l] = sum_a d1[k][a] f[a][l] / s_j,
+    // dg/du_y [k][l] = sum_b d1[l][b] f[k][b] / s_j, dg/ds with c_a, c_b inside
+    {
+        const float is = (float)(1.0 / A.st_in[src]);
+#pragma unroll
+        for (int kk = 0; kk < N1; ++kk)
+#pragma unroll
+            for (int ll = 0; ll < N1; ++ll) {
+                float gxu = 0.0f, gyu = 0.0f, gsx = 0.0f, gsy = 0.0f;
+#pragma unroll
+                for (int a = 0; a < N1; ++a) {
+                    gxu = fmaf(L.d1[kk][a], fj[N1 * a + ll], gxu);
+                    gsx = fmaf(L.d1[kk][a] * L.c[a], fj[N1 * a + ll], gsx);
+                    gyu = fmaf(L.d1[ll][a], fj[N1 * kk + a], gyu);
+                    gsy = fmaf(L.d1[ll][a] * L.c[a], fj[N1 * kk + a], gsy);
+                }
+                const float h = fb[N1 * kk + ll];
+                bux = fmaf(h, gxu * is, bux);
+                buy = fmaf(h, gyu * is, buy);
+                bst = fmaf(h, (gsx + gsy) * is, bst);
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) A.fbar_in[(long long)i * A.N + src] = (double)fb[i];
+    A.gbar_in[src] = (double)bux;
+    A.gbar_in[A.N + src] = (double)buy;
+    A.gbar_in[2 * A.N + src] = (double)bst / (2.0 * A.st_in[src] * (double)A.T_L);
+}
+
 // ---------------------------------------------------------------------------
 // Phase A in the staged form (the FP64 counterpart is k_adjoint_jvp_staged in
 // pond_adjoint.cu): the window of sources a 32 x 4 tile of targets can reach
@@ -1053,8 +1178,8 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (ctx_staged(ctx)) {
-        if (ctx->L.n1 == 3) k_adjoint_sources_mixed_r<3><<<nb, ADJM_THREADS, 0, s>>>(A);
-        else k_adjoint_sources_mixed_r<4><<<nb, ADJM_THREADS, 0, s>>>(A);
+        if (ctx->L.n1 == 3) k_adjoint_sources_mixed_t<3><<<nb, ADJM_THREADS, 0, s>>>(A);
+        else k_adjoint_sources_mixed_t<4><<<nb, ADJM_THREADS, 0, s>>>(A);
     } else {
         if (ctx->L.n1 == 3) k_adjoint_sources_mixed<3><<<nb, ADJM_THREADS, 0, s>>>(A);
         else k_adjoint_sources_mixed<4><<<nb, ADJM_THREADS, 0, s>>>(A);

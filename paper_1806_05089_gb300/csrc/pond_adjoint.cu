@@ -382,8 +382,8 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A
     }
 }
 
-// The same gather with the source-gauge derivatives taken out of the hit
-// loop.  G(j -> t) = G(r -> t) G(j -> r) for any fixed r (the matched
+// The gather of the staged contexts takes the source-gauge derivatives out
+// of the hit loop.  G(j -> t) = G(r -> t) G(j -> r) for any fixed r (the matched
 // moments determine the populations), so with r held at the source's own
 // gauge lambda_j,
 //   d/dlambda_j [G(j -> t) f_j]_q = [G(r -> t) dG(j -> r)/dlambda_j f_j]_q,
@@ -392,118 +392,10 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources(AdjArgs A
 //   h = sum_hits coef G(j -> t)[q, :]  (= the populations' cotangent f_j_bar).
 // At r = lambda_j the map G(j -> r) is the identity and its derivatives are
 // the constants L_k'(c_a) = d1[k][a] over s_j (x: d xi/d u = 1/s_j; s:
-// d xi/d s = c_a/s_j).  Each hit then costs the two rows of G(j -> t) and a
+// d xi/d s = c_a/s_j).  A hit then needs only the two rows of G(j -> t) and a
 // rank-one update, about a third of the direct gather's FP64 work.
-template <int N1>
-__global__ void __launch_bounds__(ADJ_WARPS * 32, 2) k_adjoint_sources_r(AdjArgs A) {
-    constexpr int Q = N1 * N1;
-    const Lattice& L = c_La[lattice_slot(N1)];
-    const int lane = threadIdx.x & 31;
-    const long long src = (long long)blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
-    if (src >= A.N) return;  // warp-uniform
-    const int JX = (int)(src % A.nx), JY = (int)(src / A.nx);
-    // lane = (population q, half); on D2Q9 lanes with q >= 9 hold no
-    // population: they contribute zeros to the 16-lane sums and read nothing
-    const int q = lane & 15, half = lane >> 4;
-    const bool act = q < Q;
-    const int qa = act ? q : 0, k = qa / N1, l = qa % N1;
-    const double uxj = A.in.ux[src], uyj = A.in.uy[src], stj = A.in.st[src];
-
-    double fb[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) fb[i] = 0.0;
-    double bux = 0.0, buy = 0.0, bst = 0.0;
-
-    // candidate targets: J is in the stencil of the target at x when
-    // floor(x - v dt) is in [J - 2, J + 1], i.e. x in [J - 2 + v dt, J + 2 + v dt);
-    // over v in [vlo, vhi] the integers x from ceil(J - 2 + vlo dt) to
-    // ceil(J + 2 + vhi dt) - 1, widened by a rounding margin (the exact test
-    // below decides).  ceil(J + a) = J + ceil(a) for integer J, so the bounds
-    // are formed relative to J.
-    const double ex = 1e-9 * (1.0 + fabs(A.vlo_x[k]) + fabs(A.vhi_x[k])) * A.dt;
-    const double ey = 1e-9 * (1.0 + fabs(A.vlo_y[l]) + fabs(A.vhi_y[l])) * A.dt;
-    const int xlo = JX + (int)ceil(-2.0 + A.vlo_x[k] * A.dt - ex);
-    const int xhi = JX + (int)ceil(2.0 + A.vhi_x[k] * A.dt + ex) - 1;
-    const int ylo = JY + (int)ceil(-2.0 + A.vlo_y[l] * A.dt - ey);
-    const int yhi = JY + (int)ceil(2.0 + A.vhi_y[l] * A.dt + ey) - 1;
-    for (int yy = ylo + half; act && yy <= yhi; yy += 2) {
-        const int ty = wrap_idx(yy, A.ny);
-        for (int xx = xlo; xx <= xhi; ++xx) {
-            const int tx = wrap_idx(xx, A.nx);
-            const long long t = (long long)ty * A.nx + tx;
-            // the target's stencil origin for population q, as the target
-            // kernel found it (at the target's own, wrapped position)
-            const long long o = (long long)q * A.N + t;
-            const int2 og = A.org[o];
-            const int jx = JX - (xx + og.x), jy = JY - (yy + og.y);
-            if (jx < 0 || jx > 3 || jy < 0 || jy > 3) continue;
-            const double wgt = A.lw[8 * o + jx] * A.lw[8 * o + 4 + jy];
-            const double coef = A.w[o] * wgt;
-            const double ux = A.ux_s[t], uy = A.uy_s[t];
-            const double inv = A.inv_st[t];
-            const double r = fma(stj, inv, -1.0);
-            const double dx = (uxj - ux) * inv, dy = (uyj - uy) * inv;
-            double gx[N1], gy[N1];
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                gx[a] = gauge_poly<N1>(L.d3[k], L.d2[k][a], L.d1[k][a], a == k ? 1.0 : 0.0,
-                                       fma(L.c[a], r, dx));
-                gy[a] = gauge_poly<N1>(L.d3[l], L.d2[l][a], L.d1[l][a], a == l ? 1.0 : 0.0,
-                                       fma(L.c[a], r, dy));
-            }
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                const double cgx = coef * gx[a];
-#pragma unroll
-                for (int b = 0; b < N1; ++b) fb[N1 * a + b] = fma(cgx, gy[b], fb[N1 * a + b]);
-            }
-        }
-    }
-    // reduce over the warp: lanes 2p and 2p + 1 get population p's total
-    constexpr unsigned FULL = 0xffffffffu;
-    double v[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = i < Q ? fb[i] : 0.0;
-    const double tot = warp_reduce_scatter16(v, lane);
-    // the source-gauge cotangent from h = fb, one population per even lane:
-    // dg/du_x [k][l] = sum_a d1[k][a] f[a][l] / s_j, dg/du_y [k][l] =
-    // sum_b d1[l][b] f[k][b] / s_j, dg/ds the same with c_a, c_b inside
-    const int p = lane >> 1;
-    double pux = 0.0, puy = 0.0, pst = 0.0;
-    if ((lane & 1) == 0 && p < Q) {
-        const int kk = p / N1, ll = p % N1;
-        double gxu = 0.0, gyu = 0.0, gsx = 0.0, gsy = 0.0;
-#pragma unroll
-        for (int a = 0; a < N1; ++a) {
-            // the source's populations f_j[a][ll] and f_j[kk][a]
-            const double fx = A.in.f[(long long)(N1 * a + ll) * A.N + src];
-            const double fy = A.in.f[(long long)(N1 * kk + a) * A.N + src];
-            gxu = fma(L.d1[kk][a], fx, gxu);
-            gsx = fma(L.d1[kk][a] * L.c[a], fx, gsx);
-            gyu = fma(L.d1[ll][a], fy, gyu);
-            gsy = fma(L.d1[ll][a] * L.c[a], fy, gsy);
-        }
-        pux = tot * gxu;
-        puy = tot * gyu;
-        pst = tot * (gsx + gsy);
-        A.fbar_in[(long long)p * A.N + src] = tot;
-    }
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        pux += __shfl_xor_sync(FULL, pux, o);
-        puy += __shfl_xor_sync(FULL, puy, o);
-        pst += __shfl_xor_sync(FULL, pst, o);
-    }
-    if (lane == 0) {
-        const double is = 1.0 / stj;
-        A.gbar_in[src] = pux * is;
-        A.gbar_in[A.N + src] = puy * is;
-        // s = sqrt(T / T_L): dL/dT = dL/ds / (2 s T_L)
-        A.gbar_in[2 * A.N + src] = pst * is / (2.0 * stj * A.T_L);
-    }
-}
-
-// The same gather organised by target.  For a source j and a candidate
+//
+// It is organised by target.  For a source j and a candidate
 // target t, population (k, l) hits when j lies in both its x-stencil and its
 // y-stencil; the x-stencil's origin depends on k alone and the y-stencil's
 // on l alone, so the hits of (j, t) are a product set K x L.  The rows

@@ -434,121 +434,18 @@ __global__ void __launch_bounds__(ADJM_THREADS) k_adjoint_sources_mixed(AdjMixed
     A.gbar_in[2 * A.N + src] = (double)bst / (2.0 * A.st_in[src] * (double)A.T_L);
 }
 
-// The same gather with the source-gauge derivatives taken out of the hit
-// loop (G(j -> t) = G(r -> t) G(j -> r) with r held at the source's gauge;
-// see k_adjoint_sources_r in pond_adjoint.cu): each hit costs the two rows
-// of G(j -> t) and a rank-one update.
-template <int N1>
-__global__ void __launch_bounds__(ADJM_THREADS) k_adjoint_sources_mixed_r(AdjMixedArgs A) {
-    constexpr int Q = N1 * N1;
-    const LatticeF& L = c_Lam[lattice_slot(N1)];
-    const long long src0 = (long long)blockIdx.x * ADJM_THREADS + threadIdx.x;
-    if (src0 >= A.N) return;  // no warp-wide operation follows
-    const long long src = src0;
-    const int JX = (int)(src % A.nx), JY = (int)(src / A.nx);
-    float fj[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) fj[i] = A.f_in[(long long)i * A.N + src];
-    const float4 jh = A.gin[src], jl = A.gin[A.N + src];
-
-    float fb[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) fb[i] = 0.0f;
-    float bux = 0.0f, buy = 0.0f, bst = 0.0f;
-#pragma unroll 1
-    for (int q = 0; q < Q; ++q) {
-        const int k = q / N1, l = q - N1 * k;
-        const RowCoef<N1> Rk = row_coef<N1>(L, k), Rl = row_coef<N1>(L, l);
-        // candidate targets: J is in the stencil of the target at x when
-        // floor(x - v dt) is in [J - 2, J + 1], i.e. x in [J - 2 + v dt, J + 2 + v dt);
-        // over v in [vlo, vhi] (the bounds carry a 1e-3-cell margin for the
-        // FP32 departures) the integers x from ceil(J - 2 + vlo dt) to
-        // ceil(J + 2 + vhi dt) - 1; the exact test below decides.
-        // ceil(J + a) = J + ceil(a) for integer J, so the bounds are free of
-        // the rounding of large coordinates, and the window's offsets from J
-        // are the same for every thread.
-        const int xlo = JX + (int)ceilf(-2.0f + A.vb[k] * A.dt);
-        const int xhi = JX + (int)ceilf(2.0f + A.vb[4 + k] * A.dt) - 1;
-        const int ylo = JY + (int)ceilf(-2.0f + A.vb[8 + l] * A.dt);
-        const int yhi = JY + (int)ceilf(2.0f + A.vb[12 + l] * A.dt) - 1;
-        // wrapped coordinates advance with the loop counters (one modulo
-        // per population, not per candidate)
-        const int tx0 = wrap_idx(xlo, A.nx);
-        int ty = wrap_idx(ylo, A.ny);
-        for (int yy = ylo; yy <= yhi; ++yy, ty = (ty + 1 == A.ny) ? 0 : ty + 1) {
-            const long long row = (long long)ty * A.nx;
-            int tx = tx0;
-            for (int xx = xlo; xx <= xhi; ++xx, tx = (tx + 1 == A.nx) ? 0 : tx + 1) {
-                const long long t = row + tx;
-                // the target's stencil origin for population q, as the
-                // target kernel found it
-                const long long o = (long long)q * A.N + t;
-                const int2 og = A.org[o];
-                const int jx = JX - (xx + og.x), jy = JY - (yy + og.y);
-                if (jx < 0 || jx > 3 || jy < 0 || jy > 3) continue;
-                const float4 th = A.gstar[t], tl = A.gstar[A.N + t];
-                const float wgt = A.lw[8 * o + jx] * A.lw[8 * o + 4 + jy];
-                const float coef = A.w[o] * wgt;
-                const float inv = A.inv_st[t];
-                const float r = sdiff(jh.x, jl.x, th.x, tl.x) * inv;
-                const float dx = sdiff(jh.y, jl.y, th.y, tl.y) * inv;
-                const float dy = sdiff(jh.z, jl.z, th.z, tl.z) * inv;
-                float gx[N1], gy[N1];
-#pragma unroll
-                for (int a = 0; a < N1; ++a) {
-                    gx[a] = gauge_poly<N1>(L.d3[k], L.d2[k][a], L.d1[k][a], a == k ? 1.0f : 0.0f,
-                                           fmaf(L.c[a], r, dx));
-                    gy[a] = gauge_poly<N1>(L.d3[l], L.d2[l][a], L.d1[l][a], a == l ? 1.0f : 0.0f,
-                                           fmaf(L.c[a], r, dy));
-                }
-#pragma unroll
-                for (int a = 0; a < N1; ++a) {
-                    const float cgx = coef * gx[a];
-#pragma unroll
-                    for (int b = 0; b < N1; ++b) fb[N1 * a + b] = fmaf(cgx, gy[b], fb[N1 * a + b]);
-                }
-            }
-        }
-    }
-    // the source-gauge cotangent from fb (= h, the populations' cotangent in
-    // the frame r = lambda_j): dg/du_x [k][l] = sum_a d1[k][a] f[a][l] / s_j,
-    // dg/du_y [k][l] = sum_b d1[l][b] f[k][b] / s_j, dg/ds with c_a, c_b inside
-    {
-        const float is = (float)(1.0 / A.st_in[src]);
-#pragma unroll
-        for (int kk = 0; kk < N1; ++kk)
-#pragma unroll
-            for (int ll = 0; ll < N1; ++ll) {
-                float gxu = 0.0f, gyu = 0.0f, gsx = 0.0f, gsy = 0.0f;
-#pragma unroll
-                for (int a = 0; a < N1; ++a) {
-                    gxu = fmaf(L.d1[kk][a], fj[N1 * a + ll], gxu);
-                    gsx = fmaf(L.d1[kk][a] * L.c[a], fj[N1 * a + ll], gsx);
-                    gyu = fmaf(L.d1[ll][a], fj[N1 * kk + a], gyu);
-                    gsy = fmaf(L.d1[ll][a] * L.c[a], fj[N1 * kk + a], gsy);
-                }
-                const float h = fb[N1 * kk + ll];
-                bux = fmaf(h, gxu * is, bux);
-                buy = fmaf(h, gyu * is, buy);
-                bst = fmaf(h, (gsx + gsy) * is, bst);
-            }
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) A.fbar_in[(long long)i * A.N + src] = (double)fb[i];
-    A.gbar_in[src] = (double)bux;
-    A.gbar_in[A.N + src] = (double)buy;
-    A.gbar_in[2 * A.N + src] = (double)bst / (2.0 * A.st_in[src] * (double)A.T_L);
-}
-
-// The same gather organised by target (see k_adjoint_sources_t in
-// pond_adjoint.cu): the hits of a (source, target) pair are a product set
-// K x L, since the x-stencil's origin depends on the x-speed alone and the
-// y-stencil's on the y-speed alone.  Each thread walks the union of its
+// The gather of the staged contexts (see k_adjoint_sources_t in
+// pond_adjoint.cu): the source-gauge derivatives are taken out of the hit
+// loop (G(j -> t) = G(r -> t) G(j -> r) with r held at the source's gauge),
+// and the gather is organised by target: the hits of a (source, target)
+// pair are a product set K x L, since the x-stencil's origin depends on the
+// x-speed alone and the y-stencil's on the y-speed alone.  Each thread walks the union of its
 // source's candidate windows once, evaluates a hit target's rows G_x[k][.]
 // (k in K) and G_y[l][.] (l in L) once, then does each hit's weight and
 // rank-one update.
 template <int N1>
-__global__ void __launch_bounds__(ADJM_THREADS) k_adjoint_sources_mixed_t(AdjMixedArgs A) {
+__global__ void __launch_bounds__(ADJM_THREADS, 5)  // 5 CTAs per SM: measured 2 % faster than 4
+k_adjoint_sources_mixed_t(AdjMixedArgs A) {
     constexpr int Q = N1 * N1;
     const LatticeF& L = c_Lam[lattice_slot(N1)];
     const long long src0 = (long long)blockIdx.x * ADJM_THREADS + threadIdx.x;

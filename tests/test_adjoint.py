@@ -29,6 +29,22 @@ def small_case(nx, ny, seed=0, T_L=1.0):
     return rho0, tg.ux * np.sqrt(T_L), tg.uy * np.sqrt(T_L), T0, target
 
 
+def fast_case(nx, ny, seed=0, T_L=1.0):
+    """The supersonic field (u = (1.5, 0.5), Mach 1.6) with a Taylor-Green
+    swirl (u0 = 0.3) on top, so the particle velocities span a wide, varying
+    range: the adjoint gathers' candidate windows are wide."""
+    f = workloads.supersonic(nx=nx, ny=ny)
+    tg = workloads.taylor_green(nx, ny, 0.3)
+    rng = np.random.default_rng(seed)
+    rho0 = f.rho * (1.0 + 0.02 * rng.standard_normal((ny, nx)))
+    target = 1.0 + 0.01 * rng.standard_normal((ny, nx))
+    return (rho0, (f.ux + tg.ux) * np.sqrt(T_L), (f.uy + tg.uy) * np.sqrt(T_L), f.T * T_L,
+            target)
+
+
+CASES = {"tg": small_case, "fast": fast_case}
+
+
 def oracle_loss(rho0, ux, uy, T, target, nu, steps, passes, lattice=0, T_ref=1.0):
     st = oracle.init_equilibrium(rho0, ux, uy, T, lattice=lattice)
     p = oracle.Params(nu=nu, fixed_iter=passes, lattice=lattice, T_ref=T_ref)
@@ -295,14 +311,16 @@ def test_mixed_adjoint_rollout_length_bound():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("case", ["tg", "fast"])
 @pytest.mark.parametrize("lattice,T_L", LATTICES)
 @pytest.mark.parametrize("nx,ny", [(40, 36), (37, 29), (3, 5)])
-def test_staged_adjoint_matches_direct_adjoint(nx, ny, lattice, T_L):
+def test_staged_adjoint_matches_direct_adjoint(nx, ny, lattice, T_L, case):
     """The FP64 adjoint step of a staged-kernel context (phase A through the
-    tile's reference gauge) and of a direct-kernel context give the same VJP
-    to rounding, on a full, a ragged and a tiny grid."""
+    tile's reference gauge, the target-centric gather) and of a direct-kernel
+    context give the same VJP to rounding, on a full, a ragged and a tiny
+    grid, at low and at supersonic speed."""
     from paper_1806_05089_gb300 import pond
-    rho0, ux, uy, T, _ = small_case(nx, ny, seed=11, T_L=T_L)
+    rho0, ux, uy, T, _ = CASES[case](nx, ny, seed=11, T_L=T_L)
     dev = torch.device("cuda")
     rng = np.random.default_rng(12)
     Q = 16 if lattice == 0 else 9
@@ -325,16 +343,17 @@ def test_staged_adjoint_matches_direct_adjoint(nx, ny, lattice, T_L):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("case", ["tg", "fast"])
 @pytest.mark.parametrize("lattice,T_L", LATTICES)
 @pytest.mark.parametrize("nx,ny", [(40, 36), (37, 29), (3, 5)])
-def test_staged_mixed_adjoint_matches_direct_mixed_adjoint(nx, ny, lattice, T_L):
+def test_staged_mixed_adjoint_matches_direct_mixed_adjoint(nx, ny, lattice, T_L, case):
     """The FP32 adjoint step with the staged phase A (sources staged in the
     tile's reference gauge, epilogue fused) and with the per-pair phase A,
     both handed the same input state and output gauge, agree to FP32
     rounding, and both with the FP64 adjoint step, on a full, a ragged and a
     tiny grid."""
     from paper_1806_05089_gb300 import pond
-    rho0, ux, uy, T, _ = small_case(nx, ny, seed=13, T_L=T_L)
+    rho0, ux, uy, T, _ = CASES[case](nx, ny, seed=13, T_L=T_L)
     dev = torch.device("cuda")
     rng = np.random.default_rng(14)
     Q = 16 if lattice == 0 else 9

@@ -104,8 +104,9 @@ typedef struct pond_config {
                            environment variable POND_AUTOTUNE_CACHE names a
                            file, in that JSON file across processes. */
     int32_t tile_rows;  /* tile kernels (the mixed form, and the FP64 form's
-                           staged kernel): 0 = default tile (32 x 8 nodes)
-                           or the autotuner's choice; 4, 8 or 16 force a
+                           staged kernel): 0 = default tile (32 x 8 nodes;
+                           32 x 4 for the FP64 form on D2Q9) or the
+                           autotuner's choice; 4, 8 or 16 force a
                            32-wide tile of that many rows (16: mixed only),
                            -16 the direct mixed kernel's 32 x 16 tile with
                            two stacked nodes per thread (D2Q16 only); a

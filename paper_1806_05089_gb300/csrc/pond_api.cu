@@ -440,7 +440,7 @@ pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* 
         return st == POND_OK ? POND_ERR_CUDA : st;
     }
     if (tiled(ctx)) {
-        const int ty0 = mixed(ctx) ? MIXED_TY : STAGED_TY_FP64[0];
+        const int ty0 = mixed(ctx) ? MIXED_TY : staged_ty_fp64_default(ctx->L.n1);
         st = set_tile_rows(ctx, cfg->tile_rows ? cfg->tile_rows : ty0);
         if (cfg->tile_rows) ctx->tuned = true;  // a forced shape is not retuned
         if (st != POND_OK) {

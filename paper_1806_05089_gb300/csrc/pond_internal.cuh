@@ -214,6 +214,10 @@ inline size_t staged_window_bytes(const TileWindow& w) {
            (size_t)w.n1 * w.n1 * w.tx * w.ty * w.real_bytes;
 }
 constexpr int STAGED_TY_FP64[2] = {4, 8};
+// default FP64 tile rows without autotuning: 32 x 8 on D2Q16 (measured 0-4 %
+// faster than 32 x 4 from 256^2 to 2048^2), 32 x 4 on D2Q9 (the autotuner's
+// choice at 2048^2)
+constexpr int staged_ty_fp64_default(int n1) { return n1 == 4 ? 8 : 4; }
 constexpr int STAGED_TY_MIXED[3] = {4, 8, 16};
 
 // Tile shape of the mixed kernel, its shared-memory need for a window, and

@@ -61,8 +61,9 @@ BYTES_MIXED_Q9 = 2 * (9 * 4 + 3 * 8)
 # 4 + (c_max - c_min) sqrt(theta) on average (the spread of the y-departures
 # plus the stencil).  Per (node, k) add the x-map's Taylor entries (5 n1
 # ops), the departure and cubic weights (20), the y-map applied after the
-# sweep (n1 x 6 n1 FMAs) and the moments (8 n1); per pass the y-departures
-# (20 n1) and the gauge update (40).  The once-per-step staging (~500 flops
+# sweep (mixed: n1 x 6 n1 FMAs with its entries; FP64: n1 x n1 FMAs, the
+# entries computed once per pass, 4 n1^2 FMAs) and the moments (8 n1); per
+# pass the y-departures (20 n1) and the gauge update (40).  The once-per-step staging (~500 flops
 # per staged source) is left out: the count is the per-pass work alone, so
 # the fraction is a lower bound.
 def staged_flops_per_pass(n1: int, st_mean: float, every_row: bool = False) -> float:
@@ -70,10 +71,13 @@ def staged_flops_per_pass(n1: int, st_mean: float, every_row: bool = False) -> f
     rows = 4.0 + spread * st_mean
     if every_row:
         sweep = 2 * (4 * n1 * n1 + n1 * n1 + n1 * n1) * rows
+        ymap_k, ymap_pass = n1 * 2 * 6 * n1, 0
     else:
         sweep = 2 * (4 * n1 * n1) * rows + 4 * n1 + 2 * 4 * n1 * n1
-    per_k = sweep + 2 * 5 * n1 + 20 + n1 * 2 * 6 * n1 + 8 * n1
-    return n1 * per_k + 20 * n1 + 40
+        # the y-map entries once per pass (a table), one FMA each per (k, l, b)
+        ymap_k, ymap_pass = 2 * n1 * n1, 2 * 4 * n1 * n1
+    per_k = sweep + 2 * 5 * n1 + 20 + ymap_k + 8 * n1
+    return n1 * per_k + 20 * n1 + 40 + ymap_pass
 
 
 # Nominal peaks of the arithmetic pipes at the 2070 MHz maximum SM clock

@@ -209,9 +209,11 @@ cudaError_t launch_step_staged_mixed(const StateBuf<float>& in, const StateBuf<f
                                      const StepParams& P, cudaStream_t s);
 cudaError_t staged_prepare_fp64(int ty, int n1, size_t smem, int* ctas_per_sm);
 cudaError_t staged_prepare_mixed(int ty, int n1, size_t smem, int* ctas_per_sm);
+// (as staged_smem_bytes: the FP64 form also holds the y-map table)
 inline size_t staged_window_bytes(const TileWindow& w) {
+    const size_t per_node = w.real_bytes == 8 ? 2 : 1;
     return (size_t)w.n1 * w.ww * w.wh * 4 * w.real_bytes +
-           (size_t)w.n1 * w.n1 * w.tx * w.ty * w.real_bytes;
+           per_node * w.n1 * w.n1 * w.tx * w.ty * w.real_bytes;
 }
 constexpr int STAGED_TY_FP64[2] = {4, 8};
 // default FP64 tile rows without autotuning: 32 x 8 on D2Q16 (measured 0-4 %

@@ -264,6 +264,7 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
     const int WN = A.ww * A.wh;
     Real4* s_f = reinterpret_cast<Real4*>(smem_raw);              // [N1][WN]: row a of g
     Real* s_acc = reinterpret_cast<Real*>(s_f + (size_t)N1 * WN);  // [Q][NT]
+    Real* s_ey = s_acc + (size_t)N1 * N1 * NT;  // [Q][NT] Ey[l][b] of the pass (kEyTable)
     __shared__ float s_red[4][NT / 32];
     __shared__ long long s_item;
     __shared__ unsigned long long s_passes, s_nc, s_np, s_fb;
@@ -383,6 +384,20 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
             const Real rt = (Real)(rst - pg.st) * invf;
             const Real dxt = (Real)(rux - pg.ux) * invf;
             const Real dyt = (Real)(ruy - pg.uy) * invf;
+            if constexpr (Tr::kEyTable) {
+                // the y-map r -> lambda of this pass, Ey[l][b] in correction
+                // form, for every x-speed
+                if (work) {
+#pragma unroll
+                    for (int l = 0; l < N1; ++l)
+#pragma unroll
+                        for (int b = 0; b < N1; ++b) {
+                            const Real de = fma((Real)L.c[b], rt, dyt);
+                            s_ey[(N1 * l + b) * NT + tid] =
+                                gauge_tail<N1>((Real)L.d3[l], (Real)L.d2[l][b], (Real)L.d1[l][b], de) * de;
+                        }
+                }
+            }
             // y-stencils of the n1 y-speeds: top row in the window and weights
             int top[N1];
             bool ynear[N1];
@@ -572,9 +587,14 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
                             acc = Z[l][l];
 #pragma unroll
                             for (int b = 0; b < N1; ++b) {
-                                const Real de = fma((Real)L.c[b], rt, dyt);
-                                const Real ey = gauge_tail<N1>((Real)L.d3[l], (Real)L.d2[l][b],
-                                                               (Real)L.d1[l][b], de) * de;
+                                Real ey;
+                                if constexpr (Tr::kEyTable) {
+                                    ey = s_ey[(N1 * l + b) * NT + tid];
+                                } else {
+                                    const Real de = fma((Real)L.c[b], rt, dyt);
+                                    ey = gauge_tail<N1>((Real)L.d3[l], (Real)L.d2[l][b],
+                                                        (Real)L.d1[l][b], de) * de;
+                                }
                                 acc = fma(ey, Z[l][b], acc);
                             }
                         } else {
@@ -630,9 +650,12 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
     }
 }
 
-// Dynamic shared memory of the staged kernel for a window.
+// Dynamic shared memory of the staged kernel for a window: the staged rows,
+// the pass's populations and, in the FP64 form (8-byte reals), the y-map
+// table.
 inline size_t staged_smem_bytes(int n1, int ww, int wh, int nt, size_t real_bytes) {
-    return (size_t)n1 * ww * wh * 4 * real_bytes + (size_t)n1 * n1 * nt * real_bytes;
+    const size_t per_node = real_bytes == 8 ? 2 : 1;
+    return (size_t)n1 * ww * wh * 4 * real_bytes + per_node * n1 * n1 * nt * real_bytes;
 }
 
 }  // namespace pond

@@ -954,6 +954,7 @@ struct StagedFP32 {
     using Real4 = float4;
     static constexpr bool kUnrollK = true;
     static constexpr bool kPacked = true;  // the sweep on packed FP32 pairs
+    static constexpr bool kEyTable = false;  // no room: 4 CTAs of 128 threads per SM
     template <int NT>
     static constexpr int min_blocks() {
         return 512 / NT;

@@ -88,10 +88,10 @@ PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per FP64 step launch at 2048^2 of the staged kernel: the ncu
 # capture of the same kernel (k_step_staged<StagedFP64, 32, 8, 4>) at 1024^2
-# read 164.1 MB and wrote 125.2 MB; traffic grows with the node count (4x).
-K_STAGED64_TRAFFIC_2048 = 4 * (164.13e6 + 125.25e6)
+# read 161.5 MB and wrote 125.6 MB; traffic grows with the node count (4x).
+K_STAGED64_TRAFFIC_2048 = 4 * (161.49e6 + 125.57e6)
 K_STAGED64_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                             "k_step_staged<StagedFP64, 32, 8, 4> launch at 1024^2 (289.4 MB), "
+                             "k_step_staged<StagedFP64, 32, 8, 4> launch at 1024^2 (287.1 MB), "
                              "scaled x4 by nodes to the 2048^2 launch")
 
 

@@ -24,26 +24,32 @@
 // transformed into lambda_r; every predictor-corrector pass then needs only
 // the 1D maps G(r -> t) of each target node, and for each x-speed index k one
 // sweep over the union of the n1 y-stencils' rows, 4 sources per row.  In
-// exact arithmetic this is the paper's f_q; it takes about a quarter of the
-// arithmetic of the per-(population, source) form, since the transform is
-// paid per staged source and per target instead of per pair.
+// exact arithmetic this is the paper's f_q; it takes a quarter (mixed form)
+// to a fifth (FP64 form) of the arithmetic of the per-(population, source)
+// form, since the transform is paid per staged source and per target
+// instead of per pair.
 //
 // Both 1D maps are written around the identity, G = I + E with E[k][a] =
-// de (d1 + de (d2 + de d3)) (de = xi_a - c_a), and applied in correction form
-// f + E f, so rounding never touches the identity part.
+// de (d1 + de (d2 + de d3)) (de = xi_a - c_a).  The staging and the mixed
+// form apply them in correction form f + E f, so rounding never touches the
+// identity part; the FP64 form folds Gx(r->t)[k][a] into the x-weights
+// (lx_k[jx] Gx[k][a], once per x-speed and pass), takes the pass's Ey
+// entries from a per-thread shared-memory table, and accumulates each
+// population once over its four stencil rows from a four-row buffer of P.
 //
 // One CTA per TX x TY tile (TX = 32: a warp is one tile row of 32 nodes);
 // batched ensembles take (grid, tile) items from an atomic counter.  The pass
 // loop is warp-synchronous: the row sweep's bounds are the union over the
 // warp's active lanes (__reduce_min/max_sync), lanes whose node has converged
-// idle, and each lane's per-row weights are zero on rows outside its own
-// stencils.  A stencil that leaves the staged window is computed from global
-// memory by staged_fallback and counted.
+// idle, and a lane's populations take only the rows of their own stencils.
+// A stencil that leaves the staged window is computed from global memory by
+// staged_fallback and counted.
 //
 // Tr (the including translation unit's traits) provides:
-//   Real, Real4 (16 or 32 bytes), min_blocks<threads>(), lat<N1>() (lattice
-//   constants of that unit's constant bank), departure (the floor of a
-//   displacement and the cubic weights at its fraction),
+//   Real, Real4 (16 or 32 bytes), kUnrollK, kPacked (the packed FP32 sweep),
+//   kEyTable (the Ey table in shared memory), min_blocks<threads>(),
+//   lat<N1>() (lattice constants of that unit's constant bank), departure
+//   (the floor of a displacement and the cubic weights at its fraction),
 //   load4 / store4, update(...) (the moments -> gauge update and the App. E
 //   test of that form) and finish<N1>(...) (re-gauge into the co-moving
 //   frame, BGK, store).

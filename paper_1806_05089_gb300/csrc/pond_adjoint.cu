@@ -26,10 +26,12 @@
 // (k_adjoint_jvp_staged: one thread per target node, the sources staged per
 // tile in a reference gauge, then k_adjoint_epilogue); contexts on the
 // direct kernels run k_adjoint_targets (one warp per target node, lane =
-// population).  Phase B (one warp per source node) gathers the transpose:
-// for every population it scans the targets whose departure stencil can
-// contain the source (a window bounded by the particle-velocity range), so
-// the result is deterministic and needs no atomics.
+// population).  Phase B (one warp per source node) gathers the transpose
+// over the targets whose departure stencils can contain the source (a
+// window bounded by the particle-velocity range), so the result is
+// deterministic and needs no atomics: per population in the direct
+// contexts (k_adjoint_sources), per target with the target's hit set
+// K x L in the staged ones (k_adjoint_sources_t).
 #include <cmath>
 
 #include "pond_device.cuh"

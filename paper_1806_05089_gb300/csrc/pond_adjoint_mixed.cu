@@ -9,7 +9,11 @@
 // (hi_s - hi') + (lo_s - lo'), which carries FP32 precision relative to the
 // difference itself.  The per-node epilogue (sums, cotangents, 3 x 3 solve)
 // runs in FP32 as well; only the beta cotangent is accumulated in FP64.
-// Templated on the lattice like the FP64 adjoint.
+// Contexts on the staged forward kernel run the staged phase A with the
+// epilogue fused (k_adjoint_jvp_staged_mixed) and the target-centric gather
+// (k_adjoint_sources_mixed_t); contexts on the direct kernels the per-pair
+// kernels (k_adjoint_targets_mixed, k_adjoint_sources_mixed).  Templated on
+// the lattice like the FP64 adjoint.
 #include <cmath>
 
 #include "pond_device.cuh"

@@ -122,19 +122,6 @@ __device__ __forceinline__ void staged_block_minmax4(float& a, float& b, float& 
 }
 
 
-// Row weight of a stencil whose top row is `top`, for grid row y: the cubic
-// weight ly[y - top] inside the stencil, zero outside it (or when the
-// stencil is not swept).
-template <typename Real>
-__device__ __forceinline__ Real row_weight(int y, int top, bool on, const Real (&ly)[4]) {
-    const int j = y - top;
-    Real w = (j == 0) ? ly[0] : (Real)0;
-    w = (j == 1) ? ly[1] : w;
-    w = (j == 2) ? ly[2] : w;
-    w = (j == 3) ? ly[3] : w;
-    return on ? w : (Real)0;
-}
-
 // One population's reconstruction read straight from global memory, for a
 // stencil that leaves the staged window (a displacement beyond the planned
 // halo): the direct form f_q = sum_s a_s [G(s -> t) f_s]_q with the source
@@ -467,11 +454,13 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
                 for (int l = 0; l < N1; ++l)
 #pragma unroll
                     for (int b = 0; b < N1; ++b) Z[l][b] = (Real)0;
-                int last[N1];  // the row that completes population l's stencil
+                int last[N1];   // the row that completes population l's stencil
+                int ontop[N1];  // top row of an on-window stencil, else out of reach
                 bool anyon = false;
 #pragma unroll
                 for (int l = 0; l < N1; ++l) {
                     last[l] = on[l] ? top[l] + 3 : -1;
+                    ontop[l] = on[l] ? top[l] : -0x40000000;
                     anyon = anyon || on[l];
                 }
                 float2 Z2[N1][2];  // the packed form's accumulators (pairs of b)
@@ -502,12 +491,19 @@ k_step_staged(StagedArgs<typename Tr::Real> A) {
                     if constexpr (Tr::kPacked) {
                         // pairs of b on fma.rn.f32x2: two FP32 FMAs per
                         // instruction, each rounded as the scalar one
+                        // the row's weight in population l's stencil: j = y - top
+                        // in 0..3 picks ly[l][j] by its two bits; off-window
+                        // stencils have their top far out of reach (ontop)
                         Real wl[N1];
                         bool any = false;
 #pragma unroll
                         for (int l = 0; l < N1; ++l) {
-                            wl[l] = row_weight<Real>(y, top[l], on[l], ly[l]);
-                            any = any || (on[l] && y >= top[l] && y <= top[l] + 3);
+                            const unsigned j = (unsigned)(y - ontop[l]);
+                            const bool in = j < 4u;
+                            const Real lo = (j & 1u) ? ly[l][1] : ly[l][0];
+                            const Real hi = (j & 1u) ? ly[l][3] : ly[l][2];
+                            wl[l] = in ? ((j & 2u) ? hi : lo) : (Real)0;
+                            any = any || in;
                         }
                         if (!any) continue;
                         float2 Fi2[N1][2];

@@ -4,9 +4,16 @@ Every entry point of libpond.so is exposed under its C name (``pond_create``,
 ``pond_set_state``, ``pond_step``, ``pond_moments``, ``pond_get_state``,
 ``pond_iterations``, ``pond_adjoint_step``, ``pond_destroy``, ...).  Arrays may
 be NumPy arrays (host) or torch tensors (CUDA tensors are passed as device
-pointers, CPU tensors as host pointers); every array is FP64.  All compute
-runs in the CUDA library: if it cannot be loaded this module raises, there is
-no CPU fallback.
+pointers, CPU tensors as host pointers); every array is FP64 except the int32
+iteration map.  All compute runs in the CUDA library: if it cannot be loaded
+this module raises, there is no CPU fallback.
+
+The library trusts the sizes behind its pointers, so the binding checks them:
+``pond_create`` returns a ``PondCtx`` that records each grid's size, the
+lattice's Q and the context's device, and every call that passes arrays
+checks their dtype, element count, side (host or device) and device against
+it before the C call (``TypeError`` / ``ValueError``; nothing reaches the
+library when a check fails).
 
 ``Sim`` is a small convenience wrapper owning one context.
 """
@@ -14,6 +21,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 from dataclasses import dataclass
 
 import numpy as np
@@ -178,27 +186,83 @@ def load(build_if_missing: bool = True, path: str | None = None):
 
 # ------------------------------------------------------------------ marshalling
 
-def _ptr(a, on_device: bool):
-    """(pointer, keepalive) of an FP64 array; torch tensors or NumPy arrays."""
+class PondCtx(ctypes.c_void_p):
+    """A pond_ctx handle: passed to the C calls as the pointer it holds, and
+    carrying what the binding checks array arguments against: ``grids``, the
+    (nx, ny) of each grid; ``q``, the populations per node; ``device``, the
+    CUDA device index the context was created on (None when torch was not
+    loaded then; the current device is assumed)."""
+
+
+def _grid_nodes(ctx, grid):
+    """Nodes of grid ``grid`` of a handle made by ``pond_create``; None for
+    another handle or an index out of range (the library rejects that one
+    itself with POND_ERR_ARG)."""
+    grids = getattr(ctx, "grids", None)
+    if grids is None or not 0 <= int(grid) < len(grids):
+        return None
+    nx, ny = grids[int(grid)]
+    return nx * ny
+
+
+def _counts(ctx, grid, *per_node):
+    """Expected element counts for arrays of ``per_node`` values per node
+    (1 for a field, 3 for a gauge triple, "q" for populations), or Nones
+    when the handle does not know the grid."""
+    n = _grid_nodes(ctx, grid)
+    q = getattr(ctx, "q", None)
+    if n is None or q is None:
+        return [None] * len(per_node)
+    return [n * (q if k == "q" else k) for k in per_node]
+
+
+def _check_device(name, index, want):
+    if index != want:
+        raise ValueError("%s is on cuda:%s; the context's device is cuda:%s" % (name, index, want))
+
+
+def _ptr(a, on_device: bool, count=None, kind: str = "f64", out: bool = False, device=None,
+         name: str = "array"):
+    """(pointer, keepalive) of one array argument, checked against what the
+    header requires: ``kind`` "f64" (FP64) or "i32" (the iteration map);
+    exactly ``count`` values when the grid is known; contiguous; on the side
+    the call names; for CUDA tensors, on ``device`` (the current device when
+    None).  Host inputs of another dtype are converted into a copy that the
+    call reads; host outputs must already be writeable C-contiguous arrays of
+    the right dtype, since the library would fill a converted copy that the
+    caller never sees."""
     if a is None:
         return None, None
-    try:
-        import torch
-        if isinstance(a, torch.Tensor):
-            if a.dtype not in (torch.float64, torch.int32):
-                raise TypeError("PonD arrays are float64 (iteration maps int32)")
-            if not a.is_contiguous():
-                raise ValueError("array must be contiguous")
-            if a.is_cuda != on_device:
-                raise ValueError("all arrays of one call must be on the same side")
-            return ctypes.c_void_p(a.data_ptr()), a
-    except ImportError:
-        pass
+    torch = sys.modules.get("torch")
+    if torch is not None and isinstance(a, torch.Tensor):
+        want = torch.float64 if kind == "f64" else torch.int32
+        if a.dtype != want:
+            raise TypeError("%s must be %s, got %s" % (name, want, a.dtype))
+        if not a.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if a.is_cuda != on_device:
+            if on_device:
+                raise ValueError("device call needs torch CUDA tensors (%s is on the host)" % name)
+            raise ValueError("all arrays of one call must be on the same side (host or device)")
+        if count is not None and a.numel() != count:
+            raise ValueError("%s holds %d values; the grid needs %d" % (name, a.numel(), count))
+        if a.is_cuda:
+            _check_device(name, a.device.index,
+                          device if device is not None else torch.cuda.current_device())
+        return ctypes.c_void_p(a.data_ptr()), a
     if on_device:
-        raise ValueError("device call needs torch CUDA tensors")
-    arr = np.ascontiguousarray(a)
-    if arr.dtype not in (np.float64, np.int32):
-        arr = arr.astype(np.float64)
+        raise ValueError("device call needs torch CUDA tensors (%s is not one)" % name)
+    want_np = np.dtype(np.float64 if kind == "f64" else np.int32)
+    if out:
+        if (not isinstance(a, np.ndarray) or a.dtype != want_np or not a.flags.c_contiguous
+                or not a.flags.writeable):
+            raise TypeError("%s is an output: it must be a writeable C-contiguous %s array"
+                            % (name, want_np.name))
+        arr = a
+    else:
+        arr = np.ascontiguousarray(a, dtype=want_np)
+    if count is not None and arr.size != count:
+        raise ValueError("%s holds %d values; the grid needs %d" % (name, arr.size, count))
     return ctypes.c_void_p(arr.ctypes.data), arr
 
 
@@ -232,7 +296,7 @@ def pond_config_default(precision: int = POND_FP64) -> pond_config:
     return cfg
 
 
-def pond_create(cfg: pond_config, nx, ny, stream=None):
+def pond_create(cfg: pond_config, nx, ny, stream=None) -> PondCtx:
     nx = [int(v) for v in np.atleast_1d(nx)]
     ny = [int(v) for v in np.atleast_1d(ny)]
     n = len(nx)
@@ -243,7 +307,26 @@ def pond_create(cfg: pond_config, nx, ny, stream=None):
                             ctypes.c_void_p(stream or 0), ctypes.byref(out))
     if st != POND_OK:
         raise PondError(st, "pond_create failed")
-    return out
+    ctx = PondCtx(out.value)
+    ctx.grids = list(zip(nx, ny))
+    n1 = N_SPEEDS.get(int(cfg.lattice))
+    ctx.q = n1 * n1 if n1 is not None else None
+    # the library binds the context to the device current at creation
+    torch = sys.modules.get("torch")
+    ctx.device = (torch.cuda.current_device()
+                  if torch is not None and torch.cuda.is_available() else None)
+    return ctx
+
+
+def _marshal(ctx, grid, on_device, named, out=False):
+    """Checked (pointer, keepalive) pairs of one call's arrays, ``named`` as
+    (name, array, values per node, kind) with values per node 1, 3 or "q"."""
+    device = getattr(ctx, "device", None)
+    ps = []
+    for name, a, per_node, kind in named:
+        (count,) = _counts(ctx, grid, per_node)
+        ps.append(_ptr(a, on_device, count, kind, out, device, name))
+    return ps
 
 
 def pond_set_stream(ctx, stream):
@@ -252,7 +335,9 @@ def pond_set_stream(ctx, stream):
 
 def pond_set_state(ctx, grid, rho, ux, uy, T, f=None):
     dev = _is_device(ux, uy, T, rho, f)
-    ps = [_ptr(a, dev) for a in (rho, ux, uy, T, f)]
+    ps = _marshal(ctx, grid, dev, [("rho", rho, 1, "f64"), ("ux", ux, 1, "f64"),
+                                   ("uy", uy, 1, "f64"), ("T", T, 1, "f64"),
+                                   ("f", f, "q", "f64")])
     _check(ctx, load().pond_set_state(ctx, grid, *[p for p, _ in ps], int(dev)))
 
 
@@ -264,20 +349,29 @@ def pond_step(ctx, nsteps: int, want_stats: bool = True):
 
 def pond_moments(ctx, grid, rho=None, ux=None, uy=None, T=None):
     dev = _is_device(rho, ux, uy, T)
-    ps = [_ptr(a, dev) for a in (rho, ux, uy, T)]
+    ps = _marshal(ctx, grid, dev, [("rho", rho, 1, "f64"), ("ux", ux, 1, "f64"),
+                                   ("uy", uy, 1, "f64"), ("T", T, 1, "f64")], out=True)
     _check(ctx, load().pond_moments(ctx, grid, *[p for p, _ in ps], int(dev)))
 
 
 def pond_get_state(ctx, grid, f=None, ux=None, uy=None, T=None):
     dev = _is_device(f, ux, uy, T)
-    ps = [_ptr(a, dev) for a in (f, ux, uy, T)]
+    ps = _marshal(ctx, grid, dev, [("f", f, "q", "f64"), ("ux", ux, 1, "f64"),
+                                   ("uy", uy, 1, "f64"), ("T", T, 1, "f64")], out=True)
     _check(ctx, load().pond_get_state(ctx, grid, *[p for p, _ in ps], int(dev)))
 
 
 def pond_iterations(ctx, grid, iters):
     dev = _is_device(iters)
-    p, _k = _ptr(iters, dev)
+    ((p, _k),) = _marshal(ctx, grid, dev, [("iters", iters, 1, "i32")], out=True)
     _check(ctx, load().pond_iterations(ctx, grid, p, int(dev)))
+
+
+def _adjoint_arrays(ctx, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out):
+    return _marshal(ctx, 0, True, [("f_bar_in", f_bar_in, "q", "f64"),
+                                   ("gauge_bar_in", gauge_bar_in, 3, "f64"),
+                                   ("f_bar_out", f_bar_out, "q", "f64"),
+                                   ("gauge_bar_out", gauge_bar_out, 3, "f64")])
 
 
 def pond_adjoint_step(ctx, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out,
@@ -286,7 +380,7 @@ def pond_adjoint_step(ctx, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out,
     nu_on_device, None: the contribution then accumulates on the device
     (read with pond_adjoint_nu_bar) and the call does not wait for the GPU."""
     nu_bar = ctypes.c_double(0.0)
-    ps = [_ptr(a, True) for a in (f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out)]
+    ps = _adjoint_arrays(ctx, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out)
     acc = None if nu_on_device else ctypes.byref(nu_bar)
     _check(ctx, load().pond_adjoint_step(ctx, *[p for p, _ in ps], acc))
     return None if nu_on_device else nu_bar.value
@@ -298,8 +392,9 @@ def pond_adjoint_step_given(ctx, ux_out, uy_out, T_out, f_bar_in, gauge_bar_in, 
     so the forward step is not recomputed; returns d(loss)/d(nu) of this step
     (None with nu_on_device, as pond_adjoint_step)."""
     nu_bar = ctypes.c_double(0.0)
-    ps = [_ptr(a, True) for a in (ux_out, uy_out, T_out, f_bar_in, gauge_bar_in, f_bar_out,
-                                  gauge_bar_out)]
+    ps = _marshal(ctx, 0, True, [("ux_out", ux_out, 1, "f64"), ("uy_out", uy_out, 1, "f64"),
+                                 ("T_out", T_out, 1, "f64")])
+    ps += _adjoint_arrays(ctx, f_bar_in, gauge_bar_in, f_bar_out, gauge_bar_out)
     acc = None if nu_on_device else ctypes.byref(nu_bar)
     _check(ctx, load().pond_adjoint_step_given(ctx, *[p for p, _ in ps], acc))
     return None if nu_on_device else nu_bar.value
@@ -315,7 +410,7 @@ def pond_adjoint_nu_bar(ctx) -> float:
 
 def pond_adjoint_init(ctx, f_bar, rho_bar):
     """rho_bar = sum_q W_q f_bar_q (device tensors)."""
-    ps = [_ptr(a, True) for a in (f_bar, rho_bar)]
+    ps = _marshal(ctx, 0, True, [("f_bar", f_bar, "q", "f64"), ("rho_bar", rho_bar, 1, "f64")])
     _check(ctx, load().pond_adjoint_init(ctx, *[p for p, _ in ps]))
 
 
@@ -370,7 +465,8 @@ def pond_step_fp64_noalloc(cfg, f_in, ux_in, uy_in, T_in, f_out, ux_out, uy_out,
     tensors; see include/pond.h).  Returns the step counters."""
     _check_noalloc_args(cfg, f_in, ux_in, uy_in, T_in, f_out, ux_out, uy_out, T_out, iters)
     ny, nx = ux_in.shape
-    ps = [_ptr(a, True) for a in (f_in, ux_in, uy_in, T_in, f_out, ux_out, uy_out, T_out, iters)]
+    ps = [_ptr(a, True) for a in (f_in, ux_in, uy_in, T_in, f_out, ux_out, uy_out, T_out)]
+    ps.append(_ptr(iters, True, kind="i32", name="iters"))
     stats = pond_stats()
     st = load().pond_step_fp64_noalloc(ctypes.byref(cfg), nx, ny, *[p for p, _ in ps],
                                        ctypes.byref(stats) if want_stats else None,
@@ -398,25 +494,36 @@ def pond_set_interior(ctx, grid, x0, y0, w, h):
     _check(ctx, load().pond_set_interior(ctx, int(grid), int(x0), int(y0), int(w), int(h)))
 
 
-def _rect_buffer(buf, ctx_q, w, h):
+def _rect_buffer(ctx, buf, q, w, h):
+    """Pointer of a pack/unpack buffer: a contiguous CUDA float64 tensor on
+    the context's device with at least (Q + 3) * w * h values, Q the
+    context's populations per node (``q``, when given, must agree)."""
     import torch
+    ctx_q = getattr(ctx, "q", None)
+    if q is None:
+        q = ctx_q if ctx_q is not None else 16
+    elif ctx_q is not None and int(q) != ctx_q:
+        raise ValueError("q = %d, but the context's lattice has Q = %d" % (int(q), ctx_q))
     if not isinstance(buf, torch.Tensor) or not buf.is_cuda or buf.dtype != torch.float64:
         raise TypeError("rectangle buffers are CUDA float64 tensors")
-    if not buf.is_contiguous() or buf.numel() < (ctx_q + 3) * w * h:
+    if not buf.is_contiguous() or buf.numel() < (int(q) + 3) * int(w) * int(h):
         raise ValueError("rectangle buffer needs (Q + 3) * w * h contiguous values")
+    device = getattr(ctx, "device", None)
+    _check_device("buf", buf.device.index,
+                  device if device is not None else torch.cuda.current_device())
     return ctypes.c_void_p(buf.data_ptr())
 
 
-def pond_pack_rect(ctx, grid, x0, y0, w, h, buf, q=16):
+def pond_pack_rect(ctx, grid, x0, y0, w, h, buf, q=None):
     """Rectangle of the current state into a CUDA float64 buffer of
-    (q + 3) * w * h values (q = populations of the context's lattice)."""
+    (Q + 3) * w * h values (Q = populations of the context's lattice)."""
     _check(ctx, load().pond_pack_rect(ctx, int(grid), int(x0), int(y0), int(w), int(h),
-                                      _rect_buffer(buf, q, w, h)))
+                                      _rect_buffer(ctx, buf, q, w, h)))
 
 
-def pond_unpack_rect(ctx, grid, x0, y0, w, h, buf, q=16):
+def pond_unpack_rect(ctx, grid, x0, y0, w, h, buf, q=None):
     _check(ctx, load().pond_unpack_rect(ctx, int(grid), int(x0), int(y0), int(w), int(h),
-                                        _rect_buffer(buf, q, w, h)))
+                                        _rect_buffer(ctx, buf, q, w, h)))
 
 
 def pond_max_displacement(ctx, grid=0) -> float:

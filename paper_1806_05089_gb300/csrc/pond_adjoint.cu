@@ -1365,8 +1365,8 @@ static pond_status adjoint_step_impl(pond_ctx* ctx, const double* const out_gaug
         const double cm = ctx->L.c_max;
         const double sx = (mm[1] - mm[0]) + 2.0 * cm * mm[5];
         const double sy = (mm[3] - mm[2]) + 2.0 * cm * mm[5];
-        int wwa = 32 + (int)std::ceil(sx * A.dt + 2.0) + 5;
-        int wha = ADJ_TY + (int)std::ceil(sy * A.dt + 2.0) + 5;
+        int wwa = 32 + window_extent(sx, A.dt, 2.0) + 5;
+        int wha = ADJ_TY + window_extent(sy, A.dt, 2.0) + 5;
         const size_t cap = 200 * 1024;
         while ((size_t)ctx->L.n1 * wwa * wha * sizeof(Double4) > cap) {
             if (wwa - 32 >= wha - ADJ_TY) --wwa; else --wha;

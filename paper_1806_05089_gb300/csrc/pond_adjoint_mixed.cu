@@ -1063,9 +1063,10 @@ cudaError_t adjoint_step_mixed(pond_ctx* ctx, const double* const out_gauge[3],
         const float* sp = &ctx->spans[0];
         const double sx = (double)sp[1] - sp[0], sy = (double)sp[3] - sp[2];
         const double dt = ctx->P.dt;
-        int wwa = 32 + (int)std::ceil(sx * dt + 2.0) + 7;
-        int wha = ADJM_TY + (int)std::ceil(sy * dt + 2.0) + 7;
-        if (!(wwa > 0 && wha > 0) || wwa > 4096 || wha > 4096) wwa = wha = 1;  // non-finite spans
+        int wwa = 32 + window_extent(sx, dt, 2.0) + 7;
+        int wha = ADJM_TY + window_extent(sy, dt, 2.0) + 7;
+        if (!std::isfinite(sx) || !std::isfinite(sy) || wwa > 4096 || wha > 4096)
+            wwa = wha = 1;  // absurd or non-finite spans
         const size_t cap = 160 * 1024;
         while ((size_t)ctx->L.n1 * wwa * wha * sizeof(float4) > cap) {
             if (wwa - 32 >= wha - ADJM_TY) --wwa; else --wha;

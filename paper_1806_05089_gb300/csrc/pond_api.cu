@@ -120,8 +120,8 @@ pond_status update_window(pond_ctx* ctx) {
     w.n1 = ctx->L.n1;
     w.staged = ctx_staged(ctx) ? 1 : 0;
     w.real_bytes = mixed(ctx) ? 4 : 8;
-    w.ww = w.tx + (int)std::ceil(sx * dt + 2 * margin) + 5;
-    w.wh = w.ty + (int)std::ceil(sy * dt + 2 * margin) + 5;
+    w.ww = w.tx + window_extent(sx, dt, 2 * margin) + 5;
+    w.wh = w.ty + window_extent(sy, dt, 2 * margin) + 5;
     // cap the staged window at the shared memory a CTA can have; stencils
     // beyond it take the global-memory path
     auto bytes = [](const TileWindow& v) {
@@ -580,7 +580,7 @@ std::string tune_key(const pond_ctx* ctx) {
     std::snprintf(buf, sizeof buf, "%s|%s|q%d|grids=%d|nodes=%lld|side=%lld-%lld|span=%d-%d",
                   mixed(ctx) ? "mixed" : "fp64", ctx_staged(ctx) ? "staged" : "direct",
                   ctx->L.q, ctx->n_grids, (long long)ctx->N, (long long)minside,
-                  (long long)maxside, (int)std::ceil(sx), (int)std::ceil(sy));
+                  (long long)maxside, window_extent(sx, 1.0, 0.0), window_extent(sy, 1.0, 0.0));
     return buf;
 }
 

@@ -11,6 +11,8 @@
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include <string>
 #include <vector>
 
@@ -209,6 +211,16 @@ cudaError_t launch_step_staged_mixed(const StateBuf<float>& in, const StateBuf<f
                                      const StepParams& P, cudaStream_t s);
 cudaError_t staged_prepare_fp64(int ty, int n1, size_t smem, int* ctas_per_sm);
 cudaError_t staged_prepare_mixed(int ty, int n1, size_t smem, int* ctas_per_sm);
+// Extra window extent, in nodes, that one step's departures need for a
+// particle-speed spread `span`: ceil(span * dt + pad), bounded by 65536 so
+// that an absurd spread (a finite but huge temperature or velocity, whose
+// FP32 bounds may even be infinite or NaN) still gives a valid int.  The
+// shared-memory caps then trim the window, and the stencils beyond it take
+// the global-memory paths, which wrap any displacement.
+inline int window_extent(double span, double dt, double pad) {
+    const double e = std::fmax(span * dt + pad, 0.0);  // a NaN spread gives 0
+    return (int)std::ceil(std::fmin(e, 65536.0));
+}
 // (as staged_smem_bytes: the FP64 form also holds the y-map table)
 inline size_t staged_window_bytes(const TileWindow& w) {
     const size_t per_node = w.real_bytes == 8 ? 2 : 1;

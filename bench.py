@@ -207,16 +207,34 @@ def max_over_ranks(world, value: float) -> float:
     return float(t.item())
 
 
+def oracle_rows_for(st, ny: int, seconds: float, params=None) -> int:
+    """Rows R of the workload whose oracle step takes about `seconds`.  The
+    first step call pays a large one-off cost (the output state's first
+    touch), and every call a fixed one, so the per-row time comes from the
+    difference of two timed probes after an untimed warm-up call."""
+    import oracle
+    oracle.step(st, params, rows=(0, 1))
+    lo, hi = min(2, ny), min(6, ny)
+    t0 = time.perf_counter()
+    oracle.step(st, params, rows=(0, lo))
+    t_lo = time.perf_counter() - t0
+    if hi == lo:
+        return ny
+    t0 = time.perf_counter()
+    oracle.step(st, params, rows=(0, hi))
+    t_hi = time.perf_counter() - t0
+    per_row = max((t_hi - t_lo) / (hi - lo), 1e-4)
+    fixed = max(t_lo - lo * per_row, 0.0)
+    return int(max(1, min(ny, (seconds - fixed) / per_row)))
+
+
 def oracle_sample(fields, seconds: float, params=None):
     """Time the FP64 CPU oracle on a bounded sample: one step of the first R
     rows of the workload, R sized for about `seconds` of CPU time."""
     import oracle
     st = oracle.init_equilibrium(fields.rho, fields.ux, fields.uy, fields.T)
     ny, nx = fields.shape
-    t0 = time.perf_counter()
-    oracle.step(st, params, rows=(0, 1))
-    per_row = max(time.perf_counter() - t0, 1e-4)
-    rows = int(max(1, min(ny, seconds / per_row)))
+    rows = oracle_rows_for(st, ny, seconds, params)
     t0 = time.perf_counter()
     oracle.step(st, params, rows=(0, rows))
     dt = time.perf_counter() - t0
@@ -316,11 +334,8 @@ def run_reference(args, world, rank):
     fields = workloads.supersonic(2048)
     st = oracle.init_equilibrium(fields.rho, fields.ux, fields.uy, fields.T)
     ny, nx = fields.shape
-    t0 = time.perf_counter()
-    oracle.step(st, None, rows=(0, 1))
-    per_row = max(time.perf_counter() - t0, 1e-4)
     budget = min(args.cpu_seconds, max(0.05, 150.0 / max(args.steps + args.warmup, 1)))
-    rows = int(max(1, min(ny, budget / per_row)))
+    rows = oracle_rows_for(st, ny, budget)
     for _ in range(args.warmup):
         oracle.step(st, None, rows=(0, 1))
     times = []

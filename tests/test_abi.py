@@ -185,3 +185,52 @@ int main(int argc, char** argv) {
     args = [str(exe)] + (["gpu"] if torch.cuda.is_available() else [])
     r = subprocess.run(args, capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+
+
+def _ctype_of(decl: str):
+    """ctypes type of one C parameter or return type of include/pond.h."""
+    t = " ".join(decl.replace("const", " ").split())
+    pointers = t.count("*")
+    base = t.replace("*", "").strip()
+    if pointers == 0:
+        return {"int32_t": ctypes.c_int32, "double": ctypes.c_double,
+                "pond_status": ctypes.c_int32, "void": None}[base]
+    if pointers == 2:
+        assert base == "pond_ctx", decl
+        return ctypes.POINTER(ctypes.c_void_p)
+    if base == "char":
+        return ctypes.c_char_p
+    return {"pond_ctx": ctypes.c_void_p, "void": ctypes.c_void_p,
+            "pond_config": ctypes.POINTER(pond.pond_config),
+            "pond_stats": ctypes.POINTER(pond.pond_stats),
+            "int32_t": ctypes.POINTER(ctypes.c_int32),
+            "double": ctypes.POINTER(ctypes.c_double)}[base]
+
+
+def test_binding_signatures_match_the_header():
+    """Every prototype of include/pond.h against the ctypes argtypes and
+    restype the binding declares: the same number of parameters, each of the
+    matching ctypes type (a mismatch would pass pointers or sizes in the
+    wrong slots, which no CPU test would otherwise see)."""
+    hdr = open(os.path.join(ROOT, "include", "pond.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    protos = re.findall(r"(pond_status|void|const\s+char\s*\*)\s*\b(pond_[a-z0-9_]+)\s*\(([^)]*)\)\s*;",
+                        hdr)
+    assert {name for _, name, _ in protos} == set(pond.EXPORTS)
+    lib = pond.load()
+    for ret, name, params in protos:
+        fn = getattr(lib, name)
+        want_ret = _ctype_of(ret)
+        assert fn.restype == want_ret, (name, fn.restype, want_ret)
+        decls = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        # drop each parameter's name: the last identifier of the declaration
+        types = [re.sub(r"\b[A-Za-z_][A-Za-z0-9_]*\s*$", "", d) for d in decls]
+        assert len(fn.argtypes) == len(types), (name, fn.argtypes, types)
+        for i, (have, t) in enumerate(zip(fn.argtypes, types)):
+            want = _ctype_of(t)
+            if "*" not in t:                       # scalars: the exact type
+                assert have == want, (name, i, have, want)
+            elif have is not ctypes.c_void_p:      # a typed pointer: the same pointee
+                assert issubclass(have, ctypes._Pointer) and issubclass(want, ctypes._Pointer), \
+                    (name, i, have, want)
+                assert have._type_ is want._type_, (name, i, have, want)

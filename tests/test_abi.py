@@ -234,3 +234,35 @@ def test_binding_signatures_match_the_header():
                 assert issubclass(have, ctypes._Pointer) and issubclass(want, ctypes._Pointer), \
                     (name, i, have, want)
                 assert have._type_ is want._type_, (name, i, have, want)
+
+
+def test_every_context_call_refuses_a_null_context():
+    """Each entry point that takes a pond_ctx returns POND_ERR_ARG for a NULL
+    context (with NULL or zero for every other argument) before it touches
+    anything: no crash, no CUDA call, the same on a machine without a GPU."""
+    lib = pond.load()
+    d = ctypes.c_double(0.0)
+    calls = {
+        "pond_set_stream": (None, None),
+        "pond_set_state": (None, 0, None, None, None, None, None, 0),
+        "pond_step": (None, 1, None),
+        "pond_moments": (None, 0, None, None, None, None, 0),
+        "pond_get_state": (None, 0, None, None, None, None, 0),
+        "pond_iterations": (None, 0, None, 0),
+        "pond_adjoint_step": (None, None, None, None, None, None),
+        "pond_adjoint_step_given": (None, None, None, None, None, None, None, None, None),
+        "pond_adjoint_nu_bar": (None, ctypes.byref(d)),
+        "pond_adjoint_init": (None, None, None),
+        "pond_set_interior": (None, 0, 0, 0, 1, 1),
+        "pond_pack_rect": (None, 0, 0, 0, 1, 1, None),
+        "pond_unpack_rect": (None, 0, 0, 0, 1, 1, None),
+        "pond_max_displacement": (None, 0, ctypes.byref(d)),
+    }
+    hdr = open(os.path.join(ROOT, "include", "pond.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    takes_ctx = set(re.findall(r"pond_status\s+(pond_[a-z0-9_]+)\s*\(\s*(?:const\s+)?pond_ctx\s*\*", hdr))
+    assert takes_ctx == set(calls)
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == pond.POND_ERR_ARG, name
+    lib.pond_destroy(None)
+    assert lib.pond_last_error(None) == b"no context"

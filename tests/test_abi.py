@@ -266,3 +266,44 @@ def test_every_context_call_refuses_a_null_context():
         assert getattr(lib, name)(*args) == pond.POND_ERR_ARG, name
     lib.pond_destroy(None)
     assert lib.pond_last_error(None) == b"no context"
+
+
+def test_context_free_calls_check_their_arguments_first():
+    """pond_step_fp64_noalloc and pond_measure_peak refuse bad arguments with
+    POND_ERR_ARG before any CUDA call (so without a GPU as well).  Without a
+    GPU a valid call ends at the device lookup with POND_ERR_CUDA and never
+    uses its pointers (no CPU fallback)."""
+    import torch
+    lib = pond.load()
+    cfg = pond.pond_config_default(pond.POND_FP64)
+    buf = (ctypes.c_double * 64)()
+    p = ctypes.cast(buf, ctypes.c_void_p)          # never dereferenced: the checks fail first
+    arrays = [p] * 8
+
+    def noalloc(c, nx, ny, arrs):
+        return lib.pond_step_fp64_noalloc(ctypes.byref(c) if c is not None else None, nx, ny,
+                                          *arrs, None, None, None)
+
+    assert noalloc(None, 1, 1, arrays) == pond.POND_ERR_ARG
+    for i in range(8):
+        holed = list(arrays)
+        holed[i] = None
+        assert noalloc(cfg, 1, 1, holed) == pond.POND_ERR_ARG, i
+    for nx, ny in ((0, 4), (4, 0), (-1, 4), (513, 512)):  # 262656 > POND_NOALLOC_MAX_NODES
+        assert noalloc(cfg, nx, ny, arrays) == pond.POND_ERR_ARG, (nx, ny)
+    mixed = pond.pond_config_default(pond.POND_FP32_MIXED)
+    assert noalloc(mixed, 1, 1, arrays) == pond.POND_ERR_ARG
+    bad = pond.pond_config_default(pond.POND_FP64)
+    bad.lattice = 7
+    assert noalloc(bad, 1, 1, arrays) == pond.POND_ERR_ARG
+    if not torch.cuda.is_available():
+        assert noalloc(cfg, 1, 1, arrays) == pond.POND_ERR_CUDA
+        assert noalloc(cfg, 512, 512, arrays) == pond.POND_ERR_CUDA   # the largest grid passes
+
+    tf = ctypes.c_double(0.0)
+    peak = lib.pond_measure_peak
+    assert peak(pond.POND_PIPE_FP64, 1, p, None, None, None) == pond.POND_ERR_ARG
+    assert peak(pond.POND_PIPE_FP64, 1, None, None, ctypes.byref(tf), None) == pond.POND_ERR_ARG
+    assert peak(pond.POND_PIPE_FP64, 0, p, None, ctypes.byref(tf), None) == pond.POND_ERR_ARG
+    assert peak(3, 1, p, None, ctypes.byref(tf), None) == pond.POND_ERR_ARG
+    assert peak(-1, 1, p, None, ctypes.byref(tf), None) == pond.POND_ERR_ARG

@@ -6,7 +6,10 @@ grid's size, the lattice's Q, the context's device) before the C call.  These
 tests drive the checks with a handle whose pointer is NULL: an array the
 binding rejects raises TypeError / ValueError, and arrays it accepts reach the
 library, which answers POND_ERR_ARG for the NULL context without touching
-them.  So no test here needs a GPU, and none can write through a pointer."""
+them.  The device-side checks and the marshalling itself (which pointer
+lands in which slot) are driven with tensors that report a CUDA device,
+against a stand-in library that only records its calls.  So no test here
+needs a GPU, and none can write through a pointer."""
 import numpy as np
 import pytest
 import torch
@@ -145,3 +148,90 @@ def test_device_of_a_tensor_must_be_the_context_device():
     pond._check_device("f", 0, 0)
     with pytest.raises(ValueError, match="f is on cuda:1; the context's device is cuda:0"):
         pond._check_device("f", 1, 0)
+
+
+class _ReportsCuda(torch.Tensor):
+    """A CPU tensor that reports itself as a CUDA tensor on device 0, so the
+    binding's device-side checks and marshalling run without a GPU."""
+
+    @property
+    def is_cuda(self):
+        return True
+
+    @property
+    def device(self):
+        return torch.device("cuda", 0)
+
+
+def _cuda(shape, dtype=torch.float64):
+    return torch.Tensor._make_subclass(_ReportsCuda, torch.zeros(shape, dtype=dtype))
+
+
+def test_device_tensors_are_checked_and_marshalled(monkeypatch):
+    """Context calls with (reported) CUDA tensors against a library that only
+    records its calls: the handle from pond_create carries the grid, Q and
+    device; the call patterns of the autograd rollout, the adjoint and the
+    decomposition reach the library with each tensor's own data pointer and
+    on_device = 1; wrong sizes, dtypes and lattices are refused first."""
+    real = pond.load()
+    calls = []
+
+    class Recording:
+        def __getattr__(self, name):
+            if name in ("pond_config_default", "pond_version"):
+                return getattr(real, name)
+
+            def call(*args):
+                calls.append((name, args))
+                if name == "pond_create":
+                    args[-1]._obj.value = 4096          # a handle nothing dereferences
+                return b"" if name == "pond_last_error" else 0
+            return call
+
+    monkeypatch.setattr(pond, "_LIB", Recording())
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: True)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+
+    def last(name):
+        return [a for n, a in calls if n == name][-1]
+
+    ny, nx = 16, 24
+    with pond.Sim(nx, ny) as s, pond.Sim(8, 6, lattice=pond.POND_D2Q9) as s9:
+        assert (s.ctx.grids, s.ctx.q, s.ctx.device) == ([(nx, ny)], 16, 0)
+        assert (s9.ctx.grids, s9.ctx.q) == ([(8, 6)], 9)
+        f = _cuda((16, ny, nx))
+        ux, uy, T = (_cuda((ny, nx)) for _ in range(3))
+        pond.pond_get_state(s.ctx, 0, f, ux, uy, T)
+        args = last("pond_get_state")
+        assert [a.value for a in args[2:6]] == [t.data_ptr() for t in (f, ux, uy, T)]
+        assert args[6] == 1
+        pond.pond_set_state(s.ctx, 0, None, ux, uy, T, f)          # the rollout's restore
+        args = last("pond_set_state")
+        assert args[2] is None and args[6].value == f.data_ptr() and args[7] == 1
+        gbar = _cuda((3, ny, nx))
+        pond.pond_adjoint_step_given(s.ctx, ux, uy, T, f, gbar, _cuda((16, ny, nx)),
+                                     _cuda((3, ny, nx)), nu_on_device=True)
+        assert last("pond_adjoint_step_given")[-1] is None        # the device accumulator
+        pond.pond_adjoint_init(s.ctx, f, _cuda((ny, nx)))
+        it = _cuda((ny, nx), torch.int32)
+        pond.pond_iterations(s.ctx, 0, it)
+        assert last("pond_iterations")[2].value == it.data_ptr()
+        buf = _cuda(((16 + 3) * nx * ny,))
+        pond.pond_pack_rect(s.ctx, 0, 0, 0, nx, ny, buf)
+        pond.pond_set_state(s9.ctx, 0, None, *(_cuda((6, 8)) for _ in range(3)), _cuda((9, 6, 8)))
+
+        n = len(calls)
+        with pytest.raises(ValueError, match="gauge_bar_in holds 768 values; the grid needs 1152"):
+            pond.pond_adjoint_step(s.ctx, f, _cuda((2, ny, nx)), _cuda((16, ny, nx)), gbar)
+        with pytest.raises(ValueError, match="f holds 3456 values; the grid needs 6144"):
+            pond.pond_get_state(s.ctx, 0, _cuda((9, ny, nx)))
+        with pytest.raises(ValueError, match="f holds 768 values; the grid needs 432"):
+            pond.pond_set_state(s9.ctx, 0, None, *(_cuda((6, 8)) for _ in range(3)),
+                                _cuda((16, 6, 8)))
+        with pytest.raises(TypeError, match="iters must be torch.int32"):
+            pond.pond_iterations(s.ctx, 0, _cuda((ny, nx)))
+        with pytest.raises(ValueError, match="q = 9, but the context's lattice has Q = 16"):
+            pond.pond_unpack_rect(s.ctx, 0, 0, 0, nx, ny, buf, q=9)
+        with pytest.raises(ValueError, match=r"device call needs torch CUDA tensors \(ux is not one\)"):
+            pond.pond_moments(s.ctx, 0, _cuda((ny, nx)), np.zeros((ny, nx)))
+        assert len(calls) == n                  # nothing refused reached the library

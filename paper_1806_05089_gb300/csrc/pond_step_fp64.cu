@@ -1,10 +1,17 @@
 // pond_step_fp64.cu -- FP64 PonD time step of one periodic grid.
 //
-// Two kernels, both bound by the FP64 pipe, all source reads through the
-// read-only L1 path, templated on the lattice (D2Q16, N1 = 4, or D2Q9,
+// This file holds the direct FP64 kernels (described here; contexts with
+// kernel = POND_KERNEL_DIRECT, and the allocation-free entry point at the
+// end of the file), the FP64 traits of the reference-gauge staged kernel of
+// pond_staged.cuh (StagedFP64, which FP64 contexts run by default), and that
+// entry point.
+//
+// The direct kernels, both bound by the FP64 pipe, all source reads through
+// the read-only L1 path, templated on the lattice (D2Q16, N1 = 4, or D2Q9,
 // N1 = 3):
-//  * k1_step_fp64_node (the default): one node per thread, a rolled loop over
-//    the populations; the per-node scalar work of a pass runs once per node.
+//  * k1_step_fp64_node (the direct form's default): one node per thread, a
+//    rolled loop over the populations; the per-node scalar work of a pass
+//    runs once per node.
 //  * k1_step_fp64<N1, NPW>: one, two or (D2Q9) three target nodes per warp,
 //    16 (D2Q9 with three nodes: 10) lanes per node, lane = population q.
 //    With one node, the lane's other index (lane >> 4) halves the four

@@ -1,7 +1,12 @@
 // pond_step_mixed.cu -- mixed-precision PonD time step (FP32 populations and
 // bulk arithmetic, FP64 gauges), for one grid or a batched ensemble.
 //
-// One CTA per tile of TX x TY target nodes, one thread per node.  The CTA
+// This file holds the direct mixed kernel (k2_step_mixed, described here;
+// contexts with kernel = POND_KERNEL_DIRECT) and, in its last section, the
+// FP32 traits of the reference-gauge staged kernel of pond_staged.cuh
+// (StagedFP32), which mixed contexts run by default.
+//
+// Direct kernel: one CTA per tile of TX x TY target nodes, one thread per node.  The CTA
 // first bounds the particle velocities of its tile (u -+ c_max sqrt(theta)),
 // stages the whole window of source nodes that the departure stencils can
 // reach (tile + halo, periodic wrap applied while staging) in shared memory:

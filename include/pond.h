@@ -130,10 +130,11 @@ typedef struct pond_config {
                            of Eq. interpolation is linear, so each CTA
                            stages the sources its tile's stencils reach
                            once per step, re-expressed in a reference
-                           gauge r (the tile's first node), and each pass
+                           gauge r (the tile's centre node), and each pass
                            reconstructs in r and applies one map r -> target
                            per population: the same f_q up to rounding, with
-                           a quarter of the per-pass arithmetic.  Tile
+                           a quarter (mixed) to a fifth (FP64) of the
+                           per-pass arithmetic.  Tile
                            shapes 32 x 4 and 32 x 8 nodes (FP64), 32 x 4,
                            32 x 8, 32 x 16 (mixed).
                            POND_KERNEL_DIRECT: the per-(population, source)

@@ -75,8 +75,9 @@ typedef struct pond_config {
                            POND_FP32_MIXED: populations and bulk arithmetic
                            FP32; gauges stored and accumulated in FP64; the
                            gauge differences of the transform formed from the
-                           FP64 gauges (tile-relative offsets); convergence
-                           test in FP64. */
+                           FP64 gauges (tile-relative offsets), the
+                           transform's polynomials and contractions in FP32;
+                           convergence test in FP64. */
     int32_t thermal;    /* 1: energy equation in the predictor-corrector
                            (compressible); 0: isothermal, T kept fixed
                            (main text after Eq. postcollision). */

@@ -953,6 +953,11 @@ __global__ void __launch_bounds__(TX* TY, 1) k2_step_mixed_pair(MixedArgs A) {
 // formed from the FP64 gauges and rounded once; the moments and gauge
 // increments of a pass in FP32, accumulated into the FP64 gauge; the App. E
 // test in FP64; the exactly conservative FP32 collision of finish_node.
+// The gauge-transform maps themselves (their Lagrange-Taylor polynomials in
+// those offsets, and the contractions) are FP32, a deliberate choice: only
+// their inputs are formed in FP64.  FP64 polynomials would put this kernel
+// on the FP64 pipe (1/64 of the FP32 rate), at the FP64 form's speed; written
+// around the identity, the FP32 maps round only their correction terms.
 
 struct StagedFP32 {
     using Real = float;

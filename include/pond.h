@@ -151,9 +151,11 @@ typedef struct pond_stats {
     int64_t node_updates;  /* nodes x steps */
     int64_t passes;        /* predictor-corrector passes over all node updates */
     int32_t max_passes;    /* largest pass count at any node */
-    int32_t tile_rows;     /* rows of the mixed kernel's tile shape in use
-                              (32 columns), negative when each thread owns
-                              two vertically adjacent nodes; 0 for FP64 */
+    int32_t tile_rows;     /* rows of the tile shape in use (32 columns) of
+                              the tile kernels (the staged kernel in either
+                              form, the direct mixed kernel); negative when
+                              each thread owns two vertically adjacent nodes;
+                              0 for the direct FP64 kernels */
     int64_t nonconverged;  /* node updates that hit max_iter unconverged */
     int64_t nonphysical;   /* node updates that met rho <= 0, T <= 0 or NaN */
     int64_t halo_fallback; /* stencils read from global memory instead of the
@@ -177,13 +179,15 @@ void pond_config_default(pond_config* cfg, int32_t precision);
 /* Create a context for n_grids independent periodic grids of sizes
  * nx[g] x ny[g] (n_grids == 1: single grid; > 1: batched ensemble advanced
  * together by one launch per step).  cuda_stream is a cudaStream_t (NULL =
- * legacy default stream).  Allocates all device state; nothing else
- * allocates afterwards except pond_adjoint_step's first call.
+ * legacy default stream).  Allocates the device state; the only later
+ * allocations are a staging area for host buffers (20 FP64 values per node,
+ * made by the first call that passes host pointers and grown for a larger
+ * grid) and the adjoint's scratch (pond_adjoint_step's first call).
  * Ensembles run on the staged kernel in either precision, and on the
  * direct mixed kernel; the direct FP64 kernels step one grid.
- * Errors: POND_ERR_ARG (NULL pointers, n_grids < 1, a side < 1, bad
- * precision, n_grids > 1 with the direct FP64 kernels), POND_ERR_OOM,
- * POND_ERR_CUDA. */
+ * Errors: POND_ERR_ARG (NULL pointers, n_grids < 1, a side < 1, a config
+ * field out of its range or a combination this header rules out, n_grids > 1
+ * with the direct FP64 kernels), POND_ERR_OOM, POND_ERR_CUDA. */
 pond_status pond_create(const pond_config* cfg, int32_t n_grids, const int32_t* nx,
                         const int32_t* ny, void* cuda_stream, pond_ctx** out);
 
@@ -201,7 +205,8 @@ pond_status pond_set_stream(pond_ctx* ctx, void* cuda_stream);
  * ignored (may be NULL).  on_device: pointers are device (1) or host (0).
  * Errors: POND_ERR_ARG, POND_ERR_NONPHYSICAL (T <= 0 or a non-finite
  * gauge at some node, host or device input, checked on the device; the grid
- * then counts as never set until a valid call), POND_ERR_CUDA. */
+ * then counts as never set until a valid call), POND_ERR_OOM (the host
+ * staging area, host input only), POND_ERR_CUDA. */
 pond_status pond_set_state(pond_ctx* ctx, int32_t grid, const void* rho, const void* ux,
                            const void* uy, const void* T, const void* f, int32_t on_device);
 
@@ -214,17 +219,23 @@ pond_status pond_step(pond_ctx* ctx, int32_t nsteps, pond_stats* stats);
 
 /* Macroscopic fields of grid `grid`, each [ny][nx] FP64 (any may be NULL):
  * rho = sum_q f_q (Eq. conservation_rho) and the stored gauge (u, T), which
- * is the co-moving frame of the populations (remark after Eq. precollision). */
+ * is the co-moving frame of the populations (remark after Eq. precollision).
+ * Errors: POND_ERR_ARG (NULL ctx, grid index), POND_ERR_STATE (grid never
+ * set), POND_ERR_OOM (the host staging area, host output only),
+ * POND_ERR_CUDA. */
 pond_status pond_moments(pond_ctx* ctx, int32_t grid, void* rho, void* ux, void* uy,
                          void* T, int32_t on_device);
 
 /* Raw state of grid `grid`: populations f [Q][ny][nx] in the stored gauge
- * and the gauge (ux, uy, T) [ny][nx]; any pointer may be NULL. */
+ * and the gauge (ux, uy, T) [ny][nx]; any pointer may be NULL.
+ * Errors: as pond_moments. */
 pond_status pond_get_state(pond_ctx* ctx, int32_t grid, void* f, void* ux, void* uy,
                            void* T, int32_t on_device);
 
 /* Predictor-corrector pass counts of the last step at every node of grid
- * `grid`, int32 [ny][nx] (the map of App. E's iteration figure). */
+ * `grid`, int32 [ny][nx] (the map of App. E's iteration figure; zeros before
+ * the first step).
+ * Errors: POND_ERR_ARG (NULL ctx or iters, grid index), POND_ERR_CUDA. */
 pond_status pond_iterations(pond_ctx* ctx, int32_t grid, void* iters, int32_t on_device);
 
 /* Vector-Jacobian product of one step (single-grid contexts).  The context's

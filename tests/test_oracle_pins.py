@@ -1,5 +1,6 @@
-"""More pins of the FP64 CPU oracle: the stop test of the predictor-corrector
-and the whole step at high Mach number and T != 1.
+"""More pins of the FP64 CPU oracle: the stop test of the predictor-corrector,
+the whole step at high Mach number and T != 1, and the composition of the
+gauge transform that the staged kernel's reformulation rests on.
 
 The stop test (App. E, Eq. convergence) is pinned through whole oracle steps
 on a 1 x 1 grid whose stored populations are built so that the first pass
@@ -82,3 +83,50 @@ def test_high_precision_bruteforce_agrees_with_fp64_bruteforce_at_low_mach():
     b = bf.step_mp(st.f, st.ux, st.uy, st.T, passes=2)
     for x, y in zip(a, b):
         assert np.abs(x - y).max() <= 1e-11 * np.abs(y).max()
+
+
+def _gauge_near(rng, base, spread, T_L):
+    """A gauge within `spread` thermal speeds and a factor 1.5 in T of base."""
+    ux, uy, T = base
+    c = np.sqrt(T / T_L)
+    return (ux + spread * c * rng.uniform(-1, 1), uy + spread * c * rng.uniform(-1, 1),
+            T * np.exp(rng.uniform(np.log(1 / 1.5), np.log(1.5))))
+
+
+@pytest.mark.parametrize("lattice", ["d2q16", "d2q9"])
+def test_transfer_composes_through_a_reference_gauge(lattice):
+    """Eq. transform composes: the Q matched moments fix the Q populations,
+    so moving f from gauge s to gauge t equals moving it to any third gauge r
+    and then on to t.  With the linearity of Eq. interpolation this makes
+    f_q = sum_s a_s [G(s -> t) f_s]_q = [G(r -> t) sum_s a_s G(s -> r) f_s]_q
+    for each population q with its own weights a_s, the exact reformulation
+    the staged kernel computes (sources moved once into a tile's reference
+    gauge r).  Checked on the oracle's transfer for gauges spread as in a
+    staged window (a few thermal speeds, T within a factor 1.5)."""
+    lat = LAT[lattice]
+    T_L = bf.LATTICES[lattice][2]
+    n1 = 4 if lattice == "d2q16" else 3
+    Q = n1 * n1
+    rng = np.random.default_rng(11)
+    for trial in range(20):
+        t = (rng.uniform(-3, 3) * np.sqrt(T_L), rng.uniform(-3, 3) * np.sqrt(T_L),
+             T_L * rng.uniform(0.5, 2.0))
+        r = _gauge_near(rng, t, 2.0, T_L)
+        s = _gauge_near(rng, t, 3.0, T_L)
+        f = rng.uniform(0.1, 1.0, Q)
+        direct = oracle.transfer(s, t, f, lat)
+        via = oracle.transfer(r, t, oracle.transfer(s, r, f, lat), lat)
+        assert np.abs(direct - via).max() <= 1e-11 * np.abs(direct).max(), trial
+
+        # one target's reconstruction from a 4 x 4 stencil of sources
+        src = [_gauge_near(rng, t, 1.0, T_L) for _ in range(16)]
+        fs = [rng.uniform(0.1, 1.0, Q) for _ in range(16)]
+        to_t = [oracle.transfer(g, t, fj, lat) for g, fj in zip(src, fs)]
+        to_r = [oracle.transfer(g, r, fj, lat) for g, fj in zip(src, fs)]
+        for q in range(Q):
+            a = np.outer(oracle.interp_weights(rng.uniform(1, 2)),
+                         oracle.interp_weights(rng.uniform(1, 2))).ravel()  # a_s of population q
+            lhs = sum(a[j] * to_t[j][q] for j in range(16))
+            rhs = oracle.transfer(r, t, sum(a[j] * to_r[j] for j in range(16)), lat)[q]
+            scale = max(abs(lhs), np.abs(np.array(to_t)).max())
+            assert abs(lhs - rhs) <= 1e-11 * scale, (trial, q)

@@ -33,8 +33,8 @@ def main():
                     help="fp64: nodes per warp of the step kernel (1, 2, 3 on d2q9, 32 = one per "
                          "thread; 0 = default)")
     ap.add_argument("--kernel", choices=["staged", "direct"], default="staged",
-                    help="fp64 / mixed / batched: the reference-gauge staged tile kernel (the "
-                         "default) or the direct per-pair kernels")
+                    help="fp64 / mixed / batched / adjoint: the reference-gauge staged tile "
+                         "kernel (the default) or the direct per-pair kernels")
     ap.add_argument("--lattice", choices=["d2q16", "d2q9"], default="d2q16",
                     help="fp64 / mixed / batched: lattice (d2q9 runs the same flow at "
                          "T_L = 1/3: T/3, u/sqrt 3)")
@@ -95,11 +95,13 @@ def main():
         dev = torch.device("cuda")
         r = torch.tensor(f.rho, device=dev, requires_grad=True)
         prec = pond.POND_FP64 if a.precision == "fp64" else pond.POND_FP32_MIXED
+        kern = pond.POND_KERNEL_STAGED if a.kernel == "staged" else pond.POND_KERNEL_DIRECT
         rho = pond_rollout(r, 0.01, *(torch.tensor(v, device=dev) for v in (f.ux, f.uy, f.T)),
-                           a.steps, a.steps, precision=prec)
+                           a.steps, a.steps, precision=prec, kernel=kern)
         (0.5 * ((rho - torch.tensor(target, device=dev)) ** 2).sum()).backward()
         torch.cuda.synchronize()
-        out.update(n=a.n, steps=a.steps, precision=a.precision, grad_norm=float(r.grad.norm()))
+        out.update(n=a.n, steps=a.steps, precision=a.precision, kernel=a.kernel,
+                   grad_norm=float(r.grad.norm()))
     print(json.dumps(out))
 
 
